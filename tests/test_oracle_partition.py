@@ -1,0 +1,133 @@
+"""Pins for the oracle's partitions and write-count checker (paper examples, hand-built maps)."""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import grouped, partition
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    vals = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = int(v)
+    return vals
+
+
+def test_listing1_worked_example():
+    g = _golden("listing1_vec_add.txt")
+    grid = partition.grid((g["n"],), (g["tile"],))
+    assert grid == (g["programs"],)
+    owner = partition.owner_map((g["n"],), (g["tile"],))
+    assert np.array_equal(owner, np.arange(g["n"]) // g["tile"])
+    assert partition.check_counts(np.bincount(np.arange(g["n"]), minlength=g["n"]))["ok"]
+
+
+def test_grid_ragged_and_rejections():
+    assert partition.grid((10,), (4,)) == (3,)
+    assert list(partition.tile_elements((10,), (4,), (2,))) == [8, 9]
+    assert partition.grid((5, 7, 3), (2, 3, 3)) == (3, 3, 1)
+    with pytest.raises(ValueError):
+        partition.grid((2, 2, 2, 2), (1, 1, 1, 1))
+    with pytest.raises(ValueError):
+        partition.grid((8,), (0,))
+    with pytest.raises(ValueError):
+        partition.grid((8, 8), (4,))
+    assert partition.grid((0,), (4,)) == (0,)
+
+
+def test_tile_elements_2d():
+    e = partition.tile_elements((5, 7), (2, 3), (2, 2))
+    assert list(e) == [4 * 7 + 6]   # ragged corner tile of a 5x7 output
+
+
+@pytest.mark.parametrize("shape,tile", [((1000,), (64,)), ((13, 29), (4, 8)), ((5, 6, 7), (2, 4, 3))])
+@pytest.mark.parametrize("kind,P", [("identity", None), ("strided", 3)])
+def test_owner_map_covers_exactly_once(shape, tile, kind, P):
+    owner = partition.owner_map(shape, tile, P, kind)
+    assert np.all(owner >= 0)
+    n = int(np.prod(shape))
+    g = partition.grid(shape, tile)
+    writes = []
+    for p, slots in partition.program_tiles(int(np.prod(g)), P, kind).items():
+        for s in slots:
+            writes += [(p, int(e)) for e in partition.tile_elements(shape, tile, partition.tile_coord(s, g))]
+    assert len(writes) == n
+    assert partition.check_counts(partition.write_counts(n, writes))["ok"]
+
+
+def test_strided_program_count_validation():
+    with pytest.raises(ValueError):
+        partition.program_tiles(8, 9, "strided")
+    with pytest.raises(ValueError):
+        partition.program_tiles(8, 0, "strided")
+    assert partition.program_tiles(8, 3, "strided") == {0: [0, 3, 6], 1: [1, 4, 7], 2: [2, 5]}
+
+
+def test_checker_flags_hand_built_maps():
+    shape, tile = (12,), (4,)
+    good = partition.writes_of_map(shape, tile, {0: [0], 1: [1], 2: [2]})
+    assert partition.check_counts(partition.write_counts(12, good))["ok"]
+    missing = partition.writes_of_map(shape, tile, {0: [0], 1: [2]})
+    r = partition.check_counts(partition.write_counts(12, missing))
+    assert not r["ok"] and list(r["missing"]) == [4, 5, 6, 7] and r["duplicate"].size == 0
+    dup = partition.writes_of_map(shape, tile, {0: [0, 1], 1: [1], 2: [2]})
+    r = partition.check_counts(partition.write_counts(12, dup))
+    assert list(r["duplicate"]) == [4, 5, 6, 7] and r["missing"].size == 0
+
+
+def test_permute_heads_race_is_flagged():
+    g = _golden("permute_heads_race.txt")
+    B, H, M, D = g["B"], g["H"], g["M"], g["D"]
+    writes = partition.permute_heads_writes(B, H, M, D, g["BM"], g["BD"])
+    counts = partition.write_counts(B * H * M * D, writes)
+    assert np.all(counts == g["writes_per_element"])
+    r = partition.check_counts(counts)
+    assert not r["ok"] and r["duplicate"].size == B * H * M * D
+    # the programs writing one destination differ only in h1
+    e0 = [p for p, e in writes if e == 0]
+    assert sorted(e0) == sorted(h1 * H + 0 for h1 in range(H))
+
+
+@pytest.mark.parametrize("gm,gn,G", [(1, 1, 1), (7, 5, 1), (7, 5, 3), (16, 16, 8), (5, 9, 16)])
+def test_raster_bijection(gm, gn, G):
+    seen = {partition.raster_tile(s, gm, gn, G) for s in range(gm * gn)}
+    assert seen == {(i, j) for i in range(gm) for j in range(gn)}
+    if G == 1:
+        assert [partition.raster_tile(s, gm, gn, 1) for s in range(gm * gn)] == \
+               [(i, j) for i in range(gm) for j in range(gn)]
+
+
+def test_raster_band_order():
+    # 4x3 grid, bands of 2 rows: first slots go down the band's rows
+    assert [partition.raster_tile(s, 4, 3, 2) for s in range(6)] == \
+        [(0, 0), (1, 0), (0, 1), (1, 1), (0, 2), (1, 2)]
+
+
+def test_gemm_owner_map_strided():
+    owner = partition.gemm_owner_map(300, 200, 128, 64, num_programs=5, kind="strided", group_m=2)
+    gm, gn = 3, 4
+    o = owner.reshape(300, 200)
+    for s in range(gm * gn):
+        tm, tn = partition.raster_tile(s, gm, gn, 2)
+        assert np.all(o[tm * 128:(tm + 1) * 128, tn * 64:(tn + 1) * 64] == s % 5)
+
+
+def test_grouped_queue_coverage():
+    probs = [(1, 300, 64), (200, 96, 64), (65, 129, 64)]
+    cfg = [(128, 16, True), (128, 64, False), (64, 32, False)]
+    tc = [grouped.problem_tiles(m, n, *c)[0] for (m, n, _), c in zip(probs, cfg)]
+    total = sum(tc)
+    counts = grouped.element_counts(probs, cfg, range(total))
+    assert all(np.all(c == 1) for c in counts)
+    counts = grouped.element_counts(probs, cfg, [g for g in range(total) if g != 3])
+    assert not all(np.all(c == 1) for c in counts)
+    assert [grouped.queue_decode(g, tc)[0] for g in range(total)] == \
+        [i for i, t in enumerate(tc) for _ in range(t)]
+    with pytest.raises(ValueError):
+        grouped.queue_decode(total, tc)
