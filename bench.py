@@ -1,0 +1,398 @@
+"""Benchmark of the partitioned tile-program hot path on GB300.
+
+Default workload (one "step"): the four element-wise maps over 2^28 elements
+with the output partitioned into 4096-element tiles, each run once:
+z = 0.5 x + y and y = gelu_tanh(x) * w, in fp32 and in bf16 (fp32 math).
+`value` is HBM throughput in TB/s: algorithmic bytes of the step (2 reads + 1
+write per element per map, as the paper counts its element-wise add) divided
+by the device time of the step. Inputs are 0.5-1 GiB per tensor, far larger
+than the 129 MB L2, so no flush is needed between steps.
+
+Secondary rows (the other hot-path configurations) are measured after the
+timed region and reported under "rows".
+
+--impl reference times the FP64 CPU oracle on the host cores instead.
+Multi-GPU (torchrun): every rank runs the same per-GPU workload on its own
+GPU (weak scaling, no collective on the data path); the step time is the max
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ELEMS = 1 << 28
+TILE = 4096
+ALPHA = 0.5
+MAPS = [("axpy", "f32"), ("gelu_mul", "f32"), ("axpy", "bf16"), ("gelu_mul", "bf16")]
+ESIZE = {"f32": 4, "bf16": 2}
+METRIC = "GEMM TFLOP/s & map TB/s vs GB300 roofline; grouped vs plain speedup at stated error"
+WORKLOAD = "element-wise maps over 2^28 elements, fp32 and bf16: z=0.5*x+y and y=gelu_tanh(x)*w, 4096-element tiles"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "src": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "src": "fallback"}
+
+
+def _traffic(kernel: str, src_file: str):
+    """dram bytes per launch for `kernel` from profiles/dram_traffic.txt, only
+    if the kernel's source file is unchanged since the capture."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    src = os.path.join(ROOT, "paper_2606_15991_gb300", "csrc", src_file)
+    if not os.path.exists(path) or not os.path.exists(src):
+        return None
+    digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 3 and not line.startswith("#") and f[0] == kernel and f[2] == digest:
+            return float(f[1])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait(timeout=5)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 8 for i in range(4) if r[4 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _barrier_max(value: float, ws: int, backend_dev):
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=backend_dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _map_bytes(dt: str) -> int:
+    return 3 * ESIZE[dt] * N_ELEMS
+
+
+# --------------------------------------------------------------------- CPU oracle leg
+def cpu_oracle_sample(seconds: float = 12.0):
+    """Times the FP64 oracle maps (as they stand) on a 2^22-element sample of
+    the same four maps, repeated until `seconds` elapse; returns TB/s over the
+    same algorithmic byte count the GPU is charged."""
+    import numpy as np
+
+    import synth
+    from oracle import maps as omaps
+
+    n = 1 << 22
+    data = {}
+    for _, dt in MAPS:
+        if dt not in data:
+            x = synth.tensor(synth.normal(n, 1), dt).double().numpy()
+            y = synth.tensor(synth.normal(n, 2), dt).double().numpy()
+            data[dt] = (x, y)
+    reps = 0
+    bytes_done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        for op, dt in MAPS:
+            x, y = data[dt]
+            z = omaps.axpy(ALPHA, x, y) if op == "axpy" else omaps.gelu_mul(x, y)
+            z.astype(np.float32)
+            bytes_done += 3 * ESIZE[dt] * n
+        reps += 1
+    el = time.perf_counter() - t0
+    return {"value": bytes_done / el / 1e12, "unit": "TB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} passes of the 4 maps over 2^22 of the 2^28 elements (numpy float64, 1 thread), "
+                      f"{el:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    steps = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(seconds=1.0)
+    for _ in range(args.steps):
+        steps.append(cpu_oracle_sample(seconds=max(1.0, 30.0 / max(1, args.steps))))
+    vals = [s["value"] for s in steps]
+    v = statistics.median(vals)
+    base = steps[0]
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "TB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": "bounded CPU sample per step"},
+        "cpu_baseline": {"value": v, "unit": "TB/s", "cores": base["cores"], "kind": "oracle",
+                         "sample": base["sample"]},
+        "e2e": {"value": v, "unit": "TB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# --------------------------------------------------------------------- GPU leg
+def run_ours(args):
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_2606_15991_gb300 import build as _build
+
+    _build.build()
+    import paper_2606_15991_gb300 as tp
+
+    ctx = tp.tp_ctx_create(dev.index)
+    stream = torch.cuda.Stream(device=dev)
+    gen = torch.Generator(device=dev)
+    inputs = {}
+    for dt in ("f32", "bf16"):
+        tdt = torch.float32 if dt == "f32" else torch.bfloat16
+        gen.manual_seed(1)
+        x = torch.randn(N_ELEMS, device=dev, generator=gen).to(tdt)
+        gen.manual_seed(2)
+        y = torch.randn(N_ELEMS, device=dev, generator=gen).to(tdt)
+        inputs[dt] = (x, y)
+    tens = {}   # one output tensor + partition per map: a partition in flight is held exclusively
+    for op, dt in MAPS:
+        x, y = inputs[dt]
+        z = torch.empty_like(x)
+        tens[(op, dt)] = (x, y, z, tp.tp_partition_create(ctx, z, (TILE,)))
+    torch.cuda.synchronize()
+    ex = tp.make_exec(stream=stream)
+    ex.mode = tp.ASYNC   # launches are chained on the stream; the event wait ends the step
+    ev = tp.tp_event_create(ctx)
+    ex.event = ev.handle.value
+
+    def launch(op, dt):
+        x, y, z, p = tens[(op, dt)]
+        if op == "axpy":
+            tp.tp_map_axpy(ctx, p, ALPHA, x, y, ex)
+        else:
+            tp.tp_map_gelu_mul(ctx, p, x, y, ex)
+
+    def step():
+        for op, dt in MAPS:
+            launch(op, dt)
+        tp.tp_event_wait(ev)   # releases the partitions (host-side protocol)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # per-launch events on the launching stream (for the roofline)
+    evs = {k: [] for k in MAPS}
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for _ in range(args.steps):
+        for op, dt in MAPS:
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launch(op, dt)
+            e1.record(stream)
+            evs[(op, dt)].append((e0, e1))
+        tp.tp_event_wait(ev)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    el_ms = t_start.elapsed_time(t_end)
+    el_ms = _barrier_max(el_ms, ws, dev)
+    ms_step = el_ms / args.steps
+    step_bytes = sum(_map_bytes(dt) for _, dt in MAPS)
+    value = ws * step_bytes / (ms_step * 1e-3) / 1e12
+
+    per_kernel = {}
+    for k, lst in evs.items():
+        d = [a.elapsed_time(b) for a, b in lst]
+        per_kernel[k] = sum(d) / len(d)
+    peaks = _peaks()
+    dom = max(per_kernel, key=per_kernel.get)
+    dom_bytes = _map_bytes(dom[1])
+    achieved = dom_bytes / (per_kernel[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": f"map_vec_kernel<{dom[0]},{dom[1]}>", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "peak_src": peaks["src"],
+                "traffic": _traffic(f"{dom[0]}_{dom[1]}", "map_kernels.cu"),
+                "algorithmic_bytes_per_launch": dom_bytes,
+                "per_map_gbs": {f"{o}_{d}": _map_bytes(d) / (t * 1e-3) / 1e9 for (o, d), t in per_kernel.items()}}
+
+    # ---------------- end-to-end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.skip_e2e:
+        host_in = {dt: (x.cpu().pin_memory(), y.cpu().pin_memory()) for dt, (x, y) in inputs.items()}
+        host_out = {k: torch.empty(v[2].shape, dtype=v[2].dtype).pin_memory() for k, v in tens.items()}
+        e2e_steps = max(2, min(args.steps, 5))
+
+        def e2e_step():
+            for op, dt in MAPS:
+                x, y, z, p = tens[(op, dt)]
+                hx, hy = host_in[dt]
+                hz = host_out[(op, dt)]
+                with torch.cuda.stream(stream):
+                    x.copy_(hx, non_blocking=True)
+                    y.copy_(hy, non_blocking=True)
+                if op == "axpy":
+                    tp.tp_map_axpy(ctx, p, ALPHA, x, y, ex)
+                else:
+                    tp.tp_map_gelu_mul(ctx, p, x, y, ex)
+                with torch.cuda.stream(stream):
+                    hz.copy_(z, non_blocking=True)
+            tp.tp_event_wait(ev)
+            stream.synchronize()
+
+        e2e_step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        t1 = time.perf_counter()
+        e2e_ms = _barrier_max((t1 - t0) * 1e3 / e2e_steps, ws, dev)
+        h2d = sum(2 * ESIZE[dt] * N_ELEMS for _, dt in MAPS)
+        d2h = sum(ESIZE[dt] * N_ELEMS for _, dt in MAPS)
+        e2e = {"value": ws * step_bytes / (e2e_ms * 1e-3) / 1e12, "unit": "TB/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e2e_steps}
+
+    rows = {}
+    if not args.skip_rows and rank == 0:
+        rows = secondary_rows(tp, ctx, dev, stream, peaks)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_cpu:
+        cpu = cpu_oracle_sample(seconds=args.cpu_seconds)
+        cpu["cores"] = 1
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": "TB/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "elements": N_ELEMS, "tile": TILE, "alpha": ALPHA,
+                       "maps": [f"{o}_{d}" for o, d in MAPS], "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": f"replicas x{ws}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": len(MAPS) * args.steps, "clocks": clocks, "rows": rows,
+        }))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def secondary_rows(tp, ctx, dev, stream, peaks):
+    """Other hot-path configurations, each timed with CUDA events after warm-up."""
+    import torch
+
+    import synth
+
+    rows = {}
+    # FP32 FFMA GEMM 512^3, 64x64 tiles (64 programs)
+    a = torch.from_numpy(synth.uniform(512 * 512, seed=0)).reshape(512, 512).to(dev)
+    b = torch.from_numpy(synth.uniform(512 * 512, seed=1)).reshape(512, 512).to(dev)
+    c = torch.empty(512, 512, device=dev)
+    p = tp.tp_partition_create(ctx, c, (64, 64))
+    ex = tp.make_exec(stream=stream)
+    for _ in range(5):
+        tp.tp_gemm(ctx, p, a, b, None, ex)
+    reps = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    exa = tp.make_exec(stream=stream)
+    exa.mode = tp.ASYNC
+    ev = tp.tp_event_create(ctx)
+    exa.event = ev.handle.value
+    e0.record(stream)
+    for _ in range(reps):
+        tp.tp_gemm(ctx, p, a, b, None, exa)
+        tp.tp_event_wait(ev)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    rows["gemm_f32_512"] = {"tflops": 2 * 512 ** 3 / (ms * 1e-3) / 1e12, "ms": ms,
+                            "note": "latency-bound FFMA tiles; includes per-call event wait"}
+    tp.tp_partition_destroy(p)
+    tp.tp_event_destroy(ev)
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-rows", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,253 @@
+/*
+ * tp.h - C ABI of the partitioned tile-program library (libtp.so).
+ *
+ * The library runs the data-parallel hot path of "Fearless Concurrency on the
+ * GPU" (cuTile Rust) on one GB300 (sm_103a): a grid of tile programs in which
+ * each program owns a provably disjoint sub-tensor of a partitioned mutable
+ * output (§3.4), computing element-wise maps (§2, Listing 1; §5.1) and tiled
+ * GEMMs with a K loop (§3.6, Listing 6; §5.1), launched synchronously, as an
+ * asynchronous stream pipeline, or by CUDA-graph replay (§3.2, Listings 2-3).
+ *
+ * Conventions shared by every entry point
+ * - Every call returns a tp_status; no call aborts, exits or prints.
+ *   tp_last_error_detail() gives a human-readable reason for the last failure
+ *   on the calling thread.
+ * - Pointers named "device" are CUDA device addresses (e.g. a torch tensor's
+ *   data_ptr()); the library never frees memory it did not allocate.
+ *   tp_tensor is a non-owning view (the borrow rows of Table 1, §3.3).
+ * - Streams are cudaStream_t values passed as void* and are borrowed.
+ * - Mutable outputs are passed as a tp_partition: an output tensor split into
+ *   disjoint tiles (rank <= 3, §3.4). Inputs are read-only tp_tensor views and
+ *   must not overlap the output's bytes (TP_ERR_ALIAS; §3.3, Appendix A).
+ * - While an operation is in flight its partition is "busy" (the C analogue of
+ *   the launch holding the tensor until the stream completes, §3.2 and §3.3):
+ *   a second operation on it, an input reading its bytes, or destroying it
+ *   returns TP_ERR_BUSY. SYNC releases it before returning; ASYNC releases it
+ *   when tp_event_query reports completion or tp_event_wait returns; CAPTURE
+ *   never marks it (the node has not run, §3.2) and graph replay marks the
+ *   graph's partitions for the replay's duration.
+ * - Element strides are in elements. Dtype sizes: F32 4, BF16 2, F8E4M3 1.
+ * - Nothing is allocated during graph capture (§3.2's rule that captured
+ *   nodes are non-allocating); a call that would need to returns TP_ERR_CAPTURE.
+ */
+#ifndef TP_H
+#define TP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum tp_status {
+  TP_OK = 0,
+  TP_ERR_INVALID = 1,     /* null or malformed argument / descriptor            */
+  TP_ERR_RANK = 2,        /* mutable rank > 3, or rank mismatch                  */
+  TP_ERR_ALIGN = 3,       /* pointer or stride misaligned for a TMA path         */
+  TP_ERR_ALIAS = 4,       /* an input overlaps the output partition              */
+  TP_ERR_BUSY = 5,        /* partition (or bytes an input reads) in flight       */
+  TP_ERR_CAPTURE = 6,     /* not allowed while capturing a graph                 */
+  TP_ERR_UNSUPPORTED = 7, /* valid request this build does not implement         */
+  TP_ERR_CUDA = 8,        /* a CUDA runtime/driver call failed                   */
+  TP_ERR_TIMEOUT = 9,     /* a device-side wait hit its iteration cap            */
+  TP_ERR_SHAPE = 10       /* operand shapes disagree                             */
+} tp_status;
+
+typedef enum tp_dtype {
+  TP_F32 = 0,
+  TP_BF16 = 1,
+  TP_F8E4M3 = 2,
+  TP_F64 = 3,
+  TP_I32 = 4,
+  TP_U32 = 5,
+  TP_U8 = 6
+} tp_dtype;
+
+#define TP_MAX_RANK 8
+
+/* Non-owning strided view of device (or host, where stated) memory. */
+typedef struct tp_tensor {
+  void* ptr;                      /* address of element (0, ..., 0)            */
+  int32_t dtype;                  /* tp_dtype                                  */
+  int32_t rank;                   /* 0 .. TP_MAX_RANK                          */
+  int64_t shape[TP_MAX_RANK];     /* extents; only the first `rank` are read   */
+  int64_t strides[TP_MAX_RANK];   /* element strides                           */
+} tp_tensor;
+
+typedef enum tp_map_kind {
+  TP_MAP_IDENTITY = 0, /* plain partition: program p owns tile p (§3.4)         */
+  TP_MAP_STRIDED = 1,  /* mapped: program p owns slots p, p+P, p+2P, ... (§3.6)  */
+  TP_MAP_QUEUE = 2     /* mapped: a device counter hands out each slot once      */
+} tp_map_kind;
+
+typedef enum tp_mode {
+  TP_SYNC = 0,    /* launch, synchronize the stream, release (§3.2 .sync())     */
+  TP_ASYNC = 1,   /* launch, record `event`, return (§3.2 .await)               */
+  TP_CAPTURE = 2  /* record into the graph open on `stream` (§3.2 .graph())     */
+} tp_mode;
+
+typedef struct tp_ctx tp_ctx;
+typedef struct tp_partition tp_partition;
+typedef struct tp_event tp_event;
+typedef struct tp_graph tp_graph;
+
+/* How an operation is executed. */
+typedef struct tp_exec {
+  int32_t mode;            /* tp_mode                                          */
+  int32_t reserved;        /* must be 0                                        */
+  void* stream;            /* cudaStream_t (borrowed); NULL = legacy stream    */
+  tp_event* event;         /* ASYNC: event that completion is recorded into     */
+  /* Optional write-count instrumentation (device pointers, NULL = off): each
+   * store of output element i also adds 1 to write_counts[i] and writes the
+   * storing program's id to write_owner[i]. Both arrays hold one entry per
+   * output element in row-major order. Used by the partition checker
+   * (Appendix A: each element written by exactly one program). */
+  uint32_t* write_counts;
+  int32_t* write_owner;
+} tp_exec;
+
+typedef struct tp_partition_info {
+  int32_t rank;
+  int32_t map_kind;        /* tp_map_kind                                      */
+  int64_t shape[3];
+  int64_t tile[3];
+  int64_t grid[3];         /* ceil(shape / tile) per axis                      */
+  int64_t num_tiles;
+  int64_t num_programs;    /* = num_tiles for TP_MAP_IDENTITY                  */
+  int32_t busy;            /* 1 while an operation on it is in flight          */
+  int32_t reserved;
+} tp_partition_info;
+
+/* GEMM tile configuration (§5.1: tile shapes tuned per size). 0 = default. */
+typedef struct tp_gemm_config {
+  int32_t bm;          /* 128 (one CTA) or 256 (CTA pair, cta_group::2)        */
+  int32_t bn;          /* 32..256, multiple of 32 (tensor-core paths)          */
+  int32_t bk;          /* K per stage: 64 (bf16) / 128 (fp8); SIMT: 8/16/32     */
+  int32_t stages;      /* shared-memory ring depth                              */
+  int32_t group_m;     /* raster band height in tiles (L2 reuse)                */
+  int32_t num_programs;/* persistent programs; 0 = number of SMs (or pairs)     */
+  int32_t swap_ab;     /* grouped GEMM only: compute C^T = B^T A^T             */
+  int32_t split_k;     /* reserved, must be 0 or 1                              */
+} tp_gemm_config;
+
+/* ---------------------------------------------------------------- errors */
+const char* tp_error_string(tp_status s);
+/* Reason for the last non-OK status returned on this thread ("" if none). */
+const char* tp_last_error_detail(void);
+/* Library version (major, minor). */
+tp_status tp_version(int32_t* major, int32_t* minor);
+
+/* --------------------------------------------------------------- context */
+/* Creates a context on CUDA device `device` (§3.2 ExecutionContext: device,
+ * stream and memory pool). Allocates the context's device workspace (error
+ * word, queue counters, scale scratch) once, so later calls can be captured.
+ * Errors: TP_ERR_INVALID (null out), TP_ERR_CUDA (no such device / no sm_103). */
+tp_status tp_ctx_create(int32_t device, tp_ctx** out);
+/* Frees the context and its workspace. TP_ERR_BUSY if work is still in flight. */
+tp_status tp_ctx_destroy(tp_ctx* ctx);
+/* Number of SMs and compute capability of the context's device. */
+tp_status tp_ctx_info(tp_ctx* ctx, int32_t* sm_count, int32_t* cc_major, int32_t* cc_minor);
+
+/* ---------------------------------------------------------------- tensors */
+/* Fills a view (§3.3 Table 1 borrow rows; §3.2 TensorView). strides may be
+ * NULL for a row-major contiguous layout. Errors: TP_ERR_INVALID (null view,
+ * rank outside 0..8, negative extent, unknown dtype). */
+tp_status tp_tensor_init(tp_tensor* t, void* ptr, int32_t dtype, int32_t rank,
+                         const int64_t* shape, const int64_t* strides);
+/* Zero-copy view of `base` (§3.2 TensorView: new shape, strides or slice over
+ * the same allocation). `offset` is in elements from base->ptr. The view's
+ * reachable elements must lie inside base's reachable range, else
+ * TP_ERR_INVALID. */
+tp_status tp_tensor_view(const tp_tensor* base, int64_t offset, int32_t rank,
+                         const int64_t* shape, const int64_t* strides, tp_tensor* out);
+
+/* ------------------------------------------------------------- partitions */
+/* Partitions a contiguous mutable output into tiles of `tile` (one extent per
+ * axis, §3.4): grid = ceil(shape / tile). Rank must be 1..3 (CUDA grids are
+ * three-dimensional), else TP_ERR_RANK; tile extents must be >= 1, else
+ * TP_ERR_INVALID. The partition starts as a plain partition (one program per
+ * tile). The tensor's memory stays owned by the caller; the partition handle
+ * is owned by the caller and freed with tp_partition_destroy. ctx may be NULL
+ * to validate and inspect a partition on the host alone; such a partition
+ * cannot be launched (operations return TP_ERR_INVALID). */
+tp_status tp_partition_create(tp_ctx* ctx, const tp_tensor* out, const int64_t* tile,
+                              tp_partition** p);
+/* Turns p into a mapped partition (§3.6): `num_programs` programs walk the
+ * tiles under map `kind`. TP_MAP_IDENTITY resets to a plain partition.
+ * num_programs must be 1..num_tiles (§3.4: mapped partitions validate their
+ * program count against the partition grid), else TP_ERR_INVALID.
+ * TP_ERR_BUSY while in flight. */
+tp_status tp_partition_map(tp_partition* p, int32_t kind, int64_t num_programs);
+tp_status tp_partition_query(const tp_partition* p, tp_partition_info* info);
+/* TP_ERR_BUSY while an operation on it is in flight. */
+tp_status tp_partition_destroy(tp_partition* p);
+
+/* ----------------------------------------------------------------- events */
+/* Completion handle for TP_ASYNC operations (§3.2 .await; the host learns of
+ * completion by polling or waiting instead of a driver callback). */
+tp_status tp_event_create(tp_ctx* ctx, tp_event** ev);
+/* *done = 1 once every operation recorded into ev has completed; then the
+ * partitions those operations held are released and any device-side error
+ * (TP_ERR_TIMEOUT) is reported. */
+tp_status tp_event_query(tp_event* ev, int32_t* done);
+/* Blocks until completion, releases the held partitions, reports errors. */
+tp_status tp_event_wait(tp_event* ev);
+/* TP_ERR_BUSY if it still holds partitions of unfinished work. */
+tp_status tp_event_destroy(tp_event* ev);
+
+/* ----------------------------------------------------------------- graphs */
+/* Starts capturing `stream` into a new graph (§3.2 CudaGraph::scope). Ops
+ * called with mode TP_CAPTURE on that stream are recorded, not run. One
+ * capture per context at a time. */
+tp_status tp_graph_begin(tp_ctx* ctx, void* stream, tp_graph** g);
+/* Ends the capture and instantiates the graph. */
+tp_status tp_graph_end(tp_graph* g);
+/* Replays the graph with one launch (§5.2: one driver call for the whole
+ * pipeline). The replay is itself an operation with a mode (SYNC or ASYNC,
+ * §3.2): the partitions recorded into the graph are busy while it runs. */
+tp_status tp_graph_replay(tp_graph* g, const tp_exec* ex);
+tp_status tp_graph_destroy(tp_graph* g);
+
+/* ----------------------------------------------------- element-wise maps */
+/* z = alpha * x + y on every element (§2 Listing 1's element-wise add is
+ * alpha = 1; §5.1 evaluates it at N = 2^28). z is a partition of an F32 or
+ * BF16 contiguous tensor; x and y have z's shape and dtype. Arithmetic in fp32
+ * (one fused multiply-add), BF16 output rounded to nearest even. Each tile
+ * program stores only its own tile(s). Errors: TP_ERR_SHAPE, TP_ERR_ALIAS,
+ * TP_ERR_BUSY, TP_ERR_UNSUPPORTED (non-contiguous), TP_ERR_CUDA. */
+tp_status tp_map_axpy(tp_ctx* ctx, tp_partition* z, float alpha, const tp_tensor* x,
+                      const tp_tensor* y, const tp_exec* ex);
+/* y = gelu_tanh(x) * w, gelu_tanh(x) = 0.5 x (1 + tanh(sqrt(2/pi)(x + 0.044715 x^3)))
+ * evaluated as x / (1 + exp(-2u)); same layout rules as tp_map_axpy. */
+tp_status tp_map_gelu_mul(tp_ctx* ctx, tp_partition* y, const tp_tensor* x,
+                          const tp_tensor* w, const tp_exec* ex);
+/* y = x * g element-wise (§5.2's pipeline kernel); same rules. */
+tp_status tp_map_scale(tp_ctx* ctx, tp_partition* y, const tp_tensor* x, const tp_tensor* g,
+                       const tp_exec* ex);
+/* c <- c + a + b (§3.4 Listing 4: the mutable tile is read, then written by
+ * the same program). */
+tp_status tp_map_add_accum(tp_ctx* ctx, tp_partition* c, const tp_tensor* a,
+                           const tp_tensor* b, const tp_exec* ex);
+
+/* ------------------------------------------------------------------ GEMM */
+/* C = A . B with one C tile per program and a K loop (§3.6 Listing 6).
+ * c: partition of a row-major M x N output whose tile is the GEMM tile.
+ * a: M x K. b: K x N (its strides decide the layout: row stride 1 means B is
+ * stored N x K, "K-major").
+ * - F32 A, B, C: FFMA tiles (no TF32), any strides; tile 64 x 64 recommended.
+ * - BF16 A, B, C: tcgen05 tensor-core path. A must be K-major (row-major
+ *   M x K) and B K-major (stored N x K); base addresses 16-byte aligned and
+ *   K a multiple of 8 (TMA rows are 16-byte multiples), else TP_ERR_ALIGN.
+ *   FP32 accumulation in tensor memory; C rounded to bf16 (nearest even).
+ *   c's tile must be (cfg.bm, cfg.bn) or (128, bn) for the default config.
+ * cfg may be NULL (defaults). The partition may be plain or mapped
+ * (TP_MAP_STRIDED: persistent programs). Errors: TP_ERR_SHAPE, TP_ERR_ALIGN,
+ * TP_ERR_ALIAS, TP_ERR_BUSY, TP_ERR_UNSUPPORTED, TP_ERR_TIMEOUT, TP_ERR_CUDA. */
+tp_status tp_gemm(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_tensor* b,
+                  const tp_gemm_config* cfg, const tp_exec* ex);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TP_H */

@@ -1,0 +1,255 @@
+"""Partitioned tile-program kernels for GB300 (sm_103a) behind a C ABI.
+
+Python binding of libtp.so with the same names as the C entry points
+(include/tp.h). It marshals torch tensors into tp_tensor views and passes
+torch's CUDA stream; all computation runs in the library's CUDA kernels.
+There is no fallback: if libtp.so is missing or no GPU is present, the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+from ._lib import (ASYNC, CAPTURE, MAP_IDENTITY, MAP_QUEUE, MAP_STRIDED, SYNC, TPError, call,
+                   tp_exec, tp_gemm_config, tp_partition_info, tp_tensor)
+
+__all__ = [
+    "TPError", "SYNC", "ASYNC", "CAPTURE", "MAP_IDENTITY", "MAP_STRIDED", "MAP_QUEUE",
+    "tensor_desc", "make_exec", "gemm_config",
+    "tp_version", "tp_ctx_create", "tp_ctx_destroy", "tp_ctx_info", "tp_tensor_init", "tp_tensor_view",
+    "tp_partition_create", "tp_partition_map", "tp_partition_query", "tp_partition_destroy",
+    "tp_event_create", "tp_event_query", "tp_event_wait", "tp_event_destroy",
+    "tp_graph_begin", "tp_graph_end", "tp_graph_replay", "tp_graph_destroy",
+    "tp_map_axpy", "tp_map_gelu_mul", "tp_map_scale", "tp_map_add_accum", "tp_gemm",
+]
+
+_DTYPES = {
+    torch.float32: _lib.F32,
+    torch.bfloat16: _lib.BF16,
+    torch.float8_e4m3fn: _lib.F8E4M3,
+    torch.float64: _lib.F64,
+    torch.int32: _lib.I32,
+    torch.uint8: _lib.U8,
+}
+if hasattr(torch, "uint32"):
+    _DTYPES[torch.uint32] = _lib.U32
+
+
+def _i64(vals):
+    arr = (ctypes.c_int64 * max(1, len(vals)))(*[int(v) for v in vals])
+    return arr
+
+
+def tensor_desc(t) -> tp_tensor:
+    """tp_tensor view of a torch tensor (or a tp_tensor passed through)."""
+    if isinstance(t, tp_tensor):
+        return t
+    if t.dtype not in _DTYPES:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    d = tp_tensor()
+    call("tp_tensor_init", ctypes.byref(d), ctypes.c_void_p(t.data_ptr()), _DTYPES[t.dtype], t.dim(),
+         _i64(t.shape), _i64(t.stride()))
+    return d
+
+
+def tp_tensor_init(t) -> tp_tensor:
+    return tensor_desc(t)
+
+
+def tp_tensor_view(base: tp_tensor, offset: int, shape, strides=None) -> tp_tensor:
+    out = tp_tensor()
+    call("tp_tensor_view", ctypes.byref(base), int(offset), len(shape), _i64(shape),
+         _i64(strides) if strides is not None else None, ctypes.byref(out))
+    return out
+
+
+def tp_version():
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    call("tp_version", ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+class Context:
+    def __init__(self, handle: int):
+        self.handle = ctypes.c_void_p(handle)
+        sm, ma, mi = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        call("tp_ctx_info", self.handle, ctypes.byref(sm), ctypes.byref(ma), ctypes.byref(mi))
+        self.sm_count, self.cc = sm.value, (ma.value, mi.value)
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+
+def tp_ctx_create(device: int = 0) -> Context:
+    h = ctypes.c_void_p()
+    call("tp_ctx_create", int(device), ctypes.byref(h))
+    return Context(h.value)
+
+
+def tp_ctx_destroy(ctx: Context) -> None:
+    if ctx.handle:
+        call("tp_ctx_destroy", ctx.handle)
+        ctx.handle = ctypes.c_void_p()
+
+
+def tp_ctx_info(ctx: Context):
+    return ctx.sm_count, ctx.cc
+
+
+class Partition:
+    """Handle of a partitioned mutable output; keeps the tensor alive."""
+
+    def __init__(self, handle, tensor, ctx):
+        self.handle = ctypes.c_void_p(handle)
+        self.tensor = tensor
+        self.ctx = ctx
+
+    @property
+    def _as_parameter_(self):
+        return self.handle
+
+
+def tp_partition_create(ctx, out, tile) -> Partition:
+    d = tensor_desc(out)
+    h = ctypes.c_void_p()
+    call("tp_partition_create", ctx.handle if ctx is not None else None, ctypes.byref(d), _i64(tile),
+         ctypes.byref(h))
+    return Partition(h.value, out, ctx)
+
+
+def tp_partition_map(p: Partition, kind: int, num_programs: int = 0) -> None:
+    call("tp_partition_map", p.handle, int(kind), int(num_programs))
+
+
+def tp_partition_query(p: Partition) -> dict:
+    info = tp_partition_info()
+    call("tp_partition_query", p.handle, ctypes.byref(info))
+    r = info.rank
+    return {"rank": r, "map_kind": info.map_kind, "shape": tuple(info.shape[:r]), "tile": tuple(info.tile[:r]),
+            "grid": tuple(info.grid[:r]), "num_tiles": info.num_tiles, "num_programs": info.num_programs,
+            "busy": bool(info.busy)}
+
+
+def tp_partition_destroy(p: Partition) -> None:
+    if p.handle:
+        call("tp_partition_destroy", p.handle)
+        p.handle = ctypes.c_void_p()
+
+
+class Event:
+    def __init__(self, handle):
+        self.handle = ctypes.c_void_p(handle)
+
+
+def tp_event_create(ctx) -> Event:
+    h = ctypes.c_void_p()
+    call("tp_event_create", ctx.handle, ctypes.byref(h))
+    return Event(h.value)
+
+
+def tp_event_query(ev: Event) -> bool:
+    d = ctypes.c_int32()
+    call("tp_event_query", ev.handle, ctypes.byref(d))
+    return bool(d.value)
+
+
+def tp_event_wait(ev: Event) -> None:
+    call("tp_event_wait", ev.handle)
+
+
+def tp_event_destroy(ev: Event) -> None:
+    if ev.handle:
+        call("tp_event_destroy", ev.handle)
+        ev.handle = ctypes.c_void_p()
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Graph:
+    def __init__(self, handle, stream):
+        self.handle = ctypes.c_void_p(handle)
+        self.stream = stream
+
+
+def tp_graph_begin(ctx, stream) -> Graph:
+    h = ctypes.c_void_p()
+    call("tp_graph_begin", ctx.handle, ctypes.c_void_p(_stream_handle(stream)), ctypes.byref(h))
+    return Graph(h.value, stream)
+
+
+def tp_graph_end(g: Graph) -> None:
+    call("tp_graph_end", g.handle)
+
+
+def tp_graph_replay(g: Graph, ex: tp_exec | None = None) -> None:
+    call("tp_graph_replay", g.handle, ctypes.byref(ex if ex is not None else make_exec(stream=g.stream)))
+
+
+def tp_graph_destroy(g: Graph) -> None:
+    if g.handle:
+        call("tp_graph_destroy", g.handle)
+        g.handle = ctypes.c_void_p()
+
+
+def make_exec(mode: int = SYNC, stream=None, event: Event | None = None, write_counts=None,
+              write_owner=None) -> tp_exec:
+    """tp_exec for `mode` on `stream` (torch.cuda.Stream, raw handle, or None =
+    torch's current stream). write_counts / write_owner: optional uint32 /
+    int32 device tensors with one entry per output element."""
+    ex = tp_exec()
+    ex.mode = mode
+    ex.reserved = 0
+    ex.stream = _stream_handle(stream)
+    ex.event = event.handle.value if event is not None else None
+    ex.write_counts = write_counts.data_ptr() if write_counts is not None else None
+    ex.write_owner = write_owner.data_ptr() if write_owner is not None else None
+    return ex
+
+
+def gemm_config(bm=0, bn=0, bk=0, stages=0, group_m=0, num_programs=0, swap_ab=0, split_k=0):
+    return tp_gemm_config(bm, bn, bk, stages, group_m, num_programs, swap_ab, split_k)
+
+
+def _ex(ex):
+    return ctypes.byref(ex if ex is not None else make_exec())
+
+
+def tp_map_axpy(ctx, z: Partition, alpha: float, x, y, ex: tp_exec | None = None) -> None:
+    """z = alpha * x + y (element-wise; z is a partition)."""
+    dx, dy = tensor_desc(x), tensor_desc(y)
+    call("tp_map_axpy", ctx.handle, z.handle, float(alpha), ctypes.byref(dx), ctypes.byref(dy), _ex(ex))
+
+
+def tp_map_gelu_mul(ctx, y: Partition, x, w, ex: tp_exec | None = None) -> None:
+    """y = gelu_tanh(x) * w (element-wise)."""
+    dx, dw = tensor_desc(x), tensor_desc(w)
+    call("tp_map_gelu_mul", ctx.handle, y.handle, ctypes.byref(dx), ctypes.byref(dw), _ex(ex))
+
+
+def tp_map_scale(ctx, y: Partition, x, g, ex: tp_exec | None = None) -> None:
+    """y = x * g (element-wise)."""
+    dx, dg = tensor_desc(x), tensor_desc(g)
+    call("tp_map_scale", ctx.handle, y.handle, ctypes.byref(dx), ctypes.byref(dg), _ex(ex))
+
+
+def tp_map_add_accum(ctx, c: Partition, a, b, ex: tp_exec | None = None) -> None:
+    """c <- c + a + b (element-wise read-modify-write of the partition)."""
+    da, db = tensor_desc(a), tensor_desc(b)
+    call("tp_map_add_accum", ctx.handle, c.handle, ctypes.byref(da), ctypes.byref(db), _ex(ex))
+
+
+def tp_gemm(ctx, c: Partition, a, b, cfg: tp_gemm_config | None = None, ex: tp_exec | None = None) -> None:
+    """C = A . B into the partition c (see include/tp.h for layouts)."""
+    da, db = tensor_desc(a), tensor_desc(b)
+    call("tp_gemm", ctx.handle, c.handle, ctypes.byref(da), ctypes.byref(db),
+         ctypes.byref(cfg) if cfg is not None else None, _ex(ex))

@@ -1,0 +1,278 @@
+// Element-wise map kernels: one tile program per output tile (plain
+// partition, §3.4) or persistent programs walking a bounded sequence of tiles
+// (mapped partition, §3.6). The rank-1 path moves 16 bytes per load/store
+// (4 fp32 or 8 bf16) with streaming cache hints; other shapes use a scalar
+// path over the tile's elements. Each program stores only inside its tile.
+#include <cuda_bf16.h>
+
+#include "tp_internal.h"
+
+namespace tp {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct MapArgs {
+  void* out;
+  const void* x;
+  const void* y;
+  float alpha;
+  int32_t kind;      // tp_map_kind
+  int64_t n;         // elements of the output
+  int64_t ntiles;
+  int64_t tile;      // rank-1 tile length
+  unsigned* queue;   // TP_MAP_QUEUE counter
+  uint32_t* counts;  // write-count instrumentation (optional)
+  int32_t* owner;
+  int64_t shape[3];  // general path, padded to rank 3 (leading 1s)
+  int64_t tshape[3];
+  int64_t grid[3];
+};
+
+// gelu_tanh(x) = 0.5 x (1 + tanh(u)), u = sqrt(2/pi) (x + 0.044715 x^3),
+// evaluated as x / (1 + exp(-2u)) (0.5 (1 + tanh u) = 1 / (1 + exp(-2u))).
+// The exponent argument is capped at 80 so 1 + exp(.) stays below 2^126,
+// the range where the fast division is defined; the result there is ~0.
+__device__ __forceinline__ float gelu_tanh(float x) {
+  const float k0 = 0.7978845608028654f;          // sqrt(2/pi)
+  const float k1 = 0.7978845608028654f * 0.044715f;
+  float u = x * fmaf(k1, x * x, k0);
+  float e = __expf(fminf(-2.f * u, 80.f));
+  return __fdividef(x, 1.f + e);
+}
+
+template <int OP>
+__device__ __forceinline__ float apply(float x, float y, float c, float alpha) {
+  if constexpr (OP == kMapAxpy) return fmaf(alpha, x, y);
+  else if constexpr (OP == kMapGeluMul) return gelu_tanh(x) * y;
+  else if constexpr (OP == kMapScale) return x * y;
+  else return c + x + y;  // kMapAddAccum: c <- c + a + b
+}
+
+template <typename T> __device__ __forceinline__ float to_f(T v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <typename T> __device__ __forceinline__ T from_f(float v);
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// Tile -> program schedule of §3.4 / §3.6. Returns the next tile of this
+// program or -1 when its sequence is exhausted.
+struct Schedule {
+  int64_t cur;
+  __device__ __forceinline__ int64_t first(const MapArgs& a, int64_t* smem_slot) {
+    if (a.kind == TP_MAP_QUEUE) return dequeue(a, smem_slot);
+    cur = blockIdx.x;
+    return cur < a.ntiles ? cur : -1;
+  }
+  __device__ __forceinline__ int64_t next(const MapArgs& a, int64_t* smem_slot) {
+    if (a.kind == TP_MAP_QUEUE) return dequeue(a, smem_slot);
+    if (a.kind == TP_MAP_IDENTITY) return -1;
+    cur += gridDim.x;
+    return cur < a.ntiles ? cur : -1;
+  }
+  __device__ __forceinline__ int64_t dequeue(const MapArgs& a, int64_t* smem_slot) {
+    __syncthreads();  // everyone has read the previous slot
+    if (threadIdx.x == 0) *smem_slot = (int64_t)atomicAdd(a.queue, 1u);
+    __syncthreads();
+    int64_t t = *smem_slot;
+    return t < a.ntiles ? t : -1;
+  }
+};
+
+template <bool COUNT>
+__device__ __forceinline__ void count_write(const MapArgs& a, int64_t i) {
+  if constexpr (COUNT) {
+    atomicAdd(a.counts + i, 1u);
+    a.owner[i] = (int32_t)blockIdx.x;
+  }
+}
+
+template <typename T> struct Vec;
+template <> struct Vec<float> { using V = float4; static constexpr int N = 4; };
+template <> struct Vec<__nv_bfloat16> { using V = uint4; static constexpr int N = 8; };
+
+template <typename T>
+__device__ __forceinline__ void unpack(const typename Vec<T>::V& v, float* f) {
+  if constexpr (sizeof(T) == 4) {
+    f[0] = v.x; f[1] = v.y; f[2] = v.z; f[3] = v.w;
+  } else {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float2 t = __bfloat1622float2(h[i]);
+      f[2 * i] = t.x;
+      f[2 * i + 1] = t.y;
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ typename Vec<T>::V pack(const float* f) {
+  typename Vec<T>::V v;
+  if constexpr (sizeof(T) == 4) {
+    v.x = f[0]; v.y = f[1]; v.z = f[2]; v.w = f[3];
+  } else {
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+  }
+  return v;
+}
+
+// Rank-1 path: tile length is a multiple of the vector width and all three
+// pointers are 16-byte aligned, so every tile starts on a vector boundary.
+template <int OP, typename T, bool COUNT>
+__global__ void __launch_bounds__(kThreads) map_vec_kernel(const __grid_constant__ MapArgs a) {
+  using V = typename Vec<T>::V;
+  constexpr int W = Vec<T>::N;
+  constexpr int U = 16 / W > 1 ? 16 / W : 1;  // vectors per thread per round: 4 (f32), 2 (bf16)
+  __shared__ int64_t slot;
+  T* __restrict__ out = static_cast<T*>(a.out);
+  const T* __restrict__ x = static_cast<const T*>(a.x);
+  const T* __restrict__ y = static_cast<const T*>(a.y);
+  Schedule s;
+  for (int64_t t = s.first(a, &slot); t >= 0; t = s.next(a, &slot)) {
+    const int64_t start = t * a.tile;
+    const int64_t len = min(a.tile, a.n - start);
+    const int64_t nv = len / W;
+    const V* xv = reinterpret_cast<const V*>(x + start);
+    const V* yv = reinterpret_cast<const V*>(y + start);
+    V* ov = reinterpret_cast<V*>(out + start);
+    int64_t v = threadIdx.x;
+    for (; v + (U - 1) * kThreads < nv; v += U * kThreads) {
+      V xr[U], yr[U], cr[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        xr[u] = __ldcs(xv + v + u * kThreads);
+        yr[u] = __ldcs(yv + v + u * kThreads);
+        if constexpr (OP == kMapAddAccum) cr[u] = ov[v + u * kThreads];
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        float fx[W], fy[W], fc[W], fo[W];
+        unpack<T>(xr[u], fx);
+        unpack<T>(yr[u], fy);
+        if constexpr (OP == kMapAddAccum) unpack<T>(cr[u], fc);
+#pragma unroll
+        for (int i = 0; i < W; ++i) fo[i] = apply<OP>(fx[i], fy[i], OP == kMapAddAccum ? fc[i] : 0.f, a.alpha);
+        __stcs(ov + v + u * kThreads, pack<T>(fo));
+        if constexpr (COUNT) {
+#pragma unroll
+          for (int i = 0; i < W; ++i) count_write<COUNT>(a, start + (v + u * kThreads) * W + i);
+        }
+      }
+    }
+    for (; v < nv; v += kThreads) {
+      float fx[W], fy[W], fc[W], fo[W];
+      unpack<T>(__ldcs(xv + v), fx);
+      unpack<T>(__ldcs(yv + v), fy);
+      if constexpr (OP == kMapAddAccum) unpack<T>(ov[v], fc);
+#pragma unroll
+      for (int i = 0; i < W; ++i) fo[i] = apply<OP>(fx[i], fy[i], OP == kMapAddAccum ? fc[i] : 0.f, a.alpha);
+      __stcs(ov + v, pack<T>(fo));
+      if constexpr (COUNT) {
+#pragma unroll
+        for (int i = 0; i < W; ++i) count_write<COUNT>(a, start + v * W + i);
+      }
+    }
+    // ragged tail of the last tile (fewer than W elements)
+    for (int64_t i = nv * W + threadIdx.x; i < len; i += kThreads) {
+      const int64_t g = start + i;
+      float c = OP == kMapAddAccum ? to_f<T>(out[g]) : 0.f;
+      out[g] = from_f<T>(apply<OP>(to_f<T>(x[g]), to_f<T>(y[g]), c, a.alpha));
+      count_write<COUNT>(a, g);
+    }
+  }
+}
+
+// General path: any rank-1..3 partition of a contiguous output, scalar
+// accesses, elements of the tile outside the tensor are skipped.
+template <int OP, typename T, bool COUNT>
+__global__ void __launch_bounds__(kThreads) map_generic_kernel(const __grid_constant__ MapArgs a) {
+  __shared__ int64_t slot;
+  T* out = static_cast<T*>(a.out);
+  const T* x = static_cast<const T*>(a.x);
+  const T* y = static_cast<const T*>(a.y);
+  const int64_t tile_elems = a.tshape[0] * a.tshape[1] * a.tshape[2];
+  Schedule s;
+  for (int64_t t = s.first(a, &slot); t >= 0; t = s.next(a, &slot)) {
+    const int64_t t2 = t % a.grid[2];
+    const int64_t t1 = (t / a.grid[2]) % a.grid[1];
+    const int64_t t0 = t / (a.grid[2] * a.grid[1]);
+    for (int64_t e = threadIdx.x; e < tile_elems; e += kThreads) {
+      const int64_t l2 = e % a.tshape[2];
+      const int64_t l1 = (e / a.tshape[2]) % a.tshape[1];
+      const int64_t l0 = e / (a.tshape[2] * a.tshape[1]);
+      const int64_t g0 = t0 * a.tshape[0] + l0, g1 = t1 * a.tshape[1] + l1, g2 = t2 * a.tshape[2] + l2;
+      if (g0 >= a.shape[0] || g1 >= a.shape[1] || g2 >= a.shape[2]) continue;
+      const int64_t g = (g0 * a.shape[1] + g1) * a.shape[2] + g2;
+      float c = OP == kMapAddAccum ? to_f<T>(out[g]) : 0.f;
+      out[g] = from_f<T>(apply<OP>(to_f<T>(x[g]), to_f<T>(y[g]), c, a.alpha));
+      count_write<COUNT>(a, g);
+    }
+  }
+}
+
+template <int OP, typename T>
+cudaError_t launch_typed(const MapArgs& a, bool vec, bool count, int64_t grid, cudaStream_t st) {
+  dim3 g((unsigned)grid), b(kThreads);
+  if (vec) {
+    if (count) map_vec_kernel<OP, T, true><<<g, b, 0, st>>>(a);
+    else map_vec_kernel<OP, T, false><<<g, b, 0, st>>>(a);
+  } else {
+    if (count) map_generic_kernel<OP, T, true><<<g, b, 0, st>>>(a);
+    else map_generic_kernel<OP, T, false><<<g, b, 0, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_op(int op, const MapArgs& a, bool vec, bool count, int64_t grid, cudaStream_t st) {
+  switch (op) {
+    case kMapAxpy: return launch_typed<kMapAxpy, T>(a, vec, count, grid, st);
+    case kMapGeluMul: return launch_typed<kMapGeluMul, T>(a, vec, count, grid, st);
+    case kMapScale: return launch_typed<kMapScale, T>(a, vec, count, grid, st);
+    default: return launch_typed<kMapAddAccum, T>(a, vec, count, grid, st);
+  }
+}
+
+}  // namespace
+
+tp_status launch_map(tp_ctx* ctx, tp_partition* out, int op, float alpha, const tp_tensor* x,
+                     const tp_tensor* y, const tp_exec* ex, cudaStream_t stream, unsigned* queue) {
+  (void)ctx;
+  MapArgs a{};
+  a.out = out->t.ptr;
+  a.x = x->ptr;
+  a.y = y->ptr;
+  a.alpha = alpha;
+  a.kind = out->kind;
+  a.n = numel(out->t);
+  a.ntiles = out->num_tiles;
+  a.tile = out->tile[0];
+  a.queue = queue;
+  a.counts = ex->write_counts;
+  a.owner = ex->write_owner;
+  if ((a.counts == nullptr) != (a.owner == nullptr))
+    return fail(TP_ERR_INVALID, "write_counts and write_owner must be given together");
+  const int pad = 3 - out->rank;
+  for (int i = 0; i < 3; ++i) {
+    a.shape[i] = i < pad ? 1 : out->shape[i - pad];
+    a.tshape[i] = i < pad ? 1 : out->tile[i - pad];
+    a.grid[i] = i < pad ? 1 : out->grid[i - pad];
+  }
+  if (a.n == 0 || a.ntiles == 0) return TP_OK;
+  const int w = out->t.dtype == TP_F32 ? 4 : 8;
+  auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  const bool vec = out->rank == 1 && (a.tile % w) == 0 && aligned(a.out) && aligned(a.x) && aligned(a.y);
+  const int64_t grid = out->kind == TP_MAP_IDENTITY ? out->num_tiles : out->num_programs;
+  if (grid > 0x7fffffff) return fail(TP_ERR_UNSUPPORTED, "more than 2^31-1 tile programs");
+  const bool count = a.counts != nullptr;
+  cudaError_t e = out->t.dtype == TP_F32 ? launch_op<float>(op, a, vec, count, grid, stream)
+                                         : launch_op<__nv_bfloat16>(op, a, vec, count, grid, stream);
+  if (e != cudaSuccess) return cuda_fail(e, "map kernel launch");
+  return TP_OK;
+}
+
+}  // namespace tp

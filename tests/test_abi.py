@@ -1,0 +1,119 @@
+"""Host-side tests of the C ABI: the library loads, exports every declared
+symbol, and validates descriptors and partitions without touching a GPU."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import paper_2606_15991_gb300 as tp
+from oracle import partition as opart
+from paper_2606_15991_gb300 import _lib
+
+
+def _desc(shape, dtype=_lib.F32, ptr=0x10000, strides=None):
+    d = _lib.tp_tensor()
+    _lib.call("tp_tensor_init", ctypes.byref(d), ctypes.c_void_p(ptr), dtype, len(shape),
+              tp._i64(shape), tp._i64(strides) if strides else None)
+    return d
+
+
+def _status(name, *args):
+    return getattr(_lib.lib(), name)(*args)
+
+
+def test_exports_every_declared_symbol(built_lib):
+    syms = _lib.header_symbols()
+    assert len(syms) >= 25
+    missing = [s for s in syms if not hasattr(built_lib, s)]
+    assert missing == []
+    assert set(_lib._PROTOS) >= set(syms)
+
+
+def test_error_strings_and_version(built_lib):
+    for s in range(11):
+        assert built_lib.tp_error_string(s)
+    assert tp.tp_version() == (0, 1)
+
+
+def test_tensor_init_validation(built_lib):
+    d = _lib.tp_tensor()
+    assert _status("tp_tensor_init", ctypes.byref(d), None, _lib.F32, 9, tp._i64([1] * 9), None) == _lib.ERR_RANK
+    assert _status("tp_tensor_init", ctypes.byref(d), None, 99, 1, tp._i64([4]), None) == _lib.ERR_INVALID
+    assert _status("tp_tensor_init", ctypes.byref(d), None, _lib.F32, 1, tp._i64([-1]), None) == _lib.ERR_INVALID
+    d = _desc((3, 5))
+    assert list(d.strides[:2]) == [5, 1]
+
+
+def test_tensor_view_bounds(built_lib):
+    base = _desc((100,), ptr=0x1000)
+    v = tp.tp_tensor_view(base, 10, (20,))
+    assert v.ptr == 0x1000 + 40 and v.shape[0] == 20
+    with pytest.raises(tp.TPError) as e:
+        tp.tp_tensor_view(base, 90, (20,))
+    assert e.value.status == _lib.ERR_INVALID
+    v2 = tp.tp_tensor_view(base, 0, (10, 10), (10, 1))
+    assert v2.rank == 2
+
+
+def _part(shape, tile, strides=None):
+    d = _desc(shape, strides=strides)
+    h = ctypes.c_void_p()
+    st = _status("tp_partition_create", None, ctypes.byref(d), tp._i64(tile), ctypes.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("shape,tile", [((1024,), (128,)), ((10,), (4,)), ((5, 7, 3), (2, 3, 3)),
+                                        ((2 ** 28,), (4096,)), ((512, 512), (64, 64)), ((0,), (4,))])
+def test_partition_grid_matches_oracle(built_lib, shape, tile):
+    st, h = _part(shape, tile)
+    assert st == _lib.OK
+    p = tp.Partition(h.value, None, None)
+    q = tp.tp_partition_query(p)
+    assert q["grid"] == opart.grid(shape, tile)
+    assert q["num_tiles"] == opart.num_tiles(shape, tile)
+    assert q["num_programs"] == q["num_tiles"] and q["map_kind"] == _lib.MAP_IDENTITY and not q["busy"]
+    tp.tp_partition_destroy(p)
+
+
+def test_partition_rejections(built_lib):
+    assert _part((2, 2, 2, 2), (1, 1, 1, 1))[0] == _lib.ERR_RANK
+    assert _part((8,), (0,))[0] == _lib.ERR_INVALID
+    assert _part((4, 4), (2, 2), strides=(1, 4))[0] == _lib.ERR_UNSUPPORTED   # non-contiguous output
+
+
+def test_mapped_partition_program_count(built_lib):
+    st, h = _part((1000,), (64,))   # 16 tiles
+    p = tp.Partition(h.value, None, None)
+    for bad in (0, 17, -1):
+        with pytest.raises(tp.TPError) as e:
+            tp.tp_partition_map(p, _lib.MAP_STRIDED, bad)
+        assert e.value.status == _lib.ERR_INVALID
+    tp.tp_partition_map(p, _lib.MAP_STRIDED, 16)
+    tp.tp_partition_map(p, _lib.MAP_QUEUE, 3)
+    q = tp.tp_partition_query(p)
+    assert q["num_programs"] == 3 and q["map_kind"] == _lib.MAP_QUEUE
+    with pytest.raises(tp.TPError):
+        tp.tp_partition_map(p, 7, 3)
+    tp.tp_partition_map(p, _lib.MAP_IDENTITY)
+    assert tp.tp_partition_query(p)["num_programs"] == 16
+    tp.tp_partition_destroy(p)
+
+
+def test_ops_reject_missing_context(built_lib):
+    st, h = _part((64,), (64,))
+    x = _desc((64,))
+    ex = tp.make_exec(stream=0)
+    assert _status("tp_map_axpy", None, h, ctypes.c_float(1.0), ctypes.byref(x), ctypes.byref(x),
+                   ctypes.byref(ex)) == _lib.ERR_INVALID
+    _status("tp_partition_destroy", h)
+
+
+def test_ctx_create_without_gpu_fails_cleanly(built_lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    st = _status("tp_ctx_create", 0, ctypes.byref(h))
+    assert st in (_lib.ERR_CUDA, _lib.ERR_INVALID) and not h.value
+    assert built_lib.tp_last_error_detail()
