@@ -1,0 +1,161 @@
+"""GPU parity of the BF16 tcgen05 GEMM (TMA -> shared-memory ring -> tcgen05.mma
+-> TMEM -> bf16 epilogue) against the FP64 oracle, and its tile coverage."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2606_15991_gb300 as tp
+import synth
+from oracle import gemm as ogemm
+from oracle import lowp
+from oracle import partition as opart
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(n, seed, kind="normal", lo=-4, hi=4):
+    if kind == "normal":
+        return synth.to_bf16(synth.normal(n, seed))
+    return synth.to_bf16(synth.integers(n, seed, lo, hi))
+
+
+def _operands(m, n, k, seed=0, kind="normal"):
+    a = _bf16(m * k, seed, kind).reshape(m, k).cuda()
+    bt = _bf16(n * k, seed + 1, kind).reshape(n, k).cuda()      # B stored N x K (K-major)
+    return a, bt
+
+
+def _gemm(ctx, a, bt, bn=128, kind=tp.MAP_STRIDED, P=None, group_m=1, stages=0, count=False, bm=128):
+    m, n = a.shape[0], bt.shape[0]
+    c = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
+    p = tp.tp_partition_create(ctx, c, (bm, bn))
+    if kind != tp.MAP_IDENTITY:
+        tiles = tp.tp_partition_query(p)["num_tiles"]
+        default = ctx.sm_count if bm == 128 else ctx.sm_count // 2
+        tp.tp_partition_map(p, kind, min(P or default, tiles))
+    counts = owner = None
+    if count:
+        counts = torch.zeros(m * n, dtype=torch.int32, device="cuda")
+        owner = torch.full((m * n,), -1, dtype=torch.int32, device="cuda")
+    tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=bm, bn=bn, group_m=group_m, stages=stages),
+               tp.make_exec(write_counts=counts, write_owner=owner))
+    info = tp.tp_partition_query(p)
+    tp.tp_partition_destroy(p)
+    return c, counts, owner, info
+
+
+@pytest.mark.parametrize("bm,bn", [(128, 32), (128, 64), (128, 128), (128, 192), (128, 256),
+                                   (256, 64), (256, 128), (256, 192), (256, 256)])
+def test_random_within_tolerance(ctx, bm, bn):
+    m, n, k = 384, 512, 640
+    a, bt = _operands(m, n, k, seed=bn)
+    c, _, _, _ = _gemm(ctx, a, bt, bn=bn, bm=bm)
+    ref = ogemm.gemm(a.cpu(), bt.cpu().t())
+    err = ogemm.rel_frobenius(c.cpu(), ref)
+    assert err <= 1e-2
+    assert err <= 5e-3          # expected ~2e-3: bf16 output rounding dominates
+
+
+@pytest.mark.parametrize("bm", [128, 256])
+@pytest.mark.parametrize("kind", [tp.MAP_IDENTITY, tp.MAP_STRIDED])
+def test_integer_inputs_bit_exact(ctx, kind, bm):
+    """Integer entries in [-4, 4]: every partial sum is exact in FP32, so C must
+    equal the round-to-nearest-even bf16 of the exact integer product."""
+    m, n, k = 256, 384, 512
+    a, bt = _operands(m, n, k, seed=3, kind="int")
+    c, _, _, _ = _gemm(ctx, a, bt, bn=128, kind=kind, P=5, bm=bm)
+    exact = ogemm.gemm(a.cpu(), bt.cpu().t())
+    assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(exact))
+
+
+def test_identity_and_permutation_bit_exact(ctx):
+    k = 256
+    bt = _bf16(192 * k, 5).reshape(192, k).cuda()             # B^T: 192 x 256
+    eye = torch.eye(k, dtype=torch.bfloat16, device="cuda")
+    c, _, _, _ = _gemm(ctx, eye, bt, bn=64)                    # I . B = B
+    assert torch.equal(c, bt.t())
+    perm = torch.tensor([(53 * i + 7) % k for i in range(k)])
+    P = torch.zeros(k, k, dtype=torch.bfloat16)
+    P[torch.arange(k), perm] = 1.0
+    c, _, _, _ = _gemm(ctx, P.cuda(), bt, bn=64)
+    assert torch.equal(c, bt.t()[perm.cuda()])
+
+
+@pytest.mark.parametrize("bm", [128, 256])
+@pytest.mark.parametrize("m,n,k", [(1, 32, 8), (129, 65, 72), (300, 200, 136), (130, 1000, 8), (7, 8, 4104)])
+def test_ragged_shapes(ctx, m, n, k, bm):
+    a, bt = _operands(m, n, k, seed=m + n)
+    c, counts, owner, info = _gemm(ctx, a, bt, bn=64, count=True, P=3, bm=bm)
+    ref = ogemm.gemm(a.cpu(), bt.cpu().t())
+    assert ogemm.rel_frobenius(c.cpu(), ref) <= 1e-2
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    assert np.array_equal(owner.cpu().numpy(),
+                          opart.gemm_owner_map(m, n, bm, 64, info["num_programs"], "strided", 1))
+
+
+@pytest.mark.parametrize("bm", [128, 256])
+@pytest.mark.parametrize("P,group_m,stages", [(7, 2, 0), (148, 8, 3), (1, 1, 2), (64, 4, 6)])
+def test_mapped_partition_coverage(ctx, P, group_m, stages, bm):
+    m, n, k = 1024, 1280, 256
+    a, bt = _operands(m, n, k, seed=P)
+    c, counts, owner, info = _gemm(ctx, a, bt, bn=128, P=P, group_m=group_m, stages=stages, count=True, bm=bm)
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    assert np.array_equal(owner.cpu().numpy(),
+                          opart.gemm_owner_map(m, n, bm, 128, info["num_programs"], "strided", group_m))
+    assert ogemm.rel_frobenius(c.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 1e-2
+
+
+@pytest.mark.parametrize("bm", [128, 256])
+def test_plain_partition_one_program_per_tile(ctx, bm):
+    m, n, k = 512, 768, 128
+    a, bt = _operands(m, n, k, seed=9)
+    c, counts, owner, info = _gemm(ctx, a, bt, bn=256, kind=tp.MAP_IDENTITY, count=True, bm=bm)
+    assert info["num_programs"] == info["num_tiles"] == (512 // bm) * 3
+    assert np.array_equal(owner.cpu().numpy(), opart.gemm_owner_map(m, n, bm, 256))
+    assert ogemm.rel_frobenius(c.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 1e-2
+
+
+def test_layout_and_alignment_errors(ctx):
+    a = torch.zeros(256, 100, dtype=torch.bfloat16, device="cuda")    # K*2 = 200 bytes: not 16-aligned
+    bt = torch.zeros(128, 100, dtype=torch.bfloat16, device="cuda")
+    c = torch.zeros(256, 128, dtype=torch.bfloat16, device="cuda")
+    p = tp.tp_partition_create(ctx, c, (128, 128))
+    with pytest.raises(tp.TPError) as e:
+        tp.tp_gemm(ctx, p, a, bt.t())
+    assert e.value.status == tp._lib.ERR_ALIGN
+    a2 = torch.zeros(256, 128, dtype=torch.bfloat16, device="cuda")
+    b_rowmajor = torch.zeros(128, 128, dtype=torch.bfloat16, device="cuda")   # K x N, N contiguous
+    with pytest.raises(tp.TPError) as e:
+        tp.tp_gemm(ctx, p, a2, b_rowmajor)
+    assert e.value.status == tp._lib.ERR_UNSUPPORTED
+    tp.tp_partition_destroy(p)
+    p = tp.tp_partition_create(ctx, c, (64, 128))
+    with pytest.raises(tp.TPError) as e:
+        tp.tp_gemm(ctx, p, a2, b_rowmajor.t())
+    assert e.value.status == tp._lib.ERR_UNSUPPORTED
+    tp.tp_partition_destroy(p)
+
+
+def test_8192_cubed_sampled_tiles(ctx):
+    """The 8192^3 configuration with N(0,1) bf16 inputs, launched as the
+    benchmark launches it (persistent CTA pairs, 256 x 256 tiles); error over
+    64 sampled 128 x 128 output tiles against FP64."""
+    M = N = K = 8192
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    a = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    bt = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    c, _, _, _ = _gemm(ctx, a, bt, bn=256, bm=256, group_m=16)
+    tiles = synth.sample_tiles(64, 64, 64, seed=0)
+    rows = sorted({tm for tm, _ in tiles})
+    cols = sorted({tn for _, tn in tiles})
+    a_h = {tm: a[tm * 128:(tm + 1) * 128].cpu() for tm in rows}
+    b_h = {tn: bt[tn * 128:(tn + 1) * 128].cpu() for tn in cols}
+    got, ref = [], []
+    for tm, tn in tiles:
+        ref.append(ogemm.gemm(a_h[tm], b_h[tn].t()))
+        got.append(c[tm * 128:(tm + 1) * 128, tn * 128:(tn + 1) * 128].cpu().double().numpy())
+    err = ogemm.rel_frobenius(np.stack(got), np.stack(ref))
+    assert err <= 1e-2
+    del a, bt, c
+    torch.cuda.empty_cache()
