@@ -247,6 +247,35 @@ tp_status tp_map_add_accum(tp_ctx* ctx, tp_partition* c, const tp_tensor* a,
 tp_status tp_gemm(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_tensor* b,
                   const tp_gemm_config* cfg, const tp_exec* ex);
 
+/* ------------------------------------------------- allocation-free entry */
+/* Queue-mapped z = alpha * x + y that needs no context and allocates nothing.
+ * The paper has no counterpart; it exists for callers that cannot call
+ * cudaMalloc: code that runs while someone else is capturing the stream into
+ * a CUDA graph (allocating there breaks or invalidates the capture), and code
+ * inside a runtime whose device memory is wholly owned by its own arena
+ * allocator. Such a caller passes only its inputs and output:
+ *   z, x, y       device pointers to n contiguous elements of `dtype`
+ *                 (TP_F32 or TP_BF16); x and y must not overlap z.
+ *   tile          elements per tile (>= 1); the output is split into
+ *                 ceil(n / tile) tiles that a device queue hands out, each
+ *                 exactly once, to `num_programs` persistent programs
+ *                 (1..number of tiles).
+ *   stream        cudaStream_t (NULL = legacy stream); the call only enqueues.
+ * The result equals tp_map_axpy on a TP_MAP_QUEUE partition.
+ * Scratch: the queue's one 32-bit tile counter, kept in a static device array
+ * of 256 bytes that every GPU loading this library holds until exit. The
+ * first call on a device looks up that array's device address with the
+ * device current, so make the first call on each device before any stream
+ * capture. Each call clears the counter on `stream` before its launch. All
+ * calls share the counter: calls that overlap on the GPU (on different
+ * streams without ordering between them) race on it and may skip or repeat
+ * tiles, so order such calls with one stream or with events.
+ * Limit: at most 2^31 tiles (TP_ERR_INVALID beyond). Errors: TP_ERR_INVALID
+ * (bad sizes, null pointers), TP_ERR_ALIAS, TP_ERR_UNSUPPORTED (dtype),
+ * TP_ERR_CUDA. Calls cudaMalloc, cudaFree or any allocating routine never. */
+tp_status tp_map_axpy_queue_noalloc(void* z, const void* x, const void* y, int32_t dtype, int64_t n,
+                                    int64_t tile, int32_t num_programs, float alpha, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

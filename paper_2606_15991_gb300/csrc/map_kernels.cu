@@ -276,3 +276,93 @@ tp_status launch_map(tp_ctx* ctx, tp_partition* out, int op, float alpha, const 
 }
 
 }  // namespace tp
+
+// ---------------------------------------------------------------------------
+// Allocation-free queue-mapped axpy (tp_map_axpy_queue_noalloc).
+//
+// Its only scratch is the device queue's tile counter. It lives in the static
+// device array below, so the entry point needs no context and allocates
+// nothing; every GPU that loads this library holds the array until exit.
+#include <mutex>
+
+namespace tp {
+namespace {
+
+constexpr int64_t kNoallocMaxTiles = int64_t(1) << 31;  // the 32-bit counter never wraps
+constexpr int kNoallocMaxDevices = 64;
+
+// One 32-bit tile counter (4 bytes used of a 256-byte-aligned array).
+static __device__ __align__(256) unsigned int g_noalloc_tile_queue[1];
+
+// Device address of g_noalloc_tile_queue per device, looked up once per
+// device with that device current. In host code the array's name is only a
+// host-side stand-in; only this looked-up address may be given to a kernel.
+void* g_noalloc_queue_addr[kNoallocMaxDevices] = {};
+std::mutex g_noalloc_mu;
+
+tp_status noalloc_queue_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(TP_ERR_UNSUPPORTED, "device index above 63");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_queue_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_tile_queue);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the tile-queue scratch");
+    g_noalloc_queue_addr[dev] = p;
+  }
+  *out = g_noalloc_queue_addr[dev];
+  return TP_OK;
+}
+
+}  // namespace
+}  // namespace tp
+
+extern "C" tp_status tp_map_axpy_queue_noalloc(void* z, const void* x, const void* y, int32_t dtype, int64_t n,
+                                               int64_t tile, int32_t num_programs, float alpha, void* stream) {
+  using namespace tp;
+  if (dtype != TP_F32 && dtype != TP_BF16) return fail(TP_ERR_UNSUPPORTED, "dtype must be TP_F32 or TP_BF16");
+  if (n < 0 || tile < 1) return fail(TP_ERR_INVALID, "need n >= 0 and tile >= 1");
+  const int64_t ntiles = (n + tile - 1) / tile;
+  if (ntiles > kNoallocMaxTiles)
+    return fail(TP_ERR_INVALID, "more than 2^31 tiles: the allocation-free tile queue holds a 32-bit counter");
+  if (n == 0) return TP_OK;
+  if (!z || !x || !y) return fail(TP_ERR_INVALID, "null pointer");
+  if (num_programs < 1 || num_programs > ntiles)
+    return fail(TP_ERR_INVALID, "num_programs must be 1..number of tiles");
+  const size_t es = dtype_size(dtype);
+  const uintptr_t z0 = reinterpret_cast<uintptr_t>(z), z1 = z0 + (uintptr_t)n * es;
+  for (const void* in : {x, y}) {
+    const uintptr_t i0 = reinterpret_cast<uintptr_t>(in), i1 = i0 + (uintptr_t)n * es;
+    if (i0 < z1 && z0 < i1) return fail(TP_ERR_ALIAS, "an input overlaps the output");
+  }
+  void* queue = nullptr;
+  tp_status s = noalloc_queue_address(&queue);
+  if (s != TP_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned int), st);  // the queue starts at slot 0
+  if (e != cudaSuccess) return cuda_fail(e, "clearing the tile-queue scratch");
+  MapArgs a{};
+  a.out = z;
+  a.x = x;
+  a.y = y;
+  a.alpha = alpha;
+  a.kind = TP_MAP_QUEUE;
+  a.n = n;
+  a.ntiles = ntiles;
+  a.tile = tile;
+  a.queue = static_cast<unsigned*>(queue);
+  for (int i = 0; i < 3; ++i) {
+    a.shape[i] = i < 2 ? 1 : n;
+    a.tshape[i] = i < 2 ? 1 : tile;
+    a.grid[i] = i < 2 ? 1 : ntiles;
+  }
+  const int w = dtype == TP_F32 ? 4 : 8;
+  auto aligned = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  const bool vec = (tile % w) == 0 && aligned(z) && aligned(x) && aligned(y);
+  e = dtype == TP_F32 ? launch_op<float>(kMapAxpy, a, vec, false, num_programs, st)
+                      : launch_op<__nv_bfloat16>(kMapAxpy, a, vec, false, num_programs, st);
+  if (e != cudaSuccess) return cuda_fail(e, "map kernel launch");
+  return TP_OK;
+}
