@@ -342,8 +342,35 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def _graph_time(tp, ctx, stream, record, reps: int, replays: int = 3) -> float:
+    """Mean device time (ms) of one recorded op: `record(ex)` is captured
+    `reps` times into one graph, the graph is replayed (after one warm-up
+    replay) and timed with CUDA events on the replay stream."""
+    import torch
+
+    g = tp.tp_graph_begin(ctx, stream)
+    cap = tp.make_exec(mode=tp.CAPTURE, stream=stream)
+    for _ in range(reps):
+        record(cap)
+    tp.tp_graph_end(g)
+    ex = tp.make_exec(stream=stream)
+    tp.tp_graph_replay(g, ex)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = None
+    for _ in range(replays):
+        e0.record(stream)
+        tp.tp_graph_replay(g, ex)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps
+        best = t if best is None else min(best, t)
+    tp.tp_graph_destroy(g)
+    return best
+
+
 def secondary_rows(tp, ctx, dev, stream, peaks):
-    """Other hot-path configurations, each timed with CUDA events after warm-up."""
+    """Other hot-path configurations. Each op is captured back to back into
+    a CUDA graph and replayed; per-op time = replay time / ops (CUDA events)."""
     import torch
 
     import synth
@@ -354,26 +381,60 @@ def secondary_rows(tp, ctx, dev, stream, peaks):
     b = torch.from_numpy(synth.uniform(512 * 512, seed=1)).reshape(512, 512).to(dev)
     c = torch.empty(512, 512, device=dev)
     p = tp.tp_partition_create(ctx, c, (64, 64))
-    ex = tp.make_exec(stream=stream)
-    for _ in range(5):
-        tp.tp_gemm(ctx, p, a, b, None, ex)
-    reps = 50
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    exa = tp.make_exec(stream=stream)
-    exa.mode = tp.ASYNC
-    ev = tp.tp_event_create(ctx)
-    exa.event = ev.handle.value
-    e0.record(stream)
-    for _ in range(reps):
-        tp.tp_gemm(ctx, p, a, b, None, exa)
-        tp.tp_event_wait(ev)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    rows["gemm_f32_512"] = {"tflops": 2 * 512 ** 3 / (ms * 1e-3) / 1e12, "ms": ms,
-                            "note": "latency-bound FFMA tiles; includes per-call event wait"}
+    ms = _graph_time(tp, ctx, stream, lambda ex: tp.tp_gemm(ctx, p, a, b, None, ex), reps=50)
+    rows["gemm_f32_512"] = {"tflops": 2 * 512 ** 3 / (ms * 1e-3) / 1e12, "ms": ms, "programs": 64,
+                            "note": "64 tile programs on 152 SMs: latency-bound FFMA"}
     tp.tp_partition_destroy(p)
-    tp.tp_event_destroy(ev)
+    del a, b, c
+
+    # BF16 and FP8 tcgen05 GEMM 8192^3, 256x256 tiles on CTA pairs
+    M = N = K = 8192
+    flops = 2 * M * N * K
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    a = torch.randn(M, K, device=dev, generator=g).to(torch.bfloat16)
+    bt = torch.randn(N, K, device=dev, generator=g).to(torch.bfloat16)   # B stored N x K (K-major)
+    c = torch.empty(M, N, device=dev, dtype=torch.bfloat16)
+    cfg = tp.gemm_config(bm=256, bn=256, group_m=8)
+    p = tp.tp_partition_create(ctx, c, (256, 256))
+    tp.tp_partition_map(p, tp.MAP_STRIDED, min(ctx.sm_count // 2, tp.tp_partition_query(p)["num_tiles"]))
+    ms = _graph_time(tp, ctx, stream, lambda ex: tp.tp_gemm(ctx, p, a, bt.t(), cfg, ex), reps=10)
+    tf = flops / (ms * 1e-3) / 1e12
+    rows["gemm_bf16_8192"] = {
+        "tflops": tf, "ms": ms, "tile": [256, 256], "programs": ctx.sm_count // 2,
+        "roofline": {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": tf / peaks["bf16_tflops"], "peak_src": peaks["src"] + " bf16 burst"}}
+
+    # FP8: amax + quantize (HBM passes, reported separately) and the GEMM
+    amax = torch.zeros(2, device=dev)
+    scale = torch.zeros(2, device=dev)
+    qa = torch.empty(M, K, device=dev, dtype=torch.float8_e4m3fn)
+    qbt = torch.empty(N, K, device=dev, dtype=torch.float8_e4m3fn)
+    pqa = tp.tp_partition_create(ctx, qa, (16, K))
+    pqb = tp.tp_partition_create(ctx, qbt, (16, K))
+
+    def quant(ex):
+        tp.tp_amax(ctx, a, amax[0:1], ex)
+        tp.tp_amax(ctx, bt, amax[1:2], ex)
+        tp.tp_quantize_fp8(ctx, pqa, a, amax[0:1], scale[0:1], ex)
+        tp.tp_quantize_fp8(ctx, pqb, bt, amax[1:2], scale[1:2], ex)
+
+    qms = _graph_time(tp, ctx, stream, quant, reps=5)
+    qbytes = 2 * (2 * M * K * 2 + M * K)   # per operand: amax read + quantize read (bf16) + write (fp8)
+    ms8 = _graph_time(tp, ctx, stream,
+                      lambda ex: tp.tp_gemm_fp8(ctx, p, qa, qbt.t(), scale[0:1], scale[1:2], cfg, ex), reps=10)
+    tf8 = flops / (ms8 * 1e-3) / 1e12
+    peak8 = 2 * peaks["bf16_tflops"]
+    rows["gemm_fp8_8192"] = {
+        "tflops": tf8, "ms": ms8, "tile": [256, 256],
+        "quantize_ms": qms, "quantize_gbs": qbytes / (qms * 1e-3) / 1e9,
+        "tflops_incl_quantize": flops / ((ms8 + qms) * 1e-3) / 1e12,
+        "roofline": {"bound": "tensor", "achieved": tf8, "peak": peak8, "unit": "TFLOP/s", "frac": tf8 / peak8,
+                     "peak_src": peaks["src"] + " bf16 burst x 2 (nominal fp8:bf16 dense ratio)"}}
+    for h in (p, pqa, pqb):
+        tp.tp_partition_destroy(h)
+    del a, bt, c, qa, qbt
+    torch.cuda.empty_cache()
     return rows
 
 

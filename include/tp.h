@@ -247,6 +247,30 @@ tp_status tp_map_add_accum(tp_ctx* ctx, tp_partition* c, const tp_tensor* a,
 tp_status tp_gemm(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_tensor* b,
                   const tp_gemm_config* cfg, const tp_exec* ex);
 
+/* ------------------------------------------------ FP8-E4M3 GEMM pipeline */
+/* Per-tensor-scaled FP8 GEMM (the FP8 workload; the paper's GEMM of §3.6 /
+ * §5.1 is f16): amax -> scale -> quantise -> tcgen05 kind::f8f6f4 GEMM with
+ * FP32 accumulation and an FP32 dequantising epilogue.
+ *
+ * tp_amax: *amax (device float) = max |x| over every element of the
+ * contiguous F32/BF16 tensor x (0 for an empty or all-zero tensor). The
+ * reduction uses atomic max on a single word, so it is not a partitioned
+ * output; *amax is cleared on the stream first. */
+tp_status tp_amax(tp_ctx* ctx, const tp_tensor* x, float* amax, const tp_exec* ex);
+/* q = E4M3(satfinite(RN(x * s))) with s = 448 / *amax in fp32 (s = 1 when
+ * *amax = 0); *scale (device float) receives s. q is a partition of an
+ * F8E4M3 (or U8) tensor with x's shape whose tiles span whole rows (rank 2:
+ * tile = [rows, K]); x is contiguous F32 or BF16. Codes are bit-exact
+ * functions of x and *amax (the product is an fp32 multiply). */
+tp_status tp_quantize_fp8(tp_ctx* ctx, tp_partition* q, const tp_tensor* x, const float* amax, float* scale,
+                          const tp_exec* ex);
+/* C (bf16) = (qA . qB) * 1 / (*scale_a * *scale_b) (dequantisation factor in
+ * fp32). qA: M x K E4M3, K-major; qB: K x N E4M3 view of N x K storage
+ * (K-major); K a multiple of 16. Same tiles, maps, configs and errors as the
+ * BF16 path of tp_gemm (128 K elements per pipeline stage). */
+tp_status tp_gemm_fp8(tp_ctx* ctx, tp_partition* c, const tp_tensor* qa, const tp_tensor* qb,
+                      const float* scale_a, const float* scale_b, const tp_gemm_config* cfg, const tp_exec* ex);
+
 /* ------------------------------------------------- allocation-free entry */
 /* Queue-mapped z = alpha * x + y that needs no context and allocates nothing.
  * The paper has no counterpart; it exists for callers that cannot call

@@ -24,6 +24,7 @@ __all__ = [
     "tp_event_create", "tp_event_query", "tp_event_wait", "tp_event_destroy",
     "tp_graph_begin", "tp_graph_end", "tp_graph_replay", "tp_graph_destroy",
     "tp_map_axpy", "tp_map_gelu_mul", "tp_map_scale", "tp_map_add_accum", "tp_gemm",
+    "tp_amax", "tp_quantize_fp8", "tp_gemm_fp8",
 ]
 
 _DTYPES = {
@@ -253,3 +254,27 @@ def tp_gemm(ctx, c: Partition, a, b, cfg: tp_gemm_config | None = None, ex: tp_e
     da, db = tensor_desc(a), tensor_desc(b)
     call("tp_gemm", ctx.handle, c.handle, ctypes.byref(da), ctypes.byref(db),
          ctypes.byref(cfg) if cfg is not None else None, _ex(ex))
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def tp_amax(ctx, x, amax, ex: tp_exec | None = None) -> None:
+    """amax[0] = max |x| (amax: a float32 device tensor with one element)."""
+    dx = tensor_desc(x)
+    call("tp_amax", ctx.handle, ctypes.byref(dx), _dptr(amax), _ex(ex))
+
+
+def tp_quantize_fp8(ctx, q: Partition, x, amax, scale, ex: tp_exec | None = None) -> None:
+    """q = E4M3(satfinite(RN(x * 448 / amax))); scale[0] receives 448 / amax."""
+    dx = tensor_desc(x)
+    call("tp_quantize_fp8", ctx.handle, q.handle, ctypes.byref(dx), _dptr(amax), _dptr(scale), _ex(ex))
+
+
+def tp_gemm_fp8(ctx, c: Partition, qa, qb, scale_a, scale_b, cfg: tp_gemm_config | None = None,
+                ex: tp_exec | None = None) -> None:
+    """C (bf16) = (qA . qB) / (scale_a * scale_b) from E4M3 operands."""
+    da, db = tensor_desc(qa), tensor_desc(qb)
+    call("tp_gemm_fp8", ctx.handle, c.handle, ctypes.byref(da), ctypes.byref(db), _dptr(scale_a),
+         _dptr(scale_b), ctypes.byref(cfg) if cfg is not None else None, _ex(ex))

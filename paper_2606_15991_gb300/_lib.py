@@ -96,6 +96,9 @@ _PROTOS = {
     "tp_map_scale": [_VP, _VP, _PT, _PT, _PE],
     "tp_map_add_accum": [_VP, _VP, _PT, _PT, _PE],
     "tp_gemm": [_VP, _VP, _PT, _PT, ctypes.POINTER(tp_gemm_config), _PE],
+    "tp_amax": [_VP, _PT, _VP, _PE],
+    "tp_quantize_fp8": [_VP, _VP, _PT, _VP, _VP, _PE],
+    "tp_gemm_fp8": [_VP, _VP, _PT, _PT, _VP, _VP, ctypes.POINTER(tp_gemm_config), _PE],
     "tp_map_axpy_queue_noalloc": [_VP, _VP, _VP, _I32, _I64, _I64, _I32, ctypes.c_float, _VP],
 }
 _RESTYPES = {"tp_error_string": ctypes.c_char_p, "tp_last_error_detail": ctypes.c_char_p}

@@ -43,7 +43,8 @@ struct TcArgs {
   int32_t c_vec;        // C rows are 16-byte aligned (N % 8 == 0, aligned base)
   int32_t kblk;         // K elements per stage (64 bf16 / 128 fp8)
   __nv_bfloat16* c;
-  const float* scale;   // optional: C = acc * (*scale)
+  const float* scale_a; // optional (FP8): C = acc * 1 / (*scale_a * *scale_b)
+  const float* scale_b;
   int* err;             // context error word
   uint32_t* counts;     // write-count instrumentation (optional)
   int32_t* owner;
@@ -212,7 +213,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // ---------------- epilogue (warps 2..5 -> TMEM lane quadrants 2,3,0,1)
     const int quad = warp & 3;
     const int row_in_tile = (int)rank * BM + quad * 32 + lane;
-    const float scale = p.scale ? *p.scale : 1.f;
+    // FP8 dequantisation factor 1 / (s_A * s_B), both steps in fp32
+    const float scale = (p.scale_a && p.scale_b) ? 1.f / (*p.scale_a * *p.scale_b) : 1.f;
     const uint32_t tempty_remote = kPair ? mapa(tempty_bar(0), 0) : 0u;
     int64_t t = 0;
     for (int64_t s = prog; s < T; s += step, ++t) {
@@ -346,7 +348,7 @@ cudaError_t launch_any(bool pair, bool count, const CUtensorMap& ma, const CUten
 // Shared by the BF16 and FP8 entry points. esize = 2 (bf16) or 1 (fp8).
 tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_tensor* b,
                               const tp_gemm_config* cfg, const tp_exec* ex, cudaStream_t stream, int esize,
-                              const float* scale) {
+                              const float* scale_a, const float* scale_b) {
   const int64_t M = a->shape[0], K = a->shape[1], N = b->shape[1];
   if ((ex->write_counts == nullptr) != (ex->write_owner == nullptr))
     return fail(TP_ERR_INVALID, "write_counts and write_owner must be given together");
@@ -385,7 +387,8 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   p.kblk = 128 / esize;
   p.c_vec = (N % 8 == 0) && (((uintptr_t)c->t.ptr & 15) == 0);
   p.c = static_cast<__nv_bfloat16*>(c->t.ptr);
-  p.scale = scale;
+  p.scale_a = scale_a;
+  p.scale_b = scale_b;
   p.err = ctx->d_err;
   p.counts = ex->write_counts;
   p.owner = ex->write_owner;
@@ -414,7 +417,7 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
 tp_status launch_gemm_tc(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_tensor* b,
                          const tp_gemm_config* cfg, const tp_exec* ex, cudaStream_t stream, unsigned* queue) {
   (void)queue;
-  return launch_gemm_tc_impl(ctx, c, a, b, cfg, ex, stream, 2, nullptr);
+  return launch_gemm_tc_impl(ctx, c, a, b, cfg, ex, stream, 2, nullptr, nullptr);
 }
 
 }  // namespace tp

@@ -119,4 +119,8 @@ tp_status launch_gemm_tc(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const
                          const tp_gemm_config* cfg, const tp_exec* ex, cudaStream_t stream,
                          unsigned* queue);
 
+tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_tensor* b,
+                              const tp_gemm_config* cfg, const tp_exec* ex, cudaStream_t stream, int esize,
+                              const float* scale_a, const float* scale_b);
+
 }  // namespace tp

@@ -1,0 +1,153 @@
+"""GPU parity of the per-tensor-scaled FP8-E4M3 path: amax (exact), quantised
+codes (bit-exact: both sides decide them in fp32), and the kind::f8f6f4
+tensor-core GEMM against FP64 references."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2606_15991_gb300 as tp
+import synth
+from oracle import gemm as ogemm
+from oracle import lowp
+from oracle import partition as opart
+
+pytestmark = pytest.mark.gpu
+
+
+def _x(n, seed, dt, std=1.0):
+    return synth.tensor(synth.normal(n, seed, std=std), dt).cuda()
+
+
+def _amax(ctx, x):
+    a = torch.full((1,), -1.0, device="cuda")
+    tp.tp_amax(ctx, x, a)
+    return a
+
+
+def _quantize(ctx, x, tile_rows=None, count=False, kind=tp.MAP_IDENTITY, P=0):
+    amax = _amax(ctx, x)
+    scale = torch.zeros(1, device="cuda")
+    q = torch.empty(x.shape, dtype=torch.float8_e4m3fn, device="cuda")
+    tile = (tile_rows, x.shape[1]) if x.dim() == 2 else (tile_rows or 4096,)
+    p = tp.tp_partition_create(ctx, q, tile)
+    if kind != tp.MAP_IDENTITY:
+        tp.tp_partition_map(p, kind, P)
+    counts = owner = None
+    if count:
+        counts = torch.zeros(x.numel(), dtype=torch.int32, device="cuda")
+        owner = torch.full((x.numel(),), -1, dtype=torch.int32, device="cuda")
+    tp.tp_quantize_fp8(ctx, p, x, amax, scale, tp.make_exec(write_counts=counts, write_owner=owner))
+    tp.tp_partition_destroy(p)
+    return q, amax, scale, counts, owner
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16"])
+@pytest.mark.parametrize("n", [1, 15, 4096 * 3 + 7, 1 << 20])
+def test_amax_exact(ctx, dt, n):
+    x = _x(n, 4 + n % 5, dt, std=3.0)
+    assert _amax(ctx, x).item() == float(ogemm.amax(x.cpu()))
+
+
+def test_amax_zero_and_negative_extreme(ctx):
+    z = torch.zeros(1000, device="cuda")
+    assert _amax(ctx, z).item() == 0.0
+    z[537] = -7.5
+    assert _amax(ctx, z).item() == 7.5
+
+
+@pytest.mark.parametrize("dt", ["f32", "bf16"])
+@pytest.mark.parametrize("shape,tile_rows", [((4096 * 5 + 3,), 4096), ((300, 256), 16), ((64, 1024), 64),
+                                             ((17, 48), 5)])
+def test_quantize_codes_bit_exact(ctx, dt, shape, tile_rows):
+    n = int(np.prod(shape))
+    x = _x(n, 7, dt).reshape(shape)
+    q, amax, scale, counts, owner = _quantize(ctx, x, tile_rows, count=True)
+    s_ref = ogemm.fp8_scale(ogemm.amax(x.cpu()))
+    assert scale.item() == float(s_ref)
+    codes = q.view(torch.uint8).cpu().numpy().reshape(-1)
+    assert np.array_equal(codes, ogemm.fp8_quantize(x.cpu().reshape(-1), s_ref))
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    tile = (tile_rows, shape[1]) if len(shape) == 2 else (tile_rows,)
+    assert np.array_equal(owner.cpu().numpy(), opart.owner_map(shape, tile))
+
+
+def test_quantize_zero_tensor_and_strided_map(ctx):
+    x = torch.zeros(4096 * 4, device="cuda")
+    q, amax, scale, _, _ = _quantize(ctx, x, 1024, kind=tp.MAP_STRIDED, P=3)
+    assert scale.item() == 1.0 and int(q.view(torch.uint8).max()) == 0
+
+
+def _fp8_gemm(ctx, a, bt, bm=128, bn=128, P=None, group_m=1, count=False):
+    qa, _, sa, _, _ = _quantize(ctx, a, 16)
+    qbt, _, sb, _, _ = _quantize(ctx, bt, 16)
+    m, n = a.shape[0], bt.shape[0]
+    c = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
+    p = tp.tp_partition_create(ctx, c, (bm, bn))
+    tiles = tp.tp_partition_query(p)["num_tiles"]
+    tp.tp_partition_map(p, tp.MAP_STRIDED, min(P or (ctx.sm_count * 128 // bm), tiles))
+    counts = owner = None
+    if count:
+        counts = torch.zeros(m * n, dtype=torch.int32, device="cuda")
+        owner = torch.full((m * n,), -1, dtype=torch.int32, device="cuda")
+    tp.tp_gemm_fp8(ctx, p, qa, qbt.t(), sa, sb, tp.gemm_config(bm=bm, bn=bn, group_m=group_m),
+                   tp.make_exec(write_counts=counts, write_owner=owner))
+    info = tp.tp_partition_query(p)
+    tp.tp_partition_destroy(p)
+    return c, qa, qbt, sa, sb, counts, owner, info
+
+
+@pytest.mark.parametrize("bm", [128, 256])
+def test_integer_inputs_exact(ctx, bm):
+    """Entries in [-7, 7] with amax 7: s = 64 (a power of two), every code and
+    partial sum is exact, so C is the bf16 rounding of the exact product."""
+    m, n, k = 256, 320, 512
+    a = synth.tensor(synth.integers(m * k, 1, -7, 7), "bf16").reshape(m, k)
+    bt = synth.tensor(synth.integers(n * k, 2, -7, 7), "bf16").reshape(n, k)
+    a[0, 0], bt[0, 0] = 7, -7
+    c, qa, qbt, sa, sb, counts, owner, info = _fp8_gemm(ctx, a.cuda(), bt.cuda(), bm=bm, bn=64, count=True, P=3)
+    assert sa.item() == 64.0 and sb.item() == 64.0
+    exact = ogemm.gemm(a, bt.t())
+    assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(exact))
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    assert np.array_equal(owner.cpu().numpy(),
+                          opart.gemm_owner_map(m, n, bm, 64, info["num_programs"], "strided", 1))
+
+
+@pytest.mark.parametrize("bm,bn", [(128, 128), (128, 256), (256, 256), (256, 128)])
+def test_random_errors(ctx, bm, bn):
+    m, n, k = 384, 512, 640
+    a = _x(m * k, 11, "bf16").reshape(m, k)
+    bt = _x(n * k, 12, "bf16").reshape(n, k)
+    c, qa, qbt, sa, sb, _, _, _ = _fp8_gemm(ctx, a, bt, bm=bm, bn=bn)
+    ref_fp8, qa_o, qb_o, sa_o, sb_o, inv = ogemm.gemm_fp8(a.cpu(), bt.cpu().t())
+    assert np.array_equal(qa.view(torch.uint8).cpu().numpy(), qa_o)
+    # kernel pin: FP32 accumulation + bf16 output against FP64 of the E4M3 values
+    assert ogemm.rel_frobenius(c.cpu(), ref_fp8) <= 5e-3
+    # end to end against the unquantised bf16 inputs: the stated FP8 tolerance
+    assert ogemm.rel_frobenius(c.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 5e-2
+
+
+def test_8192_cubed_sampled_tiles(ctx):
+    """8192^3 with N(0,1) bf16 inputs quantised per tensor, launched as the
+    benchmark launches it; errors over 64 sampled 128 x 128 tiles."""
+    M = N = K = 8192
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    a = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
+    bt = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
+    c, qa, qbt, sa, sb, _, _, _ = _fp8_gemm(ctx, a, bt, bm=256, bn=256, group_m=16)
+    inv = float(ogemm.fp8_dequant_factor(sa.item(), sb.item()))
+    tiles = synth.sample_tiles(64, 64, 64, seed=0)
+    got, ref_q, ref_in = [], [], []
+    for tm, tn in tiles:
+        rs, cs = slice(tm * 128, (tm + 1) * 128), slice(tn * 128, (tn + 1) * 128)
+        qa_t = lowp.e4m3_decode(qa[rs].view(torch.uint8).cpu().numpy())
+        qb_t = lowp.e4m3_decode(qbt[cs].view(torch.uint8).cpu().numpy())
+        ref_q.append((qa_t @ qb_t.T) * inv)
+        ref_in.append(ogemm.gemm(a[rs].cpu(), bt[cs].cpu().t()))
+        got.append(c[rs, cs].cpu().double().numpy())
+    got = np.stack(got)
+    assert ogemm.rel_frobenius(got, np.stack(ref_q)) <= 5e-3
+    assert ogemm.rel_frobenius(got, np.stack(ref_in)) <= 5e-2
+    del a, bt, c, qa, qbt
+    torch.cuda.empty_cache()
