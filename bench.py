@@ -435,7 +435,78 @@ def secondary_rows(tp, ctx, dev, stream, peaks):
         tp.tp_partition_destroy(h)
     del a, bt, c, qa, qbt
     torch.cuda.empty_cache()
+    rows["grouped_64"] = grouped_row(tp, ctx, dev, stream, peaks)
     return rows
+
+
+def grouped_row(tp, ctx, dev, stream, peaks):
+    """64 BF16 GEMMs (M log-uniform on [1, 4096], four (K, N) pairs, seed 0):
+    one persistent grouped launch against 64 plain per-call launches."""
+    import torch
+
+    import synth
+
+    shapes = synth.grouped_problems(64, seed=0)
+    g = torch.Generator(device=dev)
+    probs = []
+    for i, (m, n, k) in enumerate(shapes):
+        g.manual_seed(1000 + i)
+        a = torch.randn(m, k, device=dev, generator=g).to(torch.bfloat16)
+        bt = torch.randn(n, k, device=dev, generator=g).to(torch.bfloat16)
+        probs.append((a, bt.t(), torch.empty(m, n, dtype=torch.bfloat16, device=dev)))
+    flops = sum(2.0 * m * n * k for m, n, k in shapes)
+    bytes_ = sum(2.0 * (m * k + k * n + m * n) for m, n, k in shapes)
+    plan = tp.tp_grouped_plan_create(ctx, probs)
+    total_tiles, swapped = tp.tp_grouped_plan_info(plan)
+    ms_grouped = _graph_time(tp, ctx, stream, lambda ex: tp.tp_grouped_gemm(ctx, plan, 0, ex), reps=3)
+    # plain per-call: one tp_gemm per problem (1-CTA tiles for M <= 128, CTA pairs above)
+    parts = []
+    for a, b, c in probs:
+        bm = 128 if a.shape[0] <= 128 else 256
+        p = tp.tp_partition_create(ctx, c, (bm, 256))
+        tiles = tp.tp_partition_query(p)["num_tiles"]
+        tp.tp_partition_map(p, tp.MAP_STRIDED, min(tiles, ctx.sm_count * 128 // bm))
+        parts.append((p, tp.gemm_config(bm=bm, bn=256, group_m=8)))
+    sync_ex = tp.make_exec(stream=stream)
+
+    def plain_sync():
+        for (a, b, c), (p, cfg) in zip(probs, parts):
+            tp.tp_gemm(ctx, p, a, b, cfg, sync_ex)
+
+    ev = tp.tp_event_create(ctx)
+    async_ex = tp.make_exec(mode=tp.ASYNC, stream=stream, event=ev)
+
+    def plain_chained():
+        for (a, b, c), (p, cfg) in zip(probs, parts):
+            tp.tp_gemm(ctx, p, a, b, cfg, async_ex)
+        tp.tp_event_wait(ev)
+
+    res = {}
+    for name, fn in (("plain_sync", plain_sync), ("plain_chained", plain_chained)):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(3):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            ts.append((time.perf_counter() - t0) * 1e3)
+        res[name] = min(ts)
+    for p, _ in parts:
+        tp.tp_partition_destroy(p)
+    tp.tp_event_destroy(ev)
+    tp.tp_grouped_plan_destroy(plan)
+    t_roof = sum(max(2.0 * m * n * k / (peaks["bf16_tflops"] * 1e12),
+                     2.0 * (m * k + k * n + m * n) / (peaks["hbm_gbs"] * 1e9)) for m, n, k in shapes) * 1e3
+    del probs
+    torch.cuda.empty_cache()
+    return {"ms_grouped": ms_grouped, "ms_plain_sync": res["plain_sync"], "ms_plain_chained": res["plain_chained"],
+            "speedup_vs_plain_sync": res["plain_sync"] / ms_grouped,
+            "speedup_vs_plain_chained": res["plain_chained"] / ms_grouped,
+            "tflops_grouped": flops / (ms_grouped * 1e-3) / 1e12, "gflop": flops / 1e9, "gbytes": bytes_ / 1e9,
+            "tiles": total_tiles, "swapped_problems": int(sum(swapped)),
+            "roofline_ms": t_roof, "frac_of_roofline": t_roof / ms_grouped,
+            "note": "roofline = sum over problems of max(flops / bf16 peak, bytes / HBM peak), measured peaks"}
 
 
 def main():

@@ -25,6 +25,7 @@ __all__ = [
     "tp_graph_begin", "tp_graph_end", "tp_graph_replay", "tp_graph_destroy",
     "tp_map_axpy", "tp_map_gelu_mul", "tp_map_scale", "tp_map_add_accum", "tp_gemm",
     "tp_amax", "tp_quantize_fp8", "tp_gemm_fp8",
+    "tp_grouped_plan_create", "tp_grouped_plan_info", "tp_grouped_plan_destroy", "tp_grouped_gemm",
 ]
 
 _DTYPES = {
@@ -278,3 +279,42 @@ def tp_gemm_fp8(ctx, c: Partition, qa, qb, scale_a, scale_b, cfg: tp_gemm_config
     da, db = tensor_desc(qa), tensor_desc(qb)
     call("tp_gemm_fp8", ctx.handle, c.handle, ctypes.byref(da), ctypes.byref(db), _dptr(scale_a),
          _dptr(scale_b), ctypes.byref(cfg) if cfg is not None else None, _ex(ex))
+
+
+class GroupedPlan:
+    """Handle of a planned group; keeps the problem tensors alive."""
+
+    def __init__(self, handle, tensors, n):
+        self.handle = ctypes.c_void_p(handle)
+        self.tensors = tensors
+        self.n = n
+
+
+def tp_grouped_plan_create(ctx, problems, swap_max_m: int = -1) -> GroupedPlan:
+    """problems: [(A [M,K], B [K,N] K-major view, C [M,N])] of bf16 CUDA tensors."""
+    arr = (_lib.tp_gemm_problem * len(problems))()
+    keep = []
+    for i, (a, b, c) in enumerate(problems):
+        arr[i].a, arr[i].b, arr[i].c = tensor_desc(a), tensor_desc(b), tensor_desc(c)
+        keep += [a, b, c]
+    h = ctypes.c_void_p()
+    call("tp_grouped_plan_create", ctx.handle, arr, len(problems), int(swap_max_m), ctypes.byref(h))
+    return GroupedPlan(h.value, keep, len(problems))
+
+
+def tp_grouped_plan_info(plan: GroupedPlan):
+    total = ctypes.c_int64()
+    sw = (ctypes.c_int32 * plan.n)()
+    call("tp_grouped_plan_info", plan.handle, ctypes.byref(total), sw)
+    return total.value, [bool(v) for v in sw]
+
+
+def tp_grouped_plan_destroy(plan: GroupedPlan) -> None:
+    if plan.handle:
+        call("tp_grouped_plan_destroy", plan.handle)
+        plan.handle = ctypes.c_void_p()
+
+
+def tp_grouped_gemm(ctx, plan: GroupedPlan, num_programs: int = 0, ex: tp_exec | None = None) -> None:
+    """All problems of the plan in one persistent launch over a device tile queue."""
+    call("tp_grouped_gemm", ctx.handle, plan.handle, int(num_programs), _ex(ex))

@@ -51,6 +51,10 @@ class tp_gemm_config(ctypes.Structure):
                 ("bm", "bn", "bk", "stages", "group_m", "num_programs", "swap_ab", "split_k")]
 
 
+class tp_gemm_problem(ctypes.Structure):
+    _fields_ = [("a", tp_tensor), ("b", tp_tensor), ("c", tp_tensor)]
+
+
 class TPError(RuntimeError):
     def __init__(self, status: int, detail: str, call: str):
         self.status = status
@@ -99,6 +103,10 @@ _PROTOS = {
     "tp_amax": [_VP, _PT, _VP, _PE],
     "tp_quantize_fp8": [_VP, _VP, _PT, _VP, _VP, _PE],
     "tp_gemm_fp8": [_VP, _VP, _PT, _PT, _VP, _VP, ctypes.POINTER(tp_gemm_config), _PE],
+    "tp_grouped_plan_create": [_VP, ctypes.POINTER(tp_gemm_problem), _I32, _I32, _PP],
+    "tp_grouped_plan_info": [_VP, _PI64, _PI32],
+    "tp_grouped_plan_destroy": [_VP],
+    "tp_grouped_gemm": [_VP, _VP, _I32, _PE],
     "tp_map_axpy_queue_noalloc": [_VP, _VP, _VP, _I32, _I64, _I64, _I32, ctypes.c_float, _VP],
 }
 _RESTYPES = {"tp_error_string": ctypes.c_char_p, "tp_last_error_detail": ctypes.c_char_p}

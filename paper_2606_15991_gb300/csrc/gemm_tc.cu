@@ -220,7 +220,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t s = prog; s < T; s += step, ++t) {
       const int acc = (int)(t & 1);
       const uint32_t use = (uint32_t)((t >> 1) & 1);
-      if (!mbar_wait(tfull_bar(acc), use, abort_flag, p.err)) break;
+      const bool ready = mbar_wait(tfull_bar(acc), use, abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, ready)) break;  // leave together (tcgen05.ld is warp-collective)
       tc_fence_after();
       int64_t tm, tn;
       raster(s, p.gm, p.gn, p.group_m, &tm, &tn);

@@ -1,0 +1,507 @@
+// Grouped persistent BF16 GEMM: many independent problems C_i = A_i . B_i of
+// uneven sizes in one launch. Every output tile of every problem is a slot of
+// one device queue (a mapped partition whose map is a shared counter, §3.6);
+// each persistent CTA dequeues slots until the queue is empty. The queue
+// order lists the most expensive tiles first (longest-processing-time first)
+// so the last wave is made of short tiles.
+//
+// A problem with M <= 256 runs transposed ("swap-AB"): C^T = B^T . A^T, so
+// the large N fills the 128 rows of the tensor-core tile and the small M is
+// the MMA's N (rounded up to 32). Its tile is a 128-column slab of C; one pass
+// streams the matching 128 rows of B_i from HBM exactly once.
+//
+// Roles per CTA (192 threads): warp 0 dequeues slots, publishes them through
+// a 4-entry shared-memory ring and streams the tile's K slices with TMA;
+// warp 1 issues tcgen05.mma into two TMEM accumulators; warps 2-5 drain TMEM
+// and store. Every wait is bounded and reports TP_ERR_TIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "sm100_ptx.cuh"
+#include "tp_internal.h"
+
+namespace tp {
+
+// Device-side description of one problem (tensor maps first: 64-byte aligned).
+struct alignas(64) GroupedProblem {
+  CUtensorMap map_x;      // MMA A operand: A_i (normal) or B_i stored N x K (swap), box 128 rows
+  CUtensorMap map_y;      // MMA B operand: B_i (normal, box 256 rows) or A_i (swap, box bn rows)
+  __nv_bfloat16* c;
+  int64_t M, N, K;
+  int64_t tile_base;      // first queue slot of this problem
+  int64_t tiles_r, tiles_c;  // tile grid in MMA orientation (rows of 128, columns of bn)
+  int64_t count_base;     // offset of C_i in the write-count arrays
+  int32_t swap, bn;       // bn = MMA N of every tile of this problem
+  int32_t pad[2];
+};
+
+}  // namespace tp
+
+struct tp_grouped_plan {
+  tp_ctx* ctx = nullptr;
+  int32_t n = 0;
+  int64_t total_tiles = 0;
+  tp::GroupedProblem* d_probs = nullptr;   // device table (queue order)
+  std::vector<tp_partition*> outs;         // one partition per C_i (busy tracking)
+  std::vector<tp_tensor> ins;              // A_i and B_i views (alias checks)
+  std::vector<int32_t> order;              // queue position -> problem index
+  int64_t total_elems = 0;
+};
+
+namespace tp {
+namespace {
+
+using namespace sm100;
+
+constexpr int kThreads = 192;
+constexpr int kStages = 4;
+constexpr int kRing = 4;
+constexpr int kMaxProblems = 256;
+constexpr uint32_t kStageX = 128 * 128;   // 128 rows x 128 bytes
+constexpr uint32_t kStageY = 256 * 128;   // up to 256 rows x 128 bytes
+
+struct GroupedArgs {
+  const GroupedProblem* probs;
+  int32_t n;
+  int64_t total;
+  unsigned* queue;
+  int* err;
+  uint32_t* counts;
+  int32_t* owner;
+};
+
+__device__ __forceinline__ int find_problem(const int64_t* base, int n, int64_t g) {
+  int lo = 0, hi = n - 1;  // largest i with base[i] <= g
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (base[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_constant__ GroupedArgs p) {
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  const int warp = threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+
+  const uint32_t x0 = base;
+  const uint32_t y0 = x0 + kStageX * kStages;
+  const uint32_t bars = y0 + kStageY * kStages;
+  auto full_bar = [&](int s) { return bars + 8u * s; };
+  auto empty_bar = [&](int s) { return bars + 32u + 8u * s; };
+  auto tfull_bar = [&](int b) { return bars + 64u + 8u * b; };
+  auto tempty_bar = [&](int b) { return bars + 80u + 8u * b; };
+  auto rfull_bar = [&](int r) { return bars + 96u + 8u * r; };
+  auto rempty_bar = [&](int r) { return bars + 128u + 8u * r; };
+  const uint32_t drain_bar = bars + 160u;
+  uint8_t* words = gbase + (bars - base) + 168u;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(words);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(words + 4);
+  volatile int64_t* ring = reinterpret_cast<volatile int64_t*>(words + 8);          // kRing slots
+  int64_t* tile_base = reinterpret_cast<int64_t*>(words + 8 + 8 * kRing);          // n entries
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull_bar(b), 1);
+      mbar_init(tempty_bar(b), 4);
+    }
+    for (int r = 0; r < kRing; ++r) {
+      mbar_init(rfull_bar(r), 1);
+      mbar_init(rempty_bar(r), 5);  // MMA thread + one per epilogue warp
+    }
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  for (int i = threadIdx.x; i < p.n; i += kThreads) tile_base[i] = p.probs[i].tile_base;
+  if (warp == 1) {
+    tmem_alloc(smem_u32(tmem_slot), 512);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  // decode a queue slot into (problem, tile row, tile column)
+  auto decode = [&](int64_t g, const GroupedProblem** pr, int64_t* tr, int64_t* tc) {
+    const int i = find_problem(tile_base, p.n, g);
+    *pr = p.probs + i;
+    // column-major over the tile grid: consecutive slots share a B slab (the
+    // big operand) while the problem's A stays resident in L2
+    const int64_t local = g - tile_base[i];
+    *tr = local % (*pr)->tiles_r;
+    *tc = local / (*pr)->tiles_r;
+  };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const uint64_t pol_stream = policy_evict_first();
+      const uint64_t pol_keep = policy_evict_last();
+      uint32_t fills[kStages] = {};
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t j = 0; ok; ++j) {
+        const int r = (int)(j % kRing);
+        if (!mbar_wait(rempty_bar(r), (uint32_t)((j / kRing) & 1) ^ 1u, abort_flag, p.err)) { ok = false; break; }
+        const int64_t g = (int64_t)atomicAdd(p.queue, 1u);
+        ring[r] = g < p.total ? g : -1;
+        mbar_arrive(rfull_bar(r));
+        if (g >= p.total) break;
+        const GroupedProblem* pr;
+        int64_t tr, tc;
+        decode(g, &pr, &tr, &tc);
+        const int32_t xrow = (int32_t)(tr * 128);
+        const int32_t yrow = (int32_t)(tc * pr->bn);
+        const uint32_t tx = kStageX + (uint32_t)pr->bn * 128u;
+        const int64_t nk = (pr->K + 63) / 64;
+        for (int64_t kb = 0; kb < nk; ++kb) {
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err)) { ok = false; break; }
+          mbar_arrive_expect_tx(full_bar(stage), tx);
+          // swap: x = B_i slab (read once), y = A_i (reused by every tile)
+          tma_load_2d(x0 + kStageX * stage, &pr->map_x, (int32_t)(kb * 64), xrow, full_bar(stage),
+                      pr->swap ? pol_stream : pol_keep);
+          tma_load_2d(y0 + kStageY * stage, &pr->map_y, (int32_t)(kb * 64), yrow, full_bar(stage), pol_keep);
+          fills[stage]++;
+          if (++stage == kStages) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (!ok) {
+        for (int s2 = 0; s2 < kStages; ++s2)
+          if (fills[s2]) mbar_wait(full_bar(s2), (fills[s2] - 1u) & 1u, nullptr, nullptr, 200000000ull);
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t j = 0; ok; ++j) {
+        const int r = (int)(j % kRing);
+        if (!mbar_wait(rfull_bar(r), (uint32_t)((j / kRing) & 1), abort_flag, p.err)) { ok = false; break; }
+        const int64_t g = ring[r];
+        mbar_arrive(rempty_bar(r));
+        if (g < 0) break;
+        const GroupedProblem* pr;
+        int64_t tr, tc;
+        decode(g, &pr, &tr, &tc);
+        const int acc = (int)(j & 1);
+        const uint32_t use = (uint32_t)((j >> 1) & 1);
+        if (!mbar_wait(tempty_bar(acc), use ^ 1u, abort_flag, p.err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t idesc = idesc_f32acc(128, (uint32_t)pr->bn, false);
+        const uint32_t d = tmem_base + (uint32_t)(acc * 256);
+        const int64_t nk = (pr->K + 63) / 64;
+        for (int64_t kb = 0; kb < nk; ++kb) {
+          if (!mbar_wait(full_bar(stage), phase, abort_flag, p.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint64_t ad = desc_kmajor_sw128(x0 + kStageX * stage);
+          const uint64_t bd = desc_kmajor_sw128(y0 + kStageY * stage);
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            mma<false>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (kb > 0 || k > 0) ? 1u : 0u);
+          mma_commit(empty_bar(stage));
+          if (++stage == kStages) { stage = 0; phase ^= 1u; }
+        }
+        if (!ok) break;
+        mma_commit(tfull_bar(acc));
+      }
+      if (!ok) {
+        mma_commit(drain_bar);
+        mbar_wait(drain_bar, 0, nullptr, nullptr, 200000000ull);
+      }
+    }
+    __syncwarp();
+  } else {
+    const int quad = warp & 3;
+    const int lane_row = quad * 32 + lane;  // TMEM lane = tile row in MMA orientation
+    for (int64_t j = 0;; ++j) {
+      const int r = (int)(j % kRing);
+      const bool got = mbar_wait(rfull_bar(r), (uint32_t)((j / kRing) & 1), abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, got)) break;  // leave together (tcgen05.ld below is warp-collective)
+      const int64_t g = ring[r];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(rempty_bar(r));
+      if (g < 0) break;
+      const GroupedProblem* pr;
+      int64_t tr, tc;
+      decode(g, &pr, &tr, &tc);
+      const int acc = (int)(j & 1);
+      const uint32_t use = (uint32_t)((j >> 1) & 1);
+      const bool ready = mbar_wait(tfull_bar(acc), use, abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, ready)) break;
+      tc_fence_after();
+      const int64_t N = pr->N, M = pr->M;
+      const int64_t rr = tr * 128 + lane_row;  // row of C (normal) or column of C (swap)
+      for (int ch = 0; ch < pr->bn / 32; ++ch) {
+        uint32_t v[32];
+        tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * 256 + ch * 32), v);
+        tmem_ld_wait();
+        const int64_t c0 = tc * pr->bn + ch * 32;  // first column of the chunk (MMA orientation)
+        if (!pr->swap) {
+          if (rr >= M || c0 >= N) continue;
+          __nv_bfloat16* crow = pr->c + rr * N;
+          if ((N & 7) == 0 && c0 + 32 <= N) {
+            uint4 w[4];
+            __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(w);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) h[i] = __floats2bfloat162_rn(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+            uint4* dst = reinterpret_cast<uint4*>(crow + c0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) dst[i] = w[i];
+          } else {
+            for (int i = 0; i < 32; ++i)
+              if (c0 + i < N) crow[c0 + i] = __float2bfloat16_rn(__uint_as_float(v[i]));
+          }
+          if constexpr (kCount) {
+            for (int i = 0; i < 32; ++i)
+              if (c0 + i < N) {
+                const int64_t e = pr->count_base + rr * N + c0 + i;
+                atomicAdd(p.counts + e, 1u);
+                p.owner[e] = (int32_t)blockIdx.x;
+              }
+          }
+        } else {
+          // swap: TMEM lane = column n of C, TMEM column = row m of C
+          if (rr >= N) continue;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const int64_t m = c0 + i;
+            if (m < M) {
+              pr->c[m * N + rr] = __float2bfloat16_rn(__uint_as_float(v[i]));
+              if constexpr (kCount) {
+                const int64_t e = pr->count_base + m * N + rr;
+                atomicAdd(p.counts + e, 1u);
+                p.owner[e] = (int32_t)blockIdx.x;
+              }
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty_bar(acc));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem_base, 512);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+tp_status kmajor_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t k, int64_t ld, int box_rows) {
+  auto fn = encode();
+  if (!fn) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+  cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return TP_OK;
+}
+
+}  // namespace
+}  // namespace tp
+
+using namespace tp;
+
+extern "C" {
+
+tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int32_t n, int32_t swap_max_m,
+                                 tp_grouped_plan** out) {
+  if (!ctx || !probs || !out) return fail(TP_ERR_INVALID, "null argument");
+  *out = nullptr;
+  if (n < 1 || n > kMaxProblems) return fail(TP_ERR_INVALID, "group size must be 1..256");
+  if (swap_max_m < 0) swap_max_m = 256;
+  if (swap_max_m > 256) return fail(TP_ERR_INVALID, "swap_max_m must be <= 256");
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->capturing) return fail(TP_ERR_CAPTURE, "a plan allocates device memory: build it before capture");
+  }
+  std::vector<GroupedProblem> host(n);
+  std::vector<double> cost(n);
+  auto* plan = new tp_grouped_plan();
+  plan->ctx = ctx;
+  plan->n = n;
+  auto cleanup = [&](tp_status s) {
+    for (auto* q : plan->outs) tp_partition_destroy(q);
+    delete plan;
+    return s;
+  };
+  int64_t elems = 0;
+  for (int i = 0; i < n; ++i) {
+    const tp_tensor& a = probs[i].a;
+    const tp_tensor& b = probs[i].b;
+    const tp_tensor& c = probs[i].c;
+    if (a.rank != 2 || b.rank != 2 || c.rank != 2) return cleanup(fail(TP_ERR_RANK, "grouped operands are rank 2"));
+    const int64_t M = a.shape[0], K = a.shape[1], N = b.shape[1];
+    if (b.shape[0] != K || c.shape[0] != M || c.shape[1] != N)
+      return cleanup(fail(TP_ERR_SHAPE, "problem " + std::to_string(i) + ": need A M x K, B K x N, C M x N"));
+    if (a.dtype != TP_BF16 || b.dtype != TP_BF16 || c.dtype != TP_BF16)
+      return cleanup(fail(TP_ERR_UNSUPPORTED, "grouped GEMM is BF16 x BF16 -> BF16"));
+    if (a.strides[1] != 1 || b.strides[0] != 1 || !is_contiguous(c))
+      return cleanup(fail(TP_ERR_UNSUPPORTED, "grouped GEMM needs K-major A and B and a contiguous C"));
+    if (M < 1 || N < 1 || K < 1) return cleanup(fail(TP_ERR_SHAPE, "empty problem"));
+    const int64_t lda = a.strides[0], ldb = b.strides[1];
+    if (((uintptr_t)a.ptr & 15) || ((uintptr_t)b.ptr & 15) || ((lda * 2) & 15) || ((ldb * 2) & 15) || (K * 2) % 16)
+      return cleanup(fail(TP_ERR_ALIGN, "TMA needs 16-byte aligned bases and row strides (K % 8 == 0)"));
+    GroupedProblem& g = host[i];
+    std::memset(&g, 0, sizeof(g));
+    g.c = static_cast<__nv_bfloat16*>(c.ptr);
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.swap = M <= swap_max_m ? 1 : 0;
+    tp_status s;
+    int64_t tile_rows, tile_cols;
+    if (g.swap) {
+      g.bn = (int32_t)(((M + 31) / 32) * 32);
+      g.tiles_r = (N + 127) / 128;
+      g.tiles_c = 1;
+      s = kmajor_map(&g.map_x, b.ptr, N, K, ldb, 128);
+      if (s == TP_OK) s = kmajor_map(&g.map_y, a.ptr, M, K, lda, g.bn);
+      tile_rows = M;
+      tile_cols = 128;
+      cost[i] = 128.0 * (double)K * 2.0 / 44e9 + 2.0 * 128 * g.bn * K / 1.2e13;
+    } else {
+      g.bn = 256;
+      g.tiles_r = (M + 127) / 128;
+      g.tiles_c = (N + 255) / 256;
+      s = kmajor_map(&g.map_x, a.ptr, M, K, lda, 128);
+      if (s == TP_OK) s = kmajor_map(&g.map_y, b.ptr, N, K, ldb, 256);
+      tile_rows = 128;
+      tile_cols = 256;
+      cost[i] = 2.0 * 128 * 256 * (double)K / 1.2e13;
+    }
+    if (s != TP_OK) return cleanup(s);
+    g.count_base = elems;
+    elems += M * N;
+    tp_partition* part = nullptr;
+    int64_t tile[2] = {tile_rows, tile_cols};
+    s = tp_partition_create(ctx, &c, tile, &part);
+    if (s != TP_OK) return cleanup(s);
+    s = tp_partition_map(part, TP_MAP_QUEUE, 1);
+    if (s != TP_OK) {
+      tp_partition_destroy(part);
+      return cleanup(s);
+    }
+    plan->outs.push_back(part);
+    plan->ins.push_back(a);
+    plan->ins.push_back(b);
+  }
+  // queue order: most expensive tiles first (longest processing time first)
+  plan->order.resize(n);
+  std::iota(plan->order.begin(), plan->order.end(), 0);
+  std::stable_sort(plan->order.begin(), plan->order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<GroupedProblem> ordered(n);
+  int64_t slot = 0;
+  for (int q = 0; q < n; ++q) {
+    ordered[q] = host[plan->order[q]];
+    ordered[q].tile_base = slot;
+    slot += ordered[q].tiles_r * ordered[q].tiles_c;
+  }
+  plan->total_tiles = slot;
+  plan->total_elems = elems;
+  if (slot >= (int64_t(1) << 31)) return cleanup(fail(TP_ERR_UNSUPPORTED, "more than 2^31 tiles in a group"));
+  cudaError_t e = cudaMalloc(&plan->d_probs, sizeof(GroupedProblem) * n);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(plan->d_probs, ordered.data(), sizeof(GroupedProblem) * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(plan->d_probs);
+    return cleanup(cuda_fail(e, "uploading the problem table"));
+  }
+  *out = plan;
+  return TP_OK;
+}
+
+tp_status tp_grouped_plan_info(const tp_grouped_plan* plan, int64_t* total_tiles, int32_t* swapped) {
+  if (!plan) return fail(TP_ERR_INVALID, "null plan");
+  if (total_tiles) *total_tiles = plan->total_tiles;
+  if (swapped) {
+    std::vector<GroupedProblem> h(plan->n);
+    cudaError_t e = cudaMemcpy(h.data(), plan->d_probs, sizeof(GroupedProblem) * plan->n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the problem table");
+    for (int q = 0; q < plan->n; ++q) swapped[plan->order[q]] = h[q].swap;
+  }
+  return TP_OK;
+}
+
+tp_status tp_grouped_plan_destroy(tp_grouped_plan* plan) {
+  if (!plan) return fail(TP_ERR_INVALID, "null plan");
+  for (auto* q : plan->outs)
+    if (q->busy.load()) return fail(TP_ERR_BUSY, "the group has work in flight");
+  for (auto* q : plan->outs) tp_partition_destroy(q);
+  cudaFree(plan->d_probs);
+  delete plan;
+  return TP_OK;
+}
+
+tp_status tp_grouped_gemm(tp_ctx* ctx, tp_grouped_plan* plan, int32_t num_programs, const tp_exec* ex) {
+  if (!ctx || !plan || !ex) return fail(TP_ERR_INVALID, "null argument");
+  if (plan->ctx != ctx) return fail(TP_ERR_INVALID, "plan belongs to another context");
+  if ((ex->write_counts == nullptr) != (ex->write_owner == nullptr))
+    return fail(TP_ERR_INVALID, "write_counts and write_owner must be given together");
+  Op o;
+  tp_status s = o.begin_lists(ctx, ex, plan->outs, plan->ins);
+  if (s != TP_OK) return s;
+  o.check_err = true;
+  unsigned* q = nullptr;
+  s = queue_counter(ctx, o.stream, &q);
+  if (s != TP_OK) {
+    o.abort();
+    return s;
+  }
+  GroupedArgs a{};
+  a.probs = plan->d_probs;
+  a.n = plan->n;
+  a.total = plan->total_tiles;
+  a.queue = q;
+  a.err = ctx->d_err;
+  a.counts = ex->write_counts;
+  a.owner = ex->write_owner;
+  int grid = num_programs > 0 ? num_programs : ctx->sm_count;
+  if (grid > plan->total_tiles) grid = (int)plan->total_tiles;
+  const size_t smem = 1024 + (kStageX + kStageY) * kStages + 168 + 8 + 8 * kRing + 8 * kMaxProblems;
+  auto k = a.counts ? grouped_kernel<true> : grouped_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) {
+    k<<<grid, kThreads, smem, o.stream>>>(a);
+    e = cudaGetLastError();
+  }
+  return o.end(e);
+}
+
+}  // extern "C"

@@ -98,6 +98,10 @@ struct Op {
 
   tp_status begin(tp_ctx* c, const tp_exec* e, std::initializer_list<tp_partition*> outputs,
                   std::initializer_list<const tp_tensor*> inputs);
+  tp_status begin_lists(tp_ctx* c, const tp_exec* e, const std::vector<tp_partition*>& outputs,
+                        const std::vector<tp_tensor>& inputs);
+  tp_status begin_impl(tp_ctx* c, const tp_exec* e, const std::vector<tp_partition*>& outputs,
+                       const std::vector<const tp_tensor*>& inputs);
   tp_status end(cudaError_t launch_err);
   // Undo begin() after a failure that launched nothing (keeps the detail).
   void abort();

@@ -105,6 +105,18 @@ tp_status queue_counter(tp_ctx* ctx, cudaStream_t stream, unsigned** out) {
 
 tp_status Op::begin(tp_ctx* c, const tp_exec* e, std::initializer_list<tp_partition*> outputs,
                     std::initializer_list<const tp_tensor*> inputs) {
+  return begin_impl(c, e, std::vector<tp_partition*>(outputs), std::vector<const tp_tensor*>(inputs));
+}
+
+tp_status Op::begin_lists(tp_ctx* c, const tp_exec* e, const std::vector<tp_partition*>& outputs,
+                          const std::vector<tp_tensor>& inputs) {
+  std::vector<const tp_tensor*> in;
+  for (const auto& t : inputs) in.push_back(&t);
+  return begin_impl(c, e, outputs, in);
+}
+
+tp_status Op::begin_impl(tp_ctx* c, const tp_exec* e, const std::vector<tp_partition*>& outputs,
+                         const std::vector<const tp_tensor*>& inputs) {
   ctx = c;
   ex = e;
   if (!ctx) return fail(TP_ERR_INVALID, "null context");
