@@ -436,7 +436,68 @@ def secondary_rows(tp, ctx, dev, stream, peaks):
     del a, bt, c, qa, qbt
     torch.cuda.empty_cache()
     rows["grouped_64"] = grouped_row(tp, ctx, dev, stream, peaks)
+    rows["decode_64"] = decode_row(tp, ctx, dev, stream, peaks)
     return rows
+
+
+def decode_row(tp, ctx, dev, stream, peaks):
+    """Batch-1 decode-shaped chain, 64 layers (d 5120, QKV 10240, gate/up
+    2 x 25600, down 25600 -> 5120), bf16 N(0, 0.02) weights: fused kernels
+    replayed as one CUDA graph against one synced call per step."""
+    import torch
+
+    d, nq, ni, L = 5120, 10240, 25600, 64
+    g = torch.Generator(device=dev)
+    layers = []
+    for i in range(L):
+        g.manual_seed(100 + i)
+        layers.append(tuple((torch.randn(r, k, device=dev, generator=g) * 0.02).to(torch.bfloat16)
+                            for r, k in ((nq, d), (2 * ni, d), (d, ni))))
+    wbytes = sum(w.numel() * 2 for lay in layers for w in lay)
+    g.manual_seed(11)
+    h0 = torch.randn(d, device=dev, generator=g)
+    h = h0.clone()
+    ch = tp.DecodeChain(ctx, h, layers)
+    gr = tp.tp_graph_begin(ctx, stream)
+    ch.record_fused(tp.make_exec(mode=tp.CAPTURE, stream=stream))
+    tp.tp_graph_end(gr)
+    ex = tp.make_exec(stream=stream)
+    tp.tp_graph_replay(gr, ex)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ts = []
+    for _ in range(5):
+        e0.record(stream)
+        tp.tp_graph_replay(gr, ex)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms_graph = min(ts)
+    tp.tp_graph_destroy(gr)
+
+    def wall(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            t = (time.perf_counter() - t0) * 1e3
+            best = t if best is None else min(best, t)
+        return best
+
+    sync_ex = tp.make_exec(stream=stream)
+    ms_plain = wall(lambda: ch.record_unfused(sync_ex))
+    ms_fused_sync = wall(lambda: ch.record_fused(sync_ex))
+    ch.close()
+    roof = wbytes / (peaks["hbm_gbs"] * 1e9) * 1e3
+    del layers
+    torch.cuda.empty_cache()
+    return {"ms_graph_fused": ms_graph, "ms_plain_sync_unfused": ms_plain, "ms_sync_fused": ms_fused_sync,
+            "speedup_vs_plain": ms_plain / ms_graph, "weight_gb": wbytes / 1e9,
+            "weight_gbs_graph": wbytes / (ms_graph * 1e-3) / 1e9, "roofline_ms": roof,
+            "frac_of_roofline": roof / ms_graph, "launches_graph": 2 * L, "launches_plain": 6 * L,
+            "note": "plain = 6 kernels per layer, each launched and synchronised on its own (per-call sync)"}
 
 
 def grouped_row(tp, ctx, dev, stream, peaks):

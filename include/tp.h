@@ -306,6 +306,32 @@ tp_status tp_grouped_plan_destroy(tp_grouped_plan* plan);
  * back in input order (C_0's elements first). Errors: as tp_gemm. */
 tp_status tp_grouped_gemm(tp_ctx* ctx, tp_grouped_plan* plan, int32_t num_programs, const tp_exec* ex);
 
+/* --------------------------------------------------- decode-shaped chain */
+/* One layer of a batch-1 decode forward pass (§3.2, Listing 3: RMSNorm,
+ * matrix-vector products and a residual add, captured once and replayed),
+ * widened to a gated MLP. Vectors are contiguous FP32 rank-1 tensors;
+ * weights are BF16 [out, in] row-major with rows 16-byte aligned. Every
+ * output vector is a partition (rank 1); each row is written by one program.
+ *
+ * n = h / sqrt(mean(h^2) + eps) * gamma (gamma may be NULL: 1). */
+tp_status tp_rmsnorm(tp_ctx* ctx, tp_partition* n_out, const tp_tensor* h, const tp_tensor* gamma, float eps,
+                     const tp_exec* ex);
+/* y = W x (W [rows, k] bf16, x [k] fp32, y [rows] fp32, FP32 accumulation). */
+tp_status tp_gemv(tp_ctx* ctx, tp_partition* y, const tp_tensor* w, const tp_tensor* x, const tp_exec* ex);
+/* a = silu(g) * u for gu = [g; u] (gu has 2n entries, a has n). */
+tp_status tp_silu_mul(tp_ctx* ctx, tp_partition* a_out, const tp_tensor* gu, const tp_exec* ex);
+/* h <- h + d (the residual add; h is read and written by its own program). */
+tp_status tp_residual_add(tp_ctx* ctx, tp_partition* h, const tp_tensor* d, const tp_exec* ex);
+/* Fused: n = rmsnorm(h) (recomputed by every program), qkv = W_qkv n and
+ * a = silu(W_gu[:ni] n) * (W_gu[ni:] n), in one launch. Write counts index
+ * qkv's rows, then a's. */
+tp_status tp_decode_norm_qkv_gu(tp_ctx* ctx, tp_partition* qkv, tp_partition* a_out, const tp_tensor* h,
+                                const tp_tensor* gamma, const tp_tensor* w_qkv, const tp_tensor* w_gu, float eps,
+                                const tp_exec* ex);
+/* Fused: h <- h + W_down a, in one launch. */
+tp_status tp_decode_down_residual(tp_ctx* ctx, tp_partition* h, const tp_tensor* w_down, const tp_tensor* a_in,
+                                  const tp_exec* ex);
+
 /* ------------------------------------------------- allocation-free entry */
 /* Queue-mapped z = alpha * x + y that needs no context and allocates nothing.
  * The paper has no counterpart; it exists for callers that cannot call

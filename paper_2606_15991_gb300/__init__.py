@@ -26,6 +26,8 @@ __all__ = [
     "tp_map_axpy", "tp_map_gelu_mul", "tp_map_scale", "tp_map_add_accum", "tp_gemm",
     "tp_amax", "tp_quantize_fp8", "tp_gemm_fp8",
     "tp_grouped_plan_create", "tp_grouped_plan_info", "tp_grouped_plan_destroy", "tp_grouped_gemm",
+    "tp_rmsnorm", "tp_gemv", "tp_silu_mul", "tp_residual_add", "tp_decode_norm_qkv_gu",
+    "tp_decode_down_residual", "DecodeChain",
 ]
 
 _DTYPES = {
@@ -318,3 +320,74 @@ def tp_grouped_plan_destroy(plan: GroupedPlan) -> None:
 def tp_grouped_gemm(ctx, plan: GroupedPlan, num_programs: int = 0, ex: tp_exec | None = None) -> None:
     """All problems of the plan in one persistent launch over a device tile queue."""
     call("tp_grouped_gemm", ctx.handle, plan.handle, int(num_programs), _ex(ex))
+
+
+def _opt(t):
+    return ctypes.byref(tensor_desc(t)) if t is not None else None
+
+
+def tp_rmsnorm(ctx, n_out: Partition, h, gamma=None, eps: float = 1e-6, ex: tp_exec | None = None) -> None:
+    call("tp_rmsnorm", ctx.handle, n_out.handle, ctypes.byref(tensor_desc(h)), _opt(gamma), float(eps), _ex(ex))
+
+
+def tp_gemv(ctx, y: Partition, w, x, ex: tp_exec | None = None) -> None:
+    call("tp_gemv", ctx.handle, y.handle, ctypes.byref(tensor_desc(w)), ctypes.byref(tensor_desc(x)), _ex(ex))
+
+
+def tp_silu_mul(ctx, a_out: Partition, gu, ex: tp_exec | None = None) -> None:
+    call("tp_silu_mul", ctx.handle, a_out.handle, ctypes.byref(tensor_desc(gu)), _ex(ex))
+
+
+def tp_residual_add(ctx, h: Partition, d, ex: tp_exec | None = None) -> None:
+    call("tp_residual_add", ctx.handle, h.handle, ctypes.byref(tensor_desc(d)), _ex(ex))
+
+
+def tp_decode_norm_qkv_gu(ctx, qkv: Partition, a_out: Partition, h, gamma, w_qkv, w_gu, eps: float = 1e-6,
+                          ex: tp_exec | None = None) -> None:
+    call("tp_decode_norm_qkv_gu", ctx.handle, qkv.handle, a_out.handle, ctypes.byref(tensor_desc(h)),
+         _opt(gamma), ctypes.byref(tensor_desc(w_qkv)), ctypes.byref(tensor_desc(w_gu)), float(eps), _ex(ex))
+
+
+def tp_decode_down_residual(ctx, h: Partition, w_down, a_in, ex: tp_exec | None = None) -> None:
+    call("tp_decode_down_residual", ctx.handle, h.handle, ctypes.byref(tensor_desc(w_down)),
+         ctypes.byref(tensor_desc(a_in)), _ex(ex))
+
+
+class DecodeChain:
+    """Buffers and partitions for a decode-shaped chain of layers
+    [(W_qkv, W_gu, W_down), ...] acting on the residual stream h (fp32 [d])."""
+
+    def __init__(self, ctx, h, layers, gamma=None, eps: float = 1e-6):
+        self.ctx, self.h, self.layers, self.gamma, self.eps = ctx, h, layers, gamma, eps
+        d = h.shape[0]
+        nq = layers[0][0].shape[0]
+        ni = layers[0][1].shape[0] // 2
+        dev = h.device
+        self.n = torch.empty(d, device=dev)
+        self.qkv = torch.empty(nq, device=dev)
+        self.gu = torch.empty(2 * ni, device=dev)
+        self.a = torch.empty(ni, device=dev)
+        self.dd = torch.empty(d, device=dev)
+        self.p = {k: tp_partition_create(ctx, t, (t.shape[0],)) for k, t in
+                  (("h", h), ("n", self.n), ("qkv", self.qkv), ("gu", self.gu), ("a", self.a), ("dd", self.dd))}
+
+    def record_fused(self, ex: tp_exec | None = None) -> None:
+        """Two launches per layer: norm+QKV+gate/up+SiLU*mul, down+residual."""
+        for w_qkv, w_gu, w_down in self.layers:
+            tp_decode_norm_qkv_gu(self.ctx, self.p["qkv"], self.p["a"], self.h, self.gamma, w_qkv, w_gu,
+                                  self.eps, ex)
+            tp_decode_down_residual(self.ctx, self.p["h"], w_down, self.a, ex)
+
+    def record_unfused(self, ex: tp_exec | None = None) -> None:
+        """Six launches per layer, one per step of the chain."""
+        for w_qkv, w_gu, w_down in self.layers:
+            tp_rmsnorm(self.ctx, self.p["n"], self.h, self.gamma, self.eps, ex)
+            tp_gemv(self.ctx, self.p["qkv"], w_qkv, self.n, ex)
+            tp_gemv(self.ctx, self.p["gu"], w_gu, self.n, ex)
+            tp_silu_mul(self.ctx, self.p["a"], self.gu, ex)
+            tp_gemv(self.ctx, self.p["dd"], w_down, self.a, ex)
+            tp_residual_add(self.ctx, self.p["h"], self.dd, ex)
+
+    def close(self) -> None:
+        for p in self.p.values():
+            tp_partition_destroy(p)

@@ -107,6 +107,12 @@ _PROTOS = {
     "tp_grouped_plan_info": [_VP, _PI64, _PI32],
     "tp_grouped_plan_destroy": [_VP],
     "tp_grouped_gemm": [_VP, _VP, _I32, _PE],
+    "tp_rmsnorm": [_VP, _VP, _PT, _PT, ctypes.c_float, _PE],
+    "tp_gemv": [_VP, _VP, _PT, _PT, _PE],
+    "tp_silu_mul": [_VP, _VP, _PT, _PE],
+    "tp_residual_add": [_VP, _VP, _PT, _PE],
+    "tp_decode_norm_qkv_gu": [_VP, _VP, _VP, _PT, _PT, _PT, _PT, ctypes.c_float, _PE],
+    "tp_decode_down_residual": [_VP, _VP, _PT, _PT, _PE],
     "tp_map_axpy_queue_noalloc": [_VP, _VP, _VP, _I32, _I64, _I64, _I32, ctypes.c_float, _VP],
 }
 _RESTYPES = {"tp_error_string": ctypes.c_char_p, "tp_last_error_detail": ctypes.c_char_p}

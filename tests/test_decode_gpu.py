@@ -1,0 +1,161 @@
+"""GPU parity of the decode-shaped chain (RMSNorm -> QKV GEMV -> gate/up GEMV
+-> SiLU*mul -> down GEMV -> residual) against the FP64 oracle, fused and
+unfused, plus graph replay of the 64-layer chain at the full dimensions."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2606_15991_gb300 as tp
+import synth
+from oracle import decode as odecode
+from oracle import gemm as ogemm
+from oracle import partition as opart
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+def _w(rows, k, seed):
+    return synth.to_bf16(synth.normal(rows * k, seed, std=0.02)).reshape(rows, k).cuda()
+
+
+def _layers(d, nq, ni, n, seed=0):
+    return [(_w(nq, d, seed + 3 * i), _w(2 * ni, d, seed + 3 * i + 1), _w(d, ni, seed + 3 * i + 2))
+            for i in range(n)]
+
+
+def _vec(n, seed, std=1.0):
+    return torch.from_numpy(synth.normal(n, seed, std=std)).cuda()
+
+
+def _f(t):
+    return t.double().cpu().numpy()
+
+
+def _gemv_bound(w, x):
+    """Summation bound of the kernel: chains of about k/64 + 12 fp32 adds."""
+    k = w.shape[1]
+    return (k / 64 + 12) * U32 * (np.abs(_f(w)) @ np.abs(_f(x))) + 1e-30
+
+
+@pytest.mark.parametrize("rows,k", [(10240, 5120), (5120, 25600), (1, 8), (77, 1000), (300, 4104)])
+def test_gemv_within_summation_bound(ctx, rows, k):
+    w = _w(rows, k, rows + k)
+    x = _vec(k, 5)
+    y = torch.full((rows,), float("nan"), device="cuda")
+    p = tp.tp_partition_create(ctx, y, (rows,))
+    counts = torch.zeros(rows, dtype=torch.int32, device="cuda")
+    owner = torch.full((rows,), -1, dtype=torch.int32, device="cuda")
+    tp.tp_gemv(ctx, p, w, x, tp.make_exec(write_counts=counts, write_owner=owner))
+    ref = _f(w) @ _f(x)
+    assert np.all(np.abs(_f(y) - ref) <= _gemv_bound(w, x))
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    tp.tp_partition_destroy(p)
+
+
+@pytest.mark.parametrize("d", [1, 100, 5120])
+def test_rmsnorm_silu_residual(ctx, d):
+    h = _vec(d, 1, std=3.0)
+    gamma = _vec(d, 2)
+    n = torch.empty(d, device="cuda")
+    p = tp.tp_partition_create(ctx, n, (d,))
+    tp.tp_rmsnorm(ctx, p, h, gamma, 1e-6)
+    ref = odecode.rmsnorm(h.cpu(), gamma.cpu(), 1e-6)
+    assert np.all(np.abs(_f(n) - ref) <= (d / 256 + 8) * U32 * np.abs(ref) + 1e-30)
+    tp.tp_rmsnorm(ctx, p, h, None, 1e-6)
+    assert np.allclose(_f(n), odecode.rmsnorm(h.cpu(), None, 1e-6), rtol=(d / 256 + 8) * U32, atol=0)
+    tp.tp_partition_destroy(p)
+    gu = _vec(2 * d, 3, std=4.0)
+    a = torch.empty(d, device="cuda")
+    p = tp.tp_partition_create(ctx, a, (d,))
+    tp.tp_silu_mul(ctx, p, gu)
+    g = gu.cpu().double().numpy()
+    ref = odecode.silu(g[:d]) * g[d:]
+    assert np.all(np.abs(_f(a) - ref) <= 1e-5 * np.abs(ref) + 1e-30)
+    tp.tp_partition_destroy(p)
+    hh = h.clone()
+    p = tp.tp_partition_create(ctx, hh, (d,))
+    dd = _vec(d, 4)
+    tp.tp_residual_add(ctx, p, dd)
+    assert np.all(np.abs(_f(hh) - (_f(h) + _f(dd))) <= U32 * np.abs(_f(h) + _f(dd)))
+    tp.tp_partition_destroy(p)
+
+
+@pytest.mark.parametrize("fused", [True, False])
+def test_small_chain_against_oracle(ctx, fused):
+    d, nq, ni, L = 256, 512, 1024, 8
+    layers = _layers(d, nq, ni, L, seed=10)
+    h0 = _vec(d, 7)
+    h = h0.clone()
+    ch = tp.DecodeChain(ctx, h, layers)
+    (ch.record_fused if fused else ch.record_unfused)()
+    href, qref = odecode.chain(h0.cpu(), [(a.cpu(), b.cpu(), c.cpu()) for a, b, c in layers])
+    assert ogemm.rel_frobenius(h.cpu(), href) <= 1e-4
+    assert ogemm.rel_frobenius(ch.qkv.cpu(), qref) <= 1e-4
+    ch.close()
+
+
+def test_fused_equals_oracle_full_dims_two_layers(ctx):
+    d, nq, ni = 5120, 10240, 25600
+    layers = _layers(d, nq, ni, 2, seed=20)
+    h0 = _vec(d, 8)
+    h = h0.clone()
+    ch = tp.DecodeChain(ctx, h, layers)
+    counts = torch.zeros(nq + ni, dtype=torch.int32, device="cuda")
+    owner = torch.full((nq + ni,), -1, dtype=torch.int32, device="cuda")
+    ex = tp.make_exec(write_counts=counts, write_owner=owner)
+    tp.tp_decode_norm_qkv_gu(ctx, ch.p["qkv"], ch.p["a"], h, None, layers[0][0], layers[0][1], 1e-6, ex)
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    tp.tp_decode_down_residual(ctx, ch.p["h"], layers[0][2], ch.a)
+    w1 = layers[1]
+    tp.tp_decode_norm_qkv_gu(ctx, ch.p["qkv"], ch.p["a"], h, None, w1[0], w1[1], 1e-6)
+    tp.tp_decode_down_residual(ctx, ch.p["h"], w1[2], ch.a)
+    href, qref = odecode.chain(h0.cpu(), [(a.cpu(), b.cpu(), c.cpu()) for a, b, c in layers])
+    assert ogemm.rel_frobenius(h.cpu(), href) <= 1e-4
+    assert ogemm.rel_frobenius(ch.qkv.cpu(), qref) <= 1e-4
+    ch.close()
+
+
+def test_zero_down_projection_is_identity(ctx):
+    d, nq, ni = 5120, 10240, 25600
+    layers = _layers(d, nq, ni, 1, seed=30)
+    layers = [(layers[0][0], layers[0][1], torch.zeros_like(layers[0][2]))]
+    h0 = _vec(d, 9)
+    h = h0.clone()
+    ch = tp.DecodeChain(ctx, h, layers)
+    ch.record_fused()
+    assert torch.equal(h, h0)
+    ch.close()
+
+
+def test_64_layer_graph_replay_matches_eager(ctx):
+    """The full decode-shaped chain (d = 5120, QKV 10240, gate/up 2 x 25600,
+    64 layers of bf16 N(0, 0.02) weights, 57 GB): the captured graph replayed
+    gives exactly the eager result, on every replay."""
+    d, nq, ni, L = 5120, 10240, 25600, 64
+    g = torch.Generator(device="cuda")
+    layers = []
+    for i in range(L):
+        g.manual_seed(100 + i)
+        layers.append(tuple((torch.randn(r, k, device="cuda", generator=g) * 0.02).to(torch.bfloat16)
+                            for r, k in ((nq, d), (2 * ni, d), (d, ni))))
+    h0 = _vec(d, 11)
+    h = h0.clone()
+    ch = tp.DecodeChain(ctx, h, layers)
+    ch.record_fused()
+    eager = h.clone()
+    assert torch.isfinite(eager).all()
+    s = torch.cuda.Stream()
+    gr = tp.tp_graph_begin(ctx, s)
+    ch.record_fused(tp.make_exec(mode=tp.CAPTURE, stream=s))
+    tp.tp_graph_end(gr)
+    for _ in range(3):
+        h.copy_(h0)
+        torch.cuda.synchronize()
+        tp.tp_graph_replay(gr, tp.make_exec(stream=s))
+        assert torch.equal(h, eager)
+    tp.tp_graph_destroy(gr)
+    ch.close()
+    del layers
+    torch.cuda.empty_cache()
