@@ -570,6 +570,55 @@ def grouped_row(tp, ctx, dev, stream, peaks):
             "note": "roofline = sum over problems of max(flops / bf16 peak, bytes / HBM peak), measured peaks"}
 
 
+def run_proposer(args):
+    """The learned-proposer experiment: ~20k autotuner measurements (625
+    shapes x 32 configs, BF16 and FP8) for training, 2000 held-out shapes tuned
+    exhaustively for evaluation; prints one JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_2606_15991_gb300 import build as _build
+
+    _build.build()
+    import paper_2606_15991_gb300 as tp
+    from paper_2606_15991_gb300 import proposer
+
+    ctx = tp.tp_ctx_create(0)
+    log = (lambda m: print(m, file=sys.stderr, flush=True))
+    train_shapes = proposer.sample_shapes(args.train_shapes, seed=1)
+    test_shapes = proposer.sample_shapes(args.test_shapes, seed=2)
+    t0 = time.perf_counter()
+    X, T, V, TF = proposer.collect(ctx, train_shapes, log=log)
+    t_collect = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    mlp, hist = proposer.train(ctx, X, T, V, epochs=args.epochs, batch=256, lr=3e-3, log=log)
+    t_train = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    Xt, Tt, Vt, TFt = proposer.collect(ctx, test_shapes, log=log)
+    t_exh = (time.perf_counter() - t0) / len(test_shapes)
+    dflt = proposer.default_config(T, V)
+    r = proposer.evaluate(mlp, Xt, TFt, dflt)
+    t0 = time.perf_counter()
+    for m, n, k, dt in test_shapes[:200]:
+        tp.tp_propose(ctx, mlp, m, n, k, dt, min_score=-1e9)
+    t_prop = (time.perf_counter() - t0) / min(200, len(test_shapes))
+    big = np.array([m * n * k >= 2 ** 33 for m, n, k, _ in test_shapes])
+    S = proposer.scores(mlp, Xt)
+    reg = 1 - TFt[np.arange(len(TFt)), S.argmax(1)] / TFt.max(1)
+    reg_d = 1 - TFt[:, dflt] / TFt.max(1)
+    space = tp.tp_autotune_space("bf16")
+    print(json.dumps({
+        "case": "learned tile proposer", "train_shapes": len(train_shapes),
+        "train_measurements": int(V.sum()), "test_shapes": len(test_shapes), "configs": int(T.shape[1]),
+        **r, "default_config": {n: getattr(space[dflt], n) for n in ("bm", "bn", "stages", "group_m")},
+        "large_shapes": int(big.sum()),
+        "large_mean_regret": float(reg[big].mean()) if big.any() else None,
+        "large_mean_regret_default": float(reg_d[big].mean()) if big.any() else None,
+        "ms_exhaustive_per_shape": t_exh * 1e3, "ms_propose_per_shape": t_prop * 1e3,
+        "tuning_time_saved_x": t_exh / t_prop, "loss_first_last": [hist[0], hist[-1]],
+        "s_collect_train": t_collect, "s_train": t_train}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -580,8 +629,15 @@ def main():
     ap.add_argument("--skip-rows", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--case", default="maps", choices=["maps", "proposer"],
+                    help="maps: the benchmark step (default); proposer: the learned-proposer experiment")
+    ap.add_argument("--train-shapes", type=int, default=625)
+    ap.add_argument("--test-shapes", type=int, default=2000)
+    ap.add_argument("--epochs", type=int, default=600)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case == "proposer":
+        run_proposer(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

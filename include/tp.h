@@ -332,6 +332,70 @@ tp_status tp_decode_norm_qkv_gu(tp_ctx* ctx, tp_partition* qkv, tp_partition* a_
 tp_status tp_decode_down_residual(tp_ctx* ctx, tp_partition* h, const tp_tensor* w_down, const tp_tensor* a_in,
                                   const tp_exec* ex);
 
+/* ------------------------------------------------------------ autotuner */
+/* Tile-configuration search for the tensor-core GEMM (§5.1 tunes tile shapes
+ * once per size). The space (same order on every call; index i is the MLP
+ * proposer's output i): tile rows {128 (one CTA), 256 (CTA pair)} x tile
+ * columns {64, 128, 192, 256} x stages {3, max} x raster bands {1, 8}.
+ * Writes up to `cap` configs to `out` (may be NULL) and the size to *count. */
+tp_status tp_autotune_space(int32_t dtype, tp_gemm_config* out, int32_t cap, int32_t* count);
+/* Times every config of the space on an M x N x K problem of `dtype`
+ * (TP_BF16 or TP_F8E4M3; K * element size a multiple of 16) held in a device
+ * workspace the context owns (grown with cudaMalloc: not during capture,
+ * TP_ERR_CAPTURE), `reps` back-to-back launches per config timed with CUDA
+ * events (0 = 3). Returns the fastest config (ties within 1% keep the earlier
+ * one), optionally the TFLOP/s of every config (space order) and the best
+ * TFLOP/s, and caches the winner for (M, N, K, dtype). */
+tp_status tp_autotune(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, int32_t reps,
+                      tp_gemm_config* best, float* tflops_per_config, float* best_tflops);
+/* Cached winner for (M, N, K, dtype): *found = 1 and *out filled, else 0. */
+tp_status tp_autotune_lookup(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, tp_gemm_config* out,
+                             int32_t* found);
+/* Persist / restore the cache (text, "tp-autotune-cache v1"). */
+tp_status tp_autotune_save(tp_ctx* ctx, const char* path);
+tp_status tp_autotune_load(tp_ctx* ctx, const char* path);
+
+/* ------------------------------------------------- learned tile proposer */
+/* A 3-layer ReLU MLP (in -> hidden -> hidden -> out) trained on the GPU by
+ * the library's own kernels. Parameters are one fp32 buffer
+ * [W1 (hidden x in), b1, W2 (hidden x hidden), b2, W3 (out x hidden), b3],
+ * matrices row-major [out, in]. Loss: sum V (y - T)^2 / max(1, sum V) over a
+ * batch (V masks invalid entries); optimiser: Adam (0.9, 0.999, 1e-8) with
+ * bias correction. X, T, V, Y, loss and grads are device pointers; X is
+ * [batch, in], T, V, Y are [batch, out]. The tp_mlp object owns its
+ * parameters, optimiser state and scratch; calls on one tp_mlp must be
+ * ordered on one stream (tp_exec.stream; SYNC waits, ASYNC returns). */
+typedef struct tp_mlp tp_mlp;
+tp_status tp_mlp_create(tp_ctx* ctx, int32_t in, int32_t hidden, int32_t out, int32_t max_batch,
+                        const float* init_params, tp_mlp** mlp);
+tp_status tp_mlp_destroy(tp_mlp* mlp);
+tp_status tp_mlp_num_params(const tp_mlp* mlp, int64_t* count);
+tp_status tp_mlp_get_params(const tp_mlp* mlp, float* host_out);
+/* Sets the parameters (host array) and resets the optimiser state. */
+tp_status tp_mlp_set_params(tp_mlp* mlp, const float* host_in);
+tp_status tp_mlp_forward(tp_mlp* mlp, const float* X, int32_t batch, float* Y, const tp_exec* ex);
+/* Forward, loss (*loss, may be NULL) and gradient of every parameter
+ * (copied to grads when not NULL). */
+tp_status tp_mlp_loss_grad(tp_mlp* mlp, const float* X, const float* T, const float* V, int32_t batch,
+                           float* loss, float* grads, const tp_exec* ex);
+/* tp_mlp_loss_grad followed by one Adam step at learning rate lr. */
+tp_status tp_mlp_train_step(tp_mlp* mlp, const float* X, const float* T, const float* V, int32_t batch,
+                            float lr, float* loss, const tp_exec* ex);
+tp_status tp_mlp_save(const tp_mlp* mlp, const char* path);
+tp_status tp_mlp_load(tp_mlp* mlp, const char* path);
+/* Proposer features of a shape: [log2 M, log2 N, log2 K, BF16?, FP8?] (host). */
+tp_status tp_mlp_features(int64_t M, int64_t N, int64_t K, int32_t dtype, float* out);
+/* Training targets of one autotuner table: target_i = tflops_i / max tflops,
+ * mask_i = 1 where config i ran (tflops_i > 0) (host arrays of `count`). */
+tp_status tp_mlp_targets(const float* tflops, int32_t count, float* target, float* mask);
+/* Proposes a config for (M, N, K, dtype): the MLP's arg-max over the
+ * autotuner's space (ties: lowest index). Falls back to the exhaustive
+ * autotuner (cached) when the best score is below min_score or a dimension
+ * exceeds 16384 (outside the trained range); *used_fallback tells which. A
+ * proposal only selects among configs that compute the same C. */
+tp_status tp_propose(tp_ctx* ctx, tp_mlp* mlp, int64_t M, int64_t N, int64_t K, int32_t dtype, float min_score,
+                     tp_gemm_config* out, float* score, int32_t* used_fallback);
+
 /* ------------------------------------------------- allocation-free entry */
 /* Queue-mapped z = alpha * x + y that needs no context and allocates nothing.
  * The paper has no counterpart; it exists for callers that cannot call

@@ -28,6 +28,10 @@ __all__ = [
     "tp_grouped_plan_create", "tp_grouped_plan_info", "tp_grouped_plan_destroy", "tp_grouped_gemm",
     "tp_rmsnorm", "tp_gemv", "tp_silu_mul", "tp_residual_add", "tp_decode_norm_qkv_gu",
     "tp_decode_down_residual", "DecodeChain",
+    "tp_autotune_space", "tp_autotune", "tp_autotune_lookup", "tp_autotune_save", "tp_autotune_load",
+    "tp_mlp_create", "tp_mlp_destroy", "tp_mlp_num_params", "tp_mlp_get_params", "tp_mlp_set_params",
+    "tp_mlp_forward", "tp_mlp_loss_grad", "tp_mlp_train_step", "tp_mlp_save", "tp_mlp_load",
+    "tp_mlp_features", "tp_mlp_targets", "tp_propose",
 ]
 
 _DTYPES = {
@@ -391,3 +395,137 @@ class DecodeChain:
     def close(self) -> None:
         for p in self.p.values():
             tp_partition_destroy(p)
+
+
+_DT_CODE = {"bf16": _lib.BF16, "fp8": _lib.F8E4M3}
+
+
+def _cfg_dict(c: tp_gemm_config) -> dict:
+    return {n: getattr(c, n) for n, _ in tp_gemm_config._fields_}
+
+
+def tp_autotune_space(dtype: str = "bf16") -> list:
+    """The autotuner's config space (index i = proposer output i)."""
+    n = ctypes.c_int32()
+    call("tp_autotune_space", _DT_CODE[dtype], None, 0, ctypes.byref(n))
+    arr = (tp_gemm_config * n.value)()
+    call("tp_autotune_space", _DT_CODE[dtype], arr, n.value, ctypes.byref(n))
+    return [arr[i] for i in range(n.value)]
+
+
+def tp_autotune(ctx, M: int, N: int, K: int, dtype: str = "bf16", reps: int = 0):
+    """Exhaustive search: returns (best config, [TFLOP/s per config], best TFLOP/s)."""
+    cnt = len(tp_autotune_space(dtype))
+    best = tp_gemm_config()
+    table = (ctypes.c_float * cnt)()
+    bt = ctypes.c_float()
+    call("tp_autotune", ctx.handle, int(M), int(N), int(K), _DT_CODE[dtype], int(reps), ctypes.byref(best),
+         table, ctypes.byref(bt))
+    return best, list(table), bt.value
+
+
+def tp_autotune_lookup(ctx, M: int, N: int, K: int, dtype: str = "bf16"):
+    out = tp_gemm_config()
+    found = ctypes.c_int32()
+    call("tp_autotune_lookup", ctx.handle, int(M), int(N), int(K), _DT_CODE[dtype], ctypes.byref(out),
+         ctypes.byref(found))
+    return out if found.value else None
+
+
+def tp_autotune_save(ctx, path: str) -> None:
+    call("tp_autotune_save", ctx.handle, path.encode())
+
+
+def tp_autotune_load(ctx, path: str) -> None:
+    call("tp_autotune_load", ctx.handle, path.encode())
+
+
+class MLP:
+    def __init__(self, handle, shape):
+        self.handle = ctypes.c_void_p(handle)
+        self.shape = shape
+
+
+def tp_mlp_create(ctx, in_features: int, hidden: int, out: int, max_batch: int, init_params) -> MLP:
+    """init_params: float32 numpy array of the flat parameter layout."""
+    import numpy as np
+
+    p = np.ascontiguousarray(init_params, dtype=np.float32)
+    h = ctypes.c_void_p()
+    call("tp_mlp_create", ctx.handle, in_features, hidden, out, max_batch, p.ctypes.data_as(ctypes.c_void_p),
+         ctypes.byref(h))
+    return MLP(h.value, (in_features, hidden, out))
+
+
+def tp_mlp_destroy(m: MLP) -> None:
+    if m.handle:
+        call("tp_mlp_destroy", m.handle)
+        m.handle = ctypes.c_void_p()
+
+
+def tp_mlp_num_params(m: MLP) -> int:
+    n = ctypes.c_int64()
+    call("tp_mlp_num_params", m.handle, ctypes.byref(n))
+    return n.value
+
+
+def tp_mlp_get_params(m: MLP):
+    import numpy as np
+
+    out = np.empty(tp_mlp_num_params(m), dtype=np.float32)
+    call("tp_mlp_get_params", m.handle, out.ctypes.data_as(ctypes.c_void_p))
+    return out
+
+
+def tp_mlp_set_params(m: MLP, params) -> None:
+    import numpy as np
+
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    call("tp_mlp_set_params", m.handle, p.ctypes.data_as(ctypes.c_void_p))
+
+
+def tp_mlp_forward(m: MLP, X, Y, ex: tp_exec | None = None) -> None:
+    """Y[batch, out] = MLP(X[batch, in]) (float32 CUDA tensors)."""
+    call("tp_mlp_forward", m.handle, _dptr(X), X.shape[0], _dptr(Y), _ex(ex))
+
+
+def tp_mlp_loss_grad(m: MLP, X, T, V, loss=None, grads=None, ex: tp_exec | None = None) -> None:
+    call("tp_mlp_loss_grad", m.handle, _dptr(X), _dptr(T), _dptr(V), X.shape[0],
+         _dptr(loss) if loss is not None else None, _dptr(grads) if grads is not None else None, _ex(ex))
+
+
+def tp_mlp_train_step(m: MLP, X, T, V, lr: float, loss=None, ex: tp_exec | None = None) -> None:
+    call("tp_mlp_train_step", m.handle, _dptr(X), _dptr(T), _dptr(V), X.shape[0], float(lr),
+         _dptr(loss) if loss is not None else None, _ex(ex))
+
+
+def tp_mlp_save(m: MLP, path: str) -> None:
+    call("tp_mlp_save", m.handle, path.encode())
+
+
+def tp_mlp_load(m: MLP, path: str) -> None:
+    call("tp_mlp_load", m.handle, path.encode())
+
+
+def tp_mlp_features(M: int, N: int, K: int, dtype: str = "bf16"):
+    out = (ctypes.c_float * 5)()
+    call("tp_mlp_features", int(M), int(N), int(K), _DT_CODE[dtype], out)
+    return list(out)
+
+
+def tp_mlp_targets(tflops):
+    n = len(tflops)
+    t = (ctypes.c_float * n)(*tflops)
+    tgt, mask = (ctypes.c_float * n)(), (ctypes.c_float * n)()
+    call("tp_mlp_targets", t, n, tgt, mask)
+    return list(tgt), list(mask)
+
+
+def tp_propose(ctx, m: MLP, M: int, N: int, K: int, dtype: str = "bf16", min_score: float = 0.0):
+    """Returns (config, score, used_fallback)."""
+    out = tp_gemm_config()
+    score = ctypes.c_float()
+    fb = ctypes.c_int32()
+    call("tp_propose", ctx.handle, m.handle, int(M), int(N), int(K), _DT_CODE[dtype], float(min_score),
+         ctypes.byref(out), ctypes.byref(score), ctypes.byref(fb))
+    return out, score.value, bool(fb.value)

@@ -113,6 +113,24 @@ _PROTOS = {
     "tp_residual_add": [_VP, _VP, _PT, _PE],
     "tp_decode_norm_qkv_gu": [_VP, _VP, _VP, _PT, _PT, _PT, _PT, ctypes.c_float, _PE],
     "tp_decode_down_residual": [_VP, _VP, _PT, _PT, _PE],
+    "tp_autotune_space": [_I32, ctypes.POINTER(tp_gemm_config), _I32, _PI32],
+    "tp_autotune": [_VP, _I64, _I64, _I64, _I32, _I32, ctypes.POINTER(tp_gemm_config), _VP, _VP],
+    "tp_autotune_lookup": [_VP, _I64, _I64, _I64, _I32, ctypes.POINTER(tp_gemm_config), _PI32],
+    "tp_autotune_save": [_VP, ctypes.c_char_p],
+    "tp_autotune_load": [_VP, ctypes.c_char_p],
+    "tp_mlp_create": [_VP, _I32, _I32, _I32, _I32, _VP, _PP],
+    "tp_mlp_destroy": [_VP],
+    "tp_mlp_num_params": [_VP, _PI64],
+    "tp_mlp_get_params": [_VP, _VP],
+    "tp_mlp_set_params": [_VP, _VP],
+    "tp_mlp_forward": [_VP, _VP, _I32, _VP, _PE],
+    "tp_mlp_loss_grad": [_VP, _VP, _VP, _VP, _I32, _VP, _VP, _PE],
+    "tp_mlp_train_step": [_VP, _VP, _VP, _VP, _I32, ctypes.c_float, _VP, _PE],
+    "tp_mlp_save": [_VP, ctypes.c_char_p],
+    "tp_mlp_load": [_VP, ctypes.c_char_p],
+    "tp_mlp_features": [_I64, _I64, _I64, _I32, _VP],
+    "tp_mlp_targets": [_VP, _I32, _VP, _VP],
+    "tp_propose": [_VP, _VP, _I64, _I64, _I64, _I32, ctypes.c_float, ctypes.POINTER(tp_gemm_config), _VP, _PI32],
     "tp_map_axpy_queue_noalloc": [_VP, _VP, _VP, _I32, _I64, _I64, _I32, ctypes.c_float, _VP],
 }
 _RESTYPES = {"tp_error_string": ctypes.c_char_p, "tp_last_error_detail": ctypes.c_char_p}

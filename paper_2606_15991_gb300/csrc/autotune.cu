@@ -1,0 +1,288 @@
+// Exhaustive autotuner for the tensor-core GEMM (§5.1 tunes tile shapes once
+// per size; here the search is automatic). The config space enumerates tile
+// rows (128 on one CTA, 256 on a CTA pair), tile columns, pipeline depth and
+// raster band height; each config is timed with CUDA events on a device
+// workspace of the requested shape and the fastest wins (ties within 1% go to
+// the earlier, smaller config). Results are cached per (M, N, K, dtype) and
+// can be saved to / loaded from a versioned text file.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "tp_internal.h"
+
+namespace tp {
+namespace {
+
+struct TuneKey {
+  int64_t m, n, k;
+  int32_t dtype;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(m, n, k, dtype) < std::tie(o.m, o.n, o.k, o.dtype);
+  }
+};
+
+struct TuneState {
+  std::mutex mu;
+  std::map<TuneKey, std::pair<tp_gemm_config, float>> cache;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t stream = nullptr;
+};
+
+std::mutex g_states_mu;
+std::map<tp_ctx*, TuneState*> g_states;
+
+TuneState* state(tp_ctx* ctx) {
+  std::lock_guard<std::mutex> lk(g_states_mu);
+  auto& s = g_states[ctx];
+  if (!s) s = new TuneState();
+  return s;
+}
+
+std::vector<tp_gemm_config> space() {
+  std::vector<tp_gemm_config> v;
+  for (int bm : {128, 256})
+    for (int bn : {64, 128, 192, 256})
+      for (int stages : {3, 0})
+        for (int gm : {1, 8}) {
+          tp_gemm_config c{};
+          c.bm = bm;
+          c.bn = bn;
+          c.stages = stages;
+          c.group_m = gm;
+          v.push_back(c);
+        }
+  return v;
+}
+
+// Fills a workspace with finite values that exercise the tensor cores the
+// way real data does (a hash of the index, small magnitudes).
+__global__ void fill_kernel(uint16_t* p, int64_t n16, int fp8) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t h = (uint32_t)(i * 2654435761u) ^ (uint32_t)(i >> 13);
+    h ^= h >> 15;
+    h *= 0x2c1b3c6du;
+    h ^= h >> 12;
+    if (fp8) p[i] = (uint16_t)(h & 0x3737);         // two E4M3 codes of magnitude < 2
+    else p[i] = (uint16_t)(0x3c00 | (h & 0x807f));  // bf16, magnitude in [2^-7, 2^-6)
+  }
+}
+
+// Holds the stream for `ns` nanoseconds (bounded by the wall clock) so the
+// host can queue every timed launch before the first one starts: the events
+// then bracket back-to-back device execution, not host launch overhead.
+__global__ void delay_kernel(uint64_t ns) {
+  uint64_t t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  do {
+    __nanosleep(1000);
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  } while (t - t0 < ns);
+}
+
+tp_status ensure_ws(tp_ctx* ctx, TuneState* st, size_t bytes) {
+  if (st->ws_bytes >= bytes) return TP_OK;
+  if (st->ws) cudaFree(st->ws);
+  st->ws = nullptr;
+  st->ws_bytes = 0;
+  cudaError_t e = cudaMalloc(&st->ws, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune workspace");
+  st->ws_bytes = bytes;
+  fill_kernel<<<ctx->sm_count * 8, 256, 0, st->stream>>>(static_cast<uint16_t*>(st->ws), (int64_t)(bytes / 2), 0);
+  e = cudaStreamSynchronize(st->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune workspace fill");
+  return TP_OK;
+}
+
+}  // namespace
+}  // namespace tp
+
+using namespace tp;
+
+extern "C" {
+
+tp_status tp_autotune_space(int32_t dtype, tp_gemm_config* out, int32_t cap, int32_t* count) {
+  if (!count) return fail(TP_ERR_INVALID, "null count");
+  if (dtype != TP_BF16 && dtype != TP_F8E4M3) return fail(TP_ERR_UNSUPPORTED, "dtype must be BF16 or F8E4M3");
+  auto v = space();
+  *count = (int32_t)v.size();
+  if (out)
+    for (int i = 0; i < (int)v.size() && i < cap; ++i) out[i] = v[i];
+  return TP_OK;
+}
+
+tp_status tp_autotune(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, int32_t reps,
+                      tp_gemm_config* best, float* tflops_per_config, float* best_tflops) {
+  if (!ctx) return fail(TP_ERR_INVALID, "null context");
+  if (dtype != TP_BF16 && dtype != TP_F8E4M3) return fail(TP_ERR_UNSUPPORTED, "dtype must be BF16 or F8E4M3");
+  const int esize = dtype == TP_BF16 ? 2 : 1;
+  if (M < 1 || N < 1 || K < 1 || (K * esize) % 16) return fail(TP_ERR_SHAPE, "need M, N, K >= 1 and K*esize % 16 == 0");
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->capturing) return fail(TP_ERR_CAPTURE, "autotuning allocates and synchronises: not during capture");
+  }
+  TuneState* st = state(ctx);
+  std::lock_guard<std::mutex> lk(st->mu);
+  if (!st->stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&st->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune stream");
+  }
+  auto align = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t ab = align((size_t)M * K * esize), bb = align((size_t)N * K * esize), cb = align((size_t)M * N * 2);
+  tp_status s = ensure_ws(ctx, st, ab + bb + cb);
+  if (s != TP_OK) return s;
+  char* ws = static_cast<char*>(st->ws);
+  tp_tensor a{}, b{};
+  a.ptr = ws;
+  a.dtype = dtype;
+  a.rank = 2;
+  a.shape[0] = M;
+  a.shape[1] = K;
+  a.strides[0] = K;
+  a.strides[1] = 1;
+  b.ptr = ws + ab;  // stored N x K, viewed as K x N
+  b.dtype = dtype;
+  b.rank = 2;
+  b.shape[0] = K;
+  b.shape[1] = N;
+  b.strides[0] = 1;
+  b.strides[1] = K;
+  tp_exec ex{};
+  ex.stream = st->stream;
+  float* one = nullptr;  // fp8 scales: the context's scratch holds 1.0f at [0] and [1]
+  if (dtype == TP_F8E4M3) {
+    const float ones[2] = {1.f, 1.f};
+    cudaError_t e = cudaMemcpy(ctx->d_scratch, ones, sizeof(ones), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "fp8 unit scales");
+    one = ctx->d_scratch;
+  }
+  auto cfgs = space();
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const double flops = 2.0 * (double)M * (double)N * (double)K;
+  // enough launches that the timed span is well above event resolution
+  const double est_us = flops / 1.0e9;  // at 1 PFLOP/s
+  const int r = reps > 0 ? reps : (est_us > 2000 ? 2 : est_us > 200 ? 4 : 10);
+  int best_i = -1;
+  float best_tf = 0.f;
+  for (size_t i = 0; i < cfgs.size(); ++i) {
+    const tp_gemm_config& c = cfgs[i];
+    tp_partition part{};
+    part.ctx = ctx;
+    part.t.ptr = ws + ab + bb;
+    part.t.dtype = TP_BF16;
+    part.t.rank = 2;
+    part.t.shape[0] = M;
+    part.t.shape[1] = N;
+    part.t.strides[0] = N;
+    part.t.strides[1] = 1;
+    part.rank = 2;
+    part.shape[0] = M;
+    part.shape[1] = N;
+    part.tile[0] = c.bm;
+    part.tile[1] = c.bn;
+    part.grid[0] = (M + c.bm - 1) / c.bm;
+    part.grid[1] = (N + c.bn - 1) / c.bn;
+    part.num_tiles = part.grid[0] * part.grid[1];
+    const int64_t cap = (int64_t)ctx->sm_count * 128 / c.bm;
+    part.kind = TP_MAP_STRIDED;
+    part.num_programs = std::min<int64_t>(part.num_tiles, cap);
+    float tf = 0.f;
+    tp_status ls = launch_gemm_tc_impl(ctx, &part, &a, &b, &c, &ex, st->stream, esize, one, one);
+    if (ls == TP_OK) {
+      delay_kernel<<<1, 32, 0, st->stream>>>(20000ull + 30000ull * (uint64_t)r);
+      cudaEventRecord(e0, st->stream);
+      for (int j = 0; j < r && ls == TP_OK; ++j)
+        ls = launch_gemm_tc_impl(ctx, &part, &a, &b, &c, &ex, st->stream, esize, one, one);
+      cudaEventRecord(e1, st->stream);
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(e, "autotune timing");
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ls == TP_OK && ms > 0.f) tf = (float)(flops * r / (ms * 1e-3) / 1e12);
+    }
+    if (tflops_per_config) tflops_per_config[i] = tf;
+    if (tf > best_tf * 1.01f) {
+      best_tf = tf;
+      best_i = (int)i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  tp_status es = read_device_error(ctx);
+  if (es != TP_OK) return es;
+  if (best_i < 0) return fail(TP_ERR_CUDA, "no configuration ran");
+  st->cache[TuneKey{M, N, K, dtype}] = {cfgs[best_i], best_tf};
+  if (best) *best = cfgs[best_i];
+  if (best_tflops) *best_tflops = best_tf;
+  return TP_OK;
+}
+
+tp_status tp_autotune_lookup(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, tp_gemm_config* out,
+                             int32_t* found) {
+  if (!ctx || !found) return fail(TP_ERR_INVALID, "null argument");
+  TuneState* st = state(ctx);
+  std::lock_guard<std::mutex> lk(st->mu);
+  auto it = st->cache.find(TuneKey{M, N, K, dtype});
+  *found = it != st->cache.end();
+  if (*found && out) *out = it->second.first;
+  return TP_OK;
+}
+
+tp_status tp_autotune_save(tp_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(TP_ERR_INVALID, "null argument");
+  TuneState* st = state(ctx);
+  std::lock_guard<std::mutex> lk(st->mu);
+  FILE* f = std::fopen(path, "w");
+  if (!f) return fail(TP_ERR_INVALID, std::string("cannot write ") + path);
+  std::fprintf(f, "tp-autotune-cache v1\n");
+  for (auto& kv : st->cache) {
+    const auto& c = kv.second.first;
+    std::fprintf(f, "%lld %lld %lld %d %d %d %d %d %d %.3f\n", (long long)kv.first.m, (long long)kv.first.n,
+                 (long long)kv.first.k, kv.first.dtype, c.bm, c.bn, c.stages, c.group_m, c.num_programs,
+                 kv.second.second);
+  }
+  std::fclose(f);
+  return TP_OK;
+}
+
+tp_status tp_autotune_load(tp_ctx* ctx, const char* path) {
+  if (!ctx || !path) return fail(TP_ERR_INVALID, "null argument");
+  FILE* f = std::fopen(path, "r");
+  if (!f) return fail(TP_ERR_INVALID, std::string("cannot read ") + path);
+  char magic[64] = {};
+  if (!std::fgets(magic, sizeof magic, f) || std::string(magic).rfind("tp-autotune-cache v1", 0) != 0) {
+    std::fclose(f);
+    return fail(TP_ERR_INVALID, "not a v1 autotune cache");
+  }
+  TuneState* st = state(ctx);
+  std::lock_guard<std::mutex> lk(st->mu);
+  long long m, n, k;
+  int dt, bm, bn, stages, gm, np;
+  float tf;
+  while (std::fscanf(f, "%lld %lld %lld %d %d %d %d %d %d %f", &m, &n, &k, &dt, &bm, &bn, &stages, &gm, &np, &tf) ==
+         10) {
+    tp_gemm_config c{};
+    c.bm = bm;
+    c.bn = bn;
+    c.stages = stages;
+    c.group_m = gm;
+    c.num_programs = np;
+    st->cache[TuneKey{m, n, k, dt}] = {c, tf};
+  }
+  std::fclose(f);
+  return TP_OK;
+}
+
+}  // extern "C"

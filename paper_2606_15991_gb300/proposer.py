@@ -1,0 +1,128 @@
+"""Learned tile proposer pipeline (driver around the library's kernels).
+
+1. collect: run the exhaustive autotuner (tp_autotune) on sampled shapes; each
+   shape gives one TFLOP/s measurement per config of the space.
+2. train:   fit the 3-layer MLP on the GPU with tp_mlp_train_step (the
+   library's forward, backward and Adam kernels), mini-batches drawn in a
+   seeded order.
+3. evaluate: on held-out shapes that were tuned exhaustively, the proposal
+   (arg-max of the MLP's scores) is charged its measured TFLOP/s; regret =
+   1 - TFLOP/s(proposal) / TFLOP/s(best). The method without the MLP is a fixed
+   default config (the best on average over the training shapes).
+
+Shapes: M, N, K log-uniform on [1, 16384]; K is rounded up to a multiple of 16
+so TMA rows are 16-byte multiples in both BF16 and FP8.
+"""
+from __future__ import annotations
+
+import math
+import time
+
+import numpy as np
+import torch
+
+import synth
+
+from . import (tp_autotune, tp_autotune_space, tp_mlp_create, tp_mlp_forward, tp_mlp_features, tp_mlp_targets,
+               tp_mlp_train_step)
+
+DTYPES = ("bf16", "fp8")
+HIDDEN = 64
+
+
+def sample_shapes(count: int, seed: int, lo: int = 1, hi: int = 16384):
+    """(M, N, K, dtype) with M, N, K log-uniform on [lo, hi], K rounded up to a
+    multiple of 16, dtype alternating BF16 / FP8."""
+    out = []
+    for i, (m, n, k) in enumerate(synth.log_uniform_shapes(count, seed, lo, hi)):
+        k = min(hi, ((k + 15) // 16) * 16)
+        out.append((m, n, k, DTYPES[i % 2]))
+    return out
+
+
+def collect(ctx, shapes, reps: int = 0, log=None):
+    """Exhaustive tables: returns X [S, 5], T [S, C], V [S, C], tflops [S, C]."""
+    C = len(tp_autotune_space("bf16"))
+    X = np.zeros((len(shapes), 5), np.float32)
+    T = np.zeros((len(shapes), C), np.float32)
+    V = np.zeros((len(shapes), C), np.float32)
+    TF = np.zeros((len(shapes), C), np.float32)
+    t0 = time.perf_counter()
+    for i, (m, n, k, dt) in enumerate(shapes):
+        _, table, _ = tp_autotune(ctx, m, n, k, dt, reps)
+        X[i] = tp_mlp_features(m, n, k, dt)
+        tg, mk = tp_mlp_targets(table)
+        T[i], V[i], TF[i] = tg, mk, table
+        if log and (i + 1) % 100 == 0:
+            log(f"collected {i + 1}/{len(shapes)} shapes in {time.perf_counter() - t0:.1f} s")
+    return X, T, V, TF
+
+
+def init_params(F: int, H: int, C: int, seed: int = 0) -> np.ndarray:
+    """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and biases, flat layout
+    [W1, b1, W2, b2, W3, b3]."""
+    parts = []
+    for i, (rows, fan_in) in enumerate(((H, F), (H, H), (C, H))):
+        b = 1.0 / math.sqrt(fan_in)
+        parts.append(synth.uniform(rows * fan_in, seed + 2 * i, -b, b))
+        parts.append(synth.uniform(rows, seed + 2 * i + 1, -b, b))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def train(ctx, X, T, V, epochs: int = 200, batch: int = 256, lr: float = 3e-3, seed: int = 0, log=None):
+    """Trains a fresh MLP on the GPU; returns (mlp, per-epoch mean loss)."""
+    S, F = X.shape
+    C = T.shape[1]
+    batch = min(batch, S)
+    mlp = tp_mlp_create(ctx, F, HIDDEN, C, max(batch, 256), init_params(F, HIDDEN, C, seed))
+    Xd = torch.from_numpy(X).cuda()
+    Td = torch.from_numpy(T).cuda()
+    Vd = torch.from_numpy(V).cuda()
+    loss = torch.zeros(1, device="cuda")
+    hist = []
+    nb = S // batch
+    for ep in range(epochs):
+        u = synth.uniform(S, seed + 1000 + ep, 0.0, 1.0, dtype=np.float64)
+        order = torch.from_numpy(np.argsort(u, kind="stable")).cuda()
+        tot = 0.0
+        for b in range(nb):
+            idx = order[b * batch:(b + 1) * batch]
+            tp_mlp_train_step(mlp, Xd[idx].contiguous(), Td[idx].contiguous(), Vd[idx].contiguous(), lr, loss)
+            tot += loss.item()
+        hist.append(tot / max(1, nb))
+        if log and (ep + 1) % 50 == 0:
+            log(f"epoch {ep + 1}: loss {hist[-1]:.5f}")
+    return mlp, hist
+
+
+def scores(mlp, X) -> np.ndarray:
+    Xd = torch.from_numpy(np.ascontiguousarray(X, np.float32)).cuda()
+    out = torch.empty(X.shape[0], mlp.shape[2], device="cuda")
+    for s in range(0, X.shape[0], 256):
+        e = min(X.shape[0], s + 256)
+        part = torch.empty(e - s, mlp.shape[2], device="cuda")
+        tp_mlp_forward(mlp, Xd[s:e].contiguous(), part)
+        out[s:e] = part
+    return out.cpu().numpy()
+
+
+def evaluate(mlp, X, TF, default_index: int, min_score: float = 0.0) -> dict:
+    """Regret of the MLP's proposals and of the fixed default config."""
+    S = scores(mlp, X)
+    best = TF.max(axis=1)
+    prop = S.argmax(axis=1)
+    reg = 1.0 - TF[np.arange(len(TF)), prop] / best
+    reg_def = 1.0 - TF[:, default_index] / best
+    fallback = S.max(axis=1) < min_score
+    reg_fb = np.where(fallback, 0.0, reg)   # the exhaustive fallback has zero regret by definition
+    return {"median_regret": float(np.median(reg)), "p90_regret": float(np.percentile(reg, 90)),
+            "mean_regret": float(reg.mean()),
+            "median_regret_default": float(np.median(reg_def)), "p90_regret_default": float(np.percentile(reg_def, 90)),
+            "mean_regret_default": float(reg_def.mean()),
+            "fallback_rate": float(fallback.mean()), "median_regret_with_fallback": float(np.median(reg_fb)),
+            "exact_pick_rate": float((reg <= 1e-6).mean()), "shapes": int(len(TF))}
+
+
+def default_config(T, V) -> int:
+    """Index of the config with the best mean relative TFLOP/s on training shapes."""
+    return int((T * V).sum(axis=0).argmax())

@@ -1,0 +1,157 @@
+"""GPU tests of the autotuner and the learned tile proposer: the MLP's
+forward, gradients and Adam steps against the FP64 oracle, the autotuner's
+table and cache, configs that change no numerics, and a small end-to-end
+train/evaluate run measured against the untrained network and against
+exhaustive tuning time."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2606_15991_gb300 as tp
+import synth
+from oracle import mlp as omlp
+from paper_2606_15991_gb300 import proposer
+
+pytestmark = pytest.mark.gpu
+
+F, H, C = 5, 64, 32
+
+
+def _split(flat):
+    o, out = 0, {}
+    for k, shape in (("W1", (H, F)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (C, H)), ("b3", (C,))):
+        n = int(np.prod(shape))
+        out[k] = np.asarray(flat[o:o + n], np.float64).reshape(shape)
+        o += n
+    return out
+
+
+def _flat(p):
+    return np.concatenate([p[k].reshape(-1) for k in omlp.PARAMS])
+
+
+def _batch(B=96, seed=0):
+    X = synth.uniform(B * F, seed, 0, 14, dtype=np.float64).reshape(B, F).astype(np.float32)
+    T = synth.uniform(B * C, seed + 1, 0, 1, dtype=np.float64).reshape(B, C).astype(np.float32)
+    V = (synth.uniform(B * C, seed + 2, 0, 1, dtype=np.float64) > 0.2).astype(np.float32).reshape(B, C)
+    return X, T, V
+
+
+def test_mlp_forward_grad_adam_match_oracle(ctx):
+    p0 = proposer.init_params(F, H, C, seed=3)
+    X, T, V = _batch()
+    m = tp.tp_mlp_create(ctx, F, H, C, 96, p0)
+    Xd, Td, Vd = (torch.from_numpy(a).cuda() for a in (X, T, V))
+    Y = torch.empty(96, C, device="cuda")
+    tp.tp_mlp_forward(m, Xd, Y)
+    P = _split(p0)
+    Yref, cache = omlp.forward(P, X.astype(np.float64))
+    assert np.max(np.abs(Y.cpu().numpy() - Yref)) <= 1e-5 * max(1.0, np.abs(Yref).max())
+    loss = torch.zeros(1, device="cuda")
+    G = torch.empty(len(p0), device="cuda")
+    tp.tp_mlp_loss_grad(m, Xd, Td, Vd, loss, G)
+    assert abs(loss.item() - omlp.loss(Yref, T, V)) <= 1e-5 * omlp.loss(Yref, T, V)
+    gref = _flat(omlp.backward(P, cache, Yref, T, V))
+    assert np.linalg.norm(G.cpu().numpy() - gref) <= 1e-4 * np.linalg.norm(gref)
+    # three Adam steps against the oracle's trajectory
+    mom = {k: np.zeros_like(v) for k, v in P.items()}
+    vel = {k: np.zeros_like(v) for k, v in P.items()}
+    for t in range(1, 4):
+        tp.tp_mlp_train_step(m, Xd, Td, Vd, 1e-3, loss)
+        Yr, cr = omlp.forward(P, X.astype(np.float64))
+        P, mom, vel = omlp.adam_step(P, omlp.backward(P, cr, Yr, T, V), mom, vel, t, 1e-3)
+    got = tp.tp_mlp_get_params(m)
+    assert np.max(np.abs(got - _flat(P))) <= 1e-5
+    tp.tp_mlp_destroy(m)
+
+
+def test_mlp_learns_separable_toy_on_gpu(ctx):
+    S = 512
+    X = synth.uniform(S * F, 40, 0, 1, dtype=np.float64).reshape(S, F).astype(np.float32)
+    cls = X[:, :3].argmax(axis=1)
+    T = np.zeros((S, C), np.float32)
+    T[np.arange(S), cls] = 1.0
+    V = np.ones_like(T)
+    mlp, hist = proposer.train(ctx, X, T, V, epochs=150, batch=128, lr=1e-2, seed=5)
+    assert hist[-1] < 0.2 * hist[0]
+    acc = (proposer.scores(mlp, X).argmax(axis=1) == cls).mean()
+    assert acc > 0.95
+    tp.tp_mlp_destroy(mlp)
+
+
+def test_features_targets_and_save_load(ctx, tmp_path):
+    assert tp.tp_mlp_features(1024, 3, 16384, "fp8") == pytest.approx(list(omlp.features(1024, 3, 16384, 1)))
+    tg, mk = tp.tp_mlp_targets([2.0, 0.0, 4.0, 1.0])
+    assert tg == [0.5, 0.0, 1.0, 0.25] and mk == [1.0, 0.0, 1.0, 1.0]
+    p0 = proposer.init_params(F, H, C, seed=9)
+    m = tp.tp_mlp_create(ctx, F, H, C, 8, p0)
+    path = os.path.join(tmp_path, "mlp.txt")
+    tp.tp_mlp_save(m, path)
+    tp.tp_mlp_set_params(m, np.zeros_like(p0))
+    tp.tp_mlp_load(m, path)
+    assert np.array_equal(tp.tp_mlp_get_params(m), p0)
+    tp.tp_mlp_destroy(m)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "fp8"])
+def test_autotune_table_cache_and_numerics(ctx, dtype, tmp_path):
+    space = tp.tp_autotune_space(dtype)
+    assert len(space) == C
+    M, N, K = 700, 900, 1024
+    best, table, best_tf = tp.tp_autotune(ctx, M, N, K, dtype)
+    assert len(table) == C and all(t > 0 for t in table)
+    assert best_tf == max(table) or best_tf >= 0.99 * max(table)
+    assert tp.tp_autotune_lookup(ctx, M, N, K, dtype).bn == best.bn
+    path = os.path.join(tmp_path, "cache.txt")
+    tp.tp_autotune_save(ctx, path)
+    tp.tp_autotune_load(ctx, path)
+    # every config computes the same C: a proposal never changes numerics
+    if dtype == "bf16":
+        a = synth.to_bf16(synth.normal(M * K, 1)).reshape(M, K).cuda()
+        bt = synth.to_bf16(synth.normal(N * K, 2)).reshape(N, K).cuda()
+        ref = None
+        for cfg in space:
+            c = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
+            p = tp.tp_partition_create(ctx, c, (cfg.bm, cfg.bn))
+            tiles = tp.tp_partition_query(p)["num_tiles"]
+            tp.tp_partition_map(p, tp.MAP_STRIDED, min(tiles, ctx.sm_count * 128 // cfg.bm))
+            tp.tp_gemm(ctx, p, a, bt.t(), cfg)
+            tp.tp_partition_destroy(p)
+            if ref is None:
+                ref = c
+            else:
+                assert torch.equal(c, ref)
+
+
+def test_small_end_to_end_gain(ctx):
+    """Train on 192 exhaustively tuned shapes (both dtypes), evaluate on 64
+    held-out ones. The trained proposer must reach the stated median regret
+    (<= 5% of the exhaustive best), lose less than the same network untrained,
+    and choose a config far faster than exhaustive tuning of the shape."""
+    import time
+
+    train_shapes = proposer.sample_shapes(192, seed=1, hi=8192)
+    test_shapes = proposer.sample_shapes(64, seed=2, hi=8192)
+    X, T, V, TF = proposer.collect(ctx, train_shapes)
+    mlp, hist = proposer.train(ctx, X, T, V, epochs=400, batch=64, lr=3e-3)
+    assert hist[-1] < 0.5 * hist[0]
+    t0 = time.perf_counter()
+    Xt, Tt, Vt, TFt = proposer.collect(ctx, test_shapes)
+    t_exhaustive = (time.perf_counter() - t0) / len(test_shapes)
+    r = proposer.evaluate(mlp, Xt, TFt, proposer.default_config(T, V))
+    assert r["median_regret"] <= 0.05
+    untrained = tp.tp_mlp_create(ctx, F, H, C, 256, proposer.init_params(F, H, C, seed=0))
+    r0 = proposer.evaluate(untrained, Xt, TFt, 0)
+    assert r["mean_regret"] < r0["mean_regret"]
+    t0 = time.perf_counter()
+    for m, n, k, dt in test_shapes:
+        cfg, score, fb = tp.tp_propose(ctx, mlp, m, n, k, dt, min_score=-1e9)
+        assert not fb
+    t_propose = (time.perf_counter() - t0) / len(test_shapes)
+    assert t_propose * 20 < t_exhaustive
+    cfg, score, fb = tp.tp_propose(ctx, mlp, 20000, 64, 64, "bf16")      # outside the trained range
+    assert fb and cfg.bm in (128, 256)
+    tp.tp_mlp_destroy(mlp)
+    tp.tp_mlp_destroy(untrained)
