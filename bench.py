@@ -619,6 +619,84 @@ def run_proposer(args):
         "s_collect_train": t_collect, "s_train": t_train}))
 
 
+def run_kernel(args):
+    """One kernel on a (small) case, warm-up plus a few launches: the target of
+    ncu captures. Prints a one-line JSON summary."""
+    import torch
+
+    from paper_2606_15991_gb300 import build as _build
+
+    _build.build()
+    import paper_2606_15991_gb300 as tp
+    import synth
+
+    ctx = tp.tp_ctx_create(0)
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(1)
+    k, n = args.kernel, args.size
+    out = {"case": "kernel", "kernel": k}
+    if k.startswith("map"):
+        dt = torch.float32 if k.endswith("f32") else torch.bfloat16
+        x = torch.randn(args.elements, device=dev, generator=g).to(dt)
+        y = torch.randn(args.elements, device=dev, generator=g).to(dt)
+        z = torch.empty_like(x)
+        p = tp.tp_partition_create(ctx, z, (TILE,))
+        fn = (lambda: tp.tp_map_axpy(ctx, p, ALPHA, x, y)) if "axpy" in k else (lambda: tp.tp_map_gelu_mul(ctx, p, x, y))
+        out["elements"] = args.elements
+    elif k in ("gemm_bf16", "gemm_fp8"):
+        a = torch.randn(n, n, device=dev, generator=g).to(torch.bfloat16)
+        bt = torch.randn(n, n, device=dev, generator=g).to(torch.bfloat16)
+        c = torch.empty(n, n, device=dev, dtype=torch.bfloat16)
+        p = tp.tp_partition_create(ctx, c, (256, 256))
+        tp.tp_partition_map(p, tp.MAP_STRIDED, min(ctx.sm_count // 2, tp.tp_partition_query(p)["num_tiles"]))
+        cfg = tp.gemm_config(bm=256, bn=256, group_m=8)
+        if k == "gemm_bf16":
+            fn = lambda: tp.tp_gemm(ctx, p, a, bt.t(), cfg)
+        else:
+            amax, scale = torch.zeros(2, device=dev), torch.zeros(2, device=dev)
+            qa = torch.empty(n, n, device=dev, dtype=torch.float8_e4m3fn)
+            qb = torch.empty(n, n, device=dev, dtype=torch.float8_e4m3fn)
+            for src, q, i in ((a, qa, 0), (bt, qb, 1)):
+                pq = tp.tp_partition_create(ctx, q, (16, n))
+                tp.tp_amax(ctx, src, amax[i:i + 1])
+                tp.tp_quantize_fp8(ctx, pq, src, amax[i:i + 1], scale[i:i + 1])
+                tp.tp_partition_destroy(pq)
+            fn = lambda: tp.tp_gemm_fp8(ctx, p, qa, qb.t(), scale[0:1], scale[1:2], cfg)
+        out["size"] = n
+    elif k == "grouped":
+        shapes = synth.grouped_problems(64, seed=0)[:args.group]
+        probs = []
+        for i, (m, nn, kk) in enumerate(shapes):
+            g.manual_seed(1000 + i)
+            probs.append((torch.randn(m, kk, device=dev, generator=g).to(torch.bfloat16),
+                          torch.randn(nn, kk, device=dev, generator=g).to(torch.bfloat16).t(),
+                          torch.empty(m, nn, device=dev, dtype=torch.bfloat16)))
+        plan = tp.tp_grouped_plan_create(ctx, probs)
+        fn = lambda: tp.tp_grouped_gemm(ctx, plan)
+        out["problems"] = len(shapes)
+    elif k == "decode":
+        d, nq, ni = 5120, 10240, 25600
+        lay = [tuple((torch.randn(r, c_, device=dev, generator=g) * 0.02).to(torch.bfloat16)
+                     for r, c_ in ((nq, d), (2 * ni, d), (d, ni)))]
+        h = torch.randn(d, device=dev, generator=g)
+        ch = tp.DecodeChain(ctx, h, lay)
+        fn = lambda: ch.record_fused()
+    else:
+        raise SystemExit(f"unknown kernel {k}")
+    for _ in range(args.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    out["ms_per_call_incl_sync"] = e0.elapsed_time(e1) / max(1, args.steps)
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -629,14 +707,22 @@ def main():
     ap.add_argument("--skip-rows", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--case", default="maps", choices=["maps", "proposer"],
-                    help="maps: the benchmark step (default); proposer: the learned-proposer experiment")
+    ap.add_argument("--case", default="maps", choices=["maps", "proposer", "kernel"],
+                    help="maps: the benchmark step (default); proposer: the learned-proposer experiment; "
+                         "kernel: one kernel on a small case (profiling target)")
+    ap.add_argument("--kernel", default="map_axpy_f32",
+                    help="map_axpy_f32|map_axpy_bf16|map_gelu_f32|map_gelu_bf16|gemm_bf16|gemm_fp8|grouped|decode")
+    ap.add_argument("--size", type=int, default=4096)
+    ap.add_argument("--elements", type=int, default=1 << 26)
+    ap.add_argument("--group", type=int, default=8)
     ap.add_argument("--train-shapes", type=int, default=625)
     ap.add_argument("--test-shapes", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=600)
     args = ap.parse_args()
     if args.case == "proposer":
         run_proposer(args)
+    elif args.case == "kernel":
+        run_kernel(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
