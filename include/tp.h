@@ -288,20 +288,23 @@ typedef struct tp_grouped_plan tp_grouped_plan;
  * queue, Appendix B). Every output tile of every problem becomes one slot of
  * a device queue, most expensive tiles first. Problems with M <= swap_max_m
  * (<= 256; a negative value means 256) run transposed, C^T = B^T . A^T, with
- * 128-column tiles of C; the others use 128 x 256 tiles. The plan owns one
+ * tiles spanning all of M; the others use tiles of 256 columns. cta_pair != 0
+ * runs every tile on a CTA pair (tcgen05 cta_group::2, 256 tile rows in the
+ * MMA orientation), 0 on single CTAs (128 rows). The plan owns one
  * queue-mapped partition per C_i and a device table of TMA descriptors; it
  * allocates device memory, so build it outside graph capture
  * (TP_ERR_CAPTURE). Errors: TP_ERR_RANK, TP_ERR_SHAPE, TP_ERR_ALIGN,
  * TP_ERR_UNSUPPORTED, TP_ERR_CUDA. */
 tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int32_t n, int32_t swap_max_m,
-                                 tp_grouped_plan** plan);
+                                 int32_t cta_pair, tp_grouped_plan** plan);
 /* Total queue slots, and per problem (input order) whether it runs
  * transposed (swapped may be NULL). */
 tp_status tp_grouped_plan_info(const tp_grouped_plan* plan, int64_t* total_tiles, int32_t* swapped);
 /* TP_ERR_BUSY while a launch of the plan is in flight. */
 tp_status tp_grouped_plan_destroy(tp_grouped_plan* plan);
-/* Runs the whole group with one launch of num_programs persistent CTAs
- * (0 = one per SM) that dequeue tiles until the queue is empty. Every C_i is
+/* Runs the whole group with one launch of num_programs persistent programs
+ * (CTAs, or CTA pairs; 0 = one per SM / SM pair) that dequeue tiles until
+ * the queue is empty. Every C_i is
  * busy while in flight. Write-count instrumentation indexes the C_i back to
  * back in input order (C_0's elements first). Errors: as tp_gemm. */
 tp_status tp_grouped_gemm(tp_ctx* ctx, tp_grouped_plan* plan, int32_t num_programs, const tp_exec* ex);

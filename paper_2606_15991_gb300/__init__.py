@@ -296,7 +296,7 @@ class GroupedPlan:
         self.n = n
 
 
-def tp_grouped_plan_create(ctx, problems, swap_max_m: int = -1) -> GroupedPlan:
+def tp_grouped_plan_create(ctx, problems, swap_max_m: int = -1, cta_pair: bool = True) -> GroupedPlan:
     """problems: [(A [M,K], B [K,N] K-major view, C [M,N])] of bf16 CUDA tensors."""
     arr = (_lib.tp_gemm_problem * len(problems))()
     keep = []
@@ -304,7 +304,8 @@ def tp_grouped_plan_create(ctx, problems, swap_max_m: int = -1) -> GroupedPlan:
         arr[i].a, arr[i].b, arr[i].c = tensor_desc(a), tensor_desc(b), tensor_desc(c)
         keep += [a, b, c]
     h = ctypes.c_void_p()
-    call("tp_grouped_plan_create", ctx.handle, arr, len(problems), int(swap_max_m), ctypes.byref(h))
+    call("tp_grouped_plan_create", ctx.handle, arr, len(problems), int(swap_max_m), int(bool(cta_pair)),
+         ctypes.byref(h))
     return GroupedPlan(h.value, keep, len(problems))
 
 

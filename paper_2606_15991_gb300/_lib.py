@@ -103,7 +103,7 @@ _PROTOS = {
     "tp_amax": [_VP, _PT, _VP, _PE],
     "tp_quantize_fp8": [_VP, _VP, _PT, _VP, _VP, _PE],
     "tp_gemm_fp8": [_VP, _VP, _PT, _PT, _VP, _VP, ctypes.POINTER(tp_gemm_config), _PE],
-    "tp_grouped_plan_create": [_VP, ctypes.POINTER(tp_gemm_problem), _I32, _I32, _PP],
+    "tp_grouped_plan_create": [_VP, ctypes.POINTER(tp_gemm_problem), _I32, _I32, _I32, _PP],
     "tp_grouped_plan_info": [_VP, _PI64, _PI32],
     "tp_grouped_plan_destroy": [_VP],
     "tp_grouped_gemm": [_VP, _VP, _I32, _PE],

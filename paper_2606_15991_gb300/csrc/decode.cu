@@ -43,7 +43,9 @@ __device__ float block_rms_scale(const float* __restrict__ h, int64_t d, float e
 
 // Dot product of one bf16 row (length k, 16-byte aligned) with x (fp32, in
 // shared memory) by the lanes of one warp, lane-partial then shuffle tree.
-// Warps of a group split the row into `parts` contiguous pieces.
+// Warps of a group split the row into `parts` contiguous pieces; each lane
+// keeps kUnroll 16-byte weight loads in flight.
+template <int kUnroll>
 __device__ __forceinline__ float row_dot(const __nv_bfloat16* __restrict__ w, const float* __restrict__ xs,
                                          int64_t k, int part, int parts) {
   const int lane = threadIdx.x & 31;
@@ -53,12 +55,12 @@ __device__ __forceinline__ float row_dot(const __nv_bfloat16* __restrict__ w, co
   const uint4* wv = reinterpret_cast<const uint4*>(w);
   float acc0 = 0.f, acc1 = 0.f;
   int64_t v = v0 + lane;
-  for (; v + 96 < v1; v += 128) {
-    uint4 q[4];
+  for (; v + 32 * (kUnroll - 1) < v1; v += 32 * kUnroll) {
+    uint4 q[kUnroll];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) q[u] = __ldcs(wv + v + 32 * u);
+    for (int u = 0; u < kUnroll; ++u) q[u] = __ldcs(wv + v + 32 * u);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kUnroll; ++u) {
       const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q[u]);
       const float4* xv = reinterpret_cast<const float4*>(xs + (v + 32 * u) * 8);
       const float4 xa = xv[0], xb = xv[1];
@@ -118,7 +120,7 @@ struct GemvArgs {
   int32_t* owner;
 };
 
-template <int kEpi, int kParts, bool kCount>
+template <int kEpi, int kParts, int kUnroll, bool kCount>
 __global__ void __launch_bounds__(kThreads) gemv_kernel(const __grid_constant__ GemvArgs p) {
   extern __shared__ float xs[];  // k floats (+ reduction scratch)
   float* red = xs + ((p.k + 3) & ~int64_t(3));
@@ -149,9 +151,9 @@ __global__ void __launch_bounds__(kThreads) gemv_kernel(const __grid_constant__ 
     if (valid) {
       const __nv_bfloat16* w = second ? p.w2 : p.w;
       const int64_t ld = second ? p.ld2 : p.ld;
-      s0 = row_dot(w + r * ld, xs, p.k, part, kParts);
+      s0 = row_dot<kUnroll>(w + r * ld, xs, p.k, part, kParts);
       if (epi == kSiluPair)
-        s1 = row_dot(w + (r + (second ? p.pair_offset2 : p.pair_offset)) * ld, xs, p.k, part, kParts);
+        s1 = row_dot<kUnroll>(w + (r + (second ? p.pair_offset2 : p.pair_offset)) * ld, xs, p.k, part, kParts);
     }
     if constexpr (kParts > 1) {
       // combine the warps of a group in a fixed order
@@ -183,6 +185,41 @@ __global__ void __launch_bounds__(kThreads) gemv_kernel(const __grid_constant__ 
         p.owner[e] = (int32_t)(blockIdx.x * kGroups + group);
       }
     }
+  }
+}
+
+// Split-row matrix-vector product: each warp owns (row, part) units, no
+// block barriers, and writes one partial dot product per unit; the finish
+// kernel adds a row's partials in part order (deterministic) to h.
+template <int kUnroll>
+__global__ void __launch_bounds__(kThreads) gemv_partial_kernel(const __grid_constant__ GemvArgs p, int parts,
+                                                                float* __restrict__ partial) {
+  extern __shared__ float xs[];
+  for (int64_t i = threadIdx.x; i < p.k; i += kThreads) xs[i] = p.x[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t units = p.rows * parts;
+  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
+  for (int64_t u = (int64_t)blockIdx.x * kWarps + threadIdx.x / 32; u < units; u += nwarps) {
+    const int64_t r = u / parts;
+    const int part = (int)(u % parts);
+    const float s = row_dot<kUnroll>(p.w + r * p.ld, xs, p.k, part, parts);
+    if (lane == 0) partial[(int64_t)part * p.rows + r] = s;
+  }
+}
+
+template <bool kCount>
+__global__ void __launch_bounds__(kThreads) residual_finish_kernel(float* __restrict__ h, const float* __restrict__ partial,
+                                                                   int64_t rows, int parts, uint32_t* counts,
+                                                                   int32_t* owner) {
+  const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  if (r >= rows) return;
+  float s = 0.f;
+  for (int q = 0; q < parts; ++q) s += partial[(int64_t)q * rows + r];
+  h[r] = h[r] + s;
+  if constexpr (kCount) {
+    atomicAdd(counts + r, 1u);
+    owner[r] = (int32_t)blockIdx.x;
   }
 }
 
@@ -229,10 +266,10 @@ bool vec_out(const tp_partition* p, int64_t n) {
   return p && p->t.dtype == TP_F32 && p->rank == 1 && p->shape[0] == n;
 }
 
-template <int kEpi, int kParts>
+template <int kEpi, int kParts, int kUnroll>
 cudaError_t launch_gemv(const GemvArgs& a, int grid, cudaStream_t st) {
   const size_t smem = (((a.k + 3) & ~int64_t(3)) + 16 + 2 * kWarps) * sizeof(float);
-  auto k = a.counts ? gemv_kernel<kEpi, kParts, true> : gemv_kernel<kEpi, kParts, false>;
+  auto k = a.counts ? gemv_kernel<kEpi, kParts, kUnroll, true> : gemv_kernel<kEpi, kParts, kUnroll, false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k<<<grid, kThreads, smem, st>>>(a);
@@ -300,7 +337,7 @@ tp_status tp_gemv(tp_ctx* ctx, tp_partition* y, const tp_tensor* w, const tp_ten
   a.counts = ex->write_counts;
   a.owner = ex->write_owner;
   cudaError_t e = cudaSuccess;
-  if (rows > 0 && k > 0) e = launch_gemv<kPlain, 1>(a, gemv_grid(ctx, k), o.stream);
+  if (rows > 0 && k > 0) e = launch_gemv<kPlain, 1, 4>(a, gemv_grid(ctx, k), o.stream);
   return o.end(e);
 }
 
@@ -375,7 +412,7 @@ tp_status tp_decode_norm_qkv_gu(tp_ctx* ctx, tp_partition* qkv, tp_partition* a_
   a.counts = ex->write_counts;
   a.owner = ex->write_owner;
   cudaError_t e = cudaSuccess;
-  if (d > 0 && nq + ni > 0) e = launch_gemv<kPlain, 1>(a, gemv_grid(ctx, d), o.stream);
+  if (d > 0 && nq + ni > 0) e = launch_gemv<kPlain, 1, 4>(a, gemv_grid(ctx, d), o.stream);
   return o.end(e);
 }
 
@@ -400,8 +437,26 @@ tp_status tp_decode_down_residual(tp_ctx* ctx, tp_partition* h, const tp_tensor*
   a.counts = ex->write_counts;
   a.owner = ex->write_owner;
   cudaError_t e = cudaSuccess;
-  // few long rows: a group of 4 warps shares each row
-  if (d > 0 && ni > 0) e = launch_gemv<kResidual, 4>(a, gemv_grid(ctx, ni), o.stream);
+  // few long rows: every row is split into 4 independent warp units whose
+  // partial sums (context scratch, allocated once) a finish kernel adds to h
+  const int parts = 4;
+  if (d > 0 && ni > 0) {
+    if (d * parts > tp_ctx::kPartialFloats) e = launch_gemv<kResidual, 4, 4>(a, gemv_grid(ctx, ni), o.stream);
+    else {
+      const size_t smem = (size_t)((ni + 3) & ~int64_t(3)) * sizeof(float);
+      auto k = gemv_partial_kernel<8>;
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e == cudaSuccess) {
+        k<<<gemv_grid(ctx, ni), kThreads, smem, o.stream>>>(a, parts, ctx->d_partial);
+        const unsigned fg = (unsigned)((d + kThreads - 1) / kThreads);
+        if (a.counts)
+          residual_finish_kernel<true><<<fg, kThreads, 0, o.stream>>>(a.y, ctx->d_partial, d, parts, a.counts, a.owner);
+        else
+          residual_finish_kernel<false><<<fg, kThreads, 0, o.stream>>>(a.y, ctx->d_partial, d, parts, nullptr, nullptr);
+        e = cudaGetLastError();
+      }
+    }
+  }
   return o.end(e);
 }
 

@@ -1,9 +1,9 @@
 // Grouped persistent BF16 GEMM: many independent problems C_i = A_i . B_i of
 // uneven sizes in one launch. Every output tile of every problem is a slot of
 // one device queue (a mapped partition whose map is a shared counter, §3.6);
-// each persistent CTA dequeues slots until the queue is empty. The queue
-// order lists the most expensive tiles first (longest-processing-time first)
-// so the last wave is made of short tiles.
+// each persistent CTA (or CTA pair) dequeues slots until the queue is empty.
+// The plan's slot map orders the queue: HBM-bound and tensor-bound tiles are
+// interleaved in proportion to their cost, each kind most expensive first.
 //
 // A problem with M <= 256 runs transposed ("swap-AB"): C^T = B^T . A^T, so
 // the large N fills the 128 rows of the tensor-core tile and the small M is
@@ -34,11 +34,11 @@ struct alignas(64) GroupedProblem {
   CUtensorMap map_y;      // MMA B operand: B_i (normal, box 256 rows) or A_i (swap, box bn rows)
   __nv_bfloat16* c;
   int64_t M, N, K;
-  int64_t tile_base;      // first queue slot of this problem
   int64_t tiles_r, tiles_c;  // tile grid in MMA orientation (rows of 128, columns of bn)
   int64_t count_base;     // offset of C_i in the write-count arrays
   int32_t swap, bn;       // bn = MMA N of every tile of this problem
-  int32_t pad[2];
+  int32_t tile_rows;      // 128 (one CTA) or 256 (CTA pair), MMA orientation
+  int32_t box_y;          // rows of the MMA B operand each CTA loads per stage
 };
 
 }  // namespace tp
@@ -47,11 +47,13 @@ struct tp_grouped_plan {
   tp_ctx* ctx = nullptr;
   int32_t n = 0;
   int64_t total_tiles = 0;
-  tp::GroupedProblem* d_probs = nullptr;   // device table (queue order)
+  tp::GroupedProblem* d_probs = nullptr;   // device table (input order)
+  int64_t* d_slots = nullptr;              // queue slot -> (problem << 32) | local tile
   std::vector<tp_partition*> outs;         // one partition per C_i (busy tracking)
   std::vector<tp_tensor> ins;              // A_i and B_i views (alias checks)
   std::vector<int32_t> order;              // queue position -> problem index
   int64_t total_elems = 0;
+  bool pair = true;                        // 256-row tiles on CTA pairs
 };
 
 namespace tp {
@@ -60,14 +62,20 @@ namespace {
 using namespace sm100;
 
 constexpr int kThreads = 192;
-constexpr int kStages = 4;
 constexpr int kRing = 4;
 constexpr int kMaxProblems = 256;
-constexpr uint32_t kStageX = 128 * 128;   // 128 rows x 128 bytes
-constexpr uint32_t kStageY = 256 * 128;   // up to 256 rows x 128 bytes
+constexpr uint32_t kStageX = 128 * 128;   // 128 rows x 128 bytes per CTA
+// B-operand rows per CTA and stage count: one CTA holds up to 256 rows
+// (4 stages of 48 KB); a CTA of a pair holds up to 128 (6 stages of 32 KB).
+template <bool kPair> struct Ring {
+  static constexpr uint32_t kStageY = kPair ? 128 * 128 : 256 * 128;
+  static constexpr int kStages = kPair ? 6 : 4;
+};
+constexpr size_t kWordsBytes = 8 + 8 * kRing;
 
 struct GroupedArgs {
   const GroupedProblem* probs;
+  const int64_t* slot_map;   // queue slot -> (problem << 32) | local tile
   int32_t n;
   int64_t total;
   unsigned* queue;
@@ -76,39 +84,36 @@ struct GroupedArgs {
   int32_t* owner;
 };
 
-__device__ __forceinline__ int find_problem(const int64_t* base, int n, int64_t g) {
-  int lo = 0, hi = n - 1;  // largest i with base[i] <= g
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) / 2;
-    if (base[mid] <= g) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-template <bool kCount>
+template <bool kPair, bool kCount>
 __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_constant__ GroupedArgs p) {
+  constexpr uint32_t kStageY = Ring<kPair>::kStageY;
+  constexpr int kStages = Ring<kPair>::kStages;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - raw);
   const int warp = threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
+  // On a pair, the even CTA dequeues slots and issues the MMAs; both CTAs
+  // load their half of each operand and store their half of each tile.
+  const uint32_t rank = kPair ? cluster_ctarank() : 0u;
+  const bool leader = rank == 0;
+  const int32_t prog = kPair ? (int32_t)(blockIdx.x / 2) : (int32_t)blockIdx.x;
 
   const uint32_t x0 = base;
   const uint32_t y0 = x0 + kStageX * kStages;
   const uint32_t bars = y0 + kStageY * kStages;
   auto full_bar = [&](int s) { return bars + 8u * s; };
-  auto empty_bar = [&](int s) { return bars + 32u + 8u * s; };
-  auto tfull_bar = [&](int b) { return bars + 64u + 8u * b; };
-  auto tempty_bar = [&](int b) { return bars + 80u + 8u * b; };
-  auto rfull_bar = [&](int r) { return bars + 96u + 8u * r; };
-  auto rempty_bar = [&](int r) { return bars + 128u + 8u * r; };
-  const uint32_t drain_bar = bars + 160u;
-  uint8_t* words = gbase + (bars - base) + 168u;
+  auto empty_bar = [&](int s) { return bars + 64u + 8u * s; };
+  auto tfull_bar = [&](int b) { return bars + 128u + 8u * b; };
+  auto tempty_bar = [&](int b) { return bars + 144u + 8u * b; };
+  auto rfull_bar = [&](int r) { return bars + 160u + 8u * r; };
+  auto rempty_bar = [&](int r) { return bars + 192u + 8u * r; };
+  const uint32_t drain_bar = bars + 224u;
+  uint8_t* words = gbase + (bars - base) + 232u;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(words);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(words + 4);
   volatile int64_t* ring = reinterpret_cast<volatile int64_t*>(words + 8);          // kRing slots
-  int64_t* tile_base = reinterpret_cast<int64_t*>(words + 8 + 8 * kRing);          // n entries
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -117,78 +122,116 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
-      mbar_init(tempty_bar(b), 4);
+      mbar_init(tempty_bar(b), kPair ? 8 : 4);  // epilogue warps (of both CTAs)
     }
     for (int r = 0; r < kRing; ++r) {
       mbar_init(rfull_bar(r), 1);
-      mbar_init(rempty_bar(r), 5);  // MMA thread + one per epilogue warp
+      // readers of a slot: the MMA thread and 4 epilogue warps (+ the odd
+      // CTA's 4 epilogue warps and producer on a pair)
+      mbar_init(rempty_bar(r), kPair ? 10 : 5);
     }
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
-  for (int i = threadIdx.x; i < p.n; i += kThreads) tile_base[i] = p.probs[i].tile_base;
   if (warp == 1) {
-    tmem_alloc(smem_u32(tmem_slot), 512);
-    tmem_relinquish();
+    if constexpr (kPair) {
+      tmem_alloc_pair(smem_u32(tmem_slot), 512);
+      tmem_relinquish_pair();
+    } else {
+      tmem_alloc(smem_u32(tmem_slot), 512);
+      tmem_relinquish();
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (kPair) cluster_sync();
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  // decode a queue slot into (problem, tile row, tile column)
+  // decode a queue slot into (problem, tile row, tile column) through the
+  // plan's slot map; a problem's tiles are column-major over its tile grid so
+  // consecutive tiles share a B slab while the problem's A stays in L2
   auto decode = [&](int64_t g, const GroupedProblem** pr, int64_t* tr, int64_t* tc) {
-    const int i = find_problem(tile_base, p.n, g);
-    *pr = p.probs + i;
-    // column-major over the tile grid: consecutive slots share a B slab (the
-    // big operand) while the problem's A stays resident in L2
-    const int64_t local = g - tile_base[i];
+    const int64_t e = p.slot_map[g];
+    *pr = p.probs + (e >> 32);
+    const int64_t local = e & 0xffffffffll;
     *tr = local % (*pr)->tiles_r;
     *tc = local / (*pr)->tiles_r;
+  };
+  // wait for a ring slot's value; on a pair it may come from the peer CTA
+  auto ring_wait = [&](uint32_t bar, uint32_t parity) {
+    return kPair ? mbar_wait_cluster(bar, parity, abort_flag, p.err) : mbar_wait(bar, parity, abort_flag, p.err);
+  };
+  auto ring_release = [&](int r) {
+    if constexpr (kPair) mbar_arrive_cluster(mapa(rempty_bar(r), 0));
+    else mbar_arrive(rempty_bar(r));
   };
 
   if (warp == 0) {
     if (lane == 0) {
       const uint64_t pol_stream = policy_evict_first();
       const uint64_t pol_keep = policy_evict_last();
-      uint32_t fills[kStages] = {};
+      uint32_t fills[8] = {};
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
       for (int64_t j = 0; ok; ++j) {
         const int r = (int)(j % kRing);
-        if (!mbar_wait(rempty_bar(r), (uint32_t)((j / kRing) & 1) ^ 1u, abort_flag, p.err)) { ok = false; break; }
-        const int64_t g = (int64_t)atomicAdd(p.queue, 1u);
-        ring[r] = g < p.total ? g : -1;
-        mbar_arrive(rfull_bar(r));
-        if (g >= p.total) break;
+        const uint32_t par = (uint32_t)((j / kRing) & 1);
+        int64_t g;
+        if (leader) {
+          if (!ring_wait(rempty_bar(r), par ^ 1u)) { ok = false; break; }
+          const int64_t d = (int64_t)atomicAdd(p.queue, 1u);
+          g = d < p.total ? d : -1;
+          ring[r] = g;
+          if constexpr (kPair) {
+            st_cluster_u64(mapa(smem_u32(const_cast<int64_t*>(ring + r)), 1), g);
+            mbar_arrive(rfull_bar(r));
+            mbar_arrive_cluster(mapa(rfull_bar(r), 1));
+          } else {
+            mbar_arrive(rfull_bar(r));
+          }
+        } else {
+          if (!ring_wait(rfull_bar(r), par)) { ok = false; break; }
+          g = ring[r];
+          ring_release(r);
+        }
+        if (g < 0) break;
         const GroupedProblem* pr;
         int64_t tr, tc;
         decode(g, &pr, &tr, &tc);
-        const int32_t xrow = (int32_t)(tr * 128);
-        const int32_t yrow = (int32_t)(tc * pr->bn);
-        const uint32_t tx = kStageX + (uint32_t)pr->bn * 128u;
+        const int32_t xrow = (int32_t)(tr * pr->tile_rows + rank * 128);
+        const int32_t yrow = (int32_t)(tc * pr->bn + rank * pr->box_y);
+        const uint32_t tx = kStageX + (uint32_t)pr->box_y * 128u;
         const int64_t nk = (pr->K + 63) / 64;
         for (int64_t kb = 0; kb < nk; ++kb) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err)) { ok = false; break; }
-          mbar_arrive_expect_tx(full_bar(stage), tx);
+          const int32_t kc = (int32_t)(kb * 64);
           // swap: x = B_i slab (read once), y = A_i (reused by every tile)
-          tma_load_2d(x0 + kStageX * stage, &pr->map_x, (int32_t)(kb * 64), xrow, full_bar(stage),
-                      pr->swap ? pol_stream : pol_keep);
-          tma_load_2d(y0 + kStageY * stage, &pr->map_y, (int32_t)(kb * 64), yrow, full_bar(stage), pol_keep);
+          const uint64_t px = pr->swap ? pol_stream : pol_keep;
+          if constexpr (kPair) {
+            const uint32_t fb = mapa(full_bar(stage), 0);  // both halves complete on the even CTA's barrier
+            if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * tx);
+            tma_load_2d_pair(x0 + kStageX * stage, &pr->map_x, kc, xrow, fb, px);
+            tma_load_2d_pair(y0 + kStageY * stage, &pr->map_y, kc, yrow, fb, pol_keep);
+          } else {
+            mbar_arrive_expect_tx(full_bar(stage), tx);
+            tma_load_2d(x0 + kStageX * stage, &pr->map_x, kc, xrow, full_bar(stage), px);
+            tma_load_2d(y0 + kStageY * stage, &pr->map_y, kc, yrow, full_bar(stage), pol_keep);
+          }
           fills[stage]++;
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
       }
-      if (!ok) {
+      if (!ok && leader) {
         for (int s2 = 0; s2 < kStages; ++s2)
           if (fills[s2]) mbar_wait(full_bar(s2), (fills[s2] - 1u) & 1u, nullptr, nullptr, 200000000ull);
       }
     }
     __syncwarp();
   } else if (warp == 1) {
-    if (lane == 0) {
+    if (lane == 0 && leader) {
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
@@ -196,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
         const int r = (int)(j % kRing);
         if (!mbar_wait(rfull_bar(r), (uint32_t)((j / kRing) & 1), abort_flag, p.err)) { ok = false; break; }
         const int64_t g = ring[r];
-        mbar_arrive(rempty_bar(r));
+        ring_release(r);
         if (g < 0) break;
         const GroupedProblem* pr;
         int64_t tr, tc;
@@ -205,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
         const uint32_t use = (uint32_t)((j >> 1) & 1);
         if (!mbar_wait(tempty_bar(acc), use ^ 1u, abort_flag, p.err)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t idesc = idesc_f32acc(128, (uint32_t)pr->bn, false);
+        const uint32_t idesc = idesc_f32acc(kPair ? 256 : 128, (uint32_t)pr->bn, false);
         const uint32_t d = tmem_base + (uint32_t)(acc * 256);
         const int64_t nk = (pr->K + 63) / 64;
         for (int64_t kb = 0; kb < nk; ++kb) {
@@ -214,30 +257,36 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
           const uint64_t ad = desc_kmajor_sw128(x0 + kStageX * stage);
           const uint64_t bd = desc_kmajor_sw128(y0 + kStageY * stage);
 #pragma unroll
-          for (int k = 0; k < 4; ++k)
-            mma<false>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, (kb > 0 || k > 0) ? 1u : 0u);
-          mma_commit(empty_bar(stage));
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t accum = (kb > 0 || k > 0) ? 1u : 0u;
+            if constexpr (kPair) mma_pair<false>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accum);
+            else mma<false>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accum);
+          }
+          if constexpr (kPair) mma_commit_pair(empty_bar(stage), 0x3);
+          else mma_commit(empty_bar(stage));
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
         if (!ok) break;
-        mma_commit(tfull_bar(acc));
+        if constexpr (kPair) mma_commit_pair(tfull_bar(acc), 0x3);
+        else mma_commit(tfull_bar(acc));
       }
       if (!ok) {
-        mma_commit(drain_bar);
+        if constexpr (kPair) mma_commit_pair(drain_bar, 0x1);
+        else mma_commit(drain_bar);
         mbar_wait(drain_bar, 0, nullptr, nullptr, 200000000ull);
       }
     }
     __syncwarp();
   } else {
     const int quad = warp & 3;
-    const int lane_row = quad * 32 + lane;  // TMEM lane = tile row in MMA orientation
+    const int lane_row = (int)rank * 128 + quad * 32 + lane;  // tile row (MMA orientation) of this TMEM lane
     for (int64_t j = 0;; ++j) {
       const int r = (int)(j % kRing);
-      const bool got = mbar_wait(rfull_bar(r), (uint32_t)((j / kRing) & 1), abort_flag, p.err);
+      const bool got = ring_wait(rfull_bar(r), (uint32_t)((j / kRing) & 1));
       if (!__all_sync(0xffffffffu, got)) break;  // leave together (tcgen05.ld below is warp-collective)
       const int64_t g = ring[r];
       __syncwarp();
-      if (lane == 0) mbar_arrive(rempty_bar(r));
+      if (lane == 0) ring_release(r);
       if (g < 0) break;
       const GroupedProblem* pr;
       int64_t tr, tc;
@@ -248,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
       if (!__all_sync(0xffffffffu, ready)) break;
       tc_fence_after();
       const int64_t N = pr->N, M = pr->M;
-      const int64_t rr = tr * 128 + lane_row;  // row of C (normal) or column of C (swap)
+      const int64_t rr = tr * pr->tile_rows + lane_row;  // row of C (normal) or column of C (swap)
       for (int ch = 0; ch < pr->bn / 32; ++ch) {
         uint32_t v[32];
         tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * 256 + ch * 32), v);
@@ -274,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
               if (c0 + i < N) {
                 const int64_t e = pr->count_base + rr * N + c0 + i;
                 atomicAdd(p.counts + e, 1u);
-                p.owner[e] = (int32_t)blockIdx.x;
+                p.owner[e] = prog;
               }
           }
         } else {
@@ -288,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
               if constexpr (kCount) {
                 const int64_t e = pr->count_base + m * N + rr;
                 atomicAdd(p.counts + e, 1u);
-                p.owner[e] = (int32_t)blockIdx.x;
+                p.owner[e] = prog;
               }
             }
           }
@@ -296,14 +345,19 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(tempty_bar(acc));
+      if (lane == 0) {
+        if constexpr (kPair) mbar_arrive_cluster(mapa(tempty_bar(acc), 0));
+        else mbar_arrive(tempty_bar(acc));
+      }
     }
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (kPair) cluster_sync();  // the peer no longer touches our shared memory / TMEM
+  else __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem_base, 512);
+    if constexpr (kPair) tmem_dealloc_pair(tmem_base, 512);
+    else tmem_dealloc(tmem_base, 512);
   }
 }
 
@@ -341,7 +395,7 @@ using namespace tp;
 extern "C" {
 
 tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int32_t n, int32_t swap_max_m,
-                                 tp_grouped_plan** out) {
+                                 int32_t cta_pair, tp_grouped_plan** out) {
   if (!ctx || !probs || !out) return fail(TP_ERR_INVALID, "null argument");
   *out = nullptr;
   if (n < 1 || n > kMaxProblems) return fail(TP_ERR_INVALID, "group size must be 1..256");
@@ -356,6 +410,8 @@ tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int3
   auto* plan = new tp_grouped_plan();
   plan->ctx = ctx;
   plan->n = n;
+  plan->pair = cta_pair != 0;
+  const int32_t trows = plan->pair ? 256 : 128;
   auto cleanup = [&](tp_status s) {
     for (auto* q : plan->outs) tp_partition_destroy(q);
     delete plan;
@@ -387,24 +443,27 @@ tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int3
     g.swap = M <= swap_max_m ? 1 : 0;
     tp_status s;
     int64_t tile_rows, tile_cols;
+    g.tile_rows = trows;
     if (g.swap) {
       g.bn = (int32_t)(((M + 31) / 32) * 32);
-      g.tiles_r = (N + 127) / 128;
+      g.box_y = plan->pair ? g.bn / 2 : g.bn;
+      g.tiles_r = (N + trows - 1) / trows;
       g.tiles_c = 1;
       s = kmajor_map(&g.map_x, b.ptr, N, K, ldb, 128);
-      if (s == TP_OK) s = kmajor_map(&g.map_y, a.ptr, M, K, lda, g.bn);
+      if (s == TP_OK) s = kmajor_map(&g.map_y, a.ptr, M, K, lda, g.box_y);
       tile_rows = M;
-      tile_cols = 128;
-      cost[i] = 128.0 * (double)K * 2.0 / 44e9 + 2.0 * 128 * g.bn * K / 1.2e13;
+      tile_cols = trows;
+      cost[i] = trows * (double)K * 2.0 / 44e9 + 2.0 * trows * g.bn * K / 1.2e13;
     } else {
       g.bn = 256;
-      g.tiles_r = (M + 127) / 128;
+      g.box_y = plan->pair ? 128 : 256;
+      g.tiles_r = (M + trows - 1) / trows;
       g.tiles_c = (N + 255) / 256;
       s = kmajor_map(&g.map_x, a.ptr, M, K, lda, 128);
-      if (s == TP_OK) s = kmajor_map(&g.map_y, b.ptr, N, K, ldb, 256);
-      tile_rows = 128;
+      if (s == TP_OK) s = kmajor_map(&g.map_y, b.ptr, N, K, ldb, g.box_y);
+      tile_rows = trows;
       tile_cols = 256;
-      cost[i] = 2.0 * 128 * 256 * (double)K / 1.2e13;
+      cost[i] = 2.0 * trows * 256 * (double)K / (plan->pair ? 2.4e13 : 1.2e13);
     }
     if (s != TP_OK) return cleanup(s);
     g.count_base = elems;
@@ -422,25 +481,57 @@ tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int3
     plan->ins.push_back(a);
     plan->ins.push_back(b);
   }
-  // queue order: most expensive tiles first (longest processing time first)
+  // Queue order. Tiles of swapped problems stream B from HBM, the others are
+  // tensor-core bound; each stream is ordered most expensive problem first
+  // (longest processing time first) and the two are merged in proportion to
+  // their total cost, so that tiles running at the same time use both HBM
+  // and the tensor cores.
+  std::vector<int> mem_p, comp_p;
+  for (int i = 0; i < n; ++i) (host[i].swap ? mem_p : comp_p).push_back(i);
+  auto by_cost = [&](int x, int y) { return cost[x] > cost[y]; };
+  std::stable_sort(mem_p.begin(), mem_p.end(), by_cost);
+  std::stable_sort(comp_p.begin(), comp_p.end(), by_cost);
+  auto expand = [&](const std::vector<int>& ps, std::vector<std::pair<int64_t, double>>& out) {
+    for (int i : ps)
+      for (int64_t t = 0; t < host[i].tiles_r * host[i].tiles_c; ++t) out.push_back({((int64_t)i << 32) | t, cost[i]});
+  };
+  std::vector<std::pair<int64_t, double>> mem_t, comp_t;
+  expand(mem_p, mem_t);
+  expand(comp_p, comp_t);
+  double mem_total = 0, comp_total = 0;
+  for (auto& x : mem_t) mem_total += x.second;
+  for (auto& x : comp_t) comp_total += x.second;
+  std::vector<int64_t> slots;
+  slots.reserve(mem_t.size() + comp_t.size());
+  size_t im = 0, ic = 0;
+  double dm = 0, dc = 0;
+  while (im < mem_t.size() || ic < comp_t.size()) {
+    const bool take_mem = ic >= comp_t.size() ||
+                          (im < mem_t.size() && dm / std::max(mem_total, 1e-30) <= dc / std::max(comp_total, 1e-30));
+    if (take_mem) {
+      dm += mem_t[im].second;
+      slots.push_back(mem_t[im++].first);
+    } else {
+      dc += comp_t[ic].second;
+      slots.push_back(comp_t[ic++].first);
+    }
+  }
   plan->order.resize(n);
   std::iota(plan->order.begin(), plan->order.end(), 0);
-  std::stable_sort(plan->order.begin(), plan->order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-  std::vector<GroupedProblem> ordered(n);
-  int64_t slot = 0;
-  for (int q = 0; q < n; ++q) {
-    ordered[q] = host[plan->order[q]];
-    ordered[q].tile_base = slot;
-    slot += ordered[q].tiles_r * ordered[q].tiles_c;
-  }
+  int64_t slot = (int64_t)slots.size();
+  std::vector<GroupedProblem>& ordered = host;
   plan->total_tiles = slot;
   plan->total_elems = elems;
   if (slot >= (int64_t(1) << 31)) return cleanup(fail(TP_ERR_UNSUPPORTED, "more than 2^31 tiles in a group"));
   cudaError_t e = cudaMalloc(&plan->d_probs, sizeof(GroupedProblem) * n);
   if (e == cudaSuccess)
     e = cudaMemcpy(plan->d_probs, ordered.data(), sizeof(GroupedProblem) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&plan->d_slots, sizeof(int64_t) * std::max<int64_t>(slot, 1));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(plan->d_slots, slots.data(), sizeof(int64_t) * slot, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(plan->d_probs);
+    cudaFree(plan->d_slots);
     return cleanup(cuda_fail(e, "uploading the problem table"));
   }
   *out = plan;
@@ -465,6 +556,7 @@ tp_status tp_grouped_plan_destroy(tp_grouped_plan* plan) {
     if (q->busy.load()) return fail(TP_ERR_BUSY, "the group has work in flight");
   for (auto* q : plan->outs) tp_partition_destroy(q);
   cudaFree(plan->d_probs);
+  cudaFree(plan->d_slots);
   delete plan;
   return TP_OK;
 }
@@ -486,20 +578,46 @@ tp_status tp_grouped_gemm(tp_ctx* ctx, tp_grouped_plan* plan, int32_t num_progra
   }
   GroupedArgs a{};
   a.probs = plan->d_probs;
+  a.slot_map = plan->d_slots;
   a.n = plan->n;
   a.total = plan->total_tiles;
   a.queue = q;
   a.err = ctx->d_err;
   a.counts = ex->write_counts;
   a.owner = ex->write_owner;
-  int grid = num_programs > 0 ? num_programs : ctx->sm_count;
-  if (grid > plan->total_tiles) grid = (int)plan->total_tiles;
-  const size_t smem = 1024 + (kStageX + kStageY) * kStages + 168 + 8 + 8 * kRing + 8 * kMaxProblems;
-  auto k = a.counts ? grouped_kernel<true> : grouped_kernel<false>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) {
-    k<<<grid, kThreads, smem, o.stream>>>(a);
-    e = cudaGetLastError();
+  const bool pair = plan->pair;
+  int64_t programs = num_programs > 0 ? num_programs : (pair ? ctx->sm_count / 2 : ctx->sm_count);
+  if (programs > plan->total_tiles) programs = plan->total_tiles;
+  if (programs < 1) {
+    o.abort();
+    return fail(TP_ERR_INVALID, "the plan has no tiles");
+  }
+  const int grid = (int)(pair ? 2 * programs : programs);
+  size_t smem;
+  cudaError_t e;
+  auto launch = [&](auto kernel, size_t bytes, int cluster) {
+    cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (err != cudaSuccess) return err;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)grid);
+    lc.blockDim = dim3(kThreads);
+    lc.dynamicSmemBytes = bytes;
+    lc.stream = o.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, kernel, a);
+  };
+  if (pair) {
+    smem = 1024 + (kStageX + Ring<true>::kStageY) * Ring<true>::kStages + 232 + kWordsBytes;
+    e = a.counts ? launch(grouped_kernel<true, true>, smem, 2) : launch(grouped_kernel<true, false>, smem, 2);
+  } else {
+    smem = 1024 + (kStageX + Ring<false>::kStageY) * Ring<false>::kStages + 232 + kWordsBytes;
+    e = a.counts ? launch(grouped_kernel<false, true>, smem, 1) : launch(grouped_kernel<false, false>, smem, 1);
   }
   return o.end(e);
 }

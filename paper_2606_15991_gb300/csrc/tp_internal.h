@@ -44,9 +44,11 @@ struct tp_ctx {
   int* d_err = nullptr;             // device error word (tp::DeviceError)
   unsigned* d_queue = nullptr;      // tile-queue counters (kQueueSlots)
   float* d_scratch = nullptr;       // small float scratch (kScratchFloats)
+  float* d_partial = nullptr;       // matrix-vector partial sums (kPartialFloats)
   std::atomic<uint32_t> queue_slot{0};
   static constexpr int kQueueSlots = 256;
   static constexpr int kScratchFloats = 4096;
+  static constexpr int64_t kPartialFloats = int64_t(1) << 20;
 };
 
 struct tp_partition {

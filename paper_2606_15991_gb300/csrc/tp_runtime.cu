@@ -273,12 +273,14 @@ tp_status tp_ctx_create(int32_t device, tp_ctx** out) {
   e = cudaMalloc(&c->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_queue, sizeof(unsigned) * tp_ctx::kQueueSlots);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_scratch, sizeof(float) * tp_ctx::kScratchFloats);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_partial, sizeof(float) * tp_ctx::kPartialFloats);
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_queue, 0, sizeof(unsigned) * tp_ctx::kQueueSlots);
   if (e != cudaSuccess) {
     cudaFree(c->d_err);
     cudaFree(c->d_queue);
     cudaFree(c->d_scratch);
+    cudaFree(c->d_partial);
     delete c;
     return cuda_fail(e, "allocating context workspace");
   }
@@ -296,6 +298,7 @@ tp_status tp_ctx_destroy(tp_ctx* ctx) {
   cudaFree(ctx->d_err);
   cudaFree(ctx->d_queue);
   cudaFree(ctx->d_scratch);
+  cudaFree(ctx->d_partial);
   delete ctx;
   return TP_OK;
 }

@@ -32,8 +32,8 @@ def _problems(shapes, kind="normal", seed=0):
     return probs
 
 
-def _run(ctx, probs, count=False, programs=0):
-    plan = tp.tp_grouped_plan_create(ctx, probs)
+def _run(ctx, probs, count=False, programs=0, pair=True):
+    plan = tp.tp_grouped_plan_create(ctx, probs, cta_pair=pair)
     total, swapped = tp.tp_grouped_plan_info(plan)
     counts = owner = None
     if count:
@@ -45,11 +45,13 @@ def _run(ctx, probs, count=False, programs=0):
     return total, swapped, counts, owner
 
 
-def test_small_group_parity_and_coverage(ctx):
+@pytest.mark.parametrize("pair", [True, False])
+def test_small_group_parity_and_coverage(ctx, pair):
     probs = _problems(SMALL)
-    total, swapped, counts, owner = _run(ctx, probs, count=True)
+    total, swapped, counts, owner = _run(ctx, probs, count=True, pair=pair)
     assert swapped == [m <= 256 for m, _, _ in SMALL]
-    cfg = [(128, ((m + 31) // 32) * 32, True) if m <= 256 else (128, 256, False) for m, _, _ in SMALL]
+    rows = 256 if pair else 128
+    cfg = [(rows, ((m + 31) // 32) * 32, True) if m <= 256 else (rows, 256, False) for m, _, _ in SMALL]
     assert total == sum(ogrouped.problem_tiles(m, n, *c)[0] for (m, n, _), c in zip(SMALL, cfg))
     for (a, b, c), shape in zip(probs, SMALL):
         assert ogemm.rel_frobenius(c.cpu(), ogemm.gemm(a.cpu(), b.cpu())) <= 1e-2, shape
@@ -57,18 +59,20 @@ def test_small_group_parity_and_coverage(ctx):
     assert owner.min().item() >= 0 and owner.max().item() < ctx.sm_count
 
 
+@pytest.mark.parametrize("pair", [True, False])
 @pytest.mark.parametrize("programs", [0, 1, 7])
-def test_integer_group_bit_exact(ctx, programs):
+def test_integer_group_bit_exact(ctx, programs, pair):
     probs = _problems(SMALL[:6], kind="int", seed=5)
-    _run(ctx, probs, programs=programs)
+    _run(ctx, probs, programs=programs, pair=pair)
     for a, b, c in probs:
         exact = ogemm.gemm(a.cpu(), b.cpu())
         assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(exact))
 
 
-def test_swap_threshold_and_single_problem(ctx):
+@pytest.mark.parametrize("pair", [True, False])
+def test_swap_threshold_and_single_problem(ctx, pair):
     probs = _problems([(200, 640, 256)])
-    plan = tp.tp_grouped_plan_create(ctx, probs, swap_max_m=0)      # force the normal orientation
+    plan = tp.tp_grouped_plan_create(ctx, probs, swap_max_m=0, cta_pair=pair)   # force the normal orientation
     assert tp.tp_grouped_plan_info(plan)[1] == [False]
     tp.tp_grouped_gemm(ctx, plan)
     tp.tp_grouped_plan_destroy(plan)
@@ -116,7 +120,8 @@ def test_async_busy_and_graph_replay(ctx):
     tp.tp_grouped_plan_destroy(plan)
 
 
-def test_full_group_sampled(ctx):
+@pytest.mark.parametrize("pair", [True, False])
+def test_full_group_sampled(ctx, pair):
     """The 64-problem group (M log-uniform on [1, 4096], four (K, N) pairs,
     seed 0), launched as the benchmark launches it; per problem, error over up
     to two sampled 128 x 128 blocks of C against FP64."""
@@ -128,7 +133,7 @@ def test_full_group_sampled(ctx):
         a = torch.randn(m, k, device="cuda", generator=g).to(torch.bfloat16)
         bt = torch.randn(n, k, device="cuda", generator=g).to(torch.bfloat16)
         probs.append((a, bt.t(), torch.full((m, n), float("nan"), dtype=torch.bfloat16, device="cuda")))
-    _run(ctx, probs)
+    _run(ctx, probs, pair=pair)
     got, ref = [], []
     for i, ((m, n, k), (a, b, c)) in enumerate(zip(shapes, probs)):
         gm, gn = -(-m // 128), -(-n // 128)
