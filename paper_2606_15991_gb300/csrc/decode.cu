@@ -188,22 +188,27 @@ __global__ void __launch_bounds__(kThreads) gemv_kernel(const __grid_constant__ 
   }
 }
 
-// Split-row matrix-vector product: each warp owns (row, part) units, no
-// block barriers, and writes one partial dot product per unit; the finish
-// kernel adds a row's partials in part order (deterministic) to h.
+// Split-K matrix-vector product for long rows: CTA b works on column slice
+// part = b % parts of every row, so it stages only that slice of x in shared
+// memory (several CTAs fit per SM); each warp computes (row, slice) dot
+// products with no block barrier and writes one partial per unit. The finish
+// kernel adds a row's partials in slice order (deterministic) to h.
 template <int kUnroll>
 __global__ void __launch_bounds__(kThreads) gemv_partial_kernel(const __grid_constant__ GemvArgs p, int parts,
                                                                 float* __restrict__ partial) {
   extern __shared__ float xs[];
-  for (int64_t i = threadIdx.x; i < p.k; i += kThreads) xs[i] = p.x[i];
+  const int part = (int)(blockIdx.x % parts);
+  const int64_t nv = p.k / 8;
+  const int64_t per = (nv + parts - 1) / parts;
+  const int64_t k0 = min(nv, part * per) * 8;
+  const int64_t k1 = part == parts - 1 ? p.k : min(nv, (part + 1) * per) * 8;
+  for (int64_t i = threadIdx.x; i < k1 - k0; i += kThreads) xs[i] = p.x[k0 + i];
   __syncthreads();
   const int lane = threadIdx.x & 31;
-  const int64_t units = p.rows * parts;
-  const int64_t nwarps = (int64_t)gridDim.x * kWarps;
-  for (int64_t u = (int64_t)blockIdx.x * kWarps + threadIdx.x / 32; u < units; u += nwarps) {
-    const int64_t r = u / parts;
-    const int part = (int)(u % parts);
-    const float s = row_dot<kUnroll>(p.w + r * p.ld, xs, p.k, part, parts);
+  const int64_t ctas = gridDim.x / parts;  // CTAs working on this slice
+  const int64_t nwarps = ctas * kWarps;
+  for (int64_t r = (int64_t)(blockIdx.x / parts) * kWarps + threadIdx.x / 32; r < p.rows; r += nwarps) {
+    const float s = row_dot<kUnroll>(p.w + r * p.ld, xs - k0, p.k, part, parts);
     if (lane == 0) partial[(int64_t)part * p.rows + r] = s;
   }
 }
@@ -437,17 +442,20 @@ tp_status tp_decode_down_residual(tp_ctx* ctx, tp_partition* h, const tp_tensor*
   a.counts = ex->write_counts;
   a.owner = ex->write_owner;
   cudaError_t e = cudaSuccess;
-  // few long rows: every row is split into 4 independent warp units whose
-  // partial sums (context scratch, allocated once) a finish kernel adds to h
-  const int parts = 4;
+  // few long rows: split K into 8 slices, one slice per CTA (so 4 CTAs fit
+  // per SM); partial sums go to context scratch allocated once, and a
+  // finish kernel adds them to h in slice order
+  const int parts = 8;
   if (d > 0 && ni > 0) {
-    if (d * parts > tp_ctx::kPartialFloats) e = launch_gemv<kResidual, 4, 4>(a, gemv_grid(ctx, ni), o.stream);
+    if (d * parts > tp_ctx::kPartialFloats || ni < 8 * parts) e = launch_gemv<kResidual, 4, 4>(a, gemv_grid(ctx, ni), o.stream);
     else {
-      const size_t smem = (size_t)((ni + 3) & ~int64_t(3)) * sizeof(float);
+      const int64_t slice = ((ni / 8 + parts - 1) / parts) * 8 + 8;
+      const size_t smem = (size_t)((slice + 3) & ~int64_t(3)) * sizeof(float);
       auto k = gemv_partial_kernel<8>;
       e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e == cudaSuccess) {
-        k<<<gemv_grid(ctx, ni), kThreads, smem, o.stream>>>(a, parts, ctx->d_partial);
+        const int grid = ctx->sm_count * 4;  // a multiple of `parts` on every GB300 SM count used (152)
+        k<<<(grid / parts) * parts, kThreads, smem, o.stream>>>(a, parts, ctx->d_partial);
         const unsigned fg = (unsigned)((d + kThreads - 1) / kThreads);
         if (a.counts)
           residual_finish_kernel<true><<<fg, kThreads, 0, o.stream>>>(a.y, ctx->d_partial, d, parts, a.counts, a.owner);
