@@ -172,6 +172,41 @@ def permute_heads_writes(B: int, H: int, M: int, D: int, BM: int, BD: int) -> li
     return writes
 
 
+def permute_heads(src, BM: int) -> np.ndarray:
+    """The head permutation that Listing 5 means to compute (§3.5), written
+    tile by tile: src has shape (B, H, M, D) with M/BM == H, and destination
+    tile (b, m, h) of shape (BM, D) is source tile (b, h, m), i.e.
+    dst[b, m, h*BM + i, :] = src[b, h, m*BM + i, :]."""
+    src = np.asarray(src)
+    B, H, M, D = src.shape
+    if M % BM or M // BM != H:
+        raise ValueError("needs M/BM == H")
+    dst = np.empty_like(src)
+    for b in range(B):
+        for m in range(H):
+            for h in range(H):
+                dst[b, m, h * BM:(h + 1) * BM, :] = src[b, h, m * BM:(m + 1) * BM, :]
+    return dst
+
+
+def permute_heads_race_candidates(src, BM: int) -> np.ndarray:
+    """For the index-swapped kernel of Listing 5: the H values that may land in
+    each destination element, shape (H, B, H, M, D). Destination tile
+    (b, m, h2) receives source tile (b, h1, m) from every h1, so candidate h1
+    of element (b, m, h2*BM + i, d) is src[b, h1, m*BM + i, d], for every h2."""
+    src = np.asarray(src)
+    B, H, M, D = src.shape
+    if M % BM or M // BM != H:
+        raise ValueError("needs M/BM == H")
+    out = np.empty((H,) + src.shape, src.dtype)
+    for h1 in range(H):
+        for b in range(B):
+            for m in range(H):
+                for h2 in range(H):
+                    out[h1, b, m, h2 * BM:(h2 + 1) * BM, :] = src[b, h1, m * BM:(m + 1) * BM, :]
+    return out
+
+
 def ceil_div(a: int, b: int) -> int:
     return -(-a // b)
 

@@ -1,6 +1,8 @@
 """Pins for the oracle's partitions and write-count checker (paper examples, hand-built maps)."""
 import os
 
+import itertools
+
 import numpy as np
 import pytest
 
@@ -92,6 +94,39 @@ def test_permute_heads_race_is_flagged():
     # the programs writing one destination differ only in h1
     e0 = [p for p, e in writes if e == 0]
     assert sorted(e0) == sorted(h1 * H + 0 for h1 in range(H))
+
+
+def test_permute_heads_worked_example():
+    # B=1, H=2, M=4, BM=2, D=1: heads [0 1 2 3] and [4 5 6 7]. Destination head
+    # m holds, for each source head h, source head h's sequence tile m.
+    src = np.arange(8, dtype=np.float64).reshape(1, 2, 4, 1)
+    dst = partition.permute_heads(src, 2)
+    assert dst[0, :, :, 0].tolist() == [[0, 1, 4, 5], [2, 3, 6, 7]]
+
+
+def test_permute_heads_is_an_involution_and_a_permutation():
+    # swapping the head index with the sequence-tile index twice is the identity
+    src = np.arange(2 * 3 * 6 * 4, dtype=np.float64).reshape(2, 3, 6, 4)
+    dst = partition.permute_heads(src, 2)
+    assert sorted(dst.reshape(-1)) == sorted(src.reshape(-1))
+    assert not np.array_equal(dst, src)
+    assert np.array_equal(partition.permute_heads(dst, 2), src)
+    # element-wise definition on every index
+    for b, m, r, d in itertools.product(range(2), range(3), range(6), range(4)):
+        h, i = divmod(r, 2)
+        assert dst[b, m, r, d] == src[b, h, m * 2 + i, d]
+
+
+def test_permute_heads_race_candidates():
+    src = np.arange(2 * 3 * 6 * 4, dtype=np.float64).reshape(2, 3, 6, 4)
+    cand = partition.permute_heads_race_candidates(src, 2)
+    good = partition.permute_heads(src, 2)
+    # the correct value is among the racing candidates (candidate h1 == h2)
+    assert np.any(cand == good[None], axis=0).all()
+    # each destination element has H distinct candidates, one per source head
+    assert all(len(set(cand[:, 0, 1, r, 2])) == 3 for r in range(6))
+    # candidates of one element come from the H heads of the same sequence tile
+    assert sorted(cand[:, 1, 2, 3, 1]) == sorted(src[1, h1, 2 * 2 + 1, 1] for h1 in range(3))
 
 
 @pytest.mark.parametrize("gm,gn,G", [(1, 1, 1), (7, 5, 1), (7, 5, 3), (16, 16, 8), (5, 9, 16)])
