@@ -122,6 +122,12 @@ def _barrier_max(value: float, ws: int, backend_dev):
     return float(t.item())
 
 
+def weak_scaling_value(ws: int, bytes_per_rank_step: float, max_ms_per_step: float) -> float:
+    """Whole-job TB/s: every rank moves the same bytes per step; the job's
+    step time is the slowest rank's."""
+    return ws * bytes_per_rank_step / (max_ms_per_step * 1e-3) / 1e12
+
+
 def _map_bytes(dt: str) -> int:
     return 3 * ESIZE[dt] * N_ELEMS
 
@@ -265,7 +271,7 @@ def run_ours(args):
     el_ms = _barrier_max(el_ms, ws, dev)
     ms_step = el_ms / args.steps
     step_bytes = sum(_map_bytes(dt) for _, dt in MAPS)
-    value = ws * step_bytes / (ms_step * 1e-3) / 1e12
+    value = weak_scaling_value(ws, step_bytes, ms_step)
 
     per_kernel = {}
     for k, lst in evs.items():
@@ -315,7 +321,7 @@ def run_ours(args):
         e2e_ms = _barrier_max((t1 - t0) * 1e3 / e2e_steps, ws, dev)
         h2d = sum(2 * ESIZE[dt] * N_ELEMS for _, dt in MAPS)
         d2h = sum(ESIZE[dt] * N_ELEMS for _, dt in MAPS)
-        e2e = {"value": ws * step_bytes / (e2e_ms * 1e-3) / 1e12, "unit": "TB/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": weak_scaling_value(ws, step_bytes, e2e_ms), "unit": "TB/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e2e_steps}
 
     rows = {}
@@ -619,6 +625,71 @@ def run_proposer(args):
         "s_collect_train": t_collect, "s_train": t_train}))
 
 
+def run_exec_modes(args):
+    """§5.2 execution-mode scaling: microseconds per op of an N-launch chain of
+    y = x * g over a 2048-element BF16 tile, N = 1..1000, in the sync, chained,
+    async and graph modes (host wall time; graph_device = CUDA-event time of
+    the replayed graph). Prints one JSON line."""
+    import torch
+
+    from paper_2606_15991_gb300 import build as _build
+
+    _build.build()
+    import paper_2606_15991_gb300 as tp
+    from paper_2606_15991_gb300 import experiments
+
+    ctx = tp.tp_ctx_create(0)
+    r = experiments.exec_mode_scaling(ctx, reps=args.reps)
+    r["case"] = "execution-mode scaling"
+    r["paper_rtx5090_us_per_op_at_1000"] = {"sync": 7.3, "chained": 3.4, "async": 3.4, "graph": 0.8}
+    print(json.dumps(r))
+
+
+def run_gemm_sweep(args):
+    """§5.1 safety-overhead sweep: BF16 GEMM M = N = K = 1024..32768, safe
+    (mapped partition) vs device-checked vs unchecked raw pointer vs plain
+    partition, cuBLAS for context. Prints one JSON line."""
+    import torch
+
+    from paper_2606_15991_gb300 import build as _build
+
+    _build.build()
+    import paper_2606_15991_gb300 as tp
+    from paper_2606_15991_gb300 import experiments
+
+    ctx = tp.tp_ctx_create(0)
+    peaks = _peaks()
+    sizes = tuple(int(x) for x in args.sizes.split(","))
+    log = (lambda m: print(m, file=sys.stderr, flush=True))
+    rows = experiments.gemm_size_sweep(ctx, sizes, log=log)
+    for r in rows:
+        r["frac_of_measured_bf16"] = {k: v / peaks["bf16_tflops"] for k, v in r["tflops"].items()}
+    print(json.dumps({"case": "gemm size sweep", "dtype": "bf16", "peak_bf16_tflops": peaks["bf16_tflops"],
+                      "peak_src": peaks["src"], "rows": rows,
+                      "paper_b200_8192": {"rust_pflops": 2.07, "vs_cublas": 0.964}}))
+
+
+def run_bimodal(args):
+    """Appendix B's bimodal work distribution: 2000 BF16 GEMMs (80% 512^3
+    interleaved with 20% 2048^3) drained serially, by S threads, by one host
+    thread over S streams, and as one grouped persistent launch; WU/ms (one
+    work unit = one GEMM). Prints one JSON line."""
+    import torch
+
+    from paper_2606_15991_gb300 import build as _build
+
+    _build.build()
+    import paper_2606_15991_gb300 as tp
+    from paper_2606_15991_gb300 import experiments
+
+    ctx = tp.tp_ctx_create(0)
+    log = (lambda m: print(m, file=sys.stderr, flush=True))
+    r = experiments.bimodal_queue(ctx, reps=args.reps if args.reps != 30 else 3, log=log)
+    r["case"] = "bimodal GEMM queue"
+    r["paper_b200_wu_per_ms"] = {"serial": 37, "plateau_S8": 77}
+    print(json.dumps(r))
+
+
 def run_kernel(args):
     """One kernel on a (small) case, warm-up plus a few launches: the target of
     ncu captures. Prints a one-line JSON summary."""
@@ -707,9 +778,11 @@ def main():
     ap.add_argument("--skip-rows", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--case", default="maps", choices=["maps", "proposer", "kernel"],
+    ap.add_argument("--case", default="maps", choices=["maps", "proposer", "kernel", "exec_modes", "gemm_sweep", "bimodal"],
                     help="maps: the benchmark step (default); proposer: the learned-proposer experiment; "
-                         "kernel: one kernel on a small case (profiling target)")
+                         "kernel: one kernel on a small case (profiling target); "
+                         "exec_modes: execution-mode scaling; gemm_sweep: GEMM size sweep; "
+                         "bimodal: bimodal GEMM queue")
     ap.add_argument("--kernel", default="map_axpy_f32",
                     help="map_axpy_f32|map_axpy_bf16|map_gelu_f32|map_gelu_bf16|gemm_bf16|gemm_fp8|grouped|decode")
     ap.add_argument("--size", type=int, default=4096)
@@ -718,11 +791,19 @@ def main():
     ap.add_argument("--train-shapes", type=int, default=625)
     ap.add_argument("--test-shapes", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=600)
+    ap.add_argument("--reps", type=int, default=30)
+    ap.add_argument("--sizes", default="1024,2048,4096,8192,16384,32768")
     args = ap.parse_args()
     if args.case == "proposer":
         run_proposer(args)
     elif args.case == "kernel":
         run_kernel(args)
+    elif args.case == "exec_modes":
+        run_exec_modes(args)
+    elif args.case == "gemm_sweep":
+        run_gemm_sweep(args)
+    elif args.case == "bimodal":
+        run_bimodal(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

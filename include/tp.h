@@ -21,11 +21,13 @@
  *   must not overlap the output's bytes (TP_ERR_ALIAS; §3.3, Appendix A).
  * - While an operation is in flight its partition is "busy" (the C analogue of
  *   the launch holding the tensor until the stream completes, §3.2 and §3.3):
- *   a second operation on it, an input reading its bytes, or destroying it
- *   returns TP_ERR_BUSY. SYNC releases it before returning; ASYNC releases it
- *   when tp_event_query reports completion or tp_event_wait returns; CAPTURE
- *   never marks it (the node has not run, §3.2) and graph replay marks the
- *   graph's partitions for the replay's duration.
+ *   an operation on another stream that writes it or reads its bytes, or
+ *   destroying or remapping it, returns TP_ERR_BUSY. Operations queued on the
+ *   same stream run after it in stream order and may read or rewrite it: the
+ *   analogue of chaining dependent work with `then` (§3.2). SYNC releases the
+ *   hold before returning; ASYNC when tp_event_query reports completion or
+ *   tp_event_wait returns; CAPTURE never marks it (the node has not run,
+ *   §3.2) and graph replay holds the graph's partitions for its duration.
  * - Element strides are in elements. Dtype sizes: F32 4, BF16 2, F8E4M3 1.
  * - Nothing is allocated during graph capture (§3.2's rule that captured
  *   nodes are non-allocating); a call that would need to returns TP_ERR_CAPTURE.
@@ -51,7 +53,8 @@ typedef enum tp_status {
   TP_ERR_UNSUPPORTED = 7, /* valid request this build does not implement         */
   TP_ERR_CUDA = 8,        /* a CUDA runtime/driver call failed                   */
   TP_ERR_TIMEOUT = 9,     /* a device-side wait hit its iteration cap            */
-  TP_ERR_SHAPE = 10       /* operand shapes disagree                             */
+  TP_ERR_SHAPE = 10,      /* operand shapes disagree                             */
+  TP_ERR_RACE = 11        /* checked launch: a tile stored twice or off the map  */
 } tp_status;
 
 typedef enum tp_dtype {
@@ -92,10 +95,33 @@ typedef struct tp_partition tp_partition;
 typedef struct tp_event tp_event;
 typedef struct tp_graph tp_graph;
 
+/* tp_exec.flags bits. */
+enum {
+  /* Device-checked launch (the debug build of a store, §3.6: a store is
+   * validated against the partition map before it is made). Before storing
+   * a tile, the storing program checks that the tile lies inside the
+   * partition's grid and that the map gives it to this program, then claims
+   * the tile in a bitmap held by the context; the launch's last CTA to
+   * finish clears the bitmap again, so the next launch and every graph
+   * replay start from a clear bitmap with no extra node enqueued. A tile
+   * that is off the grid, not the program's, or already claimed by another
+   * program (two programs writing one sub-tensor: a data race, Appendix A)
+   * is not stored, and the operation reports TP_ERR_RACE where it reports
+   * device errors (SYNC: on return; ASYNC: from tp_event_query /
+   * tp_event_wait; graph: from a SYNC replay or the replay's event).
+   * Supported by tp_gemm and tp_gemm_fp8 on the tensor-core path (tiles of
+   * 128 or 256 rows) and by tp_permute_heads_unchecked, up to 2^23 tiles per
+   * launch; other operations return TP_ERR_UNSUPPORTED when it is set. The
+   * bitmap and its finished-CTA counter are one per context: checked
+   * launches of one context must not overlap in time (order them on one
+   * stream), or they see each other's claims. */
+  TP_EXEC_CHECKED = 1
+};
+
 /* How an operation is executed. */
 typedef struct tp_exec {
   int32_t mode;            /* tp_mode                                          */
-  int32_t reserved;        /* must be 0                                        */
+  int32_t flags;           /* TP_EXEC_* bits; undefined bits must be 0         */
   void* stream;            /* cudaStream_t (borrowed); NULL = legacy stream    */
   tp_event* event;         /* ASYNC: event that completion is recorded into     */
   /* Optional write-count instrumentation (device pointers, NULL = off): each
@@ -230,6 +256,37 @@ tp_status tp_map_scale(tp_ctx* ctx, tp_partition* y, const tp_tensor* x, const t
 tp_status tp_map_add_accum(tp_ctx* ctx, tp_partition* c, const tp_tensor* a,
                            const tp_tensor* b, const tp_exec* ex);
 
+/* ------------------------------------------------------ head permutation */
+/* Head permutation of a rank-4 attention tensor (§3.5, Listing 5), in units of
+ * (BM, D) tiles: with src of shape (B, H, M, D) and M / BM == H,
+ *   dst[b, m, h*BM + i, :] = src[b, h, m*BM + i, :]   (0 <= m, h < H, 0 <= i < BM),
+ * i.e. destination tile (b, m, h) is source tile (b, h, m).
+ * tp_permute_heads is the partitioned form (§3.5): `dst` is a plain partition
+ * of the F32 output viewed as (B*H, M, D) with tiles (1, BM, D); program t
+ * stores only sub-tensor t, so no destination index is chosen in the kernel.
+ * `src` is a contiguous F32 tensor (B, H, M, D), not overlapping dst.
+ * Errors: TP_ERR_SHAPE (M % BM, M / BM != H, tiles not (1, BM, D)),
+ * TP_ERR_ALIAS, TP_ERR_BUSY, TP_ERR_UNSUPPORTED (non-contiguous, mapped
+ * partition), TP_ERR_CUDA. */
+tp_status tp_permute_heads(tp_ctx* ctx, tp_partition* dst, const tp_tensor* src, int64_t H, const tp_exec* ex);
+/* The same permutation written against raw device pointers (the unchecked
+ * escape hatch of §3.6), launched with Listing 5's grid (B*H, H, 1):
+ * program (bh1, h2), b = bh1 / H, h1 = bh1 % H, loops m over the H source
+ * tiles and stores source tile (b, h1, m) at destination tile (b, m, hd) with
+ * hd = h2 when `swap_bug` is non-zero (Listing 5's swapped index) and hd = h1
+ * otherwise (then only the programs with h2 == 0 store). With swap_bug, the H
+ * programs that differ in h1 store to the same destination tile: a data race
+ * whose surviving values are unordered; the write counts report H writes per
+ * element (program id = bh1 * H + h2). dst and src: contiguous F32
+ * (B, H, M, D) device buffers that must not overlap; M / BM == H keeps every
+ * store in bounds. `ex` gives the stream, the mode (no partition is held, so
+ * nothing becomes busy), the optional write counts and TP_EXEC_CHECKED: the
+ * checked launch lets only the first program that claims a destination tile
+ * store it and reports TP_ERR_RACE when any claim was refused.
+ * Errors: TP_ERR_SHAPE, TP_ERR_INVALID, TP_ERR_ALIAS, TP_ERR_RACE, TP_ERR_CUDA. */
+tp_status tp_permute_heads_unchecked(tp_ctx* ctx, void* dst, const void* src, int64_t B, int64_t H, int64_t M,
+                                     int64_t D, int64_t BM, int32_t swap_bug, const tp_exec* ex);
+
 /* ------------------------------------------------------------------ GEMM */
 /* C = A . B with one C tile per program and a K loop (§3.6 Listing 6).
  * c: partition of a row-major M x N output whose tile is the GEMM tile.
@@ -246,6 +303,19 @@ tp_status tp_map_add_accum(tp_ctx* ctx, tp_partition* c, const tp_tensor* a,
  * TP_ERR_ALIAS, TP_ERR_BUSY, TP_ERR_UNSUPPORTED, TP_ERR_TIMEOUT, TP_ERR_CUDA. */
 tp_status tp_gemm(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_tensor* b,
                   const tp_gemm_config* cfg, const tp_exec* ex);
+
+/* The BF16 tensor-core GEMM against a raw output pointer: the unchecked
+ * baseline of §5.1 (the same schedule with manual raw-pointer output access).
+ * `c` is a contiguous BF16 M x N device buffer; A and B as for tp_gemm.
+ * cfg->bm (128 or 256) and cfg->bn give the tile; cfg->num_programs > 0
+ * maps tiles strided over that many programs (CTA pairs for bm = 256), 0
+ * launches one program per tile; cfg->stages and cfg->group_m as for tp_gemm.
+ * No partition is involved: nothing is checked against aliasing or work in
+ * flight and nothing is marked busy; the call only enqueues on `stream`.
+ * Errors: TP_ERR_INVALID, TP_ERR_RANK, TP_ERR_SHAPE, TP_ERR_ALIGN,
+ * TP_ERR_UNSUPPORTED, TP_ERR_CUDA. */
+tp_status tp_gemm_unchecked(tp_ctx* ctx, void* c, const tp_tensor* a, const tp_tensor* b, const tp_gemm_config* cfg,
+                            void* stream);
 
 /* ------------------------------------------------ FP8-E4M3 GEMM pipeline */
 /* Per-tensor-scaled FP8 GEMM (the FP8 workload; the paper's GEMM of §3.6 /
@@ -283,7 +353,7 @@ typedef struct tp_gemm_problem {
 
 typedef struct tp_grouped_plan tp_grouped_plan;
 
-/* Plans a group of 1..256 independent GEMMs for one persistent launch (the
+/* Plans a group of 1..65536 independent GEMMs for one persistent launch (the
  * many-uneven-GEMMs workload; the paper's nearest setting is its bimodal GEMM
  * queue, Appendix B). Every output tile of every problem becomes one slot of
  * a device queue, most expensive tiles first. Problems with M <= swap_max_m
@@ -398,6 +468,19 @@ tp_status tp_mlp_targets(const float* tflops, int32_t count, float* target, floa
  * proposal only selects among configs that compute the same C. */
 tp_status tp_propose(tp_ctx* ctx, tp_mlp* mlp, int64_t M, int64_t N, int64_t K, int32_t dtype, float min_score,
                      tp_gemm_config* out, float* score, int32_t* used_fallback);
+
+/* ------------------------------------------------------------ diagnostics */
+/* Exercises the failure path every pipelined kernel (the tensor-core GEMMs,
+ * the grouped GEMM) relies on: one GPU thread waits on a shared-memory
+ * mbarrier with the same bounded wait those kernels' roles use. With
+ * arrive != 0 the barrier is signalled first and the wait completes (TP_OK).
+ * With arrive == 0 nothing ever signals it: the wait gives up after
+ * `limit_ns` of GPU wall time (1e3..2e9), records a timeout in the context's
+ * error word and the kernel returns, so the operation reports TP_ERR_TIMEOUT
+ * where it reports device errors (SYNC: on return; ASYNC: from
+ * tp_event_query / tp_event_wait; graph: from the replay) and the context
+ * stays usable. No output is involved, so nothing becomes busy. */
+tp_status tp_diag_bounded_wait(tp_ctx* ctx, int64_t limit_ns, int32_t arrive, const tp_exec* ex);
 
 /* ------------------------------------------------- allocation-free entry */
 /* Queue-mapped z = alpha * x + y that needs no context and allocates nothing.

@@ -27,7 +27,8 @@ __all__ = [
     "tp_amax", "tp_quantize_fp8", "tp_gemm_fp8",
     "tp_grouped_plan_create", "tp_grouped_plan_info", "tp_grouped_plan_destroy", "tp_grouped_gemm",
     "tp_rmsnorm", "tp_gemv", "tp_silu_mul", "tp_residual_add", "tp_decode_norm_qkv_gu",
-    "tp_decode_down_residual", "DecodeChain",
+    "tp_decode_down_residual", "DecodeChain", "tp_permute_heads", "tp_permute_heads_unchecked",
+    "tp_gemm_unchecked", "tp_diag_bounded_wait",
     "tp_autotune_space", "tp_autotune", "tp_autotune_lookup", "tp_autotune_save", "tp_autotune_load",
     "tp_mlp_create", "tp_mlp_destroy", "tp_mlp_num_params", "tp_mlp_get_params", "tp_mlp_set_params",
     "tp_mlp_forward", "tp_mlp_loss_grad", "tp_mlp_train_step", "tp_mlp_save", "tp_mlp_load",
@@ -210,13 +211,14 @@ def tp_graph_destroy(g: Graph) -> None:
 
 
 def make_exec(mode: int = SYNC, stream=None, event: Event | None = None, write_counts=None,
-              write_owner=None) -> tp_exec:
+              write_owner=None, checked: bool = False) -> tp_exec:
     """tp_exec for `mode` on `stream` (torch.cuda.Stream, raw handle, or None =
     torch's current stream). write_counts / write_owner: optional uint32 /
-    int32 device tensors with one entry per output element."""
+    int32 device tensors with one entry per output element. checked: the
+    device-checked launch (TP_EXEC_CHECKED)."""
     ex = tp_exec()
     ex.mode = mode
-    ex.reserved = 0
+    ex.flags = _lib.EXEC_CHECKED if checked else 0
     ex.stream = _stream_handle(stream)
     ex.event = event.handle.value if event is not None else None
     ex.write_counts = write_counts.data_ptr() if write_counts is not None else None
@@ -261,6 +263,20 @@ def tp_gemm(ctx, c: Partition, a, b, cfg: tp_gemm_config | None = None, ex: tp_e
     da, db = tensor_desc(a), tensor_desc(b)
     call("tp_gemm", ctx.handle, c.handle, ctypes.byref(da), ctypes.byref(db),
          ctypes.byref(cfg) if cfg is not None else None, _ex(ex))
+
+
+def tp_gemm_unchecked(ctx, c, a, b, cfg: tp_gemm_config, stream=None) -> None:
+    """C = A . B into the raw contiguous BF16 tensor c (no partition; the
+    unchecked baseline). cfg.num_programs = 0 launches one program per tile."""
+    da, db = tensor_desc(a), tensor_desc(b)
+    call("tp_gemm_unchecked", ctx.handle, c.data_ptr(), ctypes.byref(da), ctypes.byref(db), ctypes.byref(cfg),
+         _stream_handle(stream))
+
+
+def tp_diag_bounded_wait(ctx, limit_ns: int, arrive: bool, ex: tp_exec | None = None) -> None:
+    """One bounded mbarrier wait on the GPU; never signalled (arrive=False),
+    it gives up after limit_ns and the call raises TPError(TP_ERR_TIMEOUT)."""
+    call("tp_diag_bounded_wait", ctx.handle, int(limit_ns), int(bool(arrive)), _ex(ex))
 
 
 def _dptr(t):
@@ -356,6 +372,20 @@ def tp_decode_norm_qkv_gu(ctx, qkv: Partition, a_out: Partition, h, gamma, w_qkv
 def tp_decode_down_residual(ctx, h: Partition, w_down, a_in, ex: tp_exec | None = None) -> None:
     call("tp_decode_down_residual", ctx.handle, h.handle, ctypes.byref(tensor_desc(w_down)),
          ctypes.byref(tensor_desc(a_in)), _ex(ex))
+
+
+def tp_permute_heads(ctx, dst: Partition, src, H: int, ex: tp_exec | None = None) -> None:
+    """Partitioned head permutation (§3.5): dst tile (b, m, h) = src tile
+    (b, h, m); dst is a partition of the (B*H, M, D) output with (1, BM, D) tiles."""
+    call("tp_permute_heads", ctx.handle, dst.handle, ctypes.byref(tensor_desc(src)), int(H), _ex(ex))
+
+
+def tp_permute_heads_unchecked(ctx, dst, src, BM: int, swap_bug: bool, ex: tp_exec | None = None) -> None:
+    """Raw-pointer head permutation with Listing 5's grid; swap_bug stores at
+    the swapped (racing) index. dst, src: contiguous F32 (B, H, M, D) tensors."""
+    B, H, M, D = src.shape
+    call("tp_permute_heads_unchecked", ctx.handle, dst.data_ptr(), src.data_ptr(), B, H, M, D, int(BM),
+         int(bool(swap_bug)), _ex(ex))
 
 
 class DecodeChain:

@@ -17,10 +17,12 @@ MAX_RANK = 8
 
 # tp_status
 OK, ERR_INVALID, ERR_RANK, ERR_ALIGN, ERR_ALIAS, ERR_BUSY, ERR_CAPTURE, ERR_UNSUPPORTED, ERR_CUDA, \
-    ERR_TIMEOUT, ERR_SHAPE = range(11)
+    ERR_TIMEOUT, ERR_SHAPE, ERR_RACE = range(12)
 STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_INVALID", 2: "TP_ERR_RANK", 3: "TP_ERR_ALIGN", 4: "TP_ERR_ALIAS",
                 5: "TP_ERR_BUSY", 6: "TP_ERR_CAPTURE", 7: "TP_ERR_UNSUPPORTED", 8: "TP_ERR_CUDA",
-                9: "TP_ERR_TIMEOUT", 10: "TP_ERR_SHAPE"}
+                9: "TP_ERR_TIMEOUT", 10: "TP_ERR_SHAPE", 11: "TP_ERR_RACE"}
+# tp_exec.flags
+EXEC_CHECKED = 1
 # tp_dtype
 F32, BF16, F8E4M3, F64, I32, U32, U8 = range(7)
 # tp_map_kind
@@ -35,7 +37,7 @@ class tp_tensor(ctypes.Structure):
 
 
 class tp_exec(ctypes.Structure):
-    _fields_ = [("mode", ctypes.c_int32), ("reserved", ctypes.c_int32), ("stream", ctypes.c_void_p),
+    _fields_ = [("mode", ctypes.c_int32), ("flags", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("event", ctypes.c_void_p), ("write_counts", ctypes.c_void_p),
                 ("write_owner", ctypes.c_void_p)]
 
@@ -132,6 +134,10 @@ _PROTOS = {
     "tp_mlp_targets": [_VP, _I32, _VP, _VP],
     "tp_propose": [_VP, _VP, _I64, _I64, _I64, _I32, ctypes.c_float, ctypes.POINTER(tp_gemm_config), _VP, _PI32],
     "tp_map_axpy_queue_noalloc": [_VP, _VP, _VP, _I32, _I64, _I64, _I32, ctypes.c_float, _VP],
+    "tp_diag_bounded_wait": [_VP, _I64, _I32, _PE],
+    "tp_gemm_unchecked": [_VP, _VP, _PT, _PT, ctypes.POINTER(tp_gemm_config), _VP],
+    "tp_permute_heads": [_VP, _VP, _PT, _I64, _PE],
+    "tp_permute_heads_unchecked": [_VP, _VP, _VP, _I64, _I64, _I64, _I64, _I64, _I32, _PE],
 }
 _RESTYPES = {"tp_error_string": ctypes.c_char_p, "tp_last_error_detail": ctypes.c_char_p}
 

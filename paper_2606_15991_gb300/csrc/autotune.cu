@@ -120,6 +120,7 @@ tp_status tp_autotune_space(int32_t dtype, tp_gemm_config* out, int32_t cap, int
 tp_status tp_autotune(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, int32_t reps,
                       tp_gemm_config* best, float* tflops_per_config, float* best_tflops) {
   if (!ctx) return fail(TP_ERR_INVALID, "null context");
+  DeviceGuard guard(ctx);
   if (dtype != TP_BF16 && dtype != TP_F8E4M3) return fail(TP_ERR_UNSUPPORTED, "dtype must be BF16 or F8E4M3");
   const int esize = dtype == TP_BF16 ? 2 : 1;
   if (M < 1 || N < 1 || K < 1 || (K * esize) % 16) return fail(TP_ERR_SHAPE, "need M, N, K >= 1 and K*esize % 16 == 0");

@@ -231,6 +231,7 @@ tp_status tp_gemm_fp8(tp_ctx* ctx, tp_partition* c, const tp_tensor* qa, const t
   if (!f8(qa->dtype) || !f8(qb->dtype) || c->t.dtype != TP_BF16)
     return fail(TP_ERR_UNSUPPORTED, "tp_gemm_fp8 takes E4M3 A and B and a BF16 C");
   Op o;
+  o.allow_checked = true;
   tp_status s = o.begin(ctx, ex, {c}, {qa, qb});
   if (s != TP_OK) return s;
   o.check_err = true;

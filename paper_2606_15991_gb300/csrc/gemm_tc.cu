@@ -21,6 +21,7 @@
 #include <mutex>
 
 #include "sm100_ptx.cuh"
+#include "tile_claim.cuh"
 #include "tp_internal.h"
 
 namespace tp {
@@ -48,6 +49,9 @@ struct TcArgs {
   int* err;             // context error word
   uint32_t* counts;     // write-count instrumentation (optional)
   int32_t* owner;
+  uint32_t* claims;     // checked launch: tile-claim bitmap (kChecked)
+  unsigned* claim_done; // checked launch: finished-CTA counter
+  int64_t claim_bits;   // bits this launch may set
 };
 
 __device__ __forceinline__ void raster(int64_t s, int64_t gm, int64_t gn, int64_t g, int64_t* tm, int64_t* tn) {
@@ -59,7 +63,7 @@ __device__ __forceinline__ void raster(int64_t s, int64_t gm, int64_t gn, int64_
   *tn = r / rows;
 }
 
-template <bool kF8, bool kPair, bool kCount>
+template <bool kF8, bool kPair, bool kCount, bool kChecked>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                    const __grid_constant__ TcArgs p) {
@@ -220,17 +224,36 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t s = prog; s < T; s += step, ++t) {
       const int acc = (int)(t & 1);
       const uint32_t use = (uint32_t)((t >> 1) & 1);
+      int64_t tm, tn;
+      raster(s, p.gm, p.gn, p.group_m, &tm, &tn);
+      bool store_ok = true;
+      if constexpr (kChecked) {
+        // validate the store against the map (the slot is this program's and
+        // its tile lies in the grid), then claim this warp's 32-row slice of
+        // the tile: (tile, CTA of the pair, lane quadrant). Done before the
+        // accumulator is ready, so the atomic's latency hides behind the K loop.
+        int ok = 1;
+        if (lane == 0) {
+          const bool on_map = s < T && (s - prog) % step == 0 && tm >= 0 && tm < p.gm && tn >= 0 && tn < p.gn;
+          if (!on_map) {
+            record_device_error(p.err, kDevRace);
+            ok = 0;
+          } else {
+            const int64_t id = ((tm * p.gn + tn) * (kPair ? 2 : 1) + rank) * 4 + quad;
+            ok = claim_tile(p.claims, id, p.err) ? 1 : 0;
+          }
+        }
+        store_ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
+      }
       const bool ready = mbar_wait(tfull_bar(acc), use, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ready)) break;  // leave together (tcgen05.ld is warp-collective)
       tc_fence_after();
-      int64_t tm, tn;
-      raster(s, p.gm, p.gn, p.group_m, &tm, &tn);
       const int64_t row = tm * tile_m + row_in_tile;
       const int64_t col0 = tn * p.bn;
       __nv_bfloat16* crow = p.c + row * p.N;
       const bool row_ok = row < p.M;
       const bool vec_ok = p.c_vec != 0;
-      for (int ch = 0; ch < p.bn / 32; ++ch) {
+      for (int ch = 0; ch < p.bn / 32 && store_ok; ++ch) {
         uint32_t r[32];
         tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * p.bn + ch * 32), r);
         tmem_ld_wait();
@@ -274,6 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if constexpr (kPair) tmem_dealloc_pair(tmem_base, (uint32_t)p.tmem_cols);
     else tmem_dealloc(tmem_base, (uint32_t)p.tmem_cols);
   }
+  if constexpr (kChecked) claims_finish(p.claims, p.claim_bits, p.claim_done, gridDim.x);
 }
 
 // ---------------------------------------------------------------- host side
@@ -310,10 +334,10 @@ tp_status make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t k, i
   return TP_OK;
 }
 
-template <bool kF8, bool kPair, bool kCount>
+template <bool kF8, bool kPair, bool kCount, bool kChecked>
 cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& p, int grid, size_t smem,
                           cudaStream_t st) {
-  auto k = gemm_tc_kernel<kF8, kPair, kCount>;
+  auto k = gemm_tc_kernel<kF8, kPair, kCount, kChecked>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
@@ -335,13 +359,20 @@ cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const Tc
   return cudaLaunchKernelEx(&cfg, k, ma, mb, p);
 }
 
+template <bool kF8, bool kPair>
+cudaError_t launch_inst(bool count, bool checked, const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& p,
+                        int grid, size_t smem, cudaStream_t st) {
+  if (checked) return count ? launch_kernel<kF8, kPair, true, true>(ma, mb, p, grid, smem, st)
+                            : launch_kernel<kF8, kPair, false, true>(ma, mb, p, grid, smem, st);
+  return count ? launch_kernel<kF8, kPair, true, false>(ma, mb, p, grid, smem, st)
+               : launch_kernel<kF8, kPair, false, false>(ma, mb, p, grid, smem, st);
+}
+
 template <bool kF8>
-cudaError_t launch_any(bool pair, bool count, const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& p,
-                       int grid, size_t smem, cudaStream_t st) {
-  if (pair) return count ? launch_kernel<kF8, true, true>(ma, mb, p, grid, smem, st)
-                         : launch_kernel<kF8, true, false>(ma, mb, p, grid, smem, st);
-  return count ? launch_kernel<kF8, false, true>(ma, mb, p, grid, smem, st)
-               : launch_kernel<kF8, false, false>(ma, mb, p, grid, smem, st);
+cudaError_t launch_any(bool pair, bool count, bool checked, const CUtensorMap& ma, const CUtensorMap& mb,
+                       const TcArgs& p, int grid, size_t smem, cudaStream_t st) {
+  return pair ? launch_inst<kF8, true>(count, checked, ma, mb, p, grid, smem, st)
+              : launch_inst<kF8, false>(count, checked, ma, mb, p, grid, smem, st);
 }
 
 }  // namespace
@@ -409,8 +440,14 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   const int64_t grid = pair ? 2 * progs : progs;
   if (grid > 0x7fffffff) return fail(TP_ERR_UNSUPPORTED, "too many tile programs");
   const bool count = ex->write_counts != nullptr;
-  cudaError_t e = esize == 2 ? launch_any<false>(pair, count, ma, mb, p, (int)grid, smem, stream)
-                             : launch_any<true>(pair, count, ma, mb, p, (int)grid, smem, stream);
+  const bool checked = (ex->flags & TP_EXEC_CHECKED) != 0;
+  if (checked) {
+    p.claim_bits = c->num_tiles * (pair ? 8 : 4);
+    s = claims_for(ctx, p.claim_bits, &p.claims, &p.claim_done);
+    if (s != TP_OK) return s;
+  }
+  cudaError_t e = esize == 2 ? launch_any<false>(pair, count, checked, ma, mb, p, (int)grid, smem, stream)
+                             : launch_any<true>(pair, count, checked, ma, mb, p, (int)grid, smem, stream);
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core GEMM launch");
   return TP_OK;
 }

@@ -63,7 +63,7 @@ using namespace sm100;
 
 constexpr int kThreads = 192;
 constexpr int kRing = 4;
-constexpr int kMaxProblems = 256;
+constexpr int kMaxProblems = 1 << 16;
 constexpr uint32_t kStageX = 128 * 128;   // 128 rows x 128 bytes per CTA
 // B-operand rows per CTA and stage count: one CTA holds up to 256 rows
 // (4 stages of 48 KB); a CTA of a pair holds up to 128 (6 stages of 32 KB).
@@ -398,7 +398,8 @@ tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int3
                                  int32_t cta_pair, tp_grouped_plan** out) {
   if (!ctx || !probs || !out) return fail(TP_ERR_INVALID, "null argument");
   *out = nullptr;
-  if (n < 1 || n > kMaxProblems) return fail(TP_ERR_INVALID, "group size must be 1..256");
+  DeviceGuard guard(ctx);
+  if (n < 1 || n > kMaxProblems) return fail(TP_ERR_INVALID, "group size must be 1..65536");
   if (swap_max_m < 0) swap_max_m = 256;
   if (swap_max_m > 256) return fail(TP_ERR_INVALID, "swap_max_m must be <= 256");
   {

@@ -122,12 +122,23 @@ __device__ __forceinline__ typename Vec<T>::V pack(const float* f) {
 
 // Rank-1 path: tile length is a multiple of the vector width and all three
 // pointers are 16-byte aligned, so every tile starts on a vector boundary.
+// Programmatic dependent launch: map launches carry the programmatic
+// stream-serialization attribute, so the next launch on the stream may be
+// scheduled while this one runs. Each map kernel first waits until the grid
+// it depends on has completed and its memory is visible (a no-op when it was
+// not launched early), then lets its own dependents be scheduled.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 template <int OP, typename T, bool COUNT>
 __global__ void __launch_bounds__(kThreads) map_vec_kernel(const __grid_constant__ MapArgs a) {
   using V = typename Vec<T>::V;
   constexpr int W = Vec<T>::N;
   constexpr int U = 16 / W > 1 ? 16 / W : 1;  // vectors per thread per round: 4 (f32), 2 (bf16)
   __shared__ int64_t slot;
+  pdl_enter();
   T* __restrict__ out = static_cast<T*>(a.out);
   const T* __restrict__ x = static_cast<const T*>(a.x);
   const T* __restrict__ y = static_cast<const T*>(a.y);
@@ -191,6 +202,7 @@ __global__ void __launch_bounds__(kThreads) map_vec_kernel(const __grid_constant
 template <int OP, typename T, bool COUNT>
 __global__ void __launch_bounds__(kThreads) map_generic_kernel(const __grid_constant__ MapArgs a) {
   __shared__ int64_t slot;
+  pdl_enter();
   T* out = static_cast<T*>(a.out);
   const T* x = static_cast<const T*>(a.x);
   const T* y = static_cast<const T*>(a.y);
@@ -214,17 +226,27 @@ __global__ void __launch_bounds__(kThreads) map_generic_kernel(const __grid_cons
   }
 }
 
+template <typename K>
+cudaError_t launch_pdl(K kernel, const MapArgs& a, int64_t grid, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, a);
+}
+
 template <int OP, typename T>
 cudaError_t launch_typed(const MapArgs& a, bool vec, bool count, int64_t grid, cudaStream_t st) {
-  dim3 g((unsigned)grid), b(kThreads);
-  if (vec) {
-    if (count) map_vec_kernel<OP, T, true><<<g, b, 0, st>>>(a);
-    else map_vec_kernel<OP, T, false><<<g, b, 0, st>>>(a);
-  } else {
-    if (count) map_generic_kernel<OP, T, true><<<g, b, 0, st>>>(a);
-    else map_generic_kernel<OP, T, false><<<g, b, 0, st>>>(a);
-  }
-  return cudaGetLastError();
+  if (vec) return count ? launch_pdl(map_vec_kernel<OP, T, true>, a, grid, st)
+                        : launch_pdl(map_vec_kernel<OP, T, false>, a, grid, st);
+  return count ? launch_pdl(map_generic_kernel<OP, T, true>, a, grid, st)
+               : launch_pdl(map_generic_kernel<OP, T, false>, a, grid, st);
 }
 
 template <typename T>

@@ -214,6 +214,7 @@ tp_status tp_mlp_create(tp_ctx* ctx, int32_t in, int32_t hidden, int32_t out, in
                         const float* init_params, tp_mlp** mlp) {
   if (!ctx || !mlp || !init_params) return fail(TP_ERR_INVALID, "null argument");
   *mlp = nullptr;
+  DeviceGuard guard(ctx);
   if (in < 1 || hidden < 1 || out < 1 || hidden > 1024 || out > 1024 || max_batch < 1)
     return fail(TP_ERR_INVALID, "need 1 <= in, 1 <= hidden, out <= 1024, max_batch >= 1");
   {
@@ -262,12 +263,14 @@ tp_status tp_mlp_num_params(const tp_mlp* n, int64_t* count) {
 
 tp_status tp_mlp_get_params(const tp_mlp* n, float* host_out) {
   if (!n || !host_out) return fail(TP_ERR_INVALID, "null argument");
+  DeviceGuard guard(n->ctx);
   cudaError_t e = cudaMemcpy(host_out, n->params, n->nparams * sizeof(float), cudaMemcpyDeviceToHost);
   return e == cudaSuccess ? TP_OK : cuda_fail(e, "reading MLP parameters");
 }
 
 tp_status tp_mlp_set_params(tp_mlp* n, const float* host_in) {
   if (!n || !host_in) return fail(TP_ERR_INVALID, "null argument");
+  DeviceGuard guard(n->ctx);
   cudaError_t e = cudaMemcpy(n->params, host_in, n->nparams * sizeof(float), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(n->m, 0, n->nparams * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(n->v, 0, n->nparams * sizeof(float));
@@ -277,6 +280,7 @@ tp_status tp_mlp_set_params(tp_mlp* n, const float* host_in) {
 
 tp_status tp_mlp_forward(tp_mlp* n, const float* X, int32_t batch, float* Y, const tp_exec* ex) {
   if (!n || !X || !Y || !ex) return fail(TP_ERR_INVALID, "null argument");
+  DeviceGuard guard(n->ctx);
   if (batch < 1 || batch > n->max_batch) return fail(TP_ERR_SHAPE, "batch must be 1..max_batch");
   cudaStream_t st = static_cast<cudaStream_t>(ex->stream);
   tp_status s = launch_forward(n, X, batch, st);
@@ -289,6 +293,7 @@ tp_status tp_mlp_forward(tp_mlp* n, const float* X, int32_t batch, float* Y, con
 tp_status tp_mlp_loss_grad(tp_mlp* n, const float* X, const float* T, const float* V, int32_t batch, float* loss,
                            float* grads, const tp_exec* ex) {
   if (!n || !X || !T || !V || !ex) return fail(TP_ERR_INVALID, "null argument");
+  DeviceGuard guard(n->ctx);
   if (batch < 1 || batch > n->max_batch) return fail(TP_ERR_SHAPE, "batch must be 1..max_batch");
   cudaStream_t st = static_cast<cudaStream_t>(ex->stream);
   tp_status s = launch_loss_grad(n, X, T, V, batch, loss, st);
@@ -302,6 +307,7 @@ tp_status tp_mlp_loss_grad(tp_mlp* n, const float* X, const float* T, const floa
 tp_status tp_mlp_train_step(tp_mlp* n, const float* X, const float* T, const float* V, int32_t batch, float lr,
                             float* loss, const tp_exec* ex) {
   if (!n || !X || !T || !V || !ex) return fail(TP_ERR_INVALID, "null argument");
+  DeviceGuard guard(n->ctx);
   if (batch < 1 || batch > n->max_batch) return fail(TP_ERR_SHAPE, "batch must be 1..max_batch");
   cudaStream_t st = static_cast<cudaStream_t>(ex->stream);
   tp_status s = launch_loss_grad(n, X, T, V, batch, loss, st);
@@ -318,6 +324,7 @@ tp_status tp_mlp_train_step(tp_mlp* n, const float* X, const float* T, const flo
 
 tp_status tp_mlp_save(const tp_mlp* n, const char* path) {
   if (!n || !path) return fail(TP_ERR_INVALID, "null argument");
+  DeviceGuard guard(n->ctx);
   std::vector<float> h(n->nparams);
   tp_status s = tp_mlp_get_params(n, h.data());
   if (s != TP_OK) return s;
@@ -331,6 +338,7 @@ tp_status tp_mlp_save(const tp_mlp* n, const char* path) {
 
 tp_status tp_mlp_load(tp_mlp* n, const char* path) {
   if (!n || !path) return fail(TP_ERR_INVALID, "null argument");
+  DeviceGuard guard(n->ctx);
   FILE* f = std::fopen(path, "r");
   if (!f) return fail(TP_ERR_INVALID, std::string("cannot read ") + path);
   int a = 0, b = 0, c = 0;

@@ -5,8 +5,11 @@
 
 #include <atomic>
 #include <cstdint>
+#include <functional>
 #include <mutex>
 #include <string>
+#include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "tp.h"
@@ -18,6 +21,7 @@ enum DeviceError : int {
   kDevOk = 0,
   kDevTimeout = 1,     // a bounded wait ran out of iterations
   kDevBounds = 2,      // debug bounds check failed
+  kDevRace = 3,        // checked launch: a tile claimed twice or off the program's map
 };
 
 void set_detail(const std::string& s);
@@ -32,23 +36,46 @@ void byte_range(const tp_tensor& t, uintptr_t* lo, uintptr_t* hi);
 
 }  // namespace tp
 
+namespace tp {
+// `count` in-flight holds of one partition by work queued on one stream.
+struct Hold {
+  tp_partition* p;
+  cudaStream_t stream;
+  int64_t count;
+};
+using HoldKey = std::pair<tp_partition*, cudaStream_t>;
+struct HoldKeyHash {
+  size_t operator()(const HoldKey& k) const {
+    return std::hash<const void*>()(k.first) * 31u ^ std::hash<const void*>()(k.second);
+  }
+};
+}  // namespace tp
+
 struct tp_ctx {
   int32_t device = 0;
   int32_t sm_count = 0;
   int32_t cc_major = 0, cc_minor = 0;
   size_t smem_optin = 0;
   std::mutex mu;
-  std::vector<tp_partition*> busy;  // partitions with work in flight
+  // in-flight holds: (partition, stream) -> count; work chained on one
+  // stream adds to the entry's count
+  std::unordered_map<tp::HoldKey, int64_t, tp::HoldKeyHash> busy;
   tp_graph* capturing = nullptr;    // graph being captured, if any
   // Device workspace, allocated once at creation.
   int* d_err = nullptr;             // device error word (tp::DeviceError)
   unsigned* d_queue = nullptr;      // tile-queue counters (kQueueSlots)
   float* d_scratch = nullptr;       // small float scratch (kScratchFloats)
   float* d_partial = nullptr;       // matrix-vector partial sums (kPartialFloats)
+  uint32_t* d_claims = nullptr;     // tile-claim bitmap of checked launches (kClaimBits), all clear
+  unsigned* d_claim_done = nullptr; // CTAs of the running checked launch that finished
+  int* h_err_slots = nullptr;       // pinned host copies of the error word (kErrSlots)
+  std::atomic<uint32_t> err_slot{0};
+  static constexpr int kErrSlots = 256;
   std::atomic<uint32_t> queue_slot{0};
   static constexpr int kQueueSlots = 256;
   static constexpr int kScratchFloats = 4096;
   static constexpr int64_t kPartialFloats = int64_t(1) << 20;
+  static constexpr int64_t kClaimBits = int64_t(1) << 26;   // 8 MiB
 };
 
 struct tp_partition {
@@ -62,7 +89,7 @@ struct tp_partition {
   int64_t num_programs = 0;
   int32_t kind = TP_MAP_IDENTITY;
   uintptr_t lo = 0, hi = 0;  // output bytes
-  std::atomic<int> busy{0};
+  std::atomic<int> busy{0};  // number of in-flight holds
 };
 
 struct tp_event {
@@ -70,7 +97,9 @@ struct tp_event {
   cudaEvent_t ev = nullptr;
   bool recorded = false;
   bool check_err = false;
-  std::vector<tp_partition*> held;
+  cudaStream_t stream = nullptr;  // stream of the last record
+  int* h_err = nullptr;           // pinned copy of the error word, staged behind the work
+  std::vector<tp::Hold> held;   // holds released when the event completes (appended per op)
 };
 
 struct tp_graph {
@@ -85,6 +114,33 @@ struct tp_graph {
 
 namespace tp {
 
+// Makes the context's device current in the calling thread for one entry
+// point: a thread that has not used CUDA yet gets the device's primary
+// context bound (driver-API calls such as TMA descriptor encoding need a
+// current context), and a caller whose current device differs gets it back
+// when the guard goes out of scope.
+struct DeviceGuard {
+  int restore = -1;
+  DeviceGuard() = default;
+  explicit DeviceGuard(const tp_ctx* ctx) { bind(ctx); }
+  DeviceGuard(const DeviceGuard&) = delete;
+  DeviceGuard& operator=(const DeviceGuard&) = delete;
+  void bind(const tp_ctx* ctx) {
+    static thread_local bool bound = false;
+    if (!ctx) return;
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess) cur = -1;
+    if (bound && cur == ctx->device) return;
+    if (cudaSetDevice(ctx->device) == cudaSuccess) {
+      if (bound && cur >= 0 && cur != ctx->device && restore < 0) restore = cur;
+      bound = true;
+    }
+  }
+  ~DeviceGuard() {
+    if (restore >= 0) cudaSetDevice(restore);
+  }
+};
+
 // Launch protocol shared by every operation (§3.2 / §3.3 semantics):
 //   begin(): validate exec + aliasing + busy state, mark the output busy
 //            (SYNC/ASYNC) or record it into the capturing graph (CAPTURE);
@@ -97,6 +153,8 @@ struct Op {
   std::vector<tp_partition*> outs;
   bool check_err = false;   // kernel may write the device error word
   bool marked = false;
+  bool allow_checked = false;  // the op implements TP_EXEC_CHECKED (set before begin)
+  DeviceGuard device;          // the context's device is current while the op launches
 
   tp_status begin(tp_ctx* c, const tp_exec* e, std::initializer_list<tp_partition*> outputs,
                   std::initializer_list<const tp_tensor*> inputs);
@@ -111,6 +169,18 @@ struct Op {
 };
 
 tp_status read_device_error(tp_ctx* ctx);
+// Enqueue a copy of the device error word into pinned `slot` on `stream`
+// (behind the work already queued there).
+cudaError_t stage_device_error(tp_ctx* ctx, cudaStream_t stream, int* slot);
+// Status for a staged error word `h` (read after the stream or event
+// completed); clears the device word when it is set.
+tp_status take_device_error(tp_ctx* ctx, int h);
+// An ASYNC launch may record `ev` on `stream`: OK when the event tracks no
+// unfinished work on another stream (completed work is released first).
+tp_status event_claim(tp_event* ev, cudaStream_t stream);
+// The context's tile-claim bitmap for one checked launch (TP_EXEC_CHECKED)
+// that may set up to `bits` bits; the launch's last CTA clears them again.
+tp_status claims_for(tp_ctx* ctx, int64_t bits, uint32_t** claims, unsigned** done);
 // Reserve a tile-queue counter for one launch and zero it on `stream`.
 tp_status queue_counter(tp_ctx* ctx, cudaStream_t stream, unsigned** out);
 

@@ -69,28 +69,92 @@ static bool overlaps(uintptr_t a0, uintptr_t a1, uintptr_t b0, uintptr_t b1) {
   return a0 < a1 && b0 < b1 && a0 < b1 && b0 < a1;
 }
 
-static void release_locked(tp_ctx* ctx, tp_partition* p) {
-  p->busy.store(0);
-  auto& v = ctx->busy;
-  auto it = std::find(v.begin(), v.end(), p);
-  if (it != v.end()) v.erase(it);
+// Byte intervals sorted by start, with the running maximum of their ends:
+// "does [lo, hi) overlap any of them" in O(log n).
+struct Spans {
+  std::vector<std::pair<uintptr_t, uintptr_t>> v;
+  std::vector<uintptr_t> max_hi;
+  void add(uintptr_t lo, uintptr_t hi) {
+    if (lo < hi) v.push_back({lo, hi});
+  }
+  void build() {
+    std::sort(v.begin(), v.end());
+    max_hi.resize(v.size());
+    uintptr_t m = 0;
+    for (size_t i = 0; i < v.size(); ++i) max_hi[i] = m = std::max(m, v[i].second);
+  }
+  bool hit(uintptr_t lo, uintptr_t hi) const {
+    if (lo >= hi || v.empty()) return false;
+    // intervals starting before hi, then whether any of them ends after lo
+    auto it = std::lower_bound(v.begin(), v.end(), std::make_pair(hi, uintptr_t(0)));
+    if (it == v.begin()) return false;
+    return max_hi[(size_t)(it - v.begin()) - 1] > lo;
+  }
+  // some two of the intervals overlap
+  bool self_overlap() const {
+    for (size_t i = 1; i < v.size(); ++i)
+      if (v[i].first < max_hi[i - 1]) return true;
+    return false;
+  }
+};
+
+// Bytes of partitions held by in-flight work on streams other than `stream`
+// (every stream when `all_streams`).
+static void busy_spans(tp_ctx* ctx, cudaStream_t stream, bool all_streams, Spans* out) {
+  for (auto& kv : ctx->busy)
+    if (all_streams || kv.first.second != stream) out->add(kv.first.first->lo, kv.first.first->hi);
+  out->build();
 }
 
-static void release(tp_ctx* ctx, const std::vector<tp_partition*>& ps) {
+static void release_locked(tp_ctx* ctx, tp_partition* p, cudaStream_t st, int64_t n = 1) {
+  auto it = ctx->busy.find({p, st});
+  if (it == ctx->busy.end()) return;
+  const int64_t k = n < it->second ? n : it->second;
+  it->second -= k;
+  p->busy.fetch_sub((int)k);
+  if (it->second == 0) ctx->busy.erase(it);
+}
+
+static void release(tp_ctx* ctx, const std::vector<tp_partition*>& ps, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(ctx->mu);
-  for (auto* p : ps) release_locked(ctx, p);
+  for (auto* p : ps) release_locked(ctx, p, st);
+}
+
+static void hold_locked(tp_ctx* ctx, tp_partition* p, cudaStream_t st) {
+  p->busy.fetch_add(1);
+  ++ctx->busy[{p, st}];
+}
+
+static tp_status error_status(int h) {
+  if (h == kDevTimeout) return fail(TP_ERR_TIMEOUT, "a device-side wait hit its iteration cap");
+  if (h == kDevRace)
+    return fail(TP_ERR_RACE, "checked launch: a tile was stored twice or outside the storing program's map");
+  return fail(TP_ERR_INVALID, "device bounds check failed");
 }
 
 tp_status read_device_error(tp_ctx* ctx) {
   int h = 0;
   cudaError_t e = cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "reading device error word");
-  if (h != kDevOk) {
-    int zero = 0;
-    cudaMemcpy(ctx->d_err, &zero, sizeof(int), cudaMemcpyHostToDevice);
-    if (h == kDevTimeout) return fail(TP_ERR_TIMEOUT, "a device-side wait hit its iteration cap");
-    return fail(TP_ERR_INVALID, "device bounds check failed");
-  }
+  return take_device_error(ctx, h);
+}
+
+cudaError_t stage_device_error(tp_ctx* ctx, cudaStream_t stream, int* slot) {
+  *slot = 0;
+  return cudaMemcpyAsync(slot, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, stream);
+}
+
+tp_status take_device_error(tp_ctx* ctx, int h) {
+  if (h == kDevOk) return TP_OK;
+  int zero = 0;
+  cudaMemcpy(ctx->d_err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  return error_status(h);
+}
+
+tp_status claims_for(tp_ctx* ctx, int64_t bits, uint32_t** claims, unsigned** done) {
+  if (bits > tp_ctx::kClaimBits) return fail(TP_ERR_UNSUPPORTED, "too many tiles for a checked launch");
+  *claims = ctx->d_claims;
+  *done = ctx->d_claim_done;
   return TP_OK;
 }
 
@@ -120,13 +184,21 @@ tp_status Op::begin_impl(tp_ctx* c, const tp_exec* e, const std::vector<tp_parti
   ctx = c;
   ex = e;
   if (!ctx) return fail(TP_ERR_INVALID, "null context");
+  device.bind(ctx);
   if (!ex) return fail(TP_ERR_INVALID, "null tp_exec");
-  if (ex->mode < TP_SYNC || ex->mode > TP_CAPTURE || ex->reserved != 0)
+  if (ex->mode < TP_SYNC || ex->mode > TP_CAPTURE)
     return fail(TP_ERR_INVALID, "tp_exec.mode must be TP_SYNC, TP_ASYNC or TP_CAPTURE");
+  if (ex->flags & ~TP_EXEC_CHECKED) return fail(TP_ERR_INVALID, "undefined tp_exec.flags bits");
+  if ((ex->flags & TP_EXEC_CHECKED) && !allow_checked)
+    return fail(TP_ERR_UNSUPPORTED, "this operation has no device-checked launch (TP_EXEC_CHECKED)");
   if (ex->mode == TP_ASYNC && !ex->event) return fail(TP_ERR_INVALID, "TP_ASYNC needs tp_exec.event");
   if (ex->mode == TP_ASYNC && ex->event->ctx != ctx)
     return fail(TP_ERR_INVALID, "event belongs to another context");
   stream = static_cast<cudaStream_t>(ex->stream);
+  if (ex->mode == TP_ASYNC) {
+    tp_status es = event_claim(ex->event, stream);
+    if (es != TP_OK) return es;
+  }
   for (auto* p : outputs) {
     if (!p) return fail(TP_ERR_INVALID, "null output partition");
     if (p->ctx != ctx) return fail(TP_ERR_INVALID, "partition belongs to another context");
@@ -142,32 +214,32 @@ tp_status Op::begin_impl(tp_ctx* c, const tp_exec* e, const std::vector<tp_parti
     if (st != cudaStreamCaptureStatusActive || !ctx->capturing || ctx->capturing->stream != stream)
       return fail(TP_ERR_CAPTURE, "TP_CAPTURE needs the stream of the graph opened by tp_graph_begin");
   }
-  std::lock_guard<std::mutex> lk(ctx->mu);
   // Alias-XOR-mutability at the launch boundary (§3.3, Appendix A): inputs
   // must not overlap an output, outputs must not overlap each other.
-  for (size_t i = 0; i < outs.size(); ++i) {
-    for (auto* t : inputs) {
-      uintptr_t lo, hi;
-      byte_range(*t, &lo, &hi);
-      if (overlaps(lo, hi, outs[i]->lo, outs[i]->hi))
-        return fail(TP_ERR_ALIAS, "an input tensor overlaps the output partition");
-    }
-    for (size_t j = i + 1; j < outs.size(); ++j)
-      if (overlaps(outs[i]->lo, outs[i]->hi, outs[j]->lo, outs[j]->hi))
-        return fail(TP_ERR_ALIAS, "two output partitions overlap");
+  std::vector<std::pair<uintptr_t, uintptr_t>> in_bytes(inputs.size());
+  for (size_t i = 0; i < inputs.size(); ++i) byte_range(*inputs[i], &in_bytes[i].first, &in_bytes[i].second);
+  if (!outs.empty()) {
+    Spans out_spans;
+    for (auto* p : outs) out_spans.add(p->lo, p->hi);
+    out_spans.build();
+    if (out_spans.self_overlap()) return fail(TP_ERR_ALIAS, "two output partitions overlap");
+    for (auto& r : in_bytes)
+      if (out_spans.hit(r.first, r.second)) return fail(TP_ERR_ALIAS, "an input tensor overlaps the output partition");
   }
+  std::lock_guard<std::mutex> lk(ctx->mu);
   // In-flight work holds its output exclusively (§3.2: host access is given
-  // up until the stream completes).
-  for (auto* b : ctx->busy) {
+  // up until the stream completes). Work queued on the same stream runs after
+  // it in stream order and may read or rewrite it: the C analogue of chaining
+  // dependent operations with `then` (§3.2). Other streams conflict.
+  if (!ctx->busy.empty()) {
+    Spans held;
+    busy_spans(ctx, stream, ex->mode == TP_CAPTURE, &held);
     for (auto* p : outs)
-      if (p == b || overlaps(p->lo, p->hi, b->lo, b->hi))
-        return fail(TP_ERR_BUSY, "output partition has work in flight");
-    for (auto* t : inputs) {
-      uintptr_t lo, hi;
-      byte_range(*t, &lo, &hi);
-      if (overlaps(lo, hi, b->lo, b->hi))
-        return fail(TP_ERR_BUSY, "an input reads bytes of a partition with work in flight");
-    }
+      if (held.hit(p->lo, p->hi))
+        return fail(TP_ERR_BUSY, "output partition has work in flight on another stream");
+    for (auto& r : in_bytes)
+      if (held.hit(r.first, r.second))
+        return fail(TP_ERR_BUSY, "an input reads bytes of a partition with work in flight on another stream");
   }
   if (ex->mode == TP_CAPTURE) {
     for (auto* p : outs) {
@@ -175,23 +247,20 @@ tp_status Op::begin_impl(tp_ctx* c, const tp_exec* e, const std::vector<tp_parti
       if (std::find(v.begin(), v.end(), p) == v.end()) v.push_back(p);
     }
   } else {
-    for (auto* p : outs) {
-      p->busy.store(1);
-      ctx->busy.push_back(p);
-    }
+    for (auto* p : outs) hold_locked(ctx, p, stream);
     marked = true;
   }
   return TP_OK;
 }
 
 void Op::abort() {
-  if (marked) release(ctx, outs);
+  if (marked) release(ctx, outs, stream);
   marked = false;
 }
 
 tp_status Op::end(cudaError_t launch_err) {
   if (launch_err != cudaSuccess) {
-    if (marked) release(ctx, outs);
+    if (marked) release(ctx, outs, stream);
     return cuda_fail(launch_err, "kernel launch");
   }
   if (ex->mode == TP_CAPTURE) {
@@ -199,21 +268,30 @@ tp_status Op::end(cudaError_t launch_err) {
     return TP_OK;
   }
   if (ex->mode == TP_SYNC) {
-    cudaError_t e = cudaStreamSynchronize(stream);
-    release(ctx, outs);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    return check_err ? read_device_error(ctx) : TP_OK;
+    int* slot = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (check_err) {
+      slot = ctx->h_err_slots + ctx->err_slot.fetch_add(1) % tp_ctx::kErrSlots;
+      e = stage_device_error(ctx, stream, slot);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(stream);
+    release(ctx, outs, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "staging the device error word");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamSynchronize");
+    return check_err ? take_device_error(ctx, *slot) : TP_OK;
   }
   tp_event* ev = ex->event;
-  cudaError_t e = cudaEventRecord(ev->ev, stream);
+  cudaError_t e = check_err ? stage_device_error(ctx, stream, ev->h_err) : cudaSuccess;
+  if (e == cudaSuccess) e = cudaEventRecord(ev->ev, stream);
   if (e != cudaSuccess) {
-    release(ctx, outs);
+    release(ctx, outs, stream);
     return cuda_fail(e, "cudaEventRecord");
   }
   std::lock_guard<std::mutex> lk(ctx->mu);
   ev->recorded = true;
+  ev->stream = stream;
   ev->check_err |= check_err;
-  for (auto* p : outs) ev->held.push_back(p);
+  for (auto* p : outs) ev->held.push_back({p, stream, 1});
   return TP_OK;
 }
 
@@ -236,6 +314,7 @@ const char* tp_error_string(tp_status s) {
     case TP_ERR_CUDA: return "CUDA error";
     case TP_ERR_TIMEOUT: return "device wait timed out";
     case TP_ERR_SHAPE: return "shape mismatch";
+    case TP_ERR_RACE: return "checked launch found a tile stored twice or off the map";
   }
   return "unknown status";
 }
@@ -274,6 +353,11 @@ tp_status tp_ctx_create(int32_t device, tp_ctx** out) {
   if (e == cudaSuccess) e = cudaMalloc(&c->d_queue, sizeof(unsigned) * tp_ctx::kQueueSlots);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_scratch, sizeof(float) * tp_ctx::kScratchFloats);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_partial, sizeof(float) * tp_ctx::kPartialFloats);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_claims, (size_t)tp_ctx::kClaimBits / 8);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_claim_done, 256);
+  if (e == cudaSuccess) e = cudaMemset(c->d_claims, 0, (size_t)tp_ctx::kClaimBits / 8);
+  if (e == cudaSuccess) e = cudaMemset(c->d_claim_done, 0, 256);
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_err_slots, sizeof(int) * tp_ctx::kErrSlots);
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_queue, 0, sizeof(unsigned) * tp_ctx::kQueueSlots);
   if (e != cudaSuccess) {
@@ -281,6 +365,9 @@ tp_status tp_ctx_create(int32_t device, tp_ctx** out) {
     cudaFree(c->d_queue);
     cudaFree(c->d_scratch);
     cudaFree(c->d_partial);
+    cudaFree(c->d_claims);
+    cudaFree(c->d_claim_done);
+    cudaFreeHost(c->h_err_slots);
     delete c;
     return cuda_fail(e, "allocating context workspace");
   }
@@ -299,6 +386,9 @@ tp_status tp_ctx_destroy(tp_ctx* ctx) {
   cudaFree(ctx->d_queue);
   cudaFree(ctx->d_scratch);
   cudaFree(ctx->d_partial);
+  cudaFree(ctx->d_claims);
+  cudaFree(ctx->d_claim_done);
+  cudaFreeHost(ctx->h_err_slots);
   delete ctx;
   return TP_OK;
 }
@@ -404,7 +494,7 @@ tp_status tp_partition_query(const tp_partition* p, tp_partition_info* info) {
   }
   info->num_tiles = p->num_tiles;
   info->num_programs = p->num_programs;
-  info->busy = p->busy.load();
+  info->busy = p->busy.load() > 0 ? 1 : 0;
   return TP_OK;
 }
 
@@ -424,6 +514,7 @@ tp_status tp_partition_destroy(tp_partition* p) {
 
 tp_status tp_event_create(tp_ctx* ctx, tp_event** out) {
   if (!ctx || !out) return fail(TP_ERR_INVALID, "null argument");
+  DeviceGuard guard(ctx);
   auto* ev = new tp_event();
   ev->ctx = ctx;
   cudaError_t e = cudaEventCreateWithFlags(&ev->ev, cudaEventDisableTiming);
@@ -431,12 +522,19 @@ tp_status tp_event_create(tp_ctx* ctx, tp_event** out) {
     delete ev;
     return cuda_fail(e, "cudaEventCreate");
   }
+  e = cudaMallocHost(&ev->h_err, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaEventDestroy(ev->ev);
+    delete ev;
+    return cuda_fail(e, "cudaMallocHost");
+  }
+  *ev->h_err = 0;
   *out = ev;
   return TP_OK;
 }
 
 static tp_status event_complete(tp_event* ev) {
-  std::vector<tp_partition*> held;
+  std::vector<Hold> held;
   bool chk;
   {
     std::lock_guard<std::mutex> lk(ev->ctx->mu);
@@ -444,10 +542,25 @@ static tp_status event_complete(tp_event* ev) {
     chk = ev->check_err;
     ev->check_err = false;
     ev->recorded = false;
-    for (auto* p : held) release_locked(ev->ctx, p);
+    for (auto& h : held) release_locked(ev->ctx, h.p, h.stream, h.count);
   }
-  return chk ? read_device_error(ev->ctx) : TP_OK;
+  return chk ? take_device_error(ev->ctx, *ev->h_err) : TP_OK;
 }
+
+}  // extern "C"
+
+tp_status tp::event_claim(tp_event* ev, cudaStream_t stream) {
+  if (!ev->recorded || ev->stream == stream) return TP_OK;
+  // the event still tracks work on another stream: re-recording it here
+  // would release that work's holds when this stream's work completes
+  cudaError_t e = cudaEventQuery(ev->ev);
+  if (e == cudaErrorNotReady)
+    return fail(TP_ERR_BUSY, "the event tracks unfinished work on another stream; wait for it or use another event");
+  if (e != cudaSuccess) return cuda_fail(e, "cudaEventQuery");
+  return event_complete(ev);
+}
+
+extern "C" {
 
 tp_status tp_event_query(tp_event* ev, int32_t* done) {
   if (!ev || !done) return fail(TP_ERR_INVALID, "null argument");
@@ -481,12 +594,14 @@ tp_status tp_event_destroy(tp_event* ev) {
     event_complete(ev);
   }
   cudaEventDestroy(ev->ev);
+  cudaFreeHost(ev->h_err);
   delete ev;
   return TP_OK;
 }
 
 tp_status tp_graph_begin(tp_ctx* ctx, void* stream, tp_graph** out) {
   if (!ctx || !out) return fail(TP_ERR_INVALID, "null argument");
+  DeviceGuard guard(ctx);
   if (!stream) return fail(TP_ERR_INVALID, "graph capture needs a non-default stream");
   std::lock_guard<std::mutex> lk(ctx->mu);
   if (ctx->capturing) return fail(TP_ERR_CAPTURE, "this context is already capturing a graph");
@@ -528,33 +643,50 @@ tp_status tp_graph_replay(tp_graph* g, const tp_exec* ex) {
   cudaStream_t stream = static_cast<cudaStream_t>(ex->stream);
   {
     std::lock_guard<std::mutex> lk(ctx->mu);
-    for (auto* p : g->parts)
-      if (p->busy.load()) return fail(TP_ERR_BUSY, "a partition of the graph has work in flight");
-    for (auto* p : g->parts) {
-      p->busy.store(1);
-      ctx->busy.push_back(p);
+    if (!ctx->busy.empty()) {
+      Spans held;
+      busy_spans(ctx, stream, false, &held);
+      for (auto* p : g->parts)
+        if (held.hit(p->lo, p->hi))
+          return fail(TP_ERR_BUSY, "a partition of the graph has work in flight on another stream");
+    }
+    for (auto* p : g->parts) hold_locked(ctx, p, stream);
+  }
+  if (ex->mode == TP_ASYNC) {
+    tp_status es = event_claim(ex->event, stream);
+    if (es != TP_OK) {
+      release(ctx, g->parts, stream);
+      return es;
     }
   }
   cudaError_t e = cudaGraphLaunch(g->exec, stream);
   if (e != cudaSuccess) {
-    release(ctx, g->parts);
+    release(ctx, g->parts, stream);
     return cuda_fail(e, "cudaGraphLaunch");
   }
   if (ex->mode == TP_SYNC) {
-    e = cudaStreamSynchronize(stream);
-    release(ctx, g->parts);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-    return g->check_err ? read_device_error(ctx) : TP_OK;
+    int* slot = nullptr;
+    if (g->check_err) {
+      slot = ctx->h_err_slots + ctx->err_slot.fetch_add(1) % tp_ctx::kErrSlots;
+      e = stage_device_error(ctx, stream, slot);
+    }
+    cudaError_t e2 = cudaStreamSynchronize(stream);
+    release(ctx, g->parts, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "staging the device error word");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamSynchronize");
+    return g->check_err ? take_device_error(ctx, *slot) : TP_OK;
   }
-  e = cudaEventRecord(ex->event->ev, stream);
+  e = g->check_err ? stage_device_error(ctx, stream, ex->event->h_err) : cudaSuccess;
+  if (e == cudaSuccess) e = cudaEventRecord(ex->event->ev, stream);
   if (e != cudaSuccess) {
-    release(ctx, g->parts);
+    release(ctx, g->parts, stream);
     return cuda_fail(e, "cudaEventRecord");
   }
   std::lock_guard<std::mutex> lk(ctx->mu);
   ex->event->recorded = true;
+  ex->event->stream = stream;
   ex->event->check_err |= g->check_err;
-  for (auto* p : g->parts) ex->event->held.push_back(p);
+  for (auto* p : g->parts) ex->event->held.push_back({p, stream, 1});
   return TP_OK;
 }
 
@@ -643,6 +775,7 @@ tp_status tp_gemm(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_ten
   bool tc = a->dtype == TP_BF16 && c->t.dtype == TP_BF16;
   if (!simt && !tc) return fail(TP_ERR_UNSUPPORTED, "tp_gemm supports F32xF32->F32 and BF16xBF16->BF16");
   Op o;
+  o.allow_checked = tc;
   tp_status s = o.begin(ctx, ex, {c}, {a, b});
   if (s != TP_OK) return s;
   unsigned* q = nullptr;
@@ -661,6 +794,47 @@ tp_status tp_gemm(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_ten
     return s;
   }
   return o.end(cudaGetLastError());
+}
+
+tp_status tp_gemm_unchecked(tp_ctx* ctx, void* c, const tp_tensor* a, const tp_tensor* b, const tp_gemm_config* cfg,
+                            void* stream) {
+  if (!ctx || !c || !a || !b || !cfg) return fail(TP_ERR_INVALID, "null argument");
+  DeviceGuard guard(ctx);
+  if (a->rank != 2 || b->rank != 2) return fail(TP_ERR_RANK, "GEMM operands are rank 2");
+  if (a->dtype != TP_BF16 || b->dtype != TP_BF16) return fail(TP_ERR_UNSUPPORTED, "BF16 operands only");
+  const int64_t M = a->shape[0], K = a->shape[1], N = b->shape[1];
+  if (b->shape[0] != K) return fail(TP_ERR_SHAPE, "need A: M x K, B: K x N");
+  if (cfg->bm != 128 && cfg->bm != 256) return fail(TP_ERR_INVALID, "cfg.bm must be 128 or 256");
+  if (cfg->bn <= 0) return fail(TP_ERR_INVALID, "cfg.bn must be given");
+  // a stack descriptor of C's tiling; nothing is registered with the context
+  tp_partition p;
+  p.ctx = ctx;
+  p.t.ptr = c;
+  p.t.dtype = TP_BF16;
+  p.t.rank = 2;
+  p.t.shape[0] = M;
+  p.t.shape[1] = N;
+  p.t.strides[0] = N;
+  p.t.strides[1] = 1;
+  p.rank = 2;
+  p.shape[0] = M;
+  p.shape[1] = N;
+  p.tile[0] = cfg->bm;
+  p.tile[1] = cfg->bn;
+  p.grid[0] = (M + cfg->bm - 1) / cfg->bm;
+  p.grid[1] = (N + cfg->bn - 1) / cfg->bn;
+  p.num_tiles = p.grid[0] * p.grid[1];
+  if (cfg->num_programs > 0) {
+    p.kind = TP_MAP_STRIDED;
+    p.num_programs = cfg->num_programs < p.num_tiles ? cfg->num_programs : p.num_tiles;
+  } else {
+    p.kind = TP_MAP_IDENTITY;
+    p.num_programs = p.num_tiles;
+  }
+  tp_exec ex{};
+  ex.mode = TP_SYNC;
+  ex.stream = stream;
+  return launch_gemm_tc(ctx, &p, a, b, cfg, &ex, static_cast<cudaStream_t>(stream), nullptr);
 }
 
 }  // extern "C"

@@ -1,0 +1,61 @@
+"""The multi-process path of bench.py on CPU: two gloo ranks (one process
+per GPU on a GPU node) agree on the slowest rank's step time, read their
+rank from the launcher's environment, and the whole-job value is the
+world size times one rank's bytes over that time (weak scaling, no data
+exchange between ranks)."""
+import multiprocessing as mp
+import os
+import socket
+
+import pytest
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, ws, port, q):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "RANK": str(rank),
+                       "WORLD_SIZE": str(ws), "LOCAL_RANK": str(rank)})
+    import torch
+    import torch.distributed as dist
+
+    import bench
+
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    got_ws, got_rank, got_local = bench._dist()
+    ms = bench._barrier_max(10.0 + 5.0 * rank, ws, torch.device("cpu"))
+    value = bench.weak_scaling_value(got_ws, 3.0e9, ms)
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, got_ws, got_rank, got_local, ms, value))
+
+
+@pytest.mark.timeout(120)
+def test_two_gloo_ranks_take_the_max_step_time():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=90) for _ in procs)
+    for p in procs:
+        p.join(timeout=30)
+        assert p.exitcode == 0
+    for rank, ws, r, local, ms, value in out:
+        assert (ws, r, local) == (2, rank, rank)
+        assert ms == 15.0                                   # the slower rank's time, on every rank
+        assert value == pytest.approx(2 * 3.0e9 / 15e-3 / 1e12)
+
+
+def test_single_process_defaults(monkeypatch):
+    import bench
+
+    for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    assert bench._dist() == (1, 0, 0)
+    assert bench._barrier_max(7.0, 1, None) == 7.0
+    assert bench.weak_scaling_value(1, 1e12, 1000.0) == pytest.approx(1.0)

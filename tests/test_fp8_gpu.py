@@ -77,7 +77,7 @@ def test_quantize_zero_tensor_and_strided_map(ctx):
     assert scale.item() == 1.0 and int(q.view(torch.uint8).max()) == 0
 
 
-def _fp8_gemm(ctx, a, bt, bm=128, bn=128, P=None, group_m=1, count=False):
+def _fp8_gemm(ctx, a, bt, bm=128, bn=128, P=None, group_m=1, count=False, checked=False):
     qa, _, sa, _, _ = _quantize(ctx, a, 16)
     qbt, _, sb, _, _ = _quantize(ctx, bt, 16)
     m, n = a.shape[0], bt.shape[0]
@@ -90,21 +90,23 @@ def _fp8_gemm(ctx, a, bt, bm=128, bn=128, P=None, group_m=1, count=False):
         counts = torch.zeros(m * n, dtype=torch.int32, device="cuda")
         owner = torch.full((m * n,), -1, dtype=torch.int32, device="cuda")
     tp.tp_gemm_fp8(ctx, p, qa, qbt.t(), sa, sb, tp.gemm_config(bm=bm, bn=bn, group_m=group_m),
-                   tp.make_exec(write_counts=counts, write_owner=owner))
+                   tp.make_exec(write_counts=counts, write_owner=owner, checked=checked))
     info = tp.tp_partition_query(p)
     tp.tp_partition_destroy(p)
     return c, qa, qbt, sa, sb, counts, owner, info
 
 
+@pytest.mark.parametrize("checked", [False, True])
 @pytest.mark.parametrize("bm", [128, 256])
-def test_integer_inputs_exact(ctx, bm):
+def test_integer_inputs_exact(ctx, bm, checked):
     """Entries in [-7, 7] with amax 7: s = 64 (a power of two), every code and
     partial sum is exact, so C is the bf16 rounding of the exact product."""
     m, n, k = 256, 320, 512
     a = synth.tensor(synth.integers(m * k, 1, -7, 7), "bf16").reshape(m, k)
     bt = synth.tensor(synth.integers(n * k, 2, -7, 7), "bf16").reshape(n, k)
     a[0, 0], bt[0, 0] = 7, -7
-    c, qa, qbt, sa, sb, counts, owner, info = _fp8_gemm(ctx, a.cuda(), bt.cuda(), bm=bm, bn=64, count=True, P=3)
+    c, qa, qbt, sa, sb, counts, owner, info = _fp8_gemm(ctx, a.cuda(), bt.cuda(), bm=bm, bn=64, count=True, P=3,
+                                                        checked=checked)
     assert sa.item() == 64.0 and sb.item() == 64.0
     exact = ogemm.gemm(a, bt.t())
     assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(exact))

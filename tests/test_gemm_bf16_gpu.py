@@ -25,7 +25,8 @@ def _operands(m, n, k, seed=0, kind="normal"):
     return a, bt
 
 
-def _gemm(ctx, a, bt, bn=128, kind=tp.MAP_STRIDED, P=None, group_m=1, stages=0, count=False, bm=128):
+def _gemm(ctx, a, bt, bn=128, kind=tp.MAP_STRIDED, P=None, group_m=1, stages=0, count=False, bm=128,
+          checked=False):
     m, n = a.shape[0], bt.shape[0]
     c = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
     p = tp.tp_partition_create(ctx, c, (bm, bn))
@@ -38,7 +39,7 @@ def _gemm(ctx, a, bt, bn=128, kind=tp.MAP_STRIDED, P=None, group_m=1, stages=0, 
         counts = torch.zeros(m * n, dtype=torch.int32, device="cuda")
         owner = torch.full((m * n,), -1, dtype=torch.int32, device="cuda")
     tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=bm, bn=bn, group_m=group_m, stages=stages),
-               tp.make_exec(write_counts=counts, write_owner=owner))
+               tp.make_exec(write_counts=counts, write_owner=owner, checked=checked))
     info = tp.tp_partition_query(p)
     tp.tp_partition_destroy(p)
     return c, counts, owner, info
@@ -159,3 +160,50 @@ def test_8192_cubed_sampled_tiles(ctx):
     assert err <= 1e-2
     del a, bt, c
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("bm", [128, 256])
+@pytest.mark.parametrize("kind,P,group_m", [(tp.MAP_IDENTITY, None, 1), (tp.MAP_STRIDED, 7, 1),
+                                            (tp.MAP_STRIDED, None, 8)])
+@pytest.mark.parametrize("m,n,k", [(384, 512, 640), (300, 200, 136), (1, 96, 64)])
+def test_checked_launch_matches_release(ctx, bm, kind, P, group_m, m, n, k):
+    """TP_EXEC_CHECKED (every tile validated against the map and claimed
+    before its store) stores exactly what the release launch stores, each
+    element once, and raises no race on a correct map."""
+    a, bt = _operands(m, n, k, seed=m + n)
+    rel, _, _, _ = _gemm(ctx, a, bt, bn=64, bm=bm, kind=kind, P=P, group_m=group_m)
+    chk, counts, _, _ = _gemm(ctx, a, bt, bn=64, bm=bm, kind=kind, P=P, group_m=group_m, checked=True, count=True)
+    assert torch.equal(rel, chk)
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+
+
+def test_checked_launch_in_a_graph(ctx):
+    """The claim bitmap is cleared by a node of the graph, so every replay of
+    a captured checked GEMM re-checks from scratch (no stale claims)."""
+    a, bt = _operands(512, 512, 256, seed=11)
+    c = torch.zeros(512, 512, device="cuda", dtype=torch.bfloat16)
+    p = tp.tp_partition_create(ctx, c, (256, 128))
+    tp.tp_partition_map(p, tp.MAP_STRIDED, 5)
+    s = torch.cuda.Stream()
+    g = tp.tp_graph_begin(ctx, s)
+    tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=256, bn=128), tp.make_exec(tp.CAPTURE, s, checked=True))
+    tp.tp_graph_end(g)
+    for _ in range(3):
+        tp.tp_graph_replay(g, tp.make_exec(stream=s))
+    ref = ogemm.gemm(a.cpu(), bt.cpu().t())
+    assert ogemm.rel_frobenius(c.cpu(), ref) <= 1e-2
+    tp.tp_graph_destroy(g)
+    tp.tp_partition_destroy(p)
+
+
+def test_checked_flag_rejected_where_unsupported(ctx):
+    a = torch.ones(64, 64, device="cuda")
+    c = torch.zeros(64, 64, device="cuda")
+    p = tp.tp_partition_create(ctx, c, (64, 64))
+    with pytest.raises(tp.TPError) as e:                      # the FP32 SIMT GEMM
+        tp.tp_gemm(ctx, p, a, a, None, tp.make_exec(checked=True))
+    assert e.value.status == tp._lib.ERR_UNSUPPORTED
+    with pytest.raises(tp.TPError) as e:                      # maps
+        tp.tp_map_axpy(ctx, p, 1.0, a, a, tp.make_exec(checked=True))
+    assert e.value.status == tp._lib.ERR_UNSUPPORTED
+    tp.tp_partition_destroy(p)

@@ -96,13 +96,16 @@ def test_plan_rejections(ctx):
 def test_async_busy_and_graph_replay(ctx):
     probs = _problems(SMALL[:4], seed=9)
     plan = tp.tp_grouped_plan_create(ctx, probs)
-    s = torch.cuda.Stream()
+    s, s2 = torch.cuda.Stream(), torch.cuda.Stream()
     ev = tp.tp_event_create(ctx)
     with torch.cuda.stream(s):
         torch.cuda._sleep(100_000_000)
     tp.tp_grouped_gemm(ctx, plan, 0, tp.make_exec(mode=tp.ASYNC, stream=s, event=ev))
+    with pytest.raises(tp.TPError) as e:      # the group's outputs are held by the in-flight launch
+        tp.tp_grouped_gemm(ctx, plan, 0, tp.make_exec(stream=s2))
+    assert e.value.status == tp._lib.ERR_BUSY
     with pytest.raises(tp.TPError) as e:
-        tp.tp_grouped_gemm(ctx, plan, 0, tp.make_exec(stream=s))
+        tp.tp_grouped_plan_destroy(plan)
     assert e.value.status == tp._lib.ERR_BUSY
     tp.tp_event_wait(ev)
     eager = [c.clone() for _, _, c in probs]

@@ -184,7 +184,7 @@ def test_async_busy_protocol(ctx):
     n = 1 << 22
     x, y, _ = _inputs(n, "f32")
     z = torch.empty_like(x)
-    s = torch.cuda.Stream()
+    s, s2 = torch.cuda.Stream(), torch.cuda.Stream()
     p = tp.tp_partition_create(ctx, z, (4096,))
     ev = tp.tp_event_create(ctx)
     with torch.cuda.stream(s):
@@ -192,26 +192,33 @@ def test_async_busy_protocol(ctx):
         tp.tp_map_axpy(ctx, p, ALPHA, x, y, tp.make_exec(mode=tp.ASYNC, stream=s, event=ev))
     assert tp.tp_partition_query(p)["busy"]
     assert not tp.tp_event_query(ev)
-    with pytest.raises(tp.TPError) as e:      # second writer while in flight
-        tp.tp_map_axpy(ctx, p, ALPHA, x, y, tp.make_exec(stream=s))
+    with pytest.raises(tp.TPError) as e:      # second writer on another stream while in flight
+        tp.tp_map_axpy(ctx, p, ALPHA, x, y, tp.make_exec(stream=s2))
     assert e.value.status == tp._lib.ERR_BUSY
     z2 = torch.empty_like(x)
     p2 = tp.tp_partition_create(ctx, z2, (4096,))
-    with pytest.raises(tp.TPError) as e:      # reader of the in-flight output
-        tp.tp_map_axpy(ctx, p2, ALPHA, z, y, tp.make_exec(stream=s))
+    with pytest.raises(tp.TPError) as e:      # reader of the in-flight output on another stream
+        tp.tp_map_axpy(ctx, p2, ALPHA, z, y, tp.make_exec(stream=s2))
     assert e.value.status == tp._lib.ERR_BUSY
     with pytest.raises(tp.TPError) as e:
         tp.tp_partition_destroy(p)
     assert e.value.status == tp._lib.ERR_BUSY
     with pytest.raises(tp.TPError) as e:
+        tp.tp_partition_map(p, tp.MAP_STRIDED, 2)
+    assert e.value.status == tp._lib.ERR_BUSY
+    with pytest.raises(tp.TPError) as e:
         tp.tp_event_destroy(ev)
     assert e.value.status == tp._lib.ERR_BUSY
+    # chained on the same stream (`then`): reads the in-flight output in stream order
+    tp.tp_map_axpy(ctx, p2, ALPHA, z, y, tp.make_exec(mode=tp.ASYNC, stream=s, event=ev))
     tp.tp_event_wait(ev)
-    assert not tp.tp_partition_query(p)["busy"]
+    assert not tp.tp_partition_query(p)["busy"] and not tp.tp_partition_query(p2)["busy"]
     assert tp.tp_event_query(ev)
     ref = omaps.axpy(ALPHA, x, y)
     assert np.all(np.abs(_f(z) - ref) <= _bound("axpy", "f32", ref, x, y, None))
-    tp.tp_map_axpy(ctx, p2, ALPHA, z, y, tp.make_exec(stream=s))   # now allowed
+    ref2 = omaps.axpy(ALPHA, ref, y)   # the chained result, composed in the oracle
+    assert np.all(np.abs(_f(z2) - ref2) <= 2.0 ** -24 * (np.abs(ref2) + ALPHA * np.abs(ref)) + 1e-37)
+    tp.tp_map_axpy(ctx, p2, ALPHA, z, y, tp.make_exec(stream=s2))   # now allowed from any stream
     for h in (p, p2):
         tp.tp_partition_destroy(h)
     tp.tp_event_destroy(ev)
