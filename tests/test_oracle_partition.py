@@ -96,6 +96,38 @@ def test_permute_heads_race_is_flagged():
     assert sorted(e0) == sorted(h1 * H + 0 for h1 in range(H))
 
 
+def test_gemm_split_schedule_worked_example():
+    # 7 tiles on 5 programs, 4 K blocks: one whole round (tiles 0..4), and the
+    # 2 remaining tiles cut in two: slots 5, 6 = tile 5 parts 0, 1 and slots
+    # 7, 8 = tile 6 parts 0, 1, run by programs 0, 1, 2, 3 (program 4 idles)
+    assert partition.gemm_split_schedule(7, 5, 4) == (5, 2)
+    w = partition.gemm_tile_writers(7 * 16, 16, 16, 16, 5, 1, 4)
+    assert w[(5, 0)] == {0, 1} and w[(6, 0)] == {2, 3}
+    assert all(w[(t, 0)] == {t} for t in range(5))
+
+
+@pytest.mark.parametrize("T,P,kb,limit,expect", [(5, 3, 4, 4, (5, 1)),      # P // R = 1: nothing cut
+                                                  (10, 3, 4, 4, (9, 3)),    # R = 1: three parts
+                                                  (10, 3, 2, 4, (9, 2)),    # at most one part per K block
+                                                  (10, 3, 4, 1, (10, 1)),   # cutting disabled
+                                                  (1024, 76, 128, 4, (988, 2)),
+                                                  (12, 4, 8, 4, (12, 1))])  # no partial round
+def test_gemm_split_schedule_cases(T, P, kb, limit, expect):
+    assert partition.gemm_split_schedule(T, P, kb, limit) == expect
+
+
+def test_gemm_tile_writers_without_cuts_is_the_strided_owner_map():
+    m, n, bm, bn, P, G = 300, 200, 32, 64, 9, 2      # 40 tiles, 4 left for the last round
+    w = partition.gemm_tile_writers(m, n, bm, bn, P, G, 5, limit=1)
+    owner = partition.gemm_owner_map(m, n, bm, bn, P, "strided", G)
+    assert all(len(v) == 1 for v in w.values())
+    assert partition.owners_allowed(owner, m, n, bm, bn, w).all()
+    # with cuts, each cut tile has S distinct writers; whole tiles keep one
+    wc = partition.gemm_tile_writers(m, n, bm, bn, P, G, 5)
+    D, S = partition.gemm_split_schedule(len(w), P, 5)
+    assert S == 2 and sorted(len(v) for v in wc.values()).count(S) == len(w) - D
+
+
 def test_permute_heads_worked_example():
     # B=1, H=2, M=4, BM=2, D=1: heads [0 1 2 3] and [4 5 6 7]. Destination head
     # m holds, for each source head h, source head h's sequence tile m.
