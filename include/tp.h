@@ -154,7 +154,16 @@ typedef struct tp_gemm_config {
   int32_t group_m;     /* raster band height in tiles (L2 reuse)                */
   int32_t num_programs;/* persistent programs; 0 = number of SMs (or pairs)     */
   int32_t swap_ab;     /* grouped GEMM only: compute C^T = B^T A^T             */
-  int32_t split_k;     /* reserved, must be 0 or 1                              */
+  int32_t split_k;     /* tensor-core GEMM on a strided map with T tiles and P
+                        * programs: each of the R = T mod P tiles of the last,
+                        * partial round may be cut along N into S narrow tiles
+                        * (S the largest power of two <= min(limit, P / R)
+                        * leaving a multiple of 32 columns, 64 for 256-row
+                        * tiles), run by programs that would otherwise idle in
+                        * that round; every C element is still computed whole
+                        * by one program, so C is bit-identical either way.
+                        * Limit: 0 = 4 (default), 1 = never cut, 2..8.
+                        * SIMT GEMM: ignored.                                 */
 } tp_gemm_config;
 
 /* ---------------------------------------------------------------- errors */

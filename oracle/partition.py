@@ -119,46 +119,41 @@ def gemm_owner_map(m: int, n: int, bm: int, bn: int, num_programs=None,
     return owner.reshape(-1)
 
 
-def gemm_split_schedule(tiles: int, programs: int, k_blocks: int, limit: int = 4):
-    """The GEMM schedule on a strided map with the last round cut along K.
-    With P programs and T tiles, the first T - R slots (R = T mod P) are
-    whole tiles, slot = tile index. When R > 0 each of the R remaining tiles
-    is cut into S = min(limit, P // R, k_blocks) parts if that gives S >= 2
-    (otherwise nothing is cut): part j of remaining tile r is slot
-    (T - R) + r * S + j and covers K blocks [j * kb // S, (j + 1) * kb // S).
-    Program p runs slots p, p + P, ... Returns (whole_slots, S)."""
+def gemm_cut_schedule(tiles: int, programs: int, bn: int, unit: int, limit: int = 4):
+    """The GEMM schedule on a strided map with the last round cut along N.
+    With P programs and T tiles of BN columns, the first T - R slots
+    (R = T mod P) are whole tiles, slot = tile index. When R > 0 each of the
+    R remaining tiles is cut into S narrow tiles of BN / S columns, S the
+    largest power of two with S <= limit, S <= P // R and BN / S a multiple
+    of `unit` (nothing is cut when that S is 1): narrow tile j of remaining
+    tile r is slot (T - R) + r * S + j and covers columns [j BN/S, (j+1) BN/S)
+    of it. Program p runs slots p, p + P, ... Returns (whole_slots, S)."""
     R = tiles % programs
-    if limit > 1 and R > 0:
-        S = min(limit, programs // R, k_blocks)
-        if S >= 2:
-            return tiles - R, S
-    return tiles, 1
+    S = 1
+    while R > 0 and 2 * S <= limit and 2 * S <= programs // R and bn % (2 * S * unit) == 0:
+        S *= 2
+    return (tiles - R, S) if S >= 2 else (tiles, 1)
 
 
-def gemm_tile_writers(m: int, n: int, bm: int, bn: int, programs: int, group_m: int, k_blocks: int,
-                      limit: int = 4) -> dict:
-    """{(tm, tn): set of programs that may store that C tile}: the one owner
-    of a whole tile, or the programs holding the parts of a cut tile (the
-    part that finishes last stores it)."""
+def gemm_owner_map_cut(m: int, n: int, bm: int, bn: int, programs: int, group_m: int = 1,
+                       limit: int = 4) -> np.ndarray:
+    """Program id per element of an M x N output under the strided map with
+    the last round cut along N (narrow tiles keep 64-column multiples for
+    256-row tiles, 32 otherwise); slots become tiles through raster_tile."""
     gm, gn = -(-m // bm), -(-n // bn)
     T = gm * gn
-    D, S = gemm_split_schedule(T, programs, k_blocks, limit)
-    writers = {}
+    D, S = gemm_cut_schedule(T, programs, bn, 64 if bm == 256 else 32, limit)
+    owner = np.full((m, n), -1, dtype=np.int64)
+    w = bn // S
     for s in range(D + (T - D) * S):
-        tile = s if s < D else D + (s - D) // S
-        writers.setdefault(raster_tile(tile, gm, gn, group_m), set()).add(s % programs)
-    return writers
-
-
-def owners_allowed(owner, m: int, n: int, bm: int, bn: int, writers: dict) -> np.ndarray:
-    """Per element of an M x N output: whether its recorded owner is one of
-    the programs allowed to store its tile."""
-    own = np.asarray(owner).reshape(m, n)
-    ok = np.zeros((m, n), dtype=bool)
-    for (tm, tn), progs in writers.items():
-        blk = own[tm * bm:(tm + 1) * bm, tn * bn:(tn + 1) * bn]
-        ok[tm * bm:(tm + 1) * bm, tn * bn:(tn + 1) * bn] = np.isin(blk, list(progs))
-    return ok.reshape(-1)
+        if s < D:
+            tile, c0, c1 = s, 0, bn
+        else:
+            tile, j = D + (s - D) // S, (s - D) % S
+            c0, c1 = j * w, (j + 1) * w
+        tm, tn = raster_tile(tile, gm, gn, group_m)
+        owner[tm * bm:(tm + 1) * bm, tn * bn + c0:tn * bn + c1] = s % programs
+    return owner.reshape(-1)
 
 
 def write_counts(n_elements: int, writes) -> np.ndarray:

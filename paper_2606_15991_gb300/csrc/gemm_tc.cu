@@ -18,6 +18,7 @@
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "sm100_ptx.cuh"
@@ -52,7 +53,40 @@ struct TcArgs {
   uint32_t* claims;     // checked launch: tile-claim bitmap (kChecked)
   unsigned* claim_done; // checked launch: finished-CTA counter
   int64_t claim_bits;   // bits this launch may set
+  // Schedule: slots [0, dp_slots) are whole tiles (slot = tile index); each
+  // remaining tile dp_slots + r is cut along N into ncut narrow tiles of
+  // bn_cut columns, narrow tile j being slot dp_slots + r * ncut + j.
+  int64_t dp_slots;
+  int64_t total_slots;  // dp_slots + (tiles - dp_slots) * ncut
+  int32_t ncut;         // 1 = no tile is cut
+  int32_t bn_cut;       // bn / ncut
 };
+
+// The work of one slot: a tile and the columns [col, col + width) of it.
+struct Unit {
+  int64_t tile;
+  int32_t col, width, part;
+  bool cut;
+};
+
+__device__ __forceinline__ Unit unit_of(int64_t s, const TcArgs& p) {
+  Unit u;
+  if (s < p.dp_slots) {
+    u.tile = s;
+    u.col = 0;
+    u.width = p.bn;
+    u.part = 0;
+    u.cut = false;
+  } else {
+    const int64_t q = s - p.dp_slots;
+    u.tile = p.dp_slots + q / p.ncut;
+    u.part = (int32_t)(q % p.ncut);
+    u.col = u.part * p.bn_cut;
+    u.width = p.bn_cut;
+    u.cut = true;
+  }
+  return u;
+}
 
 __device__ __forceinline__ void raster(int64_t s, int64_t gm, int64_t gn, int64_t g, int64_t* tm, int64_t* tn) {
   const int64_t per = g * gn;
@@ -66,7 +100,7 @@ __device__ __forceinline__ void raster(int64_t s, int64_t gm, int64_t gn, int64_
 template <bool kF8, bool kPair, bool kCount, bool kChecked>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-                   const __grid_constant__ TcArgs p) {
+                   const __grid_constant__ CUtensorMap map_b_cut, const __grid_constant__ TcArgs p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -110,6 +144,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     fence_mbar_init();
     tma_prefetch_desc(&map_a);
     tma_prefetch_desc(&map_b);
+    if (p.ncut > 1) tma_prefetch_desc(&map_b_cut);
   }
   if (warp == 1) {
     if constexpr (kPair) {
@@ -125,11 +160,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   else __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // The prologue above touches no global memory, so it may overlap the tail
+  // of the grid this launch depends on (programmatic dependent launch).
+  grid_dependency_wait();
+  allow_dependents();
 
   const int64_t T = p.gm * p.gn;
+  const int64_t TS = p.total_slots;
   const int64_t step = p.kind == TP_MAP_IDENTITY ? T : nprog;
   const int64_t nk = (p.K + p.kblk - 1) / p.kblk;
-  const uint32_t stage_tx = a_stage + b_stage;
 
   if (warp == 0) {
     // ---------------- TMA producer (one thread; the rest of the warp waits)
@@ -140,24 +179,30 @@ __global__ void __launch_bounds__(kThreads, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int64_t s = prog; s < T && ok; s += step) {
+      for (int64_t s = prog; s < TS && ok; s += step) {
+        const Unit u = unit_of(s, p);
         int64_t tm, tn;
-        raster(s, p.gm, p.gn, p.group_m, &tm, &tn);
+        raster(u.tile, p.gm, p.gn, p.group_m, &tm, &tn);
+        // a narrow tile loads only its own columns of B, through the map whose
+        // box has that many rows
+        const int ub_rows = kPair ? u.width / 2 : u.width;
+        const CUtensorMap* mb = u.cut ? &map_b_cut : &map_b;
+        const uint32_t utx = a_stage + (uint32_t)ub_rows * 128;
         const int32_t arow = (int32_t)(tm * tile_m + rank * BM);
-        const int32_t brow = (int32_t)(tn * p.bn + rank * b_rows);
+        const int32_t brow = (int32_t)(tn * p.bn + u.col + rank * ub_rows);
         for (int64_t kb = 0; kb < nk; ++kb) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err)) { ok = false; break; }
           const int32_t kc = (int32_t)(kb * p.kblk);
           if constexpr (kPair) {
             // both CTAs' copies complete on the even CTA's full barrier
             const uint32_t fb = mapa(full_bar(stage), 0);
-            if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * stage_tx);
+            if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * utx);
             tma_load_2d_pair(a0 + a_stage * stage, &map_a, kc, arow, fb, pol_a);
-            tma_load_2d_pair(b0 + b_stage * stage, &map_b, kc, brow, fb, pol_b);
+            tma_load_2d_pair(b0 + b_stage * stage, mb, kc, brow, fb, pol_b);
           } else {
-            mbar_arrive_expect_tx(full_bar(stage), stage_tx);
+            mbar_arrive_expect_tx(full_bar(stage), utx);
             tma_load_2d(a0 + a_stage * stage, &map_a, kc, arow, full_bar(stage), pol_a);
-            tma_load_2d(b0 + b_stage * stage, &map_b, kc, brow, full_bar(stage), pol_b);
+            tma_load_2d(b0 + b_stage * stage, mb, kc, brow, full_bar(stage), pol_b);
           }
           fills[stage]++;
           if (++stage == p.stages) { stage = 0; phase ^= 1u; }
@@ -174,12 +219,15 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer (one thread of the even CTA)
     if (lane == 0 && leader) {
-      const uint32_t idesc = idesc_f32acc((uint32_t)tile_m, (uint32_t)p.bn, kF8);
+      const uint32_t idesc_full = idesc_f32acc((uint32_t)tile_m, (uint32_t)p.bn, kF8);
+      const uint32_t idesc_cut = idesc_f32acc((uint32_t)tile_m, (uint32_t)p.bn_cut, kF8);
       int stage = 0;
       uint32_t phase = 0;
       int64_t t = 0;
       bool ok = true;
-      for (int64_t s = prog; s < T && ok; s += step, ++t) {
+      for (int64_t s = prog; s < TS && ok; s += step, ++t) {
+        const Unit u = unit_of(s, p);
+        const uint32_t idesc = u.cut ? idesc_cut : idesc_full;
         const int acc = (int)(t & 1);
         const uint32_t use = (uint32_t)((t >> 1) & 1);
         if (!mbar_wait(tempty_bar(acc), use ^ 1u, abort_flag, p.err)) { ok = false; break; }
@@ -221,72 +269,83 @@ __global__ void __launch_bounds__(kThreads, 1)
     const float scale = (p.scale_a && p.scale_b) ? 1.f / (*p.scale_a * *p.scale_b) : 1.f;
     const uint32_t tempty_remote = kPair ? mapa(tempty_bar(0), 0) : 0u;
     int64_t t = 0;
-    for (int64_t s = prog; s < T; s += step, ++t) {
-      const int acc = (int)(t & 1);
-      const uint32_t use = (uint32_t)((t >> 1) & 1);
-      int64_t tm, tn;
-      raster(s, p.gm, p.gn, p.group_m, &tm, &tn);
-      bool store_ok = true;
-      if constexpr (kChecked) {
-        // validate the store against the map (the slot is this program's and
-        // its tile lies in the grid), then claim this warp's 32-row slice of
-        // the tile: (tile, CTA of the pair, lane quadrant). Done before the
-        // accumulator is ready, so the atomic's latency hides behind the K loop.
-        int ok = 1;
-        if (lane == 0) {
-          const bool on_map = s < T && (s - prog) % step == 0 && tm >= 0 && tm < p.gm && tn >= 0 && tn < p.gn;
-          if (!on_map) {
-            record_device_error(p.err, kDevRace);
-            ok = 0;
-          } else {
-            const int64_t id = ((tm * p.gn + tn) * (kPair ? 2 : 1) + rank) * 4 + quad;
-            ok = claim_tile(p.claims, id, p.err) ? 1 : 0;
-          }
-        }
-        store_ok = __shfl_sync(0xffffffffu, ok, 0) != 0;
-      }
-      const bool ready = mbar_wait(tfull_bar(acc), use, abort_flag, p.err);
-      if (!__all_sync(0xffffffffu, ready)) break;  // leave together (tcgen05.ld is warp-collective)
-      tc_fence_after();
-      const int64_t row = tm * tile_m + row_in_tile;
-      const int64_t col0 = tn * p.bn;
-      __nv_bfloat16* crow = p.c + row * p.N;
-      const bool row_ok = row < p.M;
-      const bool vec_ok = p.c_vec != 0;
-      for (int ch = 0; ch < p.bn / 32 && store_ok; ++ch) {
-        uint32_t r[32];
-        tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * p.bn + ch * 32), r);
-        tmem_ld_wait();
-        const int64_t c0 = col0 + ch * 32;
-        if (!row_ok || c0 >= p.N) continue;
-        if (vec_ok && c0 + 32 <= p.N) {
-          uint4 v[4];
-          __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(v);
-#pragma unroll
-          for (int i = 0; i < 16; ++i)
-            h[i] = __floats2bfloat162_rn(__uint_as_float(r[2 * i]) * scale, __uint_as_float(r[2 * i + 1]) * scale);
-          uint4* dst = reinterpret_cast<uint4*>(crow + c0);
-#pragma unroll
-          for (int i = 0; i < 4; ++i) dst[i] = v[i];
+    // validate a store against the map (the slot is this program's and its
+    // tile lies in the grid), then claim this warp's 32-row slice of the
+    // (narrow) tile: (tile, narrow part, CTA of the pair, lane quadrant);
+    // warp-uniform result
+    auto claim = [&](int64_t s, int64_t tm, int64_t tn, int32_t part) -> bool {
+      int ok = 1;
+      if (lane == 0) {
+        const bool on_map = s < TS && (s - prog) % step == 0 && tm >= 0 && tm < p.gm && tn >= 0 && tn < p.gn;
+        if (!on_map) {
+          record_device_error(p.err, kDevRace);
+          ok = 0;
         } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (c0 + i < p.N) crow[c0 + i] = __float2bfloat16_rn(__uint_as_float(r[i]) * scale);
-        }
-        if constexpr (kCount) {
-          for (int i = 0; i < 32; ++i)
-            if (c0 + i < p.N) {
-              atomicAdd(p.counts + row * p.N + c0 + i, 1u);
-              p.owner[row * p.N + c0 + i] = (int32_t)prog;
-            }
+          const int64_t id = (((tm * p.gn + tn) * p.ncut + part) * (kPair ? 2 : 1) + rank) * 4 + quad;
+          ok = claim_tile(p.claims, id, p.err) ? 1 : 0;
         }
       }
+      return __shfl_sync(0xffffffffu, ok, 0) != 0;
+    };
+    // one row's 32 columns [c0, c0 + 32) of C from FP32 values f
+    auto store_chunk = [&](const float* f, int64_t row, int64_t c0) {
+      if (row >= p.M || c0 >= p.N) return;
+      __nv_bfloat16* crow = p.c + row * p.N;
+      if (p.c_vec != 0 && c0 + 32 <= p.N) {
+        uint4 v[4];
+        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) h[i] = __floats2bfloat162_rn(f[2 * i] * scale, f[2 * i + 1] * scale);
+        uint4* dst = reinterpret_cast<uint4*>(crow + c0);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dst[i] = v[i];
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+          if (c0 + i < p.N) crow[c0 + i] = __float2bfloat16_rn(f[i] * scale);
+      }
+      if constexpr (kCount) {
+        for (int i = 0; i < 32; ++i)
+          if (c0 + i < p.N) {
+            atomicAdd(p.counts + row * p.N + c0 + i, 1u);
+            p.owner[row * p.N + c0 + i] = (int32_t)prog;
+          }
+      }
+    };
+    auto release_acc = [&](int acc) {
       tc_fence_before();
       __syncwarp();
       if (lane == 0) {
         if constexpr (kPair) mbar_arrive_cluster(tempty_remote + 8u * acc);
         else mbar_arrive(tempty_bar(acc));
       }
+    };
+    for (int64_t s = prog; s < TS; s += step, ++t) {
+      const Unit u = unit_of(s, p);
+      const int acc = (int)(t & 1);
+      const uint32_t use = (uint32_t)((t >> 1) & 1);
+      int64_t tm, tn;
+      raster(u.tile, p.gm, p.gn, p.group_m, &tm, &tn);
+      bool store_ok = true;
+      // claimed before the accumulator is ready, so the atomic's latency
+      // hides behind the K loop
+      if constexpr (kChecked) store_ok = claim(s, tm, tn, u.part);
+      const bool ready = mbar_wait(tfull_bar(acc), use, abort_flag, p.err);
+      if (!__all_sync(0xffffffffu, ready)) break;  // leave together (tcgen05.ld is warp-collective)
+      tc_fence_after();
+      const int64_t row = tm * tile_m + row_in_tile;
+      const int64_t col0 = tn * p.bn + u.col;
+      const uint32_t tacc = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * p.bn);
+      for (int ch = 0; ch < u.width / 32 && store_ok; ++ch) {
+        uint32_t r[32];
+        tmem_ld32(tacc + (uint32_t)(ch * 32), r);
+        tmem_ld_wait();
+        float f[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) f[i] = __uint_as_float(r[i]);
+        store_chunk(f, row, col0 + ch * 32);
+      }
+      release_acc(acc);
     }
   }
   tc_fence_before();
@@ -335,7 +394,8 @@ tp_status make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t k, i
 }
 
 template <bool kF8, bool kPair, bool kCount, bool kChecked>
-cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& p, int grid, size_t smem,
+cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mbc, const TcArgs& p,
+                          int grid, size_t smem,
                           cudaStream_t st) {
   auto k = gemm_tc_kernel<kF8, kPair, kCount, kChecked>;
   static bool attr_set = false;
@@ -349,30 +409,34 @@ cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const Tc
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = kPair ? 2 : 1;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k, ma, mb, p);
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, k, ma, mb, mbc, p);
 }
 
 template <bool kF8, bool kPair>
-cudaError_t launch_inst(bool count, bool checked, const CUtensorMap& ma, const CUtensorMap& mb, const TcArgs& p,
+cudaError_t launch_inst(bool count, bool checked, const CUtensorMap& ma, const CUtensorMap& mb,
+                        const CUtensorMap& mbc, const TcArgs& p,
                         int grid, size_t smem, cudaStream_t st) {
-  if (checked) return count ? launch_kernel<kF8, kPair, true, true>(ma, mb, p, grid, smem, st)
-                            : launch_kernel<kF8, kPair, false, true>(ma, mb, p, grid, smem, st);
-  return count ? launch_kernel<kF8, kPair, true, false>(ma, mb, p, grid, smem, st)
-               : launch_kernel<kF8, kPair, false, false>(ma, mb, p, grid, smem, st);
+  if (checked) return count ? launch_kernel<kF8, kPair, true, true>(ma, mb, mbc, p, grid, smem, st)
+                            : launch_kernel<kF8, kPair, false, true>(ma, mb, mbc, p, grid, smem, st);
+  return count ? launch_kernel<kF8, kPair, true, false>(ma, mb, mbc, p, grid, smem, st)
+               : launch_kernel<kF8, kPair, false, false>(ma, mb, mbc, p, grid, smem, st);
 }
 
 template <bool kF8>
 cudaError_t launch_any(bool pair, bool count, bool checked, const CUtensorMap& ma, const CUtensorMap& mb,
+                       const CUtensorMap& mbc,
                        const TcArgs& p, int grid, size_t smem, cudaStream_t st) {
-  return pair ? launch_inst<kF8, true>(count, checked, ma, mb, p, grid, smem, st)
-              : launch_inst<kF8, false>(count, checked, ma, mb, p, grid, smem, st);
+  return pair ? launch_inst<kF8, true>(count, checked, ma, mb, mbc, p, grid, smem, st)
+              : launch_inst<kF8, false>(count, checked, ma, mb, mbc, p, grid, smem, st);
 }
 
 }  // namespace
@@ -438,16 +502,40 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   const size_t smem = fixed + stages * stage_bytes;
   const int64_t progs = c->kind == TP_MAP_IDENTITY ? c->num_tiles : c->num_programs;
   const int64_t grid = pair ? 2 * progs : progs;
-  if (grid > 0x7fffffff) return fail(TP_ERR_UNSUPPORTED, "too many tile programs");
+  // Schedule: whole tiles, except that on a strided map the R = T mod P tiles
+  // of the last, partial round may each be cut along N into S narrow tiles
+  // run by the programs that would otherwise sit idle in that round.
+  const int64_t T = c->num_tiles;
+  p.dp_slots = T;
+  p.total_slots = T;
+  p.ncut = 1;
+  p.bn_cut = bn;
+  const int32_t limit = (cfg && cfg->split_k > 0) ? cfg->split_k : 4;
+  if (limit > 8) return fail(TP_ERR_INVALID, "split_k must be 0..8");
+  CUtensorMap mb_cut = mb;
+  if (c->kind == TP_MAP_STRIDED) {
+    const int64_t R = T % progs;
+    const int unit = pair ? 64 : 32;  // narrow tiles keep whole 32-row B boxes per CTA
+    int64_t S = 1;
+    while (R > 0 && 2 * S <= limit && 2 * S <= progs / R && bn % (2 * S * unit) == 0) S *= 2;
+    if (S >= 2) {
+      p.ncut = (int32_t)S;
+      p.bn_cut = (int32_t)(bn / S);
+      p.dp_slots = T - R;
+      p.total_slots = T - R + R * S;
+      s = make_map(&mb_cut, b->ptr, N, K, ldb, esize, pair ? p.bn_cut / 2 : p.bn_cut);
+      if (s != TP_OK) return s;
+    }
+  }
   const bool count = ex->write_counts != nullptr;
   const bool checked = (ex->flags & TP_EXEC_CHECKED) != 0;
   if (checked) {
-    p.claim_bits = c->num_tiles * (pair ? 8 : 4);
+    p.claim_bits = c->num_tiles * p.ncut * (pair ? 8 : 4);
     s = claims_for(ctx, p.claim_bits, &p.claims, &p.claim_done);
     if (s != TP_OK) return s;
   }
-  cudaError_t e = esize == 2 ? launch_any<false>(pair, count, checked, ma, mb, p, (int)grid, smem, stream)
-                             : launch_any<true>(pair, count, checked, ma, mb, p, (int)grid, smem, stream);
+  cudaError_t e = esize == 2 ? launch_any<false>(pair, count, checked, ma, mb, mb_cut, p, (int)grid, smem, stream)
+                             : launch_any<true>(pair, count, checked, ma, mb, mb_cut, p, (int)grid, smem, stream);
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core GEMM launch");
   return TP_OK;
 }

@@ -148,6 +148,12 @@ tp_status take_device_error(tp_ctx* ctx, int h) {
   if (h == kDevOk) return TP_OK;
   int zero = 0;
   cudaMemcpy(ctx->d_err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+  // a checked launch that gave up part-way may have left claim state
+  // behind; the next launch must start from zero
+  if (h == kDevTimeout) {
+    cudaMemset(ctx->d_claim_done, 0, 256);
+    cudaMemset(ctx->d_claims, 0, (size_t)tp_ctx::kClaimBits / 8);
+  }
   return error_status(h);
 }
 

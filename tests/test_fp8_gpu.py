@@ -111,8 +111,7 @@ def test_integer_inputs_exact(ctx, bm, checked):
     exact = ogemm.gemm(a, bt.t())
     assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(exact))
     assert opart.check_counts(counts.cpu().numpy())["ok"]
-    assert np.array_equal(owner.cpu().numpy(),
-                          opart.gemm_owner_map(m, n, bm, 64, info["num_programs"], "strided", 1))
+    assert np.array_equal(owner.cpu().numpy(), opart.gemm_owner_map_cut(m, n, bm, 64, info["num_programs"], 1))
 
 
 @pytest.mark.parametrize("bm,bn", [(128, 128), (128, 256), (256, 256), (256, 128)])

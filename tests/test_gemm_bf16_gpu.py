@@ -26,7 +26,7 @@ def _operands(m, n, k, seed=0, kind="normal"):
 
 
 def _gemm(ctx, a, bt, bn=128, kind=tp.MAP_STRIDED, P=None, group_m=1, stages=0, count=False, bm=128,
-          checked=False):
+          checked=False, split_k=0):
     m, n = a.shape[0], bt.shape[0]
     c = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
     p = tp.tp_partition_create(ctx, c, (bm, bn))
@@ -38,7 +38,7 @@ def _gemm(ctx, a, bt, bn=128, kind=tp.MAP_STRIDED, P=None, group_m=1, stages=0, 
     if count:
         counts = torch.zeros(m * n, dtype=torch.int32, device="cuda")
         owner = torch.full((m * n,), -1, dtype=torch.int32, device="cuda")
-    tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=bm, bn=bn, group_m=group_m, stages=stages),
+    tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=bm, bn=bn, group_m=group_m, stages=stages, split_k=split_k),
                tp.make_exec(write_counts=counts, write_owner=owner, checked=checked))
     info = tp.tp_partition_query(p)
     tp.tp_partition_destroy(p)
@@ -90,8 +90,7 @@ def test_ragged_shapes(ctx, m, n, k, bm):
     ref = ogemm.gemm(a.cpu(), bt.cpu().t())
     assert ogemm.rel_frobenius(c.cpu(), ref) <= 1e-2
     assert opart.check_counts(counts.cpu().numpy())["ok"]
-    assert np.array_equal(owner.cpu().numpy(),
-                          opart.gemm_owner_map(m, n, bm, 64, info["num_programs"], "strided", 1))
+    assert np.array_equal(owner.cpu().numpy(), opart.gemm_owner_map_cut(m, n, bm, 64, info["num_programs"], 1))
 
 
 @pytest.mark.parametrize("bm", [128, 256])
@@ -102,8 +101,14 @@ def test_mapped_partition_coverage(ctx, P, group_m, stages, bm):
     c, counts, owner, info = _gemm(ctx, a, bt, bn=128, P=P, group_m=group_m, stages=stages, count=True, bm=bm)
     assert opart.check_counts(counts.cpu().numpy())["ok"]
     assert np.array_equal(owner.cpu().numpy(),
-                          opart.gemm_owner_map(m, n, bm, 128, info["num_programs"], "strided", group_m))
+                          opart.gemm_owner_map_cut(m, n, bm, 128, info["num_programs"], group_m))
     assert ogemm.rel_frobenius(c.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 1e-2
+    # without cutting the last round, the owners are exactly the strided map's
+    c1, counts1, owner1, info1 = _gemm(ctx, a, bt, bn=128, P=P, group_m=group_m, stages=stages, count=True, bm=bm,
+                                       split_k=1)
+    assert np.array_equal(owner1.cpu().numpy(),
+                          opart.gemm_owner_map(m, n, bm, 128, info1["num_programs"], "strided", group_m))
+    assert torch.equal(c1, c)
 
 
 @pytest.mark.parametrize("bm", [128, 256])
@@ -207,3 +212,35 @@ def test_checked_flag_rejected_where_unsupported(ctx):
         tp.tp_map_axpy(ctx, p, 1.0, a, a, tp.make_exec(checked=True))
     assert e.value.status == tp._lib.ERR_UNSUPPORTED
     tp.tp_partition_destroy(p)
+
+
+@pytest.mark.parametrize("bm", [128, 256])
+@pytest.mark.parametrize("limit", [0, 2, 3, 8])
+def test_last_round_cut_along_n(ctx, bm, limit):
+    """The tiles of the last, partial round cut along N into narrow tiles run
+    by otherwise idle programs: every element is stored once, by the program
+    the oracle's schedule names, and C is bit-identical to the uncut run
+    (integer inputs: the exact product rounded once)."""
+    m, n, k = 1024, 640, 512            # 128-row tiles: 8 x 5 = 40 tiles of 128 columns; 256-row: 20
+    P = 13 if bm == 128 else 9          # 40 mod 13 = 1 and 20 mod 9 = 2 tiles in the last round
+    bn = 128
+    T = (m // bm) * (n // bn)
+    D, S = opart.gemm_cut_schedule(T, P, bn, 64 if bm == 256 else 32, limit or 4)
+    assert S >= 2
+    a, bt = _operands(m, n, k, seed=3, kind="int")
+    c, counts, owner, info = _gemm(ctx, a, bt, bn=bn, P=P, bm=bm, count=True, split_k=limit)
+    assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(ogemm.gemm(a.cpu(), bt.cpu().t())))
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    assert np.array_equal(owner.cpu().numpy(), opart.gemm_owner_map_cut(m, n, bm, bn, P, 1, limit or 4))
+    a, bt = _operands(m, n, k, seed=4)
+    c1, _, _, _ = _gemm(ctx, a, bt, bn=bn, P=P, bm=bm, split_k=limit)
+    c0, _, _, _ = _gemm(ctx, a, bt, bn=bn, P=P, bm=bm, split_k=1)
+    assert torch.equal(c1, c0)
+    assert ogemm.rel_frobenius(c1.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 5e-3
+
+
+def test_split_k_validation(ctx):
+    a, bt = _operands(256, 256, 128)
+    with pytest.raises(tp.TPError) as e:
+        _gemm(ctx, a, bt, bn=64, P=3, split_k=9)
+    assert e.value.status == tp._lib.ERR_INVALID

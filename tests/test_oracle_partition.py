@@ -96,36 +96,42 @@ def test_permute_heads_race_is_flagged():
     assert sorted(e0) == sorted(h1 * H + 0 for h1 in range(H))
 
 
-def test_gemm_split_schedule_worked_example():
-    # 7 tiles on 5 programs, 4 K blocks: one whole round (tiles 0..4), and the
-    # 2 remaining tiles cut in two: slots 5, 6 = tile 5 parts 0, 1 and slots
-    # 7, 8 = tile 6 parts 0, 1, run by programs 0, 1, 2, 3 (program 4 idles)
-    assert partition.gemm_split_schedule(7, 5, 4) == (5, 2)
-    w = partition.gemm_tile_writers(7 * 16, 16, 16, 16, 5, 1, 4)
-    assert w[(5, 0)] == {0, 1} and w[(6, 0)] == {2, 3}
-    assert all(w[(t, 0)] == {t} for t in range(5))
+def test_gemm_cut_schedule_worked_example():
+    # 7 tiles of 64 columns on 5 programs: one whole round (tiles 0..4), and
+    # the 2 remaining tiles cut into 2 narrow tiles of 32 columns: slots 5, 6
+    # = tile 5 columns [0, 32), [32, 64) and slots 7, 8 = tile 6, run by
+    # programs 0, 1, 2, 3 (program 4 idles in the last round)
+    assert partition.gemm_cut_schedule(7, 5, 64, 32) == (5, 2)
+    own = partition.gemm_owner_map_cut(16, 7 * 64, 16, 64, 5).reshape(16, 7 * 64)
+    assert [int(own[0, c]) for c in range(0, 7 * 64, 32)] == [0, 0, 1, 1, 2, 2, 3, 3, 4, 4, 0, 1, 2, 3]
 
 
-@pytest.mark.parametrize("T,P,kb,limit,expect", [(5, 3, 4, 4, (5, 1)),      # P // R = 1: nothing cut
-                                                  (10, 3, 4, 4, (9, 3)),    # R = 1: three parts
-                                                  (10, 3, 2, 4, (9, 2)),    # at most one part per K block
-                                                  (10, 3, 4, 1, (10, 1)),   # cutting disabled
-                                                  (1024, 76, 128, 4, (988, 2)),
-                                                  (12, 4, 8, 4, (12, 1))])  # no partial round
-def test_gemm_split_schedule_cases(T, P, kb, limit, expect):
-    assert partition.gemm_split_schedule(T, P, kb, limit) == expect
+@pytest.mark.parametrize("T,P,bn,unit,limit,expect", [(5, 3, 64, 32, 4, (5, 1)),     # P // R = 1: nothing cut
+                                                       (10, 3, 128, 32, 4, (9, 2)),   # 3 parts is no power of 2
+                                                       (11, 5, 128, 32, 4, (10, 4)),
+                                                       (11, 5, 128, 64, 4, (10, 2)),  # 64-column narrow tiles
+                                                       (11, 5, 64, 64, 4, (11, 1)),
+                                                       (11, 5, 128, 32, 1, (11, 1)),  # cutting disabled
+                                                       (1024, 76, 256, 64, 4, (988, 2)),
+                                                       (12, 4, 128, 32, 4, (12, 1))]) # no partial round
+def test_gemm_cut_schedule_cases(T, P, bn, unit, limit, expect):
+    assert partition.gemm_cut_schedule(T, P, bn, unit, limit) == expect
 
 
-def test_gemm_tile_writers_without_cuts_is_the_strided_owner_map():
-    m, n, bm, bn, P, G = 300, 200, 32, 64, 9, 2      # 40 tiles, 4 left for the last round
-    w = partition.gemm_tile_writers(m, n, bm, bn, P, G, 5, limit=1)
-    owner = partition.gemm_owner_map(m, n, bm, bn, P, "strided", G)
-    assert all(len(v) == 1 for v in w.values())
-    assert partition.owners_allowed(owner, m, n, bm, bn, w).all()
-    # with cuts, each cut tile has S distinct writers; whole tiles keep one
-    wc = partition.gemm_tile_writers(m, n, bm, bn, P, G, 5)
-    D, S = partition.gemm_split_schedule(len(w), P, 5)
-    assert S == 2 and sorted(len(v) for v in wc.values()).count(S) == len(w) - D
+@pytest.mark.parametrize("m,n,bm,bn,P,G", [(300, 200, 32, 64, 9, 2), (1024, 640, 128, 64, 13, 1),
+                                           (1024, 640, 256, 64, 13, 3), (96, 96, 32, 32, 4, 1)])
+def test_gemm_owner_map_cut_partitions_the_output(m, n, bm, bn, P, G):
+    own = partition.gemm_owner_map_cut(m, n, bm, bn, P, G)
+    assert own.min() >= 0 and own.max() < P            # every element owned by a program
+    no_cut = partition.gemm_owner_map_cut(m, n, bm, bn, P, G, limit=1)
+    assert np.array_equal(no_cut, partition.gemm_owner_map(m, n, bm, bn, P, "strided", G))
+    # whole tiles keep their strided owner; only the last round's tiles change
+    gm, gn = -(-m // bm), -(-n // bn)
+    D, S = partition.gemm_cut_schedule(gm * gn, P, bn, 64 if bm == 256 else 32)
+    diff = own.reshape(m, n) != no_cut.reshape(m, n)
+    for s in range(D):
+        tm, tn = partition.raster_tile(s, gm, gn, G)
+        assert not diff[tm * bm:(tm + 1) * bm, tn * bn:(tn + 1) * bn].any()
 
 
 def test_permute_heads_worked_example():

@@ -107,7 +107,8 @@ def test_autotune_table_cache_and_numerics(ctx, dtype, tmp_path):
     path = os.path.join(tmp_path, "cache.txt")
     tp.tp_autotune_save(ctx, path)
     tp.tp_autotune_load(ctx, path)
-    # every config computes the same C: a proposal never changes numerics
+    # every config computes the same C (each element is summed over K in the
+    # same order by one program): a proposal never changes numerics
     if dtype == "bf16":
         a = synth.to_bf16(synth.normal(M * K, 1)).reshape(M, K).cuda()
         bt = synth.to_bf16(synth.normal(N * K, 2)).reshape(N, K).cuda()
