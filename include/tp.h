@@ -101,9 +101,9 @@ enum {
    * validated against the partition map before it is made). Before storing
    * a tile, the storing program checks that the tile lies inside the
    * partition's grid and that the map gives it to this program, then claims
-   * the tile in a bitmap held by the context; the launch's last CTA to
-   * finish clears the bitmap again, so the next launch and every graph
-   * replay start from a clear bitmap with no extra node enqueued. A tile
+   * the tile in a bitmap held by the context; the launch's last claimant to
+   * finish claiming clears the bitmap again, so the next launch and every
+   * graph replay start from a clear bitmap with no extra node enqueued. A tile
    * that is off the grid, not the program's, or already claimed by another
    * program (two programs writing one sub-tensor: a data race, Appendix A)
    * is not stored, and the operation reports TP_ERR_RACE where it reports
@@ -112,7 +112,7 @@ enum {
    * Supported by tp_gemm and tp_gemm_fp8 on the tensor-core path (tiles of
    * 128 or 256 rows) and by tp_permute_heads_unchecked, up to 2^23 tiles per
    * launch; other operations return TP_ERR_UNSUPPORTED when it is set. The
-   * bitmap and its finished-CTA counter are one per context: checked
+   * bitmap and its finished-claimant counter are one per context: checked
    * launches of one context must not overlap in time (order them on one
    * stream), or they see each other's claims. */
   TP_EXEC_CHECKED = 1

@@ -320,6 +320,26 @@ __global__ void __launch_bounds__(kThreads, 1)
         else mbar_arrive(tempty_bar(acc));
       }
     };
+    // Checked launch: each epilogue warp counts itself done right after its
+    // last claim (still ahead of its last accumulator); the warp that counts
+    // last clears the bitmap for the next launch. A warp that leaves its loop
+    // early counts itself at the exit.
+    bool counted = false;
+    auto finish_claims = [&]() {
+      if (counted) return;
+      counted = true;
+      int last = 0;
+      if (lane == 0) {
+        __threadfence();
+        last = atomicAdd(p.claim_done, 1u) == gridDim.x * 4u - 1u ? 1 : 0;
+      }
+      if (__shfl_sync(0xffffffffu, last, 0)) {
+        __threadfence();
+        const int64_t words = (p.claim_bits + 31) / 32;
+        for (int64_t i = lane; i < words; i += 32) p.claims[i] = 0u;
+        if (lane == 0) *p.claim_done = 0u;
+      }
+    };
     for (int64_t s = prog; s < TS; s += step, ++t) {
       const Unit u = unit_of(s, p);
       const int acc = (int)(t & 1);
@@ -329,7 +349,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       bool store_ok = true;
       // claimed before the accumulator is ready, so the atomic's latency
       // hides behind the K loop
-      if constexpr (kChecked) store_ok = claim(s, tm, tn, u.part);
+      if constexpr (kChecked) {
+        store_ok = claim(s, tm, tn, u.part);
+        if (s + step >= TS) finish_claims();
+      }
       const bool ready = mbar_wait(tfull_bar(acc), use, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ready)) break;  // leave together (tcgen05.ld is warp-collective)
       tc_fence_after();
@@ -347,6 +370,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       release_acc(acc);
     }
+    if constexpr (kChecked) finish_claims();
   }
   tc_fence_before();
   if constexpr (kPair) cluster_sync();  // the peer no longer touches our shared memory / TMEM
@@ -356,7 +380,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     if constexpr (kPair) tmem_dealloc_pair(tmem_base, (uint32_t)p.tmem_cols);
     else tmem_dealloc(tmem_base, (uint32_t)p.tmem_cols);
   }
-  if constexpr (kChecked) claims_finish(p.claims, p.claim_bits, p.claim_done, gridDim.x);
 }
 
 // ---------------------------------------------------------------- host side

@@ -3,9 +3,11 @@
 // is already set means a second program is about to write the same
 // sub-tensor (a data race in the sense of Appendix A); the claim fails and
 // the context's error word records kDevRace. Off-map tiles record kDevRace as
-// well. The bitmap starts a launch all clear: the last CTA of every checked
-// launch to finish clears the bits the launch could have set, so the next
-// launch (and every replay of a captured one) starts clear without a memset.
+// well. The bitmap starts a launch all clear: every checked launch counts its
+// claimants (CTAs, or the GEMM's epilogue warps) as they make their last
+// claim, and the last one clears the bits the launch could have set, so the
+// next launch (and every replay of a captured one) starts clear without a
+// memset.
 #pragma once
 
 #include <cstdint>

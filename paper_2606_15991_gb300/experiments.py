@@ -187,6 +187,64 @@ def graph_time_ms(ctx, stream, record, reps: int, replays: int = 3) -> float:
     return best
 
 
+class _Captured:
+    """`reps` back-to-back calls captured once into a graph (the library's
+    for `record(ex)`, torch's for a plain callable); time() replays it once,
+    bracketed by CUDA events on `stream`, and returns ms per call."""
+
+    def __init__(self, ctx, stream, reps: int, record=None, torch_fn=None):
+        self.stream, self.reps = stream, reps
+        self.e0, self.e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if record is not None:
+            self.g = tp_graph_begin(ctx, stream)
+            cap = make_exec(CAPTURE, stream)
+            for _ in range(reps):
+                record(cap)
+            tp_graph_end(self.g)
+            self.ex = make_exec(SYNC, stream)
+            self.torch_graph = None
+        else:
+            with torch.cuda.stream(stream):
+                torch_fn()
+            torch.cuda.synchronize()
+            self.torch_graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.torch_graph, stream=stream):
+                for _ in range(reps):
+                    torch_fn()
+            self.g = None
+        self.time()                                    # warm-up replay
+
+    def time(self) -> float:
+        if self.g is not None:
+            self.e0.record(self.stream)
+            _check(_lib.lib().tp_graph_replay(self.g.handle, ctypes.byref(self.ex)), "tp_graph_replay")
+            self.e1.record(self.stream)
+        else:
+            with torch.cuda.stream(self.stream):
+                self.e0.record(self.stream)
+                self.torch_graph.replay()
+                self.e1.record(self.stream)
+        self.e1.synchronize()
+        return self.e0.elapsed_time(self.e1) / self.reps
+
+    def close(self) -> None:
+        if self.g is not None:
+            tp_graph_destroy(self.g)
+        self.torch_graph = None
+
+
+def _interleaved_best(variants: dict, rounds: int) -> dict:
+    """Best (lowest) ms per call of each captured variant over `rounds`
+    rounds, each round replaying every variant once in turn, so that clock
+    and power drift during the sweep falls on all variants alike."""
+    best = {k: None for k in variants}
+    for _ in range(rounds):
+        for k, v in variants.items():
+            t = v.time()
+            best[k] = t if best[k] is None else min(best[k], t)
+    return best
+
+
 def _torch_graph_time_ms(fn, stream, reps: int, replays: int = 3) -> float:
     with torch.cuda.stream(stream):
         fn()
@@ -221,7 +279,7 @@ def _host_enqueue_us(fn, calls: int = 200) -> float:
 
 
 def gemm_size_sweep(ctx, sizes=(1024, 2048, 4096, 8192, 16384, 32768), target_ms: float = 25.0,
-                    with_cublas: bool = True, log=None) -> list:
+                    with_cublas: bool = True, rounds: int = 3, log=None) -> list:
     """§5.1's safety-overhead GEMM sweep, M = N = K over `sizes`, BF16 in,
     FP32 accumulate, BF16 out, tile config tuned once per size by the
     exhaustive autotuner and shared by every variant:
@@ -232,7 +290,8 @@ def gemm_size_sweep(ctx, sizes=(1024, 2048, 4096, 8192, 16384, 32768), target_ms
       plain       tp_gemm on a plain partition (one program per tile);
       cublas      torch.matmul (cuBLAS) into a preallocated C, for context.
     Device time per GEMM from CUDA graphs of back-to-back launches (operands
-    stay L2/HBM-resident between launches, as in a loop of GEMMs). Host
+    stay L2/HBM-resident between launches, as in a loop of GEMMs), the best of
+    `rounds` interleaved rounds over the variants. Host
     enqueue cost per call (safe vs unchecked, ctypes arguments built once) is
     reported for the smallest size."""
     from . import (tp_autotune, tp_gemm, tp_gemm_unchecked, tp_partition_map, tp_partition_query, gemm_config,
@@ -262,15 +321,20 @@ def gemm_size_sweep(ctx, sizes=(1024, 2048, 4096, 8192, 16384, 32768), target_ms
         chk = make_exec(CAPTURE, stream, checked=True)
         ucfg = gemm_config(bm=best.bm, bn=best.bn, stages=best.stages, group_m=best.group_m, num_programs=progs)
         pcfg = gemm_config(bm=best.bm, bn=best.bn, stages=best.stages)
-        ms = {
-            "safe": graph_time_ms(ctx, stream, lambda ex: tp_gemm(ctx, p, a, bT, cfg, ex), reps),
-            "checked": graph_time_ms(ctx, stream, lambda ex: tp_gemm(ctx, p, a, bT, cfg, chk), reps),
-            "unchecked": graph_time_ms(ctx, stream, lambda ex: tp_gemm_unchecked(ctx, c, a, bT, ucfg, stream), reps),
-            "plain": graph_time_ms(ctx, stream, lambda ex: tp_gemm(ctx, pp, a, bT, pcfg, ex), reps),
+        variants = {
+            "safe": _Captured(ctx, stream, reps, record=lambda ex: tp_gemm(ctx, p, a, bT, cfg, ex)),
+            "checked": _Captured(ctx, stream, reps, record=lambda ex: tp_gemm(ctx, p, a, bT, cfg, chk)),
+            "unchecked": _Captured(ctx, stream, reps,
+                                   record=lambda ex: tp_gemm_unchecked(ctx, c, a, bT, ucfg, stream)),
+            "plain": _Captured(ctx, stream, reps, record=lambda ex: tp_gemm(ctx, pp, a, bT, pcfg, ex)),
         }
         if with_cublas:
             c2 = torch.empty_like(c)
-            ms["cublas"] = _torch_graph_time_ms(lambda: torch.matmul(a, bT, out=c2), stream, reps)
+            variants["cublas"] = _Captured(ctx, stream, reps, torch_fn=lambda: torch.matmul(a, bT, out=c2))
+        ms = _interleaved_best(variants, rounds)
+        for v in variants.values():
+            v.close()
+        if with_cublas:
             del c2
         row = {"n": n, "tile": [best.bm, best.bn], "stages": best.stages, "group_m": best.group_m,
                "programs": progs, "tiles": tiles, "reps": reps, "tune_s": t_tune,
