@@ -54,13 +54,17 @@ __device__ __forceinline__ float row_dot(const __nv_bfloat16* __restrict__ w, co
   const int64_t v0 = part * per, v1 = min(nv, v0 + per);
   const uint4* wv = reinterpret_cast<const uint4*>(w);
   float acc0 = 0.f, acc1 = 0.f;
-  int64_t v = v0 + lane;
-  for (; v + 32 * (kUnroll - 1) < v1; v += 32 * kUnroll) {
+  // kUnroll vectors per lane in flight per round; a row's last round is
+  // predicated rather than handled one vector at a time, so every round costs
+  // one DRAM round trip. A lane's vectors are consumed in the same order as
+  // an unrolled-then-tail loop would, so the sums are unchanged.
+  for (int64_t v = v0 + lane; v < v1; v += 32 * kUnroll) {
     uint4 q[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) q[u] = __ldcs(wv + v + 32 * u);
+    for (int u = 0; u < kUnroll; ++u) q[u] = v + 32 * u < v1 ? __ldcs(wv + v + 32 * u) : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
+      if (v + 32 * u >= v1) break;
       const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q[u]);
       const float4* xv = reinterpret_cast<const float4*>(xs + (v + 32 * u) * 8);
       const float4 xa = xv[0], xb = xv[1];
@@ -71,18 +75,6 @@ __device__ __forceinline__ float row_dot(const __nv_bfloat16* __restrict__ w, co
       acc0 = fmaf(f2.x, xb.x, acc0); acc1 = fmaf(f2.y, xb.y, acc1);
       acc0 = fmaf(f3.x, xb.z, acc0); acc1 = fmaf(f3.y, xb.w, acc1);
     }
-  }
-  for (; v < v1; v += 32) {
-    const uint4 q = __ldcs(wv + v);
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
-    const float4* xv = reinterpret_cast<const float4*>(xs + v * 8);
-    const float4 xa = xv[0], xb = xv[1];
-    float2 f0 = __bfloat1622float2(h[0]), f1 = __bfloat1622float2(h[1]);
-    float2 f2 = __bfloat1622float2(h[2]), f3 = __bfloat1622float2(h[3]);
-    acc0 = fmaf(f0.x, xa.x, acc0); acc1 = fmaf(f0.y, xa.y, acc1);
-    acc0 = fmaf(f1.x, xa.z, acc0); acc1 = fmaf(f1.y, xa.w, acc1);
-    acc0 = fmaf(f2.x, xb.x, acc0); acc1 = fmaf(f2.y, xb.y, acc1);
-    acc0 = fmaf(f3.x, xb.z, acc0); acc1 = fmaf(f3.y, xb.w, acc1);
   }
   // elements past the last full vector (k % 8), handled by the last part
   if (part == parts - 1)
