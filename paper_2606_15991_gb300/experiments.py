@@ -235,12 +235,15 @@ class _Captured:
 
 def _interleaved_best(variants: dict, rounds: int) -> dict:
     """Best (lowest) ms per call of each captured variant over `rounds`
-    rounds, each round replaying every variant once in turn, so that clock
-    and power drift during the sweep falls on all variants alike."""
-    best = {k: None for k in variants}
-    for _ in range(rounds):
-        for k, v in variants.items():
-            t = v.time()
+    rounds (at least one per variant), each round replaying every variant
+    once in turn, the starting variant rotating from round to round, so that
+    clock and power drift (and the burst after an idle gap) fall on all
+    variants alike."""
+    names = list(variants)
+    best = {k: None for k in names}
+    for r in range(max(rounds, len(names))):
+        for k in names[r % len(names):] + names[:r % len(names)]:
+            t = variants[k].time()
             best[k] = t if best[k] is None else min(best[k], t)
     return best
 

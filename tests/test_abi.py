@@ -117,3 +117,13 @@ def test_ctx_create_without_gpu_fails_cleanly(built_lib):
     st = _status("tp_ctx_create", 0, ctypes.byref(h))
     assert st in (_lib.ERR_CUDA, _lib.ERR_INVALID) and not h.value
     assert built_lib.tp_last_error_detail()
+
+
+def test_empty_outputs_with_any_strides_are_partitionable():
+    # torch gives a (128, 0) tensor strides (1, 1): an empty view is contiguous
+    import torch
+    for shape in ((128, 0), (0, 64), (0,), (3, 0, 5)):
+        t = torch.zeros(shape)
+        p = tp.tp_partition_create(None, t, tuple(4 for _ in shape))
+        assert tp.tp_partition_query(p)["num_tiles"] == 0
+        tp.tp_partition_destroy(p)
