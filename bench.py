@@ -36,6 +36,7 @@ TILE = 4096
 ALPHA = 0.5
 MAPS = [("axpy", "f32"), ("gelu_mul", "f32"), ("axpy", "bf16"), ("gelu_mul", "bf16")]
 ESIZE = {"f32": 4, "bf16": 2}
+NOMINAL = {"hbm_gbs": 8000.0, "bf16_tflops": 2250.0, "fp8_tflops": 4500.0}   # GB300 dense, per GPU
 METRIC = "GEMM TFLOP/s & map TB/s vs GB300 roofline; grouped vs plain speedup at stated error"
 WORKLOAD = "element-wise maps over 2^28 elements, fp32 and bf16: z=0.5*x+y and y=gelu_tanh(x)*w, 4096-element tiles"
 
@@ -163,6 +164,40 @@ def cpu_oracle_sample(seconds: float = 12.0):
     return {"value": bytes_done / el / 1e12, "unit": "TB/s", "cores": 1, "kind": "oracle",
             "sample": f"{reps} passes of the 4 maps over 2^22 of the 2^28 elements (numpy float64, 1 thread), "
                       f"{el:.1f} s"}
+
+
+def cpu_oracle_gemm_rows(seconds: float = 4.0) -> dict:
+    """The FP64 GEMM oracle (as it stands: a float64 matmul over the exact
+    input values) on the host: the full 512^3 FP32 configuration, and 128x128
+    output tiles of the 8192^3 configuration (K = 8192) timed and
+    extrapolated to the 4096 tiles of the full product."""
+    import numpy as np
+
+    import synth
+    from oracle import gemm as ogemm
+
+    out = {}
+    a = synth.uniform(512 * 512, 0).reshape(512, 512)
+    b = synth.uniform(512 * 512, 1).reshape(512, 512)
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds / 2:
+        ogemm.gemm(a, b)
+        reps += 1
+    el = (time.perf_counter() - t0) / reps
+    out["gemm_f32_512"] = {"tflops": 2 * 512 ** 3 / el / 1e12, "ms": el * 1e3, "kind": "oracle", "sample": "full"}
+    K = 8192
+    at = synth.normal(128 * K, 2).reshape(128, K)
+    bt = synth.normal(128 * K, 3).reshape(K, 128)
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds / 2:
+        ogemm.gemm(at, bt)
+        reps += 1
+    el = (time.perf_counter() - t0) / reps
+    out["gemm_bf16_8192"] = {"tflops": 2 * 128 * 128 * K / el / 1e12, "ms_extrapolated": el * 4096 * 1e3,
+                             "kind": "oracle", "sample": f"{reps} 128x128 output tiles with K = 8192, "
+                                                          "extrapolated to the 4096 tiles of 8192^3"}
+    out["threads"] = "numpy's BLAS threads (all host cores unless limited)"
+    return out
 
 
 def _oracle_worker_init(n: int, seed: int):
@@ -352,7 +387,7 @@ def run_ours(args):
     achieved = dom_bytes / (per_kernel[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": f"map_vec_kernel<{dom[0]},{dom[1]}>", "achieved": achieved,
                 "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                "peak_src": peaks["src"],
+                "peak_src": peaks["src"], "frac_of_nominal": achieved / NOMINAL["hbm_gbs"],
                 "traffic": _traffic(f"{dom[0]}_{dom[1]}", "map_kernels.cu"),
                 "algorithmic_bytes_per_launch": dom_bytes,
                 "per_map_gbs": {f"{o}_{d}": _map_bytes(d) / (t * 1e-3) / 1e9 for (o, d), t in per_kernel.items()}}
@@ -413,6 +448,7 @@ def run_ours(args):
         pool.close()
         single = cpu_oracle_sample(seconds=args.cpu_seconds / 2)
         cpu["single_thread"] = {"value": single["value"], "unit": "TB/s", "sample": single["sample"]}
+        cpu["rows"] = cpu_oracle_gemm_rows()
 
     if rank == 0:
         print(json.dumps({
@@ -490,6 +526,7 @@ def secondary_rows(tp, ctx, dev, stream, peaks):
     rows["gemm_bf16_8192"] = {
         "tflops": tf, "ms": ms, "tile": [256, 256], "programs": ctx.sm_count // 2,
         "roofline": {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac_of_nominal": tf / NOMINAL["bf16_tflops"],
                      "frac": tf / peaks["bf16_tflops"], "peak_src": peaks["src"] + " bf16 burst"}}
 
     # FP8: amax + quantize (HBM passes, reported separately) and the GEMM
@@ -517,6 +554,7 @@ def secondary_rows(tp, ctx, dev, stream, peaks):
         "quantize_ms": qms, "quantize_gbs": qbytes / (qms * 1e-3) / 1e9,
         "tflops_incl_quantize": flops / ((ms8 + qms) * 1e-3) / 1e12,
         "roofline": {"bound": "tensor", "achieved": tf8, "peak": peak8, "unit": "TFLOP/s", "frac": tf8 / peak8,
+                     "frac_of_nominal": tf8 / NOMINAL["fp8_tflops"],
                      "peak_src": peaks["src"] + " bf16 burst x 2 (nominal fp8:bf16 dense ratio)"}}
     for h in (p, pqa, pqb):
         tp.tp_partition_destroy(h)
