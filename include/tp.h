@@ -254,7 +254,8 @@ tp_status tp_graph_destroy(tp_graph* g);
 tp_status tp_map_axpy(tp_ctx* ctx, tp_partition* z, float alpha, const tp_tensor* x,
                       const tp_tensor* y, const tp_exec* ex);
 /* y = gelu_tanh(x) * w, gelu_tanh(x) = 0.5 x (1 + tanh(sqrt(2/pi)(x + 0.044715 x^3)))
- * evaluated as x / (1 + exp(-2u)); same layout rules as tp_map_axpy. */
+ * evaluated as x / (1 + exp(-2u)) with exp(-2u) = 2^(-2u log2 e) on the
+ * hardware base-2 exponential; same layout rules as tp_map_axpy. */
 tp_status tp_map_gelu_mul(tp_ctx* ctx, tp_partition* y, const tp_tensor* x,
                           const tp_tensor* w, const tp_exec* ex);
 /* y = x * g element-wise (§5.2's pipeline kernel); same rules. */

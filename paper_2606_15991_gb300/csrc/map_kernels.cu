@@ -29,16 +29,24 @@ struct MapArgs {
   int64_t grid[3];
 };
 
+// 2^a by the hardware base-2 exponential (flush-to-zero).
+__device__ __forceinline__ float ex2_approx(float a) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
+
 // gelu_tanh(x) = 0.5 x (1 + tanh(u)), u = sqrt(2/pi) (x + 0.044715 x^3),
-// evaluated as x / (1 + exp(-2u)) (0.5 (1 + tanh u) = 1 / (1 + exp(-2u))).
-// The exponent argument is capped at 80 so 1 + exp(.) stays below 2^126,
-// the range where the fast division is defined; the result there is ~0.
+// evaluated as x / (1 + exp(-2u)) (0.5 (1 + tanh u) = 1 / (1 + exp(-2u))),
+// with exp(-2u) = 2^t, t = -2 log2(e) u = x (c0 + c1 x^2): one polynomial,
+// one base-2 exponential, one fast division. t is capped at 125 so 1 + 2^t
+// stays below 2^126, the range where the fast division is defined; the
+// result there is ~0.
 __device__ __forceinline__ float gelu_tanh(float x) {
-  const float k0 = 0.7978845608028654f;          // sqrt(2/pi)
-  const float k1 = 0.7978845608028654f * 0.044715f;
-  float u = x * fmaf(k1, x * x, k0);
-  float e = __expf(fminf(-2.f * u, 80.f));
-  return __fdividef(x, 1.f + e);
+  const float c0 = -2.f * 1.4426950408889634f * 0.7978845608028654f;  // -2 log2(e) sqrt(2/pi)
+  const float c1 = c0 * 0.044715f;
+  const float t = fminf(x * fmaf(c1, x * x, c0), 125.f);
+  return __fdividef(x, 1.f + ex2_approx(t));
 }
 
 template <int OP>

@@ -49,7 +49,7 @@ def _bound(op, dt, ref, x, y, c0):
     elif op == "add_accum":
         b = 2 * u32 * (np.abs(_f(c0)) + np.abs(_f(x)) + np.abs(_f(y)))
     else:
-        b = 2e-5 * ref                               # __expf + fast division, see kernel
+        b = 2e-5 * ref                               # base-2 exponential + fast division, see kernel
     if dt == "bf16":
         b = b + (u16 + u32) * ref
     return b + 1e-37
