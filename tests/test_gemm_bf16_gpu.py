@@ -244,3 +244,23 @@ def test_split_k_validation(ctx):
     with pytest.raises(tp.TPError) as e:
         _gemm(ctx, a, bt, bn=64, P=3, split_k=9)
     assert e.value.status == tp._lib.ERR_INVALID
+
+
+@pytest.mark.parametrize("bm,P", [(128, 0), (128, 7), (256, 0), (256, 5)])
+def test_unchecked_raw_pointer_gemm_matches_partitioned(ctx, bm, P):
+    """tp_gemm_unchecked runs the same schedule on a raw C pointer: C is
+    bit-identical to tp_gemm on the equivalent partition (plain for
+    num_programs = 0, strided otherwise), and matches the oracle."""
+    m, n, k = 640, 768, 320
+    a, bt = _operands(m, n, k, seed=21)
+    kind = tp.MAP_IDENTITY if P == 0 else tp.MAP_STRIDED
+    ref, _, _, _ = _gemm(ctx, a, bt, bn=128, kind=kind, P=P or None, bm=bm)
+    c = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
+    s = torch.cuda.Stream()
+    tp.tp_gemm_unchecked(ctx, c, a, bt.t(), tp.gemm_config(bm=bm, bn=128, num_programs=P), s)
+    s.synchronize()
+    assert torch.equal(c, ref)
+    assert ogemm.rel_frobenius(c.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 1e-2
+    with pytest.raises(tp.TPError) as e:
+        tp.tp_gemm_unchecked(ctx, c, a, bt.t(), tp.gemm_config(bm=64, bn=128), s)
+    assert e.value.status == tp._lib.ERR_INVALID
