@@ -1,9 +1,12 @@
 // Tensor-core GEMM for sm_103a: C (bf16) = A . B with BF16 (kind::f16) or
 // FP8-E4M3 (kind::f8f6f4) operands and FP32 accumulation in TMEM.
 //
-// One output tile of 128 x BN per tile program with a K loop (§3.6,
-// Listing 6: the program walks its mapped sequence of output tiles and, for
-// each, accumulates mma over the K tiles). A persistent CTA runs one program:
+// One output tile of 128 x BN (one CTA) or 256 x BN (a CTA pair running
+// cta_group::2 MMAs) per tile program step, with a K loop (§3.6, Listing 6:
+// the program walks its mapped sequence of output tiles and, for each,
+// accumulates mma over the K tiles). On a strided map the tiles of the last,
+// partial round may be cut along N into narrow tiles for programs that would
+// otherwise idle. A persistent CTA (or CTA pair) runs one program:
 //   warp 0   TMA producer: streams (A, B) K-slices into a ring of shared-
 //            memory stages (128-byte swizzle), guarded by full/empty mbarriers;
 //   warp 1   MMA issuer: one thread issues tcgen05.mma into one of two TMEM
@@ -13,7 +16,9 @@
 //            bf16 and store only inside this program's tile, while the MMA
 //            warp already fills the other accumulator.
 // Every mbarrier wait is bounded; on timeout the kernel records an error,
-// drains its in-flight copies and MMAs, frees TMEM and returns.
+// drains its in-flight copies and MMAs, frees TMEM and returns. The checked
+// build (TP_EXEC_CHECKED) validates and claims every tile before storing it;
+// the write-count build records each stored element's writer.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
