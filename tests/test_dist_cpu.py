@@ -28,9 +28,11 @@ def _rank_main(rank, ws, port, q):
     got_ws, got_rank, got_local = bench._dist()
     ms = bench._barrier_max(10.0 + 5.0 * rank, ws, torch.device("cpu"))
     value = bench.weak_scaling_value(got_ws, 3.0e9, ms)
+    all_ok = bench._all_ranks_ok(True, ws, torch.device("cpu"))
+    one_failed = bench._all_ranks_ok(rank == 0, ws, torch.device("cpu"))   # rank 1 reports a failure
     dist.barrier()
     dist.destroy_process_group()
-    q.put((rank, got_ws, got_rank, got_local, ms, value))
+    q.put((rank, got_ws, got_rank, got_local, ms, value, all_ok, one_failed))
 
 
 @pytest.mark.timeout(120)
@@ -45,7 +47,8 @@ def test_two_gloo_ranks_take_the_max_step_time():
     for p in procs:
         p.join(timeout=30)
         assert p.exitcode == 0
-    for rank, ws, r, local, ms, value in out:
+    for rank, ws, r, local, ms, value, all_ok, one_failed in out:
+        assert all_ok and not one_failed                   # every rank sees the same verdict
         assert (ws, r, local) == (2, rank, rank)
         assert ms == 15.0                                   # the slower rank's time, on every rank
         assert value == pytest.approx(2 * 3.0e9 / 15e-3 / 1e12)
@@ -59,3 +62,4 @@ def test_single_process_defaults(monkeypatch):
     assert bench._dist() == (1, 0, 0)
     assert bench._barrier_max(7.0, 1, None) == 7.0
     assert bench.weak_scaling_value(1, 1e12, 1000.0) == pytest.approx(1.0)
+    assert bench._all_ranks_ok(True, 1, None) and not bench._all_ranks_ok(False, 1, None)
