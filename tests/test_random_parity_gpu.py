@@ -104,3 +104,37 @@ def test_random_map(ctx, case):
         assert np.array_equal(owner.cpu().numpy(), opart.owner_map((n,), (tile,), P, kname))
     else:
         assert owner.min().item() >= 0 and owner.max().item() < P
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_random_grouped(ctx, case):
+    """Random groups (1..24 problems, M in [1, 900], N in [1, 700], K a
+    multiple of 8 up to 512, both orientations, single CTAs or pairs):
+    integer inputs, every C_i bit-exact against the oracle and every element
+    of every C_i written exactly once."""
+    from oracle import grouped as ogrouped
+
+    u = synth.uniform(8 * 64, 700, 0.0, 1.0, dtype=np.float64).reshape(8, 64)[case]
+    count = 1 + int(u[0] * 24)
+    pair = u[1] < 0.5
+    probs, shapes = [], []
+    for i in range(count):
+        m = 1 + int(u[2 + 3 * (i % 20)] ** 2 * 900)
+        n = 1 + int(u[3 + 3 * (i % 20)] * 700)
+        k = 8 * (1 + int(u[4 + 3 * (i % 20)] * 64))
+        a = synth.to_bf16(synth.integers(m * k, 800 + 10 * case + i, -4, 4)).reshape(m, k).cuda()
+        bt = synth.to_bf16(synth.integers(n * k, 900 + 10 * case + i, -4, 4)).reshape(n, k).cuda()
+        probs.append((a, bt.t(), torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)))
+        shapes.append((m, n, k))
+    plan = tp.tp_grouped_plan_create(ctx, probs, cta_pair=pair)
+    total, swapped = tp.tp_grouped_plan_info(plan)
+    assert swapped == [m <= 256 for m, _, _ in shapes]
+    n_el = sum(m * n for m, n, _ in shapes)
+    counts = torch.zeros(n_el, dtype=torch.int32, device="cuda")
+    owner = torch.full((n_el,), -1, dtype=torch.int32, device="cuda")
+    tp.tp_grouped_gemm(ctx, plan, 0, tp.make_exec(write_counts=counts, write_owner=owner))
+    tp.tp_grouped_plan_destroy(plan)
+    for (a, b, c), shape in zip(probs, shapes):
+        exact = ogemm.gemm(a.cpu(), b.cpu())
+        assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(exact)), shape
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
