@@ -28,7 +28,7 @@ __all__ = [
     "tp_grouped_plan_create", "tp_grouped_plan_info", "tp_grouped_plan_destroy", "tp_grouped_gemm",
     "tp_rmsnorm", "tp_gemv", "tp_silu_mul", "tp_residual_add", "tp_decode_norm_qkv_gu",
     "tp_decode_down_residual", "DecodeChain", "tp_permute_heads", "tp_permute_heads_unchecked",
-    "tp_gemm_unchecked", "tp_diag_bounded_wait",
+    "tp_gemm_unchecked", "tp_diag_bounded_wait", "tp_gemm_resident_programs",
     "tp_autotune_space", "tp_autotune", "tp_autotune_lookup", "tp_autotune_save", "tp_autotune_load",
     "tp_mlp_create", "tp_mlp_destroy", "tp_mlp_num_params", "tp_mlp_get_params", "tp_mlp_set_params",
     "tp_mlp_forward", "tp_mlp_loss_grad", "tp_mlp_train_step", "tp_mlp_save", "tp_mlp_load",
@@ -226,8 +226,8 @@ def make_exec(mode: int = SYNC, stream=None, event: Event | None = None, write_c
     return ex
 
 
-def gemm_config(bm=0, bn=0, bk=0, stages=0, group_m=0, num_programs=0, swap_ab=0, split_k=0):
-    return tp_gemm_config(bm, bn, bk, stages, group_m, num_programs, swap_ab, split_k)
+def gemm_config(bm=0, bn=0, bk=0, stages=0, group_m=0, num_programs=0, swap_ab=0, split_k=0, cluster_pairs=0):
+    return tp_gemm_config(bm, bn, bk, stages, group_m, num_programs, swap_ab, split_k, cluster_pairs)
 
 
 def _ex(ex):
@@ -263,6 +263,13 @@ def tp_gemm(ctx, c: Partition, a, b, cfg: tp_gemm_config | None = None, ex: tp_e
     da, db = tensor_desc(a), tensor_desc(b)
     call("tp_gemm", ctx.handle, c.handle, ctypes.byref(da), ctypes.byref(db),
          ctypes.byref(cfg) if cfg is not None else None, _ex(ex))
+
+
+def tp_gemm_resident_programs(ctx, cfg: tp_gemm_config) -> int:
+    """Programs (CTA pairs for 256-row tiles, else CTAs) resident at once."""
+    n = ctypes.c_int32()
+    call("tp_gemm_resident_programs", ctx.handle, ctypes.byref(cfg), ctypes.byref(n))
+    return n.value
 
 
 def tp_gemm_unchecked(ctx, c, a, b, cfg: tp_gemm_config, stream=None) -> None:

@@ -50,7 +50,7 @@ class tp_partition_info(ctypes.Structure):
 
 class tp_gemm_config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
-                ("bm", "bn", "bk", "stages", "group_m", "num_programs", "swap_ab", "split_k")]
+                ("bm", "bn", "bk", "stages", "group_m", "num_programs", "swap_ab", "split_k", "cluster_pairs")]
 
 
 class tp_gemm_problem(ctypes.Structure):
@@ -135,6 +135,7 @@ _PROTOS = {
     "tp_propose": [_VP, _VP, _I64, _I64, _I64, _I32, ctypes.c_float, ctypes.POINTER(tp_gemm_config), _VP, _PI32],
     "tp_map_axpy_queue_noalloc": [_VP, _VP, _VP, _I32, _I64, _I64, _I32, ctypes.c_float, _VP],
     "tp_diag_bounded_wait": [_VP, _I64, _I32, _PE],
+    "tp_gemm_resident_programs": [_VP, ctypes.POINTER(tp_gemm_config), _PI32],
     "tp_gemm_unchecked": [_VP, _VP, _PT, _PT, ctypes.POINTER(tp_gemm_config), _VP],
     "tp_permute_heads": [_VP, _VP, _PT, _I64, _PE],
     "tp_permute_heads_unchecked": [_VP, _VP, _VP, _I64, _I64, _I64, _I64, _I64, _I32, _PE],

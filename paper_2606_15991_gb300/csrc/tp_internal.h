@@ -195,6 +195,10 @@ tp_status launch_gemm_tc(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const
                          const tp_gemm_config* cfg, const tp_exec* ex, cudaStream_t stream,
                          unsigned* queue);
 
+// Programs of the tensor-core GEMM (CTA pairs for 256-row tiles, CTAs
+// otherwise) that can be resident at once for `cfg`.
+tp_status gemm_tc_resident(tp_ctx* ctx, const tp_gemm_config* cfg, int32_t* programs);
+
 tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_tensor* b,
                               const tp_gemm_config* cfg, const tp_exec* ex, cudaStream_t stream, int esize,
                               const float* scale_a, const float* scale_b);

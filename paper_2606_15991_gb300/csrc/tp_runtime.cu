@@ -803,6 +803,12 @@ tp_status tp_gemm(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_ten
   return o.end(cudaGetLastError());
 }
 
+tp_status tp_gemm_resident_programs(tp_ctx* ctx, const tp_gemm_config* cfg, int32_t* programs) {
+  if (!ctx || !cfg || !programs) return fail(TP_ERR_INVALID, "null argument");
+  DeviceGuard guard(ctx);
+  return gemm_tc_resident(ctx, cfg, programs);
+}
+
 tp_status tp_gemm_unchecked(tp_ctx* ctx, void* c, const tp_tensor* a, const tp_tensor* b, const tp_gemm_config* cfg,
                             void* stream) {
   if (!ctx || !c || !a || !b || !cfg) return fail(TP_ERR_INVALID, "null argument");
