@@ -164,13 +164,6 @@ typedef struct tp_gemm_config {
                         * by one program, so C is bit-identical either way.
                         * Limit: 0 = 4 (default), 1 = never cut, 2..8.
                         * SIMT GEMM: ignored.                                 */
-  int32_t cluster_pairs;/* 0 or 1: one CTA pair (or CTA) per program. 2: with
-                        * 256-row tiles on a strided map, a program is a
-                        * cluster of two CTA pairs computing the horizontally
-                        * adjacent tiles (r, 2j) and (r, 2j + 1): the rows of
-                        * A they share are loaded once and multicast to both
-                        * pairs; num_programs counts CTA pairs and must be
-                        * even; the last round is not cut.                    */
 } tp_gemm_config;
 
 /* ---------------------------------------------------------------- errors */
@@ -322,8 +315,7 @@ tp_status tp_gemm(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_ten
                   const tp_gemm_config* cfg, const tp_exec* ex);
 
 /* How many programs of the tensor-core GEMM can be resident on the device at
- * once for `cfg` (bm 128 or 256, bn, stages, cluster_pairs; 0 fields take
- * the defaults): CTA pairs for 256-row tiles, CTAs for 128-row tiles. A
+ * once for `cfg` (bm 128 or 256, bn, stages; 0 fields take the defaults): CTA pairs for 256-row tiles, CTAs for 128-row tiles. A
  * persistent launch with more programs than this runs the extra ones after
  * others finish. Errors: TP_ERR_INVALID, TP_ERR_UNSUPPORTED, TP_ERR_CUDA. */
 tp_status tp_gemm_resident_programs(tp_ctx* ctx, const tp_gemm_config* cfg, int32_t* programs);

@@ -156,29 +156,6 @@ def gemm_owner_map_cut(m: int, n: int, bm: int, bn: int, programs: int, group_m:
     return owner.reshape(-1)
 
 
-def gemm_owner_map_pair_clusters(m: int, n: int, bn: int, pairs: int, group_m: int = 1) -> np.ndarray:
-    """Writer id per element of an M x N output with 256-row tiles computed
-    by clusters of two CTA pairs: P pairs form P // 2 cluster programs; units
-    are pairs of horizontally adjacent tiles, unit (r, j) covering tiles
-    (r, 2j) and (r, 2j + 1) of the grid, placed by raster_tile over the
-    (rows x ceil(cols / 2)) unit grid; cluster c runs units c, c + P/2, ...,
-    and its pair q (0 or 1) writes tile (r, 2j + q) as writer 2c + q (a tile
-    past the last column is not written)."""
-    bm = 256
-    gm, gn = -(-m // bm), -(-n // bn)
-    gu = -(-gn // 2)
-    clusters = pairs // 2
-    owner = np.full((m, n), -1, dtype=np.int64)
-    for s in range(gm * gu):
-        c = s % clusters
-        tm, j = raster_tile(s, gm, gu, group_m)
-        for q in (0, 1):
-            tn = 2 * j + q
-            if tn < gn:
-                owner[tm * bm:(tm + 1) * bm, tn * bn:(tn + 1) * bn] = 2 * c + q
-    return owner.reshape(-1)
-
-
 def write_counts(n_elements: int, writes) -> np.ndarray:
     """Count per element from an iterable of (program, flat element index)."""
     counts = np.zeros(n_elements, dtype=np.int64)

@@ -102,7 +102,7 @@ __device__ __forceinline__ void raster(int64_t s, int64_t gm, int64_t gn, int64_
   *tn = r / rows;
 }
 
-template <bool kF8, bool kPair, bool kCount, bool kChecked, bool kMc>
+template <bool kF8, bool kPair, bool kCount, bool kChecked>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                    const __grid_constant__ CUtensorMap map_b_cut, const __grid_constant__ TcArgs p) {
@@ -115,19 +115,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int lane = threadIdx.x % 32;
   // A CTA pair computes a 256-row tile: this CTA holds rows [rank*128, +128)
   // of A and of the accumulator, and B rows (tile columns) [rank*bn/2, +bn/2).
-  // With kMc a program is a cluster of two CTA pairs computing horizontally
-  // adjacent tiles (columns 2j and 2j + 1 of the same tile row): the first
-  // pair's CTAs load the shared A rows once and multicast them to both pairs.
-  const uint32_t crank = kPair ? cluster_ctarank() : 0u;  // rank in the cluster
-  const uint32_t rank = crank & 1u;                       // rank in the CTA pair
-  const uint32_t pidx = kMc ? (crank >> 1) : 0u;          // pair within the cluster
-  const uint32_t lrank = crank & ~1u;                     // cluster rank of this pair's leader
+  const uint32_t rank = kPair ? cluster_ctarank() : 0u;
   const bool leader = rank == 0;
-  constexpr int64_t kCtasPerProg = kMc ? 4 : (kPair ? 2 : 1);
-  const int64_t prog = (int64_t)blockIdx.x / kCtasPerProg;
-  const int64_t nprog = (int64_t)gridDim.x / kCtasPerProg;
-  // id recorded as the writer of each stored element (one per CTA pair)
-  const int64_t writer = kMc ? 2 * prog + pidx : prog;
+  const int64_t prog = kPair ? (int64_t)(blockIdx.x / 2) : (int64_t)blockIdx.x;
+  const int64_t nprog = kPair ? (int64_t)(gridDim.x / 2) : (int64_t)gridDim.x;
   const int tile_m = kPair ? 2 * BM : BM;
   const int b_rows = kPair ? p.bn / 2 : p.bn;
   const uint32_t a_stage = BM * 128;
@@ -147,7 +138,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) {
       mbar_init(full_bar(s), 1);
-      mbar_init(empty_bar(s), kMc ? 2 : 1);  // kMc: a stage is free once both pairs consumed it
+      mbar_init(empty_bar(s), 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull_bar(b), 1);
@@ -183,16 +174,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int64_t TS = p.total_slots;
   const int64_t step = p.kind == TP_MAP_IDENTITY ? T : nprog;
   const int64_t nk = (p.K + p.kblk - 1) / p.kblk;
-  // tile of a unit; with kMc units are tile pairs (tile row, column pair)
-  auto tile_of = [&](const Unit& u, int64_t* tm, int64_t* tn) {
-    if constexpr (kMc) {
-      int64_t tsn;
-      raster(u.tile, p.gm, (p.gn + 1) / 2, p.group_m, tm, &tsn);
-      *tn = 2 * tsn + pidx;
-    } else {
-      raster(u.tile, p.gm, p.gn, p.group_m, tm, tn);
-    }
-  };
 
   if (warp == 0) {
     // ---------------- TMA producer (one thread; the rest of the warp waits)
@@ -206,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t s = prog; s < TS && ok; s += step) {
         const Unit u = unit_of(s, p);
         int64_t tm, tn;
-        tile_of(u, &tm, &tn);
+        raster(u.tile, p.gm, p.gn, p.group_m, &tm, &tn);
         // a narrow tile loads only its own columns of B, through the map whose
         // box has that many rows
         const int ub_rows = kPair ? u.width / 2 : u.width;
@@ -218,17 +199,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err)) { ok = false; break; }
           const int32_t kc = (int32_t)(kb * p.kblk);
           if constexpr (kPair) {
-            // both CTAs' copies complete on the pair leader's full barrier
-            const uint32_t fb = mapa(full_bar(stage), lrank);
+            // both CTAs' copies complete on the even CTA's full barrier
+            const uint32_t fb = mapa(full_bar(stage), 0);
             if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * utx);
-            if constexpr (kMc) {
-              // this CTA's A rows go to both pairs (same rank in each pair)
-              if (pidx == 0)
-                tma_load_2d_pair_multicast(a0 + a_stage * stage, &map_a, kc, arow, fb,
-                                           (uint16_t)((1u << rank) | (1u << (2 + rank))), pol_a);
-            } else {
-              tma_load_2d_pair(a0 + a_stage * stage, &map_a, kc, arow, fb, pol_a);
-            }
+            tma_load_2d_pair(a0 + a_stage * stage, &map_a, kc, arow, fb, pol_a);
             tma_load_2d_pair(b0 + b_stage * stage, mb, kc, brow, fb, pol_b);
           } else {
             mbar_arrive_expect_tx(full_bar(stage), utx);
@@ -277,17 +251,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             if constexpr (kPair) mma_pair<kF8>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accum);
             else mma<kF8>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accum);
           }
-          if constexpr (kMc) mma_commit_pair(empty_bar(stage), 0xF);  // both pairs' stages
-          else if constexpr (kPair) mma_commit_pair(empty_bar(stage), 0x3);
+          if constexpr (kPair) mma_commit_pair(empty_bar(stage), 0x3);
           else mma_commit(empty_bar(stage));
           if (++stage == p.stages) { stage = 0; phase ^= 1u; }
         }
         if (!ok) break;
-        if constexpr (kPair) mma_commit_pair(tfull_bar(acc), (uint16_t)(0x3u << (2 * pidx)));
+        if constexpr (kPair) mma_commit_pair(tfull_bar(acc), 0x3);
         else mma_commit(tfull_bar(acc));
       }
       if (!ok) {
-        if constexpr (kPair) mma_commit_pair(drain_bar, (uint16_t)(1u << crank));
+        if constexpr (kPair) mma_commit_pair(drain_bar, 0x1);
         else mma_commit(drain_bar);
         mbar_wait(drain_bar, 0, nullptr, nullptr, 200000000ull);
       }
@@ -299,7 +272,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row_in_tile = (int)rank * BM + quad * 32 + lane;
     // FP8 dequantisation factor 1 / (s_A * s_B), both steps in fp32
     const float scale = (p.scale_a && p.scale_b) ? 1.f / (*p.scale_a * *p.scale_b) : 1.f;
-    const uint32_t tempty_remote = kPair ? mapa(tempty_bar(0), lrank) : 0u;
+    const uint32_t tempty_remote = kPair ? mapa(tempty_bar(0), 0) : 0u;
     int64_t t = 0;
     // validate a store against the map (the slot is this program's and its
     // tile lies in the grid), then claim this warp's 32-row slice of the
@@ -340,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int i = 0; i < 32; ++i)
           if (c0 + i < p.N) {
             atomicAdd(p.counts + row * p.N + c0 + i, 1u);
-            p.owner[row * p.N + c0 + i] = (int32_t)writer;
+            p.owner[row * p.N + c0 + i] = (int32_t)prog;
           }
       }
     };
@@ -377,13 +350,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int acc = (int)(t & 1);
       const uint32_t use = (uint32_t)((t >> 1) & 1);
       int64_t tm, tn;
-      tile_of(u, &tm, &tn);
-      // kMc: the second pair's tile of the last column pair may fall past N
-      bool store_ok = !kMc || tn < p.gn;
+      raster(u.tile, p.gm, p.gn, p.group_m, &tm, &tn);
+      bool store_ok = true;
       // claimed before the accumulator is ready, so the atomic's latency
       // hides behind the K loop
       if constexpr (kChecked) {
-        if (store_ok) store_ok = claim(s, tm, tn, u.part);
+        store_ok = claim(s, tm, tn, u.part);
         if (s + step >= TS) finish_claims();
       }
       const bool ready = mbar_wait(tfull_bar(acc), use, abort_flag, p.err);
@@ -449,10 +421,10 @@ tp_status make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t k, i
   return TP_OK;
 }
 
-template <bool kF8, bool kPair, bool kCount, bool kChecked, bool kMc>
+template <bool kF8, bool kPair, bool kCount, bool kChecked>
 cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mbc, const TcArgs& p,
                           int grid, size_t smem, cudaStream_t st) {
-  auto k = gemm_tc_kernel<kF8, kPair, kCount, kChecked, kMc>;
+  auto k = gemm_tc_kernel<kF8, kPair, kCount, kChecked>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
@@ -466,7 +438,7 @@ cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const CU
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kMc ? 4 : (kPair ? 2 : 1);
+  attr[0].val.clusterDim.x = kPair ? 2 : 1;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -476,36 +448,35 @@ cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const CU
   return cudaLaunchKernelEx(&cfg, k, ma, mb, mbc, p);
 }
 
-template <bool kF8, bool kPair, bool kMc>
+template <bool kF8, bool kPair>
 cudaError_t launch_inst(bool count, bool checked, const CUtensorMap& ma, const CUtensorMap& mb,
                         const CUtensorMap& mbc, const TcArgs& p, int grid, size_t smem, cudaStream_t st) {
-  if (checked) return count ? launch_kernel<kF8, kPair, true, true, kMc>(ma, mb, mbc, p, grid, smem, st)
-                            : launch_kernel<kF8, kPair, false, true, kMc>(ma, mb, mbc, p, grid, smem, st);
-  return count ? launch_kernel<kF8, kPair, true, false, kMc>(ma, mb, mbc, p, grid, smem, st)
-               : launch_kernel<kF8, kPair, false, false, kMc>(ma, mb, mbc, p, grid, smem, st);
+  if (checked) return count ? launch_kernel<kF8, kPair, true, true>(ma, mb, mbc, p, grid, smem, st)
+                            : launch_kernel<kF8, kPair, false, true>(ma, mb, mbc, p, grid, smem, st);
+  return count ? launch_kernel<kF8, kPair, true, false>(ma, mb, mbc, p, grid, smem, st)
+               : launch_kernel<kF8, kPair, false, false>(ma, mb, mbc, p, grid, smem, st);
 }
 
 template <bool kF8>
-cudaError_t launch_any(bool pair, bool mc, bool count, bool checked, const CUtensorMap& ma, const CUtensorMap& mb,
+cudaError_t launch_any(bool pair, bool count, bool checked, const CUtensorMap& ma, const CUtensorMap& mb,
                        const CUtensorMap& mbc, const TcArgs& p, int grid, size_t smem, cudaStream_t st) {
-  if (mc) return launch_inst<kF8, true, true>(count, checked, ma, mb, mbc, p, grid, smem, st);
-  return pair ? launch_inst<kF8, true, false>(count, checked, ma, mb, mbc, p, grid, smem, st)
-              : launch_inst<kF8, false, false>(count, checked, ma, mb, mbc, p, grid, smem, st);
+  return pair ? launch_inst<kF8, true>(count, checked, ma, mb, mbc, p, grid, smem, st)
+              : launch_inst<kF8, false>(count, checked, ma, mb, mbc, p, grid, smem, st);
 }
 
-// Clusters of `cluster` CTAs of the kernel variant that can be resident at
+// Clusters (CTA pairs, or single CTAs) of the kernel that can be resident at
 // once (0 when the query fails).
-template <bool kF8, bool kPair, bool kMc>
+template <bool kPair>
 int max_active_clusters(size_t smem) {
-  auto k = gemm_tc_kernel<kF8, kPair, false, false, kMc>;
+  auto k = gemm_tc_kernel<false, kPair, false, false>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) != cudaSuccess) return 0;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kMc ? 4 : (kPair ? 2 : 1));
+  cfg.gridDim = dim3(kPair ? 2 : 1);
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kMc ? 4 : (kPair ? 2 : 1);
+  attr[0].val.clusterDim.x = kPair ? 2 : 1;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
@@ -581,13 +552,6 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   const size_t smem = fixed + stages * stage_bytes;
   const int64_t progs = c->kind == TP_MAP_IDENTITY ? c->num_tiles : c->num_programs;
   const int64_t grid = pair ? 2 * progs : progs;
-  // two CTA pairs per cluster sharing A by multicast (cfg->cluster_pairs = 2)
-  const int32_t cpairs = cfg ? cfg->cluster_pairs : 0;
-  if (cpairs < 0 || cpairs > 2) return fail(TP_ERR_INVALID, "cluster_pairs must be 0, 1 or 2");
-  const bool mc = cpairs == 2;
-  if (mc && (!pair || c->kind != TP_MAP_STRIDED || progs % 2))
-    return fail(TP_ERR_UNSUPPORTED,
-                "two-pair clusters need 256-row tiles on a strided map with an even number of programs");
   // Schedule: whole tiles, except that on a strided map the R = T mod P tiles
   // of the last, partial round may each be cut along N into S narrow tiles
   // run by the programs that would otherwise sit idle in that round.
@@ -599,10 +563,7 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   const int32_t limit = (cfg && cfg->split_k > 0) ? cfg->split_k : 4;
   if (limit > 8) return fail(TP_ERR_INVALID, "split_k must be 0..8");
   CUtensorMap mb_cut = mb;
-  if (mc) {
-    // units are pairs of horizontally adjacent tiles, one per cluster step
-    p.dp_slots = p.total_slots = c->grid[0] * ((c->grid[1] + 1) / 2);
-  } else if (c->kind == TP_MAP_STRIDED) {
+  if (c->kind == TP_MAP_STRIDED) {
     const int64_t R = T % progs;
     const int unit = pair ? 64 : 32;  // narrow tiles keep whole 32-row B boxes per CTA
     int64_t S = 1;
@@ -623,8 +584,8 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
     s = claims_for(ctx, p.claim_bits, &p.claims, &p.claim_done);
     if (s != TP_OK) return s;
   }
-  cudaError_t e = esize == 2 ? launch_any<false>(pair, mc, count, checked, ma, mb, mb_cut, p, (int)grid, smem, stream)
-                             : launch_any<true>(pair, mc, count, checked, ma, mb, mb_cut, p, (int)grid, smem, stream);
+  cudaError_t e = esize == 2 ? launch_any<false>(pair, count, checked, ma, mb, mb_cut, p, (int)grid, smem, stream)
+                             : launch_any<true>(pair, count, checked, ma, mb, mb_cut, p, (int)grid, smem, stream);
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core GEMM launch");
   return TP_OK;
 }
@@ -632,8 +593,7 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
 tp_status gemm_tc_resident(tp_ctx* ctx, const tp_gemm_config* cfg, int32_t* programs) {
   const int bm = cfg->bm ? cfg->bm : BM, bn = cfg->bn ? cfg->bn : 256;
   if (bm != BM && bm != 2 * BM) return fail(TP_ERR_UNSUPPORTED, "tiles have 128 or 256 rows");
-  const bool pair = bm == 2 * BM, mc = cfg->cluster_pairs == 2;
-  if (mc && !pair) return fail(TP_ERR_UNSUPPORTED, "two-pair clusters need 256-row tiles");
+  const bool pair = bm == 2 * BM;
   const size_t stage_bytes = (size_t)BM * 128 + (size_t)(pair ? bn / 2 : bn) * 128;
   const size_t fixed = 1024 + 256, budget = 232448;
   int stages = cfg->stages > 0 ? cfg->stages : (int)((budget - fixed) / stage_bytes);
@@ -642,11 +602,9 @@ tp_status gemm_tc_resident(tp_ctx* ctx, const tp_gemm_config* cfg, int32_t* prog
     return fail(TP_ERR_UNSUPPORTED, "shared memory too small for the requested stages");
   const size_t smem = fixed + stages * stage_bytes;
   (void)ctx;
-  const int clusters = mc ? max_active_clusters<false, true, true>(smem)
-                          : pair ? max_active_clusters<false, true, false>(smem)
-                                 : max_active_clusters<false, false, false>(smem);
+  const int clusters = pair ? max_active_clusters<true>(smem) : max_active_clusters<false>(smem);
   if (clusters <= 0) return fail(TP_ERR_CUDA, "cudaOccupancyMaxActiveClusters failed");
-  *programs = mc ? 2 * clusters : clusters;  // CTA pairs (256-row tiles) or CTAs
+  *programs = clusters;  // CTA pairs (256-row tiles) or CTAs
   return TP_OK;
 }
 

@@ -236,21 +236,6 @@ __device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap
       : "memory");
 }
 
-// TMA load multicast to the CTAs of the cluster in `mask`: the box lands at
-// offset `dst` in each destination's shared memory, and each destination
-// CTA's bytes complete on the mbarrier at `bar`'s offset in that
-// destination's CTA pair leader (`bar` is given with the pair bit clear,
-// e.g. mapa(barrier, rank & ~1), as for tma_load_2d_pair).
-__device__ __forceinline__ void tma_load_2d_pair_multicast(uint32_t dst, const CUtensorMap* map, int32_t c0,
-                                                           int32_t c1, uint32_t bar, uint16_t mask,
-                                                           uint64_t cache_hint) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      ".multicast::cluster.L2::cache_hint [%0], [%1, {%2, %3}], [%4], %5, %6;" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar), "h"(mask), "l"(cache_hint)
-      : "memory");
-}
-
 __device__ __forceinline__ void tmem_alloc_pair(uint32_t dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "r"(ncols)
                : "memory");

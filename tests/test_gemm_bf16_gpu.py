@@ -266,55 +266,13 @@ def test_unchecked_raw_pointer_gemm_matches_partitioned(ctx, bm, P):
     assert e.value.status == tp._lib.ERR_INVALID
 
 
-@pytest.mark.parametrize("m,n,k,P,G", [(1024, 1280, 256, 4, 1), (1000, 1100, 320, 6, 2), (512, 192, 128, 2, 8),
-                                       (300, 640, 64, 8, 1)])
-def test_two_pair_clusters(ctx, m, n, k, P, G):
-    """cluster_pairs = 2: clusters of two CTA pairs share the A rows by TMA
-    multicast. Integer inputs bit-exact, every element written once by the
-    pair the oracle's schedule names, identical to the one-pair launch, and
-    random inputs within tolerance; the checked launch agrees."""
-    a, bt = _operands(m, n, k, seed=m + k, kind="int")
-    c = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
-    p = tp.tp_partition_create(ctx, c, (256, 128))
-    tp.tp_partition_map(p, tp.MAP_STRIDED, P)
-    counts = torch.zeros(m * n, dtype=torch.int32, device="cuda")
-    owner = torch.full((m * n,), -1, dtype=torch.int32, device="cuda")
-    cfg = tp.gemm_config(bm=256, bn=128, group_m=G, cluster_pairs=2)
-    tp.tp_gemm(ctx, p, a, bt.t(), cfg, tp.make_exec(write_counts=counts, write_owner=owner))
-    assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(ogemm.gemm(a.cpu(), bt.cpu().t())))
-    assert opart.check_counts(counts.cpu().numpy())["ok"]
-    assert np.array_equal(owner.cpu().numpy(), opart.gemm_owner_map_pair_clusters(m, n, 128, P, G))
-    one = torch.empty_like(c)
-    p1 = tp.tp_partition_create(ctx, one, (256, 128))
-    tp.tp_partition_map(p1, tp.MAP_STRIDED, P)
-    tp.tp_gemm(ctx, p1, a, bt.t(), tp.gemm_config(bm=256, bn=128, group_m=G))
-    assert torch.equal(one, c)
-    a, bt = _operands(m, n, k, seed=m + k + 1)
-    tp.tp_gemm(ctx, p, a, bt.t(), cfg)
-    assert ogemm.rel_frobenius(c.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 1e-2
-    chk = torch.empty_like(c)
-    pc = tp.tp_partition_create(ctx, chk, (256, 128))
-    tp.tp_partition_map(pc, tp.MAP_STRIDED, P)
-    tp.tp_gemm(ctx, pc, a, bt.t(), cfg, tp.make_exec(checked=True))
-    assert torch.equal(chk, c)
-    for h in (p, p1, pc):
-        tp.tp_partition_destroy(h)
-
-
-def test_two_pair_cluster_rules_and_residency(ctx):
-    a, bt = _operands(512, 512, 128)
-    c = torch.empty(512, 512, device="cuda", dtype=torch.bfloat16)
-    for tile, P, kind in (((128, 128), 4, tp.MAP_STRIDED), ((256, 128), 3, tp.MAP_STRIDED),
-                          ((256, 128), 0, tp.MAP_IDENTITY)):
-        p = tp.tp_partition_create(ctx, c, tile)
-        if kind == tp.MAP_STRIDED:
-            tp.tp_partition_map(p, kind, P)
-        with pytest.raises(tp.TPError) as e:
-            tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=tile[0], bn=128, cluster_pairs=2))
-        assert e.value.status == tp._lib.ERR_UNSUPPORTED
-        tp.tp_partition_destroy(p)
+def test_resident_programs(ctx):
+    """The resident-program query: CTA pairs for 256-row tiles, CTAs for
+    128-row tiles, never more than the SMs allow."""
     pairs = tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=256, bn=256))
-    clustered = tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=256, bn=256, cluster_pairs=2))
     ctas = tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=128, bn=256))
-    print(f"resident: {ctas} CTAs, {pairs} CTA pairs, {clustered} pairs in two-pair clusters")
-    assert 0 < clustered <= pairs <= ctx.sm_count // 2 and 0 < ctas <= ctx.sm_count
+    print(f"resident: {ctas} CTAs, {pairs} CTA pairs")
+    assert 0 < pairs <= ctx.sm_count // 2 and 0 < ctas <= ctx.sm_count
+    with pytest.raises(tp.TPError) as e:
+        tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=64, bn=256))
+    assert e.value.status == tp._lib.ERR_UNSUPPORTED

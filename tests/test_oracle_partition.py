@@ -134,29 +134,6 @@ def test_gemm_owner_map_cut_partitions_the_output(m, n, bm, bn, P, G):
         assert not diff[tm * bm:(tm + 1) * bm, tn * bn:(tn + 1) * bn].any()
 
 
-def test_pair_cluster_owner_map_worked_example():
-    # 2 tile rows x 3 tile columns (N = 3 * 64): units are (r, {0,1}) and
-    # (r, {2, -}); 4 pairs = 2 clusters; units in raster order (band of 1
-    # row): (0,0) (0,1) (1,0) (1,1) -> clusters 0, 1, 0, 1
-    own = partition.gemm_owner_map_pair_clusters(512, 192, 64, 4).reshape(512, 192)
-    tiles = [[int(own[r * 256, c * 64]) for c in range(3)] for r in range(2)]
-    assert tiles == [[0, 1, 2], [0, 1, 2]]
-    assert own.min() >= 0                                # every element written
-
-
-@pytest.mark.parametrize("m,n,bn,P,G", [(1000, 1300, 128, 6, 1), (768, 640, 64, 8, 2), (300, 100, 192, 2, 8)])
-def test_pair_cluster_owner_map_covers_and_pairs_share_rows(m, n, bn, P, G):
-    own = partition.gemm_owner_map_pair_clusters(m, n, bn, P, G).reshape(m, n)
-    assert own.min() >= 0 and own.max() < P
-    # the two tiles of a unit (same tile row, columns 2j and 2j+1) belong to
-    # the two pairs of one cluster: writers 2c and 2c + 1
-    gn = -(-n // bn)
-    for r in range(0, m, 256):
-        for j in range(0, gn - 1, 2):
-            w0, w1 = own[r, j * bn], own[r, (j + 1) * bn]
-            assert w0 % 2 == 0 and w1 == w0 + 1
-
-
 def test_permute_heads_worked_example():
     # B=1, H=2, M=4, BM=2, D=1: heads [0 1 2 3] and [4 5 6 7]. Destination head
     # m holds, for each source head h, source head h's sequence tile m.
