@@ -109,9 +109,10 @@ enum {
    * is not stored, and the operation reports TP_ERR_RACE where it reports
    * device errors (SYNC: on return; ASYNC: from tp_event_query /
    * tp_event_wait; graph: from a SYNC replay or the replay's event).
-   * Supported by tp_gemm and tp_gemm_fp8 on the tensor-core path (tiles of
-   * 128 or 256 rows) and by tp_permute_heads_unchecked, up to 2^23 tiles per
-   * launch; other operations return TP_ERR_UNSUPPORTED when it is set. The
+   * Supported by the element-wise maps (tp_map_*), by tp_gemm and
+   * tp_gemm_fp8 on the tensor-core path (tiles of 128 or 256 rows) and by
+   * tp_permute_heads_unchecked, up to 2^23 tiles per launch; other
+   * operations return TP_ERR_UNSUPPORTED when it is set. The
    * bitmap and its finished-claimant counter are one per context: checked
    * launches of one context must not overlap in time (order them on one
    * stream), or they see each other's claims. */

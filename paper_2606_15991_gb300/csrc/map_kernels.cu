@@ -5,6 +5,7 @@
 // path over the tile's elements. Each program stores only inside its tile.
 #include <cuda_bf16.h>
 
+#include "tile_claim.cuh"
 #include "tp_internal.h"
 
 namespace tp {
@@ -27,6 +28,9 @@ struct MapArgs {
   int64_t shape[3];  // general path, padded to rank 3 (leading 1s)
   int64_t tshape[3];
   int64_t grid[3];
+  uint32_t* claims;      // checked launch: tile-claim bitmap (null = release)
+  unsigned* claim_done;  // checked launch: finished-CTA counter
+  int* err;              // context error word
 };
 
 // 2^a by the hardware base-2 exponential (flush-to-zero).
@@ -96,6 +100,31 @@ __device__ __forceinline__ void count_write(const MapArgs& a, int64_t i) {
   }
 }
 
+// Checked launch: before storing tile t the program validates it against
+// the map (a tile of the grid, and for a strided map one of this program's
+// slots) and claims it; a refused claim skips the tile. Block-uniform.
+template <bool kCheck = true>
+__device__ __forceinline__ bool claim_map_tile(const MapArgs& a, int64_t t) {
+  if constexpr (!kCheck) return true;
+  if (a.claims == nullptr) return true;
+  int won = 0;
+  if (threadIdx.x == 0) {
+    bool on_map = t >= 0 && t < a.ntiles;
+    if (a.kind == TP_MAP_IDENTITY) on_map = on_map && t == (int64_t)blockIdx.x;
+    if (a.kind == TP_MAP_STRIDED) on_map = on_map && (t - (int64_t)blockIdx.x) % gridDim.x == 0;
+    if (!on_map) record_device_error(a.err, kDevRace);
+    won = on_map && claim_tile(a.claims, t, a.err) ? 1 : 0;
+  }
+  return __syncthreads_or(won) != 0;
+}
+
+template <bool kCheck = true>
+__device__ __forceinline__ void finish_map_claims(const MapArgs& a) {
+  if constexpr (kCheck) {
+    if (a.claims != nullptr) claims_finish(a.claims, a.ntiles, a.claim_done, gridDim.x);
+  }
+}
+
 template <typename T> struct Vec;
 template <> struct Vec<float> { using V = float4; static constexpr int N = 4; };
 template <> struct Vec<__nv_bfloat16> { using V = uint4; static constexpr int N = 8; };
@@ -140,7 +169,7 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-template <int OP, typename T, bool COUNT>
+template <int OP, typename T, bool COUNT, bool CHECKED>
 __global__ void __launch_bounds__(kThreads) map_vec_kernel(const __grid_constant__ MapArgs a) {
   using V = typename Vec<T>::V;
   constexpr int W = Vec<T>::N;
@@ -152,6 +181,7 @@ __global__ void __launch_bounds__(kThreads) map_vec_kernel(const __grid_constant
   const T* __restrict__ y = static_cast<const T*>(a.y);
   Schedule s;
   for (int64_t t = s.first(a, &slot); t >= 0; t = s.next(a, &slot)) {
+    if (!claim_map_tile<CHECKED>(a, t)) continue;
     const int64_t start = t * a.tile;
     const int64_t len = min(a.tile, a.n - start);
     const int64_t nv = len / W;
@@ -203,6 +233,7 @@ __global__ void __launch_bounds__(kThreads) map_vec_kernel(const __grid_constant
       count_write<COUNT>(a, g);
     }
   }
+  finish_map_claims<CHECKED>(a);
 }
 
 // General path: any rank-1..3 partition of a contiguous output, scalar
@@ -217,6 +248,7 @@ __global__ void __launch_bounds__(kThreads) map_generic_kernel(const __grid_cons
   const int64_t tile_elems = a.tshape[0] * a.tshape[1] * a.tshape[2];
   Schedule s;
   for (int64_t t = s.first(a, &slot); t >= 0; t = s.next(a, &slot)) {
+    if (!claim_map_tile(a, t)) continue;
     const int64_t t2 = t % a.grid[2];
     const int64_t t1 = (t / a.grid[2]) % a.grid[1];
     const int64_t t0 = t / (a.grid[2] * a.grid[1]);
@@ -232,6 +264,7 @@ __global__ void __launch_bounds__(kThreads) map_generic_kernel(const __grid_cons
       count_write<COUNT>(a, g);
     }
   }
+  finish_map_claims(a);
 }
 
 template <typename K>
@@ -251,8 +284,11 @@ cudaError_t launch_pdl(K kernel, const MapArgs& a, int64_t grid, cudaStream_t st
 
 template <int OP, typename T>
 cudaError_t launch_typed(const MapArgs& a, bool vec, bool count, int64_t grid, cudaStream_t st) {
-  if (vec) return count ? launch_pdl(map_vec_kernel<OP, T, true>, a, grid, st)
-                        : launch_pdl(map_vec_kernel<OP, T, false>, a, grid, st);
+  const bool checked = a.claims != nullptr;
+  if (vec && checked) return count ? launch_pdl(map_vec_kernel<OP, T, true, true>, a, grid, st)
+                                   : launch_pdl(map_vec_kernel<OP, T, false, true>, a, grid, st);
+  if (vec) return count ? launch_pdl(map_vec_kernel<OP, T, true, false>, a, grid, st)
+                        : launch_pdl(map_vec_kernel<OP, T, false, false>, a, grid, st);
   return count ? launch_pdl(map_generic_kernel<OP, T, true>, a, grid, st)
                : launch_pdl(map_generic_kernel<OP, T, false>, a, grid, st);
 }
@@ -271,7 +307,6 @@ cudaError_t launch_op(int op, const MapArgs& a, bool vec, bool count, int64_t gr
 
 tp_status launch_map(tp_ctx* ctx, tp_partition* out, int op, float alpha, const tp_tensor* x,
                      const tp_tensor* y, const tp_exec* ex, cudaStream_t stream, unsigned* queue) {
-  (void)ctx;
   MapArgs a{};
   a.out = out->t.ptr;
   a.x = x->ptr;
@@ -286,6 +321,11 @@ tp_status launch_map(tp_ctx* ctx, tp_partition* out, int op, float alpha, const 
   a.owner = ex->write_owner;
   if ((a.counts == nullptr) != (a.owner == nullptr))
     return fail(TP_ERR_INVALID, "write_counts and write_owner must be given together");
+  if (ex->flags & TP_EXEC_CHECKED) {
+    tp_status cs = claims_for(ctx, out->num_tiles, &a.claims, &a.claim_done);
+    if (cs != TP_OK) return cs;
+    a.err = ctx->d_err;
+  }
   const int pad = 3 - out->rank;
   for (int i = 0; i < 3; ++i) {
     a.shape[i] = i < pad ? 1 : out->shape[i - pad];

@@ -732,8 +732,10 @@ static tp_status map_op(tp_ctx* ctx, tp_partition* out, int op, float alpha, con
   tp_status s = check_elementwise(out, x, y);
   if (s != TP_OK) return s;
   Op o;
+  o.allow_checked = true;
   s = o.begin(ctx, ex, {out}, {x, y});
   if (s != TP_OK) return s;
+  o.check_err = (ex->flags & TP_EXEC_CHECKED) != 0;
   unsigned* q = nullptr;
   if (out->kind == TP_MAP_QUEUE) {
     s = queue_counter(ctx, o.stream, &q);

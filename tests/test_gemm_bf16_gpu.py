@@ -208,9 +208,6 @@ def test_checked_flag_rejected_where_unsupported(ctx):
     with pytest.raises(tp.TPError) as e:                      # the FP32 SIMT GEMM
         tp.tp_gemm(ctx, p, a, a, None, tp.make_exec(checked=True))
     assert e.value.status == tp._lib.ERR_UNSUPPORTED
-    with pytest.raises(tp.TPError) as e:                      # maps
-        tp.tp_map_axpy(ctx, p, 1.0, a, a, tp.make_exec(checked=True))
-    assert e.value.status == tp._lib.ERR_UNSUPPORTED
     tp.tp_partition_destroy(p)
 
 

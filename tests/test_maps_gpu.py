@@ -294,3 +294,32 @@ def test_full_size_write_counts(ctx):
     tp.tp_partition_destroy(p)
     del x, z, counts, owner
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("kind,P", [(tp.MAP_IDENTITY, 0), (tp.MAP_STRIDED, 5), (tp.MAP_QUEUE, 7)])
+@pytest.mark.parametrize("shape,tile", [((40000,), (4096,)), ((37, 300), (8, 64)), ((5, 6, 7), (2, 3, 4))])
+def test_checked_launch_matches_release(ctx, kind, P, shape, tile):
+    """TP_EXEC_CHECKED on the maps: every tile is validated against the map
+    and claimed before it is stored; on a correct map the result equals the
+    release launch bit for bit, each element is written once, and repeated
+    checked launches (the bitmap clears itself) keep succeeding."""
+    n = int(np.prod(shape))
+    x = synth.tensor(synth.normal(n, 11), "f32").reshape(shape).cuda()
+    y = synth.tensor(synth.normal(n, 12), "f32").reshape(shape).cuda()
+    rel, chk = torch.empty_like(x), torch.empty_like(x)
+    outs = []
+    for out in (rel, chk):
+        p = tp.tp_partition_create(ctx, out, tile)
+        if kind != tp.MAP_IDENTITY:
+            tp.tp_partition_map(p, kind, P)
+        outs.append(p)
+    tp.tp_map_gelu_mul(ctx, outs[0], x, y)
+    counts = torch.zeros(n, dtype=torch.int32, device="cuda")
+    owner = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    for _ in range(3):
+        counts.zero_()
+        tp.tp_map_gelu_mul(ctx, outs[1], x, y, tp.make_exec(write_counts=counts, write_owner=owner, checked=True))
+        assert torch.equal(rel, chk)
+        assert opart.check_counts(counts.cpu().numpy())["ok"]
+    for p in outs:
+        tp.tp_partition_destroy(p)
