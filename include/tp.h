@@ -31,6 +31,10 @@
  * - Element strides are in elements. Dtype sizes: F32 4, BF16 2, F8E4M3 1.
  * - Nothing is allocated during graph capture (§3.2's rule that captured
  *   nodes are non-allocating); a call that would need to returns TP_ERR_CAPTURE.
+ * - No call prints, except that with the environment variable TP_LOG set (to
+ *   anything but "" or "0") every operation writes one trace line to stderr:
+ *   entry point, outcome (done / enqueued / recorded / refused / aborted),
+ *   mode, stream, the output's tiles and programs, and the status.
  */
 #ifndef TP_H
 #define TP_H

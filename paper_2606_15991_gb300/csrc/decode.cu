@@ -301,7 +301,7 @@ tp_status tp_rmsnorm(tp_ctx* ctx, tp_partition* n_out, const tp_tensor* h, const
     return fail(TP_ERR_SHAPE, "rmsnorm takes fp32 vectors of one length");
   tp_status s = check_counts(ex);
   if (s != TP_OK) return s;
-  Op o;
+  Op o(__func__);
   s = gamma ? o.begin(ctx, ex, {n_out}, {h, gamma}) : o.begin(ctx, ex, {n_out}, {h});
   if (s != TP_OK) return s;
   VecArgs a{h ? static_cast<const float*>(h->ptr) : nullptr, gamma ? static_cast<const float*>(gamma->ptr) : nullptr,
@@ -321,7 +321,7 @@ tp_status tp_gemv(tp_ctx* ctx, tp_partition* y, const tp_tensor* w, const tp_ten
   if (!weights(w, rows, k)) return fail(TP_ERR_SHAPE, "gemv: W must be bf16 [rows, k], rows 16-byte aligned");
   tp_status s = check_counts(ex);
   if (s != TP_OK) return s;
-  Op o;
+  Op o(__func__);
   s = o.begin(ctx, ex, {y}, {w, x});
   if (s != TP_OK) return s;
   GemvArgs a{};
@@ -344,7 +344,7 @@ tp_status tp_silu_mul(tp_ctx* ctx, tp_partition* a_out, const tp_tensor* gu, con
   if (!vec_out(a_out, n) || !vec_f32(gu, 2 * n)) return fail(TP_ERR_SHAPE, "silu_mul: a [n], gu [2n] fp32");
   tp_status s = check_counts(ex);
   if (s != TP_OK) return s;
-  Op o;
+  Op o(__func__);
   s = o.begin(ctx, ex, {a_out}, {gu});
   if (s != TP_OK) return s;
   VecArgs a{static_cast<const float*>(gu->ptr), nullptr, static_cast<float*>(a_out->t.ptr), n, 0.f, 1,
@@ -363,7 +363,7 @@ tp_status tp_residual_add(tp_ctx* ctx, tp_partition* h, const tp_tensor* d, cons
   if (!vec_out(h, n) || !vec_f32(d, n)) return fail(TP_ERR_SHAPE, "residual_add: h [n], d [n] fp32");
   tp_status s = check_counts(ex);
   if (s != TP_OK) return s;
-  Op o;
+  Op o(__func__);
   s = o.begin(ctx, ex, {h}, {d});
   if (s != TP_OK) return s;
   VecArgs a{static_cast<const float*>(d->ptr), nullptr, static_cast<float*>(h->t.ptr), n, 0.f, 2,
@@ -387,7 +387,7 @@ tp_status tp_decode_norm_qkv_gu(tp_ctx* ctx, tp_partition* qkv, tp_partition* a_
     return fail(TP_ERR_SHAPE, "norm_qkv_gu: W_qkv bf16 [nq, d], W_gu bf16 [2 ni, d]");
   tp_status s = check_counts(ex);
   if (s != TP_OK) return s;
-  Op o;
+  Op o(__func__);
   s = gamma ? o.begin(ctx, ex, {qkv, a_out}, {h, gamma, w_qkv, w_gu}) : o.begin(ctx, ex, {qkv, a_out}, {h, w_qkv, w_gu});
   if (s != TP_OK) return s;
   GemvArgs a{};
@@ -421,7 +421,7 @@ tp_status tp_decode_down_residual(tp_ctx* ctx, tp_partition* h, const tp_tensor*
   if (!weights(w_down, d, ni)) return fail(TP_ERR_SHAPE, "down_residual: W_down bf16 [d, ni]");
   tp_status s = check_counts(ex);
   if (s != TP_OK) return s;
-  Op o;
+  Op o(__func__);
   s = o.begin(ctx, ex, {h}, {w_down, a_in});
   if (s != TP_OK) return s;
   GemvArgs a{};

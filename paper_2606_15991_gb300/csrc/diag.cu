@@ -33,7 +33,7 @@ using namespace tp;
 extern "C" tp_status tp_diag_bounded_wait(tp_ctx* ctx, int64_t limit_ns, int32_t arrive, const tp_exec* ex) {
   if (!ctx || !ex) return fail(TP_ERR_INVALID, "null argument");
   if (limit_ns < 1000 || limit_ns > 2000000000) return fail(TP_ERR_INVALID, "limit_ns must be in [1e3, 2e9]");
-  Op o;
+  Op o(__func__);
   tp_status s = o.begin(ctx, ex, {}, {});
   if (s != TP_OK) return s;
   o.check_err = true;

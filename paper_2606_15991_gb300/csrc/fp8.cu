@@ -148,7 +148,7 @@ tp_status tp_amax(tp_ctx* ctx, const tp_tensor* x, float* amax, const tp_exec* e
   if (!ctx || !x || !amax || !ex) return fail(TP_ERR_INVALID, "null argument");
   if (x->dtype != TP_F32 && x->dtype != TP_BF16) return fail(TP_ERR_UNSUPPORTED, "amax supports F32 and BF16");
   if (!is_contiguous(*x)) return fail(TP_ERR_UNSUPPORTED, "amax input must be contiguous");
-  Op o;
+  Op o(__func__);
   tp_status s = o.begin(ctx, ex, {}, {x});
   if (s != TP_OK) return s;
   cudaError_t e = cudaMemsetAsync(amax, 0, sizeof(float), o.stream);
@@ -188,7 +188,7 @@ tp_status tp_quantize_fp8(tp_ctx* ctx, tp_partition* q, const tp_tensor* x, cons
   if (q->kind == TP_MAP_QUEUE) return fail(TP_ERR_UNSUPPORTED, "quantize maps tiles by slot (identity/strided)");
   if ((ex->write_counts == nullptr) != (ex->write_owner == nullptr))
     return fail(TP_ERR_INVALID, "write_counts and write_owner must be given together");
-  Op o;
+  Op o(__func__);
   tp_status s = o.begin(ctx, ex, {q}, {x});
   if (s != TP_OK) return s;
   QuantArgs a{};
@@ -230,7 +230,7 @@ tp_status tp_gemm_fp8(tp_ctx* ctx, tp_partition* c, const tp_tensor* qa, const t
   auto f8 = [](int32_t d) { return d == TP_F8E4M3 || d == TP_U8; };
   if (!f8(qa->dtype) || !f8(qb->dtype) || c->t.dtype != TP_BF16)
     return fail(TP_ERR_UNSUPPORTED, "tp_gemm_fp8 takes E4M3 A and B and a BF16 C");
-  Op o;
+  Op o(__func__);
   o.allow_checked = true;
   tp_status s = o.begin(ctx, ex, {c}, {qa, qb});
   if (s != TP_OK) return s;

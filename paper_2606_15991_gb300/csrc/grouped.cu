@@ -567,7 +567,7 @@ tp_status tp_grouped_gemm(tp_ctx* ctx, tp_grouped_plan* plan, int32_t num_progra
   if (plan->ctx != ctx) return fail(TP_ERR_INVALID, "plan belongs to another context");
   if ((ex->write_counts == nullptr) != (ex->write_owner == nullptr))
     return fail(TP_ERR_INVALID, "write_counts and write_owner must be given together");
-  Op o;
+  Op o(__func__);
   tp_status s = o.begin_lists(ctx, ex, plan->outs, plan->ins);
   if (s != TP_OK) return s;
   o.check_err = true;

@@ -105,7 +105,7 @@ tp_status tp_permute_heads(tp_ctx* ctx, tp_partition* dst, const tp_tensor* src,
   if (dst->kind != TP_MAP_IDENTITY) return fail(TP_ERR_UNSUPPORTED, "plain partition only");
   if ((ex->write_counts == nullptr) != (ex->write_owner == nullptr))
     return fail(TP_ERR_INVALID, "write_counts and write_owner must be given together");
-  Op o;
+  Op o(__func__);
   s = o.begin(ctx, ex, {dst}, {src});
   if (s != TP_OK) return s;
   float* d = static_cast<float*>(dst->t.ptr);
@@ -129,7 +129,7 @@ tp_status tp_permute_heads_unchecked(tp_ctx* ctx, void* dst, const void* src, in
   const uintptr_t bytes = (uintptr_t)(B * H * M * D) * 4;
   if (d0 < s0 + bytes && s0 < d0 + bytes) return fail(TP_ERR_ALIAS, "src overlaps dst");
   // raw pointers: no partition is held, so the op tracks no busy state
-  Op o;
+  Op o(__func__);
   o.allow_checked = true;
   s = o.begin(ctx, ex, {}, {});
   if (s != TP_OK) return s;

@@ -147,9 +147,12 @@ struct DeviceGuard {
 //   end():   after the kernel launches, synchronize + release (SYNC), record
 //            the completion event (ASYNC), or nothing (CAPTURE).
 struct Op {
-  tp_ctx* ctx;
-  const tp_exec* ex;
-  cudaStream_t stream;
+  Op() = default;
+  explicit Op(const char* op_name) : name(op_name) {}
+  const char* name = "op";   // entry point, for the TP_LOG trace
+  tp_ctx* ctx = nullptr;
+  const tp_exec* ex = nullptr;
+  cudaStream_t stream = nullptr;
   std::vector<tp_partition*> outs;
   bool check_err = false;   // kernel may write the device error word
   bool marked = false;
@@ -163,6 +166,7 @@ struct Op {
   tp_status begin_impl(tp_ctx* c, const tp_exec* e, const std::vector<tp_partition*>& outputs,
                        const std::vector<const tp_tensor*>& inputs);
   tp_status end(cudaError_t launch_err);
+  tp_status end_impl(cudaError_t launch_err);
   // Undo begin() after a failure that launched nothing (keeps the detail).
   void abort();
   bool capturing() const { return ex->mode == TP_CAPTURE; }

@@ -1,6 +1,8 @@
 // Host runtime of libtp: errors, contexts, tensor views, partitions, the
 // launch protocol (SYNC / ASYNC / CAPTURE, §3.2), events and graphs.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "tp_internal.h"
@@ -174,16 +176,43 @@ tp_status queue_counter(tp_ctx* ctx, cudaStream_t stream, unsigned** out) {
   return TP_OK;
 }
 
+// TP_LOG (any value but empty or 0): one line per operation on stderr.
+static bool trace_on() {
+  static const bool on = [] {
+    const char* v = std::getenv("TP_LOG");
+    return v && *v && std::strcmp(v, "0") != 0;
+  }();
+  return on;
+}
+
+static void trace(const Op& o, const char* event, tp_status st) {
+  if (!trace_on()) return;
+  static const char* const kModes[] = {"SYNC", "ASYNC", "CAPTURE"};
+  const int mode = o.ex ? o.ex->mode : -1;
+  char part[96] = "";
+  if (!o.outs.empty() && o.outs[0])
+    std::snprintf(part, sizeof part, " tiles=%lld programs=%lld map=%d outputs=%zu", (long long)o.outs[0]->num_tiles,
+                  (long long)o.outs[0]->num_programs, (int)o.outs[0]->kind, o.outs.size());
+  std::fprintf(stderr, "[tp] %s %s mode=%s stream=%p%s checked=%d status=%s%s%s\n", o.name, event,
+               mode >= 0 && mode <= 2 ? kModes[mode] : "?", (void*)o.stream, part,
+               o.ex ? (o.ex->flags & TP_EXEC_CHECKED ? 1 : 0) : 0, tp_error_string(st), st ? " detail=" : "",
+               st ? g_detail.c_str() : "");
+}
+
 tp_status Op::begin(tp_ctx* c, const tp_exec* e, std::initializer_list<tp_partition*> outputs,
                     std::initializer_list<const tp_tensor*> inputs) {
-  return begin_impl(c, e, std::vector<tp_partition*>(outputs), std::vector<const tp_tensor*>(inputs));
+  tp_status s = begin_impl(c, e, std::vector<tp_partition*>(outputs), std::vector<const tp_tensor*>(inputs));
+  if (s != TP_OK) trace(*this, "refused", s);
+  return s;
 }
 
 tp_status Op::begin_lists(tp_ctx* c, const tp_exec* e, const std::vector<tp_partition*>& outputs,
                           const std::vector<tp_tensor>& inputs) {
   std::vector<const tp_tensor*> in;
   for (const auto& t : inputs) in.push_back(&t);
-  return begin_impl(c, e, outputs, in);
+  tp_status s = begin_impl(c, e, outputs, in);
+  if (s != TP_OK) trace(*this, "refused", s);
+  return s;
 }
 
 tp_status Op::begin_impl(tp_ctx* c, const tp_exec* e, const std::vector<tp_partition*>& outputs,
@@ -263,9 +292,16 @@ tp_status Op::begin_impl(tp_ctx* c, const tp_exec* e, const std::vector<tp_parti
 void Op::abort() {
   if (marked) release(ctx, outs, stream);
   marked = false;
+  trace(*this, "aborted", TP_ERR_INVALID);
 }
 
 tp_status Op::end(cudaError_t launch_err) {
+  tp_status s = end_impl(launch_err);
+  trace(*this, ex && ex->mode == TP_CAPTURE ? "recorded" : (ex && ex->mode == TP_ASYNC ? "enqueued" : "done"), s);
+  return s;
+}
+
+tp_status Op::end_impl(cudaError_t launch_err) {
   if (launch_err != cudaSuccess) {
     if (marked) release(ctx, outs, stream);
     return cuda_fail(launch_err, "kernel launch");
@@ -731,7 +767,8 @@ static tp_status map_op(tp_ctx* ctx, tp_partition* out, int op, float alpha, con
   if (!ctx || !out || !x || !y || !ex) return fail(TP_ERR_INVALID, "null argument");
   tp_status s = check_elementwise(out, x, y);
   if (s != TP_OK) return s;
-  Op o;
+  static const char* const kNames[] = {"tp_map_axpy", "tp_map_gelu_mul", "tp_map_scale", "tp_map_add_accum"};
+  Op o(kNames[op & 3]);
   o.allow_checked = true;
   s = o.begin(ctx, ex, {out}, {x, y});
   if (s != TP_OK) return s;
@@ -783,7 +820,7 @@ tp_status tp_gemm(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_ten
   bool simt = a->dtype == TP_F32 && c->t.dtype == TP_F32;
   bool tc = a->dtype == TP_BF16 && c->t.dtype == TP_BF16;
   if (!simt && !tc) return fail(TP_ERR_UNSUPPORTED, "tp_gemm supports F32xF32->F32 and BF16xBF16->BF16");
-  Op o;
+  Op o(__func__);
   o.allow_checked = tc;
   tp_status s = o.begin(ctx, ex, {c}, {a, b});
   if (s != TP_OK) return s;

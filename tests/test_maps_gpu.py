@@ -323,3 +323,30 @@ def test_checked_launch_matches_release(ctx, kind, P, shape, tile):
         assert opart.check_counts(counts.cpu().numpy())["ok"]
     for p in outs:
         tp.tp_partition_destroy(p)
+
+
+def test_trace_log_lines():
+    """TP_LOG: one stderr line per operation, including refused ones; nothing
+    is printed without it."""
+    import os
+    import subprocess
+    import sys
+
+    code = ("import torch, paper_2606_15991_gb300 as tp\n"
+            "ctx = tp.tp_ctx_create(0)\n"
+            "x = torch.ones(8192, device='cuda'); z = torch.empty_like(x)\n"
+            "p = tp.tp_partition_create(ctx, z, (4096,))\n"
+            "tp.tp_map_axpy(ctx, p, 2.0, x, x)\n"
+            "try:\n    tp.tp_map_axpy(ctx, p, 2.0, z, x)\nexcept tp.TPError:\n    pass\n"
+            "torch.cuda.synchronize()\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, TP_LOG="1", PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stderr.splitlines() if l.startswith("[tp] ")]
+    assert any(l.startswith("[tp] tp_map_axpy done mode=SYNC") and "tiles=2 programs=2" in l and "status=ok" in l
+               for l in lines), lines
+    assert any("tp_map_axpy refused" in l and "input aliases output" in l for l in lines), lines
+    env.pop("TP_LOG")
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and "[tp] " not in r.stderr
