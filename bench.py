@@ -432,8 +432,9 @@ def run_ours(args):
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": "TB/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "elements": N_ELEMS, "tile": TILE, "alpha": ALPHA,
+                       "storage_dtypes": ["f32", "bf16"], "arithmetic": "f32 (bf16 inputs widened, results rounded)",
                        "maps": [f"{o}_{d}" for o, d in MAPS], "l2": "inputs larger than L2 (no flush)",
                        "parallelism": f"replicas x{ws}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
