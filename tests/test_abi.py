@@ -127,3 +127,11 @@ def test_empty_outputs_with_any_strides_are_partitionable():
         p = tp.tp_partition_create(None, t, tuple(4 for _ in shape))
         assert tp.tp_partition_query(p)["num_tiles"] == 0
         tp.tp_partition_destroy(p)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    # without the built CUDA library every call raises: there is no fallback path
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(_lib, "LIB_PATH", "/nonexistent/libtp.so")
+    with pytest.raises(RuntimeError, match="no fallback"):
+        tp.tp_version()
