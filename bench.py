@@ -500,29 +500,11 @@ def _e2e_leg(tp, ctx, ex, ev, inputs, tens, step_bytes, ws, dev, args):
 
 
 def _graph_time(tp, ctx, stream, record, reps: int, replays: int = 3) -> float:
-    """Mean device time (ms) of one recorded op: `record(ex)` is captured
-    `reps` times into one graph, the graph is replayed (after one warm-up
-    replay) and timed with CUDA events on the replay stream."""
-    import torch
+    """Device time (ms) of one recorded op (`record(ex)` captured `reps`
+    times into one graph and replayed; the fastest replay / reps)."""
+    from paper_2606_15991_gb300 import experiments
 
-    g = tp.tp_graph_begin(ctx, stream)
-    cap = tp.make_exec(mode=tp.CAPTURE, stream=stream)
-    for _ in range(reps):
-        record(cap)
-    tp.tp_graph_end(g)
-    ex = tp.make_exec(stream=stream)
-    tp.tp_graph_replay(g, ex)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    best = None
-    for _ in range(replays):
-        e0.record(stream)
-        tp.tp_graph_replay(g, ex)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / reps
-        best = t if best is None else min(best, t)
-    tp.tp_graph_destroy(g)
-    return best
+    return experiments.graph_time_ms(ctx, stream, record, reps, replays)
 
 
 def secondary_rows(tp, ctx, dev, stream, peaks):
