@@ -407,7 +407,7 @@ def run_ours(args):
     # ---------------- end-to-end through the C ABI with pinned host buffers
     # The inputs and outputs live in pinned host memory; the partitions are
     # over the host output buffers, so each map kernel reads its operands from
-    # host memory and writes its result back over NVLink-C2C inside the timed
+    # host memory and writes its result back over the host link inside the timed
     # region (measured faster than staging through device copies: ~300 vs
     # ~200 GB/s of host traffic on GB300).
     e2e = None
@@ -447,8 +447,8 @@ def run_ours(args):
 def _e2e_leg(tp, ctx, ex, ev, inputs, tens, step_bytes, ws, dev, args):
     """The maps step end to end: inputs and outputs in pinned host memory;
     the partitions are over the host output buffers, so every map kernel
-    reads its operands from host memory and writes its result back over
-    NVLink-C2C inside the timed region (measured faster than staging through
+    reads its operands from host memory and writes its result back over the
+    host link inside the timed region (measured faster than staging through
     device copies: ~300 vs ~200 GB/s of host traffic on GB300)."""
     import torch
 
