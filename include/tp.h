@@ -460,10 +460,17 @@ tp_status tp_autotune_load(tp_ctx* ctx, const char* path);
  * parameters, optimiser state and scratch; calls on one tp_mlp must be
  * ordered on one stream (tp_exec.stream; SYNC waits, ASYNC returns). */
 typedef struct tp_mlp tp_mlp;
+/* Creates an MLP with in, hidden, out <= 1024 units (in >= 1) for batches of
+ * up to max_batch rows, parameters copied from the host array init_params
+ * (layout above); allocates device memory, so not during graph capture
+ * (TP_ERR_CAPTURE). Errors: TP_ERR_INVALID, TP_ERR_CAPTURE, TP_ERR_CUDA. */
 tp_status tp_mlp_create(tp_ctx* ctx, int32_t in, int32_t hidden, int32_t out, int32_t max_batch,
                         const float* init_params, tp_mlp** mlp);
+/* Frees the MLP and its device memory (no work of it may be in flight). */
 tp_status tp_mlp_destroy(tp_mlp* mlp);
+/* Number of fp32 parameters (the length of the parameter layout above). */
 tp_status tp_mlp_num_params(const tp_mlp* mlp, int64_t* count);
+/* Copies the parameters to the host array host_out (synchronous). */
 tp_status tp_mlp_get_params(const tp_mlp* mlp, float* host_out);
 /* Sets the parameters (host array) and resets the optimiser state. */
 tp_status tp_mlp_set_params(tp_mlp* mlp, const float* host_in);
@@ -475,6 +482,9 @@ tp_status tp_mlp_loss_grad(tp_mlp* mlp, const float* X, const float* T, const fl
 /* tp_mlp_loss_grad followed by one Adam step at learning rate lr. */
 tp_status tp_mlp_train_step(tp_mlp* mlp, const float* X, const float* T, const float* V, int32_t batch,
                             float lr, float* loss, const tp_exec* ex);
+/* Persist / restore the parameters and sizes as text ("tp-mlp v1"); load
+ * requires matching sizes (TP_ERR_SHAPE) and resets the optimiser state.
+ * Errors: TP_ERR_INVALID (unreadable / malformed file), TP_ERR_SHAPE. */
 tp_status tp_mlp_save(const tp_mlp* mlp, const char* path);
 tp_status tp_mlp_load(tp_mlp* mlp, const char* path);
 /* Proposer features of a shape: [log2 M, log2 N, log2 K, BF16?, FP8?] (host). */
