@@ -159,16 +159,28 @@ typedef struct tp_gemm_config {
   int32_t group_m;     /* raster band height in tiles (L2 reuse)                */
   int32_t num_programs;/* persistent programs; 0 = number of SMs (or pairs)     */
   int32_t swap_ab;     /* grouped GEMM only: compute C^T = B^T A^T             */
-  int32_t split_k;     /* tensor-core GEMM on a strided map with T tiles and P
-                        * programs: each of the R = T mod P tiles of the last,
-                        * partial round may be cut along N into S narrow tiles
-                        * (S the largest power of two <= min(limit, P / R)
-                        * leaving a multiple of 32 columns, 64 for 256-row
-                        * tiles), run by programs that would otherwise idle in
-                        * that round; every C element is still computed whole
-                        * by one program, so C is bit-identical either way.
-                        * Limit: 0 = 4 (default), 1 = never cut, 2..8.
-                        * SIMT GEMM: ignored.                                 */
+  int32_t split_k;     /* tensor-core GEMM, 128-row tiles: K slices per tile,
+                        * 0 or 1 = none, 2, 4 or 8. A program is then a
+                        * cluster of split_k CTAs; CTA s accumulates the K
+                        * blocks [s*nk/split_k, (s+1)*nk/split_k) of the
+                        * program's tile (nk = ceil(K / bk) >= split_k), and
+                        * CTA j adds the split_k partial sums of column slice
+                        * j (bn / split_k columns, a multiple of 32) in slice
+                        * order and stores it, so every C element still has
+                        * one writer and C is bit-reproducible (its rounding
+                        * differs from split_k = 1). Needs at most one tile
+                        * per program (an identity map, or a strided map with
+                        * num_programs >= tiles). SIMT GEMM: ignored.         */
+  int32_t cut_limit;   /* tensor-core GEMM on a strided map with T tiles and P
+                        * programs (split_k <= 1): each of the R = T mod P
+                        * tiles of the last, partial round may be cut along N
+                        * into S narrow tiles (S the largest power of two <=
+                        * min(limit, P / R) leaving a multiple of 32 columns,
+                        * 64 for 256-row tiles), run by programs that would
+                        * otherwise idle in that round; every C element is
+                        * still computed whole by one program, so C is
+                        * bit-identical either way. Limit: 0 = 4 (default),
+                        * 1 = never cut, 2..8. SIMT GEMM: ignored.           */
 } tp_gemm_config;
 
 /* ---------------------------------------------------------------- errors */
@@ -322,7 +334,8 @@ tp_status tp_gemm(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_ten
 /* How many programs of the tensor-core GEMM can be resident on the device at
  * once for `cfg` (bm 128 or 256, bn, stages; 0 fields take the defaults): CTA pairs for 256-row tiles, CTAs for 128-row tiles. A
  * persistent launch with more programs than this runs the extra ones after
- * others finish. Errors: TP_ERR_INVALID, TP_ERR_UNSUPPORTED, TP_ERR_CUDA. */
+ * others finish. With split_k > 1 the count is of split programs (clusters
+ * of split_k CTAs). Errors: TP_ERR_INVALID, TP_ERR_UNSUPPORTED, TP_ERR_CUDA. */
 tp_status tp_gemm_resident_programs(tp_ctx* ctx, const tp_gemm_config* cfg, int32_t* programs);
 
 /* The BF16 tensor-core GEMM against a raw output pointer: the unchecked
@@ -430,7 +443,10 @@ tp_status tp_decode_down_residual(tp_ctx* ctx, tp_partition* h, const tp_tensor*
 /* Tile-configuration search for the tensor-core GEMM (§5.1 tunes tile shapes
  * once per size). The space (same order on every call; index i is the MLP
  * proposer's output i): tile rows {128 (one CTA), 256 (CTA pair)} x tile
- * columns {64, 128, 192, 256} x stages {3, max} x raster bands {1, 8}.
+ * columns {64, 128, 192, 256} x stages {3, max} x raster bands {1, 8}, then
+ * split-K programs of 128-row tiles: (bn 128, split_k 2 / 4) and (bn 256,
+ * split_k 2 / 4 / 8), 37 configs. Split configs are skipped (0 TFLOP/s) when
+ * the shape's tiles x split_k exceed twice the SM count.
  * Writes up to `cap` configs to `out` (may be NULL) and the size to *count. */
 tp_status tp_autotune_space(int32_t dtype, tp_gemm_config* out, int32_t cap, int32_t* count);
 /* Times every config of the space on an M x N x K problem of `dtype`
@@ -445,7 +461,9 @@ tp_status tp_autotune(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtyp
 /* Cached winner for (M, N, K, dtype): *found = 1 and *out filled, else 0. */
 tp_status tp_autotune_lookup(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, tp_gemm_config* out,
                              int32_t* found);
-/* Persist / restore the cache (text, "tp-autotune-cache v1"). */
+/* Persist / restore the cache (text, "tp-autotune-cache v2": one line per
+ * entry, M N K dtype bm bn stages group_m num_programs split_k TFLOP/s;
+ * load also reads v1 files, whose lines lack split_k). */
 tp_status tp_autotune_save(tp_ctx* ctx, const char* path);
 tp_status tp_autotune_load(tp_ctx* ctx, const char* path);
 

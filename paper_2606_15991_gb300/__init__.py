@@ -226,8 +226,8 @@ def make_exec(mode: int = SYNC, stream=None, event: Event | None = None, write_c
     return ex
 
 
-def gemm_config(bm=0, bn=0, bk=0, stages=0, group_m=0, num_programs=0, swap_ab=0, split_k=0):
-    return tp_gemm_config(bm, bn, bk, stages, group_m, num_programs, swap_ab, split_k)
+def gemm_config(bm=0, bn=0, bk=0, stages=0, group_m=0, num_programs=0, swap_ab=0, split_k=0, cut_limit=0):
+    return tp_gemm_config(bm, bn, bk, stages, group_m, num_programs, swap_ab, split_k, cut_limit)
 
 
 def _ex(ex):

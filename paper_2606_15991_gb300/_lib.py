@@ -50,7 +50,8 @@ class tp_partition_info(ctypes.Structure):
 
 class tp_gemm_config(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in
-                ("bm", "bn", "bk", "stages", "group_m", "num_programs", "swap_ab", "split_k")]
+                ("bm", "bn", "bk", "stages", "group_m", "num_programs", "swap_ab", "split_k",
+                 "cut_limit")]
 
 
 class tp_gemm_problem(ctypes.Structure):

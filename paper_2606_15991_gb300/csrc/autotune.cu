@@ -58,6 +58,18 @@ std::vector<tp_gemm_config> space() {
           c.group_m = gm;
           v.push_back(c);
         }
+  // split-K programs (128-row tiles; a cluster of split_k CTAs per tile) for
+  // shapes with fewer tiles than SMs
+  for (int bn : {128, 256})
+    for (int sk : {2, 4, 8}) {
+      if (bn % (32 * sk)) continue;
+      tp_gemm_config c{};
+      c.bm = 128;
+      c.bn = bn;
+      c.group_m = 1;
+      c.split_k = sk;
+      v.push_back(c);
+    }
   return v;
 }
 
@@ -196,7 +208,10 @@ tp_status tp_autotune(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtyp
     part.kind = TP_MAP_STRIDED;
     part.num_programs = std::min<int64_t>(part.num_tiles, cap);
     float tf = 0.f;
-    tp_status ls = launch_gemm_tc_impl(ctx, &part, &a, &b, &c, &ex, st->stream, esize, one, one);
+    // a split program holds one tile; past two waves of clusters it cannot win
+    const bool skip = c.split_k > 1 && part.num_tiles * c.split_k > 2 * (int64_t)ctx->sm_count;
+    if (c.split_k > 1) part.num_programs = part.num_tiles;
+    tp_status ls = skip ? TP_ERR_UNSUPPORTED : launch_gemm_tc_impl(ctx, &part, &a, &b, &c, &ex, st->stream, esize, one, one);
     if (ls == TP_OK) {
       delay_kernel<<<1, 32, 0, st->stream>>>(20000ull + 30000ull * (uint64_t)r);
       cudaEventRecord(e0, st->stream);
@@ -247,11 +262,11 @@ tp_status tp_autotune_save(tp_ctx* ctx, const char* path) {
   std::lock_guard<std::mutex> lk(st->mu);
   FILE* f = std::fopen(path, "w");
   if (!f) return fail(TP_ERR_INVALID, std::string("cannot write ") + path);
-  std::fprintf(f, "tp-autotune-cache v1\n");
+  std::fprintf(f, "tp-autotune-cache v2\n");
   for (auto& kv : st->cache) {
     const auto& c = kv.second.first;
-    std::fprintf(f, "%lld %lld %lld %d %d %d %d %d %d %.3f\n", (long long)kv.first.m, (long long)kv.first.n,
-                 (long long)kv.first.k, kv.first.dtype, c.bm, c.bn, c.stages, c.group_m, c.num_programs,
+    std::fprintf(f, "%lld %lld %lld %d %d %d %d %d %d %d %.3f\n", (long long)kv.first.m, (long long)kv.first.n,
+                 (long long)kv.first.k, kv.first.dtype, c.bm, c.bn, c.stages, c.group_m, c.num_programs, c.split_k,
                  kv.second.second);
   }
   std::fclose(f);
@@ -262,24 +277,32 @@ tp_status tp_autotune_load(tp_ctx* ctx, const char* path) {
   if (!ctx || !path) return fail(TP_ERR_INVALID, "null argument");
   FILE* f = std::fopen(path, "r");
   if (!f) return fail(TP_ERR_INVALID, std::string("cannot read ") + path);
+  // v1 lines lack the split_k column
   char magic[64] = {};
-  if (!std::fgets(magic, sizeof magic, f) || std::string(magic).rfind("tp-autotune-cache v1", 0) != 0) {
+  const bool ok = std::fgets(magic, sizeof magic, f) != nullptr;
+  const bool v2 = ok && std::string(magic).rfind("tp-autotune-cache v2", 0) == 0;
+  if (!v2 && !(ok && std::string(magic).rfind("tp-autotune-cache v1", 0) == 0)) {
     std::fclose(f);
-    return fail(TP_ERR_INVALID, "not a v1 autotune cache");
+    return fail(TP_ERR_INVALID, "not an autotune cache (v1 or v2)");
   }
   TuneState* st = state(ctx);
   std::lock_guard<std::mutex> lk(st->mu);
   long long m, n, k;
-  int dt, bm, bn, stages, gm, np;
+  int dt, bm, bn, stages, gm, np, sk = 0;
   float tf;
-  while (std::fscanf(f, "%lld %lld %lld %d %d %d %d %d %d %f", &m, &n, &k, &dt, &bm, &bn, &stages, &gm, &np, &tf) ==
-         10) {
+  for (;;) {
+    const int got = v2 ? std::fscanf(f, "%lld %lld %lld %d %d %d %d %d %d %d %f", &m, &n, &k, &dt, &bm, &bn, &stages,
+                                     &gm, &np, &sk, &tf)
+                       : std::fscanf(f, "%lld %lld %lld %d %d %d %d %d %d %f", &m, &n, &k, &dt, &bm, &bn, &stages,
+                                     &gm, &np, &tf);
+    if (got != (v2 ? 11 : 10)) break;
     tp_gemm_config c{};
     c.bm = bm;
     c.bn = bn;
     c.stages = stages;
     c.group_m = gm;
     c.num_programs = np;
+    c.split_k = sk;
     st->cache[TuneKey{m, n, k, dt}] = {c, tf};
   }
   std::fclose(f);

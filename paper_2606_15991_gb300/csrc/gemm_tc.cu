@@ -6,15 +6,22 @@
 // the program walks its mapped sequence of output tiles and, for each,
 // accumulates mma over the K tiles). On a strided map the tiles of the last,
 // partial round may be cut along N into narrow tiles for programs that would
-// otherwise idle. A persistent CTA (or CTA pair) runs one program:
+// otherwise idle. With split_k = S > 1 a program is a cluster of S CTAs that
+// each accumulate one contiguous slice of the K blocks of the program's
+// (single) tile; the partial sums then meet through distributed shared
+// memory, CTA j adding the S partials of column slice j in slice order
+// (a fixed order, so C is bit-reproducible) and storing that slice.
+// A persistent CTA (or CTA pair) runs one program:
 //   warp 0   TMA producer: streams (A, B) K-slices into a ring of shared-
 //            memory stages (128-byte swizzle), guarded by full/empty mbarriers;
 //   warp 1   MMA issuer: one thread issues tcgen05.mma into one of two TMEM
 //            accumulators and commits each consumed stage back to the producer;
 //   warps 2-5 epilogue: tcgen05.ld the finished accumulator (each warp owns the
 //            32 TMEM lanes = tile rows its warp index selects), scale, round to
-//            bf16 and store only inside this program's tile, while the MMA
-//            warp already fills the other accumulator.
+//            bf16 and store only inside this program's tile (32 x 32 blocks
+//            staged in shared memory and written by TMA stores, or per-row
+//            stores when C rows are not 16-byte aligned), while the MMA warp
+//            already fills the other accumulator.
 // Every mbarrier wait is bounded; on timeout the kernel records an error,
 // drains its in-flight copies and MMAs, frees TMEM and returns. The checked
 // build (TP_EXEC_CHECKED) validates and claims every tile before storing it;
@@ -38,10 +45,11 @@ using namespace sm100;
 constexpr int BM = 128;
 constexpr int kThreads = 192;
 constexpr int kMaxStages = 8;
+constexpr uint32_t kStageC = 4u * 2u * 2048u;  // epilogue staging: 4 warps x 2 buffers x (32 rows x 64 B)
 
 struct TcArgs {
   int64_t M, N, K;
-  int64_t gm, gn;       // tile grid
+  int32_t gm, gn;       // tile grid (gm * gn < 2^31)
   int32_t bn;           // tile columns (32..256, multiple of 32)
   int32_t stages;
   int32_t kind;         // tp_map_kind (IDENTITY or STRIDED)
@@ -49,6 +57,11 @@ struct TcArgs {
   int32_t tmem_cols;    // allocated TMEM columns (2 * bn rounded to a power of two)
   int32_t c_vec;        // C rows are 16-byte aligned (N % 8 == 0, aligned base)
   int32_t kblk;         // K elements per stage (64 bf16 / 128 fp8)
+  int32_t nk;           // K blocks per tile: ceil(K / kblk)
+  int32_t split;        // K slices per tile (cluster size of a split program); 1 = none
+  int32_t stage_c;      // epilogue writes C by TMA stores of 32 x 32 blocks staged in shared memory
+  int32_t body_bytes;   // shared memory before the staging area: max(ring, split receive buffer)
+  int32_t parts;        // claim parts per tile: narrow tiles (ncut) or K slices (split)
   __nv_bfloat16* c;
   const float* scale_a; // optional (FP8): C = acc * 1 / (*scale_a * *scale_b)
   const float* scale_b;
@@ -61,20 +74,20 @@ struct TcArgs {
   // Schedule: slots [0, dp_slots) are whole tiles (slot = tile index); each
   // remaining tile dp_slots + r is cut along N into ncut narrow tiles of
   // bn_cut columns, narrow tile j being slot dp_slots + r * ncut + j.
-  int64_t dp_slots;
-  int64_t total_slots;  // dp_slots + (tiles - dp_slots) * ncut
+  int32_t dp_slots;
+  int32_t total_slots;  // dp_slots + (tiles - dp_slots) * ncut (< 2^31)
   int32_t ncut;         // 1 = no tile is cut
   int32_t bn_cut;       // bn / ncut
 };
 
 // The work of one slot: a tile and the columns [col, col + width) of it.
 struct Unit {
-  int64_t tile;
+  int32_t tile;
   int32_t col, width, part;
   bool cut;
 };
 
-__device__ __forceinline__ Unit unit_of(int64_t s, const TcArgs& p) {
+__device__ __forceinline__ Unit unit_of(int32_t s, const TcArgs& p) {
   Unit u;
   if (s < p.dp_slots) {
     u.tile = s;
@@ -83,9 +96,9 @@ __device__ __forceinline__ Unit unit_of(int64_t s, const TcArgs& p) {
     u.part = 0;
     u.cut = false;
   } else {
-    const int64_t q = s - p.dp_slots;
+    const int32_t q = s - p.dp_slots;
     u.tile = p.dp_slots + q / p.ncut;
-    u.part = (int32_t)(q % p.ncut);
+    u.part = q % p.ncut;
     u.col = u.part * p.bn_cut;
     u.width = p.bn_cut;
     u.cut = true;
@@ -93,19 +106,24 @@ __device__ __forceinline__ Unit unit_of(int64_t s, const TcArgs& p) {
   return u;
 }
 
-__device__ __forceinline__ void raster(int64_t s, int64_t gm, int64_t gn, int64_t g, int64_t* tm, int64_t* tn) {
-  const int64_t per = g * gn;
-  const int64_t first = (s / per) * g;
-  const int64_t rows = min(g, gm - first);
-  const int64_t r = s % per;
-  *tm = first + r % rows;
-  *tn = r / rows;
+// Band raster: bands of g tile rows, column-major inside a band (32-bit
+// arithmetic: the host keeps the tile count below 2^31 and g <= gm).
+__device__ __forceinline__ void raster(uint32_t s, uint32_t gm, uint32_t gn, uint32_t g, int32_t* tm, int32_t* tn) {
+  const uint32_t per = g * gn;
+  const uint32_t band = s / per;
+  const uint32_t first = band * g;
+  const uint32_t rows = min(g, gm - first);
+  const uint32_t r = s - band * per;
+  const uint32_t col = r / rows;
+  *tm = (int32_t)(first + (r - col * rows));
+  *tn = (int32_t)col;
 }
 
 template <bool kF8, bool kPair, bool kCount, bool kChecked>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
-                   const __grid_constant__ CUtensorMap map_b_cut, const __grid_constant__ TcArgs p) {
+                   const __grid_constant__ CUtensorMap map_b_cut, const __grid_constant__ CUtensorMap map_c,
+                   const __grid_constant__ TcArgs p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -115,18 +133,26 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int lane = threadIdx.x % 32;
   // A CTA pair computes a 256-row tile: this CTA holds rows [rank*128, +128)
   // of A and of the accumulator, and B rows (tile columns) [rank*bn/2, +bn/2).
-  const uint32_t rank = kPair ? cluster_ctarank() : 0u;
+  // A split program (cluster of S single CTAs) gives CTA `kslice` the K
+  // blocks [kslice*nk/S, (kslice+1)*nk/S) of the tile.
+  const int32_t S = kPair ? 1 : p.split;
+  const uint32_t crank = (kPair || S > 1) ? cluster_ctarank() : 0u;
+  const uint32_t rank = kPair ? crank : 0u;
+  const uint32_t kslice = kPair ? 0u : crank;
   const bool leader = rank == 0;
-  const int64_t prog = kPair ? (int64_t)(blockIdx.x / 2) : (int64_t)blockIdx.x;
-  const int64_t nprog = kPair ? (int64_t)(gridDim.x / 2) : (int64_t)gridDim.x;
+  const int32_t csize = kPair ? 2 : S;
+  const int32_t prog = (int32_t)blockIdx.x / csize;
+  const int32_t nprog = (int32_t)gridDim.x / csize;
   const int tile_m = kPair ? 2 * BM : BM;
   const int b_rows = kPair ? p.bn / 2 : p.bn;
   const uint32_t a_stage = BM * 128;
   const uint32_t b_stage = (uint32_t)b_rows * 128;
   const uint32_t a0 = base;
   const uint32_t b0 = base + a_stage * p.stages;
-  const uint32_t bars = b0 + b_stage * p.stages;
-  // barrier block: full[8], empty[8], tfull[2], tempty[2], drain, then words
+  const uint32_t cst = base + (uint32_t)p.body_bytes;           // epilogue staging
+  const uint32_t bars = cst + (p.stage_c ? kStageC : 0u);
+  // barrier block: full[8], empty[8], tfull[2], tempty[2], drain, two
+  // words, recv (split-K)
   auto full_bar = [&](int s) { return bars + 8u * s; };
   auto empty_bar = [&](int s) { return bars + 64u + 8u * s; };
   auto tfull_bar = [&](int b) { return bars + 128u + 8u * b; };
@@ -134,6 +160,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t drain_bar = bars + 160u;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + (bars - base) + 168u);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + (bars - base) + 172u);
+  const uint32_t recv_bar = bars + 176u;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) {
@@ -145,11 +172,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(tempty_bar(b), kPair ? 8 : 4);  // one arrive per epilogue warp (of both CTAs)
     }
     mbar_init(drain_bar, 1);
+    mbar_init(recv_bar, 1);
     *abort_flag = 0;
     fence_mbar_init();
     tma_prefetch_desc(&map_a);
     tma_prefetch_desc(&map_b);
     if (p.ncut > 1) tma_prefetch_desc(&map_b_cut);
+    if (p.stage_c) tma_prefetch_desc(&map_c);
   }
   if (warp == 1) {
     if constexpr (kPair) {
@@ -170,10 +199,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   grid_dependency_wait();
   allow_dependents();
 
-  const int64_t T = p.gm * p.gn;
-  const int64_t TS = p.total_slots;
-  const int64_t step = p.kind == TP_MAP_IDENTITY ? T : nprog;
-  const int64_t nk = (p.K + p.kblk - 1) / p.kblk;
+  const int32_t TS = p.total_slots;
+  const int32_t step = p.kind == TP_MAP_IDENTITY ? p.gm * p.gn : nprog;
+  const int32_t kb0 = (int32_t)(((int64_t)kslice * p.nk) / S);
+  const int32_t kb1 = (int32_t)(((int64_t)(kslice + 1) * p.nk) / S);
+  // split programs: the tile this CTA accumulated and whether its partial sum is complete
+  int32_t sp_tm = 0, sp_tn = 0;
+  bool sp_have = false;
 
   if (warp == 0) {
     // ---------------- TMA producer (one thread; the rest of the warp waits)
@@ -184,20 +216,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      for (int64_t s = prog; s < TS && ok; s += step) {
+      for (int32_t s = prog; s < TS && ok; s += step) {
         const Unit u = unit_of(s, p);
-        int64_t tm, tn;
-        raster(u.tile, p.gm, p.gn, p.group_m, &tm, &tn);
+        int32_t tm, tn;
+        raster((uint32_t)u.tile, (uint32_t)p.gm, (uint32_t)p.gn, (uint32_t)p.group_m, &tm, &tn);
         // a narrow tile loads only its own columns of B, through the map whose
         // box has that many rows
         const int ub_rows = kPair ? u.width / 2 : u.width;
         const CUtensorMap* mb = u.cut ? &map_b_cut : &map_b;
         const uint32_t utx = a_stage + (uint32_t)ub_rows * 128;
-        const int32_t arow = (int32_t)(tm * tile_m + rank * BM);
-        const int32_t brow = (int32_t)(tn * p.bn + u.col + rank * ub_rows);
-        for (int64_t kb = 0; kb < nk; ++kb) {
+        const int32_t arow = tm * tile_m + (int32_t)rank * BM;
+        const int32_t brow = tn * p.bn + u.col + (int32_t)rank * ub_rows;
+        for (int32_t kb = kb0; kb < kb1; ++kb) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err)) { ok = false; break; }
-          const int32_t kc = (int32_t)(kb * p.kblk);
+          const int32_t kc = kb * p.kblk;
           if constexpr (kPair) {
             // both CTAs' copies complete on the even CTA's full barrier
             const uint32_t fb = mapa(full_bar(stage), 0);
@@ -228,17 +260,17 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t idesc_cut = idesc_f32acc((uint32_t)tile_m, (uint32_t)p.bn_cut, kF8);
       int stage = 0;
       uint32_t phase = 0;
-      int64_t t = 0;
+      int32_t t = 0;
       bool ok = true;
-      for (int64_t s = prog; s < TS && ok; s += step, ++t) {
+      for (int32_t s = prog; s < TS && ok; s += step, ++t) {
         const Unit u = unit_of(s, p);
         const uint32_t idesc = u.cut ? idesc_cut : idesc_full;
-        const int acc = (int)(t & 1);
+        const int acc = t & 1;
         const uint32_t use = (uint32_t)((t >> 1) & 1);
         if (!mbar_wait(tempty_bar(acc), use ^ 1u, abort_flag, p.err)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d = tmem_base + (uint32_t)(acc * p.bn);
-        for (int64_t kb = 0; kb < nk; ++kb) {
+        for (int32_t kb = kb0; kb < kb1; ++kb) {
           if (!mbar_wait(full_bar(stage), phase, abort_flag, p.err)) { ok = false; break; }
           tc_fence_after();
           const uint64_t ad = desc_kmajor_sw128(a0 + a_stage * stage);
@@ -247,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           // apart inside the swizzle atom (start address advances by 32 >> 4).
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
-            const uint32_t accum = (kb > 0 || k > 0) ? 1u : 0u;
+            const uint32_t accum = (kb > kb0 || k > 0) ? 1u : 0u;
             if constexpr (kPair) mma_pair<kF8>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accum);
             else mma<kF8>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accum);
           }
@@ -266,19 +298,102 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     __syncwarp();
-  } else {
-    // ---------------- epilogue (warps 2..5 -> TMEM lane quadrants 2,3,0,1)
-    const int quad = warp & 3;
-    const int row_in_tile = (int)rank * BM + quad * 32 + lane;
-    // FP8 dequantisation factor 1 / (s_A * s_B), both steps in fp32
-    const float scale = (p.scale_a && p.scale_b) ? 1.f / (*p.scale_a * *p.scale_b) : 1.f;
+  }
+
+  // ------------------------------------------------------------ epilogue
+  // (warps 2..5 -> TMEM lane quadrants 2,3,0,1)
+  const int quad = warp & 3;
+  const int32_t warp_row0 = (int32_t)rank * BM + quad * 32;  // first tile row of this warp
+  const uint32_t tlane = (uint32_t)(quad * 32) << 16;         // TMEM lane offset of this warp
+  // FP8 dequantisation factor 1 / (s_A * s_B), both steps in fp32
+  const float scale = (p.scale_a && p.scale_b) ? 1.f / (*p.scale_a * *p.scale_b) : 1.f;
+  // this warp's two staging buffers of 32 rows x 64 bytes (64-byte swizzle)
+  const uint32_t stg = cst + (uint32_t)quad * 4096u;
+  uint32_t nstaged = 0;
+  // one row's 32 columns [c0, c0 + 32) of C from FP32 values f (plain stores)
+  auto store_chunk = [&](const float* f, int64_t row, int64_t c0) {
+    if (row >= p.M || c0 >= p.N) return;
+    __nv_bfloat16* crow = p.c + row * p.N;
+    if (p.c_vec != 0 && c0 + 32 <= p.N) {
+      uint4 v[4];
+      __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(v);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) h[i] = __floats2bfloat162_rn(f[2 * i] * scale, f[2 * i + 1] * scale);
+      uint4* dst = reinterpret_cast<uint4*>(crow + c0);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) dst[i] = v[i];
+    } else {
+#pragma unroll
+      for (int i = 0; i < 32; ++i)
+        if (c0 + i < p.N) crow[c0 + i] = __float2bfloat16_rn(f[i] * scale);
+    }
+    if constexpr (kCount) {
+      for (int i = 0; i < 32; ++i)
+        if (c0 + i < p.N) {
+          atomicAdd(p.counts + row * p.N + c0 + i, 1u);
+          p.owner[row * p.N + c0 + i] = (int32_t)prog;
+        }
+    }
+  };
+  // the 32 x 32 block of C at rows [row0, +32), columns [c0, +32): lane i
+  // holds row row0 + i in f. Staged in shared memory and written by one TMA
+  // store (clipped to C's bounds by the tensor map), or by per-row stores.
+  auto store_block = [&](const float* f, int64_t row0, int64_t c0) {
+    if (!kCount && p.stage_c) {
+      if (row0 >= p.M || c0 >= p.N) return;  // warp-uniform: the block lies outside C
+      const uint32_t buf = stg + (nstaged & 1u) * 2048u;
+      if (lane == 0) bulk_wait_read<1>();  // the store issued from this buffer two blocks ago has read it
+      __syncwarp();
+      uint32_t w[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(f[2 * i] * scale, f[2 * i + 1] * scale);
+        w[i] = *reinterpret_cast<uint32_t*>(&h);
+      }
+      // 16-byte piece u of row `lane` sits at piece u ^ ((lane >> 1) & 3)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        st_shared_v4(buf + (uint32_t)lane * 64u + ((uint32_t)(u ^ ((lane >> 1) & 3)) << 4), w[4 * u], w[4 * u + 1],
+                     w[4 * u + 2], w[4 * u + 3]);
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        tma_store_2d(&map_c, buf, (int32_t)c0, (int32_t)row0);
+        bulk_commit();
+      }
+      ++nstaged;
+    } else {
+      store_chunk(f, row0 + lane, c0);
+    }
+  };
+  bool counted = false;
+  // Checked launch: each epilogue warp counts itself done right after its
+  // last claim (still ahead of its last accumulator); the warp that counts
+  // last clears the bitmap for the next launch. A warp that leaves its loop
+  // early counts itself at the exit.
+  auto finish_claims = [&]() {
+    if (counted) return;
+    counted = true;
+    int last = 0;
+    if (lane == 0) {
+      __threadfence();
+      last = atomicAdd(p.claim_done, 1u) == gridDim.x * 4u - 1u ? 1 : 0;
+    }
+    if (__shfl_sync(0xffffffffu, last, 0)) {
+      __threadfence();
+      const int64_t words = (p.claim_bits + 31) / 32;
+      for (int64_t i = lane; i < words; i += 32) p.claims[i] = 0u;
+      if (lane == 0) *p.claim_done = 0u;
+    }
+  };
+  if (warp >= 2) {
     const uint32_t tempty_remote = kPair ? mapa(tempty_bar(0), 0) : 0u;
-    int64_t t = 0;
+    int32_t t = 0;
     // validate a store against the map (the slot is this program's and its
     // tile lies in the grid), then claim this warp's 32-row slice of the
-    // (narrow) tile: (tile, narrow part, CTA of the pair, lane quadrant);
-    // warp-uniform result
-    auto claim = [&](int64_t s, int64_t tm, int64_t tn, int32_t part) -> bool {
+    // (narrow) tile or K-slice part: (tile, part, CTA of the pair, lane
+    // quadrant); warp-uniform result
+    auto claim = [&](int32_t s, int32_t tm, int32_t tn, int32_t part) -> bool {
       int ok = 1;
       if (lane == 0) {
         const bool on_map = s < TS && (s - prog) % step == 0 && tm >= 0 && tm < p.gm && tn >= 0 && tn < p.gn;
@@ -286,36 +401,11 @@ __global__ void __launch_bounds__(kThreads, 1)
           record_device_error(p.err, kDevRace);
           ok = 0;
         } else {
-          const int64_t id = (((tm * p.gn + tn) * p.ncut + part) * (kPair ? 2 : 1) + rank) * 4 + quad;
+          const int64_t id = ((((int64_t)tm * p.gn + tn) * p.parts + part) * (kPair ? 2 : 1) + rank) * 4 + quad;
           ok = claim_tile(p.claims, id, p.err) ? 1 : 0;
         }
       }
       return __shfl_sync(0xffffffffu, ok, 0) != 0;
-    };
-    // one row's 32 columns [c0, c0 + 32) of C from FP32 values f
-    auto store_chunk = [&](const float* f, int64_t row, int64_t c0) {
-      if (row >= p.M || c0 >= p.N) return;
-      __nv_bfloat16* crow = p.c + row * p.N;
-      if (p.c_vec != 0 && c0 + 32 <= p.N) {
-        uint4 v[4];
-        __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) h[i] = __floats2bfloat162_rn(f[2 * i] * scale, f[2 * i + 1] * scale);
-        uint4* dst = reinterpret_cast<uint4*>(crow + c0);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) dst[i] = v[i];
-      } else {
-#pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if (c0 + i < p.N) crow[c0 + i] = __float2bfloat16_rn(f[i] * scale);
-      }
-      if constexpr (kCount) {
-        for (int i = 0; i < 32; ++i)
-          if (c0 + i < p.N) {
-            atomicAdd(p.counts + row * p.N + c0 + i, 1u);
-            p.owner[row * p.N + c0 + i] = (int32_t)prog;
-          }
-      }
     };
     auto release_acc = [&](int acc) {
       tc_fence_before();
@@ -325,45 +415,32 @@ __global__ void __launch_bounds__(kThreads, 1)
         else mbar_arrive(tempty_bar(acc));
       }
     };
-    // Checked launch: each epilogue warp counts itself done right after its
-    // last claim (still ahead of its last accumulator); the warp that counts
-    // last clears the bitmap for the next launch. A warp that leaves its loop
-    // early counts itself at the exit.
-    bool counted = false;
-    auto finish_claims = [&]() {
-      if (counted) return;
-      counted = true;
-      int last = 0;
-      if (lane == 0) {
-        __threadfence();
-        last = atomicAdd(p.claim_done, 1u) == gridDim.x * 4u - 1u ? 1 : 0;
-      }
-      if (__shfl_sync(0xffffffffu, last, 0)) {
-        __threadfence();
-        const int64_t words = (p.claim_bits + 31) / 32;
-        for (int64_t i = lane; i < words; i += 32) p.claims[i] = 0u;
-        if (lane == 0) *p.claim_done = 0u;
-      }
-    };
-    for (int64_t s = prog; s < TS; s += step, ++t) {
+    for (int32_t s = prog; s < TS; s += step, ++t) {
       const Unit u = unit_of(s, p);
-      const int acc = (int)(t & 1);
+      const int acc = t & 1;
       const uint32_t use = (uint32_t)((t >> 1) & 1);
-      int64_t tm, tn;
-      raster(u.tile, p.gm, p.gn, p.group_m, &tm, &tn);
+      int32_t tm, tn;
+      raster((uint32_t)u.tile, (uint32_t)p.gm, (uint32_t)p.gn, (uint32_t)p.group_m, &tm, &tn);
       bool store_ok = true;
       // claimed before the accumulator is ready, so the atomic's latency
       // hides behind the K loop
       if constexpr (kChecked) {
-        store_ok = claim(s, tm, tn, u.part);
+        store_ok = claim(s, tm, tn, S > 1 ? (int32_t)kslice : u.part);
         if (s + step >= TS) finish_claims();
       }
       const bool ready = mbar_wait(tfull_bar(acc), use, abort_flag, p.err);
       if (!__all_sync(0xffffffffu, ready)) break;  // leave together (tcgen05.ld is warp-collective)
       tc_fence_after();
-      const int64_t row = tm * tile_m + row_in_tile;
-      const int64_t col0 = tn * p.bn + u.col;
-      const uint32_t tacc = tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * p.bn);
+      if (S > 1) {
+        // split program: the partial sum meets the others' below
+        sp_have = store_ok;
+        sp_tm = tm;
+        sp_tn = tn;
+        break;
+      }
+      const int64_t row0 = (int64_t)tm * tile_m + warp_row0;
+      const int64_t col0 = (int64_t)tn * p.bn + u.col;
+      const uint32_t tacc = tmem_base + tlane + (uint32_t)(acc * p.bn);
       for (int ch = 0; ch < u.width / 32 && store_ok; ++ch) {
         uint32_t r[32];
         tmem_ld32(tacc + (uint32_t)(ch * 32), r);
@@ -371,11 +448,81 @@ __global__ void __launch_bounds__(kThreads, 1)
         float f[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) f[i] = __uint_as_float(r[i]);
-        store_chunk(f, row, col0 + ch * 32);
+        store_block(f, row0, col0 + ch * 32);
       }
       release_acc(acc);
     }
+  }
+
+  if (!kPair && S > 1) {
+    // ---------------- split-K reduction across the cluster's CTAs
+    // Column slice j (width w = bn / S) of the tile belongs to CTA j. Every
+    // CTA copies its partial sums of the other slices, as 4 KB blocks (one
+    // lane quadrant x 32 columns, 16-byte pieces lane-major), from a send
+    // area into the owners' receive areas; both areas overlay the operand
+    // ring, idle once every CTA's MMAs have completed. The copies complete on
+    // the owner's recv barrier; the owner then adds the S partials of its
+    // slice in slice order 0..S-1 and stores the slice.
+    const int32_t w = p.bn / S;
+    const int32_t nch = w / 32;
+    const uint32_t slot_bytes = 128u * (uint32_t)w * 4u;  // one source's partial of one slice
+    const uint32_t send0 = a0 + (uint32_t)(S - 1) * slot_bytes;
+    const bool tile = prog < TS;  // the same for every CTA of the cluster
+    auto block = [&](uint32_t area, int32_t slot, int32_t ch) {
+      return area + (uint32_t)((slot * 4 + quad) * nch + ch) * 4096u;
+    };
+    if (warp == 2 && lane == 0 && tile) mbar_arrive_expect_tx(recv_bar, (uint32_t)(S - 1) * slot_bytes);
+    cluster_sync();  // (1) every CTA's accumulator is final and its ring is free
+    if (warp >= 2 && tile) {
+      for (int32_t j = 0; j < S; ++j) {
+        if (j == (int32_t)kslice) continue;
+        const int32_t dslot = j < (int32_t)kslice ? j : j - 1;                  // among this CTA's destinations
+        const int32_t rslot = (int32_t)kslice < j ? (int32_t)kslice : (int32_t)kslice - 1;  // at the owner
+        for (int32_t ch = 0; ch < nch; ++ch) {
+          uint32_t r[32];
+          tmem_ld32(tmem_base + tlane + (uint32_t)(j * w + ch * 32), r);
+          tmem_ld_wait();
+          const uint32_t src = block(send0, dslot, ch);
+#pragma unroll
+          for (uint32_t q = 0; q < 8; ++q)
+            st_shared_v4(src + q * 512u + (uint32_t)lane * 16u, r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0)
+            bulk_copy_to_cluster(mapa(block(a0, rslot, ch), (uint32_t)j), src, 4096u, mapa(recv_bar, (uint32_t)j));
+        }
+      }
+    }
+    if (warp >= 2 && tile) {
+      const bool got = mbar_wait(recv_bar, 0, abort_flag, p.err);
+      if (__all_sync(0xffffffffu, got) && sp_have) {
+        const int64_t row0 = (int64_t)sp_tm * tile_m + warp_row0;
+        const int64_t col0 = (int64_t)sp_tn * p.bn + (int64_t)kslice * w;
+        for (int32_t ch = 0; ch < nch; ++ch) {
+          float f[32];
+          for (int32_t src = 0; src < S; ++src) {
+            uint32_t v[32];
+            if (src == (int32_t)kslice) {
+              tmem_ld32(tmem_base + tlane + (uint32_t)((int32_t)kslice * w + ch * 32), v);
+              tmem_ld_wait();
+            } else {
+              const uint32_t at = block(a0, src < (int32_t)kslice ? src : src - 1, ch);
+#pragma unroll
+              for (uint32_t q = 0; q < 8; ++q) ld_shared_v4(at + q * 512u + (uint32_t)lane * 16u, v + 4 * q);
+            }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) f[i] = src == 0 ? __uint_as_float(v[i]) : f[i] + __uint_as_float(v[i]);
+          }
+          store_block(f, row0, col0 + ch * 32);
+        }
+      }
+    }
+    cluster_sync();  // (2) every copy into every CTA of the cluster has completed (sources read)
+  }
+  if (warp >= 2) {
     if constexpr (kChecked) finish_claims();
+    if (!kCount && p.stage_c && lane == 0) bulk_wait_all();  // C written before the CTA retires
+    __syncwarp();
   }
   tc_fence_before();
   if constexpr (kPair) cluster_sync();  // the peer no longer touches our shared memory / TMEM
@@ -421,9 +568,13 @@ tp_status make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t k, i
   return TP_OK;
 }
 
+// The tensor maps of a launch: A, B, B for narrow tiles, C (TMA stores).
+struct Maps {
+  CUtensorMap a, b, b_cut, c;
+};
+
 template <bool kF8, bool kPair, bool kCount, bool kChecked>
-cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mbc, const TcArgs& p,
-                          int grid, size_t smem, cudaStream_t st) {
+cudaError_t launch_kernel(const Maps& m, const TcArgs& p, int grid, int csize, size_t smem, cudaStream_t st) {
   auto k = gemm_tc_kernel<kF8, kPair, kCount, kChecked>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -438,45 +589,45 @@ cudaError_t launch_kernel(const CUtensorMap& ma, const CUtensorMap& mb, const CU
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kPair ? 2 : 1;
+  attr[0].val.clusterDim.x = (unsigned)csize;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  return cudaLaunchKernelEx(&cfg, k, ma, mb, mbc, p);
+  return cudaLaunchKernelEx(&cfg, k, m.a, m.b, m.b_cut, m.c, p);
 }
 
 template <bool kF8, bool kPair>
-cudaError_t launch_inst(bool count, bool checked, const CUtensorMap& ma, const CUtensorMap& mb,
-                        const CUtensorMap& mbc, const TcArgs& p, int grid, size_t smem, cudaStream_t st) {
-  if (checked) return count ? launch_kernel<kF8, kPair, true, true>(ma, mb, mbc, p, grid, smem, st)
-                            : launch_kernel<kF8, kPair, false, true>(ma, mb, mbc, p, grid, smem, st);
-  return count ? launch_kernel<kF8, kPair, true, false>(ma, mb, mbc, p, grid, smem, st)
-               : launch_kernel<kF8, kPair, false, false>(ma, mb, mbc, p, grid, smem, st);
+cudaError_t launch_inst(bool count, bool checked, const Maps& m, const TcArgs& p, int grid, int csize, size_t smem,
+                        cudaStream_t st) {
+  if (checked) return count ? launch_kernel<kF8, kPair, true, true>(m, p, grid, csize, smem, st)
+                            : launch_kernel<kF8, kPair, false, true>(m, p, grid, csize, smem, st);
+  return count ? launch_kernel<kF8, kPair, true, false>(m, p, grid, csize, smem, st)
+               : launch_kernel<kF8, kPair, false, false>(m, p, grid, csize, smem, st);
 }
 
 template <bool kF8>
-cudaError_t launch_any(bool pair, bool count, bool checked, const CUtensorMap& ma, const CUtensorMap& mb,
-                       const CUtensorMap& mbc, const TcArgs& p, int grid, size_t smem, cudaStream_t st) {
-  return pair ? launch_inst<kF8, true>(count, checked, ma, mb, mbc, p, grid, smem, st)
-              : launch_inst<kF8, false>(count, checked, ma, mb, mbc, p, grid, smem, st);
+cudaError_t launch_any(bool pair, bool count, bool checked, const Maps& m, const TcArgs& p, int grid, int csize,
+                       size_t smem, cudaStream_t st) {
+  return pair ? launch_inst<kF8, true>(count, checked, m, p, grid, csize, smem, st)
+              : launch_inst<kF8, false>(count, checked, m, p, grid, csize, smem, st);
 }
 
-// Clusters (CTA pairs, or single CTAs) of the kernel that can be resident at
-// once (0 when the query fails).
+// Clusters of `csize` CTAs (a CTA pair, a split program, or single CTAs) of
+// the kernel that can be resident at once (0 when the query fails).
 template <bool kPair>
-int max_active_clusters(size_t smem) {
+int max_active_clusters(int csize, size_t smem) {
   auto k = gemm_tc_kernel<false, kPair, false, false>;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448) != cudaSuccess) return 0;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kPair ? 2 : 1);
+  cfg.gridDim = dim3((unsigned)csize);
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kPair ? 2 : 1;
+  attr[0].val.clusterDim.x = (unsigned)csize;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
@@ -487,6 +638,59 @@ int max_active_clusters(size_t smem) {
     return 0;
   }
   return n;
+}
+
+// Shared-memory plan of a launch: ring stages, the region before the
+// epilogue staging (the ring, or the larger split-K receive buffer), whether
+// the epilogue stages C blocks, and the dynamic size requested.
+struct SmemPlan {
+  int stages = 0;
+  size_t body = 0;
+  bool stage_c = false;
+  size_t smem = 0;
+};
+
+constexpr size_t kSmemFixed = 1024 + 256;  // alignment slack + barriers
+constexpr size_t kSmemBudget = 232448;     // 227 KB opt-in
+
+// stages_req = 0 asks for the deepest ring that fits beside the staging
+// area. The staging area is dropped (per-row stores) when an explicitly
+// requested ring leaves no room for it.
+tp_status plan_smem(bool pair, int bn, int split, int stages_req, bool want_stage_c, SmemPlan* out) {
+  const size_t stage_bytes = (size_t)BM * 128 + (size_t)(pair ? bn / 2 : bn) * 128;
+  // split-K: receive and send areas of (split - 1) slice partials each
+  const size_t recv = split > 1 ? 2 * (size_t)(split - 1) * 128 * (size_t)(bn / split) * 4 : 0;
+  for (int stage_c = want_stage_c ? 1 : 0; stage_c >= 0; --stage_c) {
+    const size_t stg = stage_c ? kStageC : 0;
+    int stages = stages_req > 0 ? stages_req : (int)((kSmemBudget - kSmemFixed - stg) / stage_bytes);
+    stages = stages > kMaxStages ? kMaxStages : stages;
+    if (stages < 2) continue;
+    size_t body = std::max((size_t)stages * stage_bytes, recv);
+    body = (body + 1023) & ~(size_t)1023;
+    if (kSmemFixed + body + stg > kSmemBudget) continue;
+    out->stages = stages;
+    out->body = body;
+    out->stage_c = stage_c != 0;
+    out->smem = kSmemFixed + body + stg;
+    return TP_OK;
+  }
+  return fail(TP_ERR_UNSUPPORTED, "shared memory too small for the requested stages");
+}
+
+// C (bf16, N columns, row stride N) as 32 x 32 boxes with the 64-byte swizzle
+// of the epilogue's staging layout.
+tp_status make_map_c(CUtensorMap* map, void* ptr, int64_t M, int64_t N) {
+  auto fn = encode_fn();
+  if (!fn) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+  cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
+  cuuint64_t strides[1] = {(cuuint64_t)(N * 2)};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled (C) failed (" + std::to_string((int)r) + ")");
+  return TP_OK;
 }
 
 }  // namespace
@@ -516,21 +720,45 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
     return fail(TP_ERR_ALIGN, "TMA needs 16-byte aligned bases and row strides (K a multiple of 16 bytes)");
   if (M == 0 || N == 0) return TP_OK;
   if (K == 0) return fail(TP_ERR_UNSUPPORTED, "K = 0");
-  CUtensorMap ma, mb;
-  tp_status s = make_map(&ma, a->ptr, M, K, lda, esize, BM);
+  const int64_t T = c->num_tiles;
+  // slots (tiles, or narrow tiles: up to 8 per tile) are counted in 32 bits
+  if (T >= ((int64_t)1 << 28) || M >= ((int64_t)1 << 31) || N >= ((int64_t)1 << 31))
+    return fail(TP_ERR_UNSUPPORTED, "tensor-core GEMM: 2^28 tiles or more, or an extent of 2^31");
+  const int64_t progs = c->kind == TP_MAP_IDENTITY ? T : c->num_programs;
+  const int kblk = 128 / esize;
+  const int64_t nk = (K + kblk - 1) / kblk;
+  const int32_t split = (cfg && cfg->split_k > 1) ? cfg->split_k : 1;
+  if (cfg && (cfg->split_k < 0 || cfg->split_k > 8 || (split > 1 && (split & (split - 1)))))
+    return fail(TP_ERR_INVALID, "split_k must be 0, 1, 2, 4 or 8");
+  if (split > 1) {
+    if (pair) return fail(TP_ERR_UNSUPPORTED, "split_k applies to 128-row tiles (one CTA per K slice)");
+    if (bn % (32 * split)) return fail(TP_ERR_UNSUPPORTED, "split_k needs tile columns a multiple of 32 * split_k");
+    if (nk < split) return fail(TP_ERR_UNSUPPORTED, "split_k exceeds the number of K blocks");
+    if (progs < T) return fail(TP_ERR_UNSUPPORTED, "split_k needs at most one tile per program");
+  }
+  const int32_t limit = (cfg && cfg->cut_limit > 0) ? cfg->cut_limit : 4;
+  if (cfg && (cfg->cut_limit < 0 || cfg->cut_limit > 8)) return fail(TP_ERR_INVALID, "cut_limit must be 0..8");
+  const bool count = ex->write_counts != nullptr;
+  const bool checked = (ex->flags & TP_EXEC_CHECKED) != 0;
+  Maps maps;
+  tp_status s = make_map(&maps.a, a->ptr, M, K, lda, esize, BM);
   if (s != TP_OK) return s;
-  s = make_map(&mb, b->ptr, N, K, ldb, esize, pair ? bn / 2 : bn);
+  s = make_map(&maps.b, b->ptr, N, K, ldb, esize, pair ? bn / 2 : bn);
   if (s != TP_OK) return s;
+  maps.b_cut = maps.b;
   TcArgs p{};
   p.M = M;
   p.N = N;
   p.K = K;
-  p.gm = c->grid[0];
-  p.gn = c->grid[1];
+  p.gm = (int32_t)c->grid[0];
+  p.gn = (int32_t)c->grid[1];
   p.bn = bn;
   p.kind = c->kind;
   p.group_m = (c->kind != TP_MAP_IDENTITY && cfg && cfg->group_m > 0) ? cfg->group_m : 1;
-  p.kblk = 128 / esize;
+  if (p.group_m > p.gm) p.group_m = p.gm;
+  p.kblk = kblk;
+  p.nk = (int32_t)nk;
+  p.split = split;
   p.c_vec = (N % 8 == 0) && (((uintptr_t)c->t.ptr & 15) == 0);
   p.c = static_cast<__nv_bfloat16*>(c->t.ptr);
   p.scale_a = scale_a;
@@ -541,29 +769,30 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   int cols = 32;
   while (cols < 2 * bn) cols *= 2;
   p.tmem_cols = cols;
-  const size_t stage_bytes = (size_t)BM * 128 + (size_t)(pair ? bn / 2 : bn) * 128;
-  const size_t fixed = 1024 + 256;  // alignment slack + barriers
-  const size_t budget = 232448;     // 227 KB opt-in
-  int stages = (cfg && cfg->stages > 0) ? cfg->stages : (int)((budget - fixed) / stage_bytes);
-  stages = stages > kMaxStages ? kMaxStages : stages;
-  if (stages < 2 || fixed + stages * stage_bytes > budget)
-    return fail(TP_ERR_UNSUPPORTED, "shared memory too small for the requested stages");
-  p.stages = stages;
-  const size_t smem = fixed + stages * stage_bytes;
-  const int64_t progs = c->kind == TP_MAP_IDENTITY ? c->num_tiles : c->num_programs;
-  const int64_t grid = pair ? 2 * progs : progs;
+  SmemPlan plan;
+  s = plan_smem(pair, bn, split, cfg ? cfg->stages : 0, p.c_vec && !count, &plan);
+  if (s != TP_OK) return s;
+  p.stages = plan.stages;
+  p.body_bytes = (int32_t)plan.body;
+  p.stage_c = plan.stage_c ? 1 : 0;
+  if (plan.stage_c) {
+    s = make_map_c(&maps.c, c->t.ptr, M, N);
+    if (s != TP_OK) return s;
+  } else {
+    maps.c = maps.a;  // unused
+  }
+  const int csize = pair ? 2 : split;
+  const int64_t grid = progs * csize;
+  if (grid >= ((int64_t)1 << 31)) return fail(TP_ERR_UNSUPPORTED, "grid too large");
   // Schedule: whole tiles, except that on a strided map the R = T mod P tiles
   // of the last, partial round may each be cut along N into S narrow tiles
-  // run by the programs that would otherwise sit idle in that round.
-  const int64_t T = c->num_tiles;
-  p.dp_slots = T;
-  p.total_slots = T;
+  // run by the programs that would otherwise sit idle in that round (not in
+  // split-K programs, which hold one tile each).
+  p.dp_slots = (int32_t)T;
+  p.total_slots = (int32_t)T;
   p.ncut = 1;
   p.bn_cut = bn;
-  const int32_t limit = (cfg && cfg->split_k > 0) ? cfg->split_k : 4;
-  if (limit > 8) return fail(TP_ERR_INVALID, "split_k must be 0..8");
-  CUtensorMap mb_cut = mb;
-  if (c->kind == TP_MAP_STRIDED) {
+  if (c->kind == TP_MAP_STRIDED && split == 1) {
     const int64_t R = T % progs;
     const int unit = pair ? 64 : 32;  // narrow tiles keep whole 32-row B boxes per CTA
     int64_t S = 1;
@@ -571,21 +800,20 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
     if (S >= 2) {
       p.ncut = (int32_t)S;
       p.bn_cut = (int32_t)(bn / S);
-      p.dp_slots = T - R;
-      p.total_slots = T - R + R * S;
-      s = make_map(&mb_cut, b->ptr, N, K, ldb, esize, pair ? p.bn_cut / 2 : p.bn_cut);
+      p.dp_slots = (int32_t)(T - R);
+      p.total_slots = (int32_t)(T - R + R * S);
+      s = make_map(&maps.b_cut, b->ptr, N, K, ldb, esize, pair ? p.bn_cut / 2 : p.bn_cut);
       if (s != TP_OK) return s;
     }
   }
-  const bool count = ex->write_counts != nullptr;
-  const bool checked = (ex->flags & TP_EXEC_CHECKED) != 0;
+  p.parts = p.ncut * split;
   if (checked) {
-    p.claim_bits = c->num_tiles * p.ncut * (pair ? 8 : 4);
+    p.claim_bits = T * p.parts * (pair ? 8 : 4);
     s = claims_for(ctx, p.claim_bits, &p.claims, &p.claim_done);
     if (s != TP_OK) return s;
   }
-  cudaError_t e = esize == 2 ? launch_any<false>(pair, count, checked, ma, mb, mb_cut, p, (int)grid, smem, stream)
-                             : launch_any<true>(pair, count, checked, ma, mb, mb_cut, p, (int)grid, smem, stream);
+  cudaError_t e = esize == 2 ? launch_any<false>(pair, count, checked, maps, p, (int)grid, csize, plan.smem, stream)
+                             : launch_any<true>(pair, count, checked, maps, p, (int)grid, csize, plan.smem, stream);
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core GEMM launch");
   return TP_OK;
 }
@@ -594,17 +822,17 @@ tp_status gemm_tc_resident(tp_ctx* ctx, const tp_gemm_config* cfg, int32_t* prog
   const int bm = cfg->bm ? cfg->bm : BM, bn = cfg->bn ? cfg->bn : 256;
   if (bm != BM && bm != 2 * BM) return fail(TP_ERR_UNSUPPORTED, "tiles have 128 or 256 rows");
   const bool pair = bm == 2 * BM;
-  const size_t stage_bytes = (size_t)BM * 128 + (size_t)(pair ? bn / 2 : bn) * 128;
-  const size_t fixed = 1024 + 256, budget = 232448;
-  int stages = cfg->stages > 0 ? cfg->stages : (int)((budget - fixed) / stage_bytes);
-  stages = stages > kMaxStages ? kMaxStages : stages;
-  if (stages < 2 || fixed + stages * stage_bytes > budget)
-    return fail(TP_ERR_UNSUPPORTED, "shared memory too small for the requested stages");
-  const size_t smem = fixed + stages * stage_bytes;
+  const int split = cfg->split_k > 1 ? cfg->split_k : 1;
+  if (split > 8 || (split & (split - 1))) return fail(TP_ERR_INVALID, "split_k must be 0, 1, 2, 4 or 8");
+  if (split > 1 && pair) return fail(TP_ERR_UNSUPPORTED, "split_k applies to 128-row tiles");
+  SmemPlan plan;
+  tp_status s = plan_smem(pair, bn, split, cfg->stages, true, &plan);
+  if (s != TP_OK) return s;
   (void)ctx;
-  const int clusters = pair ? max_active_clusters<true>(smem) : max_active_clusters<false>(smem);
+  const int csize = pair ? 2 : split;
+  const int clusters = pair ? max_active_clusters<true>(csize, plan.smem) : max_active_clusters<false>(csize, plan.smem);
   if (clusters <= 0) return fail(TP_ERR_CUDA, "cudaOccupancyMaxActiveClusters failed");
-  *programs = clusters;  // CTA pairs (256-row tiles) or CTAs
+  *programs = clusters;  // CTA pairs (256-row tiles), split programs, or CTAs
   return TP_OK;
 }
 

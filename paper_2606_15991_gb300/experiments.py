@@ -187,6 +187,19 @@ def graph_time_ms(ctx, stream, record, reps: int, replays: int = 3) -> float:
     return best
 
 
+def tuned_config(ctx, best, tiles: int):
+    """A launch config from an autotuned one: persistent programs (CTAs, CTA
+    pairs for 256-row tiles) up to the SM count, or one split program per
+    tile for a split-K config."""
+    from . import gemm_config
+    if best.split_k > 1:
+        progs = tiles
+    else:
+        progs = min(best.num_programs or (ctx.sm_count // (2 if best.bm == 256 else 1)), tiles)
+    return gemm_config(bm=best.bm, bn=best.bn, stages=best.stages, group_m=best.group_m, num_programs=progs,
+                       split_k=best.split_k)
+
+
 class _Captured:
     """`reps` back-to-back calls captured once into a graph (the library's
     for `record(ex)`, torch's for a plain callable); time() replays it once,
@@ -313,17 +326,16 @@ def gemm_size_sweep(ctx, sizes=(1024, 2048, 4096, 8192, 16384, 32768), target_ms
         best, table, best_tf = tp_autotune(ctx, n, n, n, "bf16")
         t_tune = time.perf_counter() - t0
         reps = int(min(200, max(1, np.ceil(target_ms / (flops / (best_tf * 1e12) * 1e3)))))
-        pair = best.bm == 256
         tiles = -(-n // best.bm) * -(-n // best.bn)
-        progs = min(best.num_programs or (ctx.sm_count // (2 if pair else 1)), tiles)
-        cfg = gemm_config(bm=best.bm, bn=best.bn, stages=best.stages, group_m=best.group_m, num_programs=progs)
+        cfg = tuned_config(ctx, best, tiles)
+        progs = cfg.num_programs
         p = tp_partition_create(ctx, c, (best.bm, best.bn))
         tp_partition_map(p, MAP_STRIDED, progs)
         pp = tp_partition_create(ctx, c, (best.bm, best.bn))
         bT = bt.t()
         chk = make_exec(CAPTURE, stream, checked=True)
-        ucfg = gemm_config(bm=best.bm, bn=best.bn, stages=best.stages, group_m=best.group_m, num_programs=progs)
-        pcfg = gemm_config(bm=best.bm, bn=best.bn, stages=best.stages)
+        ucfg = tuned_config(ctx, best, tiles)
+        pcfg = gemm_config(bm=best.bm, bn=best.bn, stages=best.stages, split_k=best.split_k)
         variants = {
             "safe": _Captured(ctx, stream, reps, record=lambda ex: tp_gemm(ctx, p, a, bT, cfg, ex)),
             "checked": _Captured(ctx, stream, reps, record=lambda ex: tp_gemm(ctx, p, a, bT, cfg, chk)),
@@ -340,6 +352,7 @@ def gemm_size_sweep(ctx, sizes=(1024, 2048, 4096, 8192, 16384, 32768), target_ms
         if with_cublas:
             del c2
         row = {"n": n, "tile": [best.bm, best.bn], "stages": best.stages, "group_m": best.group_m,
+               "split_k": best.split_k,
                "programs": progs, "tiles": tiles, "reps": reps, "tune_s": t_tune,
                "ms": ms, "tflops": {k: flops / (v * 1e-3) / 1e12 for k, v in ms.items()}}
         row["checked_overhead"] = ms["checked"] / ms["safe"] - 1.0
@@ -465,10 +478,7 @@ def bimodal_queue(ctx, n_units: int = 2000, streams=(1, 2, 4, 8, 16, 32), small:
     cfgs = []
     for n in sizes:
         best, _, _ = tp_autotune(ctx, n, n, n, "bf16")
-        tiles = -(-n // best.bm) * -(-n // best.bn)
-        progs = min(ctx.sm_count // (2 if best.bm == 256 else 1), tiles)
-        cfgs.append(gemm_config(bm=best.bm, bn=best.bn, stages=best.stages, group_m=best.group_m,
-                                num_programs=progs))
+        cfgs.append(tuned_config(ctx, best, -(-n // best.bm) * -(-n // best.bn)))
     kinds = bimodal_kinds(n_units)
     flops = sum(2.0 * sizes[k] ** 3 for k in kinds)
     S_max = max(streams)

@@ -77,19 +77,19 @@ def test_quantize_zero_tensor_and_strided_map(ctx):
     assert scale.item() == 1.0 and int(q.view(torch.uint8).max()) == 0
 
 
-def _fp8_gemm(ctx, a, bt, bm=128, bn=128, P=None, group_m=1, count=False, checked=False):
+def _fp8_gemm(ctx, a, bt, bm=128, bn=128, P=None, group_m=1, count=False, checked=False, split_k=0):
     qa, _, sa, _, _ = _quantize(ctx, a, 16)
     qbt, _, sb, _, _ = _quantize(ctx, bt, 16)
     m, n = a.shape[0], bt.shape[0]
     c = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
     p = tp.tp_partition_create(ctx, c, (bm, bn))
     tiles = tp.tp_partition_query(p)["num_tiles"]
-    tp.tp_partition_map(p, tp.MAP_STRIDED, min(P or (ctx.sm_count * 128 // bm), tiles))
+    tp.tp_partition_map(p, tp.MAP_STRIDED, tiles if split_k > 1 else min(P or (ctx.sm_count * 128 // bm), tiles))
     counts = owner = None
     if count:
         counts = torch.zeros(m * n, dtype=torch.int32, device="cuda")
         owner = torch.full((m * n,), -1, dtype=torch.int32, device="cuda")
-    tp.tp_gemm_fp8(ctx, p, qa, qbt.t(), sa, sb, tp.gemm_config(bm=bm, bn=bn, group_m=group_m),
+    tp.tp_gemm_fp8(ctx, p, qa, qbt.t(), sa, sb, tp.gemm_config(bm=bm, bn=bn, group_m=group_m, split_k=split_k),
                    tp.make_exec(write_counts=counts, write_owner=owner, checked=checked))
     info = tp.tp_partition_query(p)
     tp.tp_partition_destroy(p)
@@ -112,6 +112,25 @@ def test_integer_inputs_exact(ctx, bm, checked):
     assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(exact))
     assert opart.check_counts(counts.cpu().numpy())["ok"]
     assert np.array_equal(owner.cpu().numpy(), opart.gemm_owner_map_cut(m, n, bm, 64, info["num_programs"], 1))
+
+
+@pytest.mark.parametrize("S", [2, 4])
+def test_split_k_integer_inputs_exact(ctx, S):
+    """FP8 split-K (K blocks of 128 codes cut into S slices): exact codes and
+    exact FP32 partial sums, so C is the bf16 rounding of the exact product."""
+    m, n, k = 256, 512, 1024
+    a = synth.tensor(synth.integers(m * k, 5, -7, 7), "bf16").reshape(m, k)
+    bt = synth.tensor(synth.integers(n * k, 6, -7, 7), "bf16").reshape(n, k)
+    a[0, 0], bt[0, 0] = 7, -7
+    c, _, _, sa, sb, counts, _, _ = _fp8_gemm(ctx, a.cuda(), bt.cuda(), bn=256, count=True, split_k=S)
+    assert sa.item() == 64.0 and sb.item() == 64.0
+    assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(ogemm.gemm(a, bt.t())))
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    x = _x(m * k, 13, "bf16").reshape(m, k)
+    y = _x(n * k, 14, "bf16").reshape(n, k)
+    c, _, _, _, _, _, _, _ = _fp8_gemm(ctx, x, y, bn=256, split_k=S)
+    ref_fp8 = ogemm.gemm_fp8(x.cpu(), y.cpu().t())[0]
+    assert ogemm.rel_frobenius(c.cpu(), ref_fp8) <= 5e-3
 
 
 @pytest.mark.parametrize("bm,bn", [(128, 128), (128, 256), (256, 256), (256, 128)])

@@ -26,19 +26,20 @@ def _operands(m, n, k, seed=0, kind="normal"):
 
 
 def _gemm(ctx, a, bt, bn=128, kind=tp.MAP_STRIDED, P=None, group_m=1, stages=0, count=False, bm=128,
-          checked=False, split_k=0):
+          checked=False, split_k=0, cut_limit=0, out=None):
     m, n = a.shape[0], bt.shape[0]
-    c = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
+    c = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16) if out is None else out
     p = tp.tp_partition_create(ctx, c, (bm, bn))
     if kind != tp.MAP_IDENTITY:
         tiles = tp.tp_partition_query(p)["num_tiles"]
         default = ctx.sm_count if bm == 128 else ctx.sm_count // 2
-        tp.tp_partition_map(p, kind, min(P or default, tiles))
+        tp.tp_partition_map(p, kind, tiles if split_k > 1 and P is None else min(P or default, tiles))
     counts = owner = None
     if count:
         counts = torch.zeros(m * n, dtype=torch.int32, device="cuda")
         owner = torch.full((m * n,), -1, dtype=torch.int32, device="cuda")
-    tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=bm, bn=bn, group_m=group_m, stages=stages, split_k=split_k),
+    tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=bm, bn=bn, group_m=group_m, stages=stages, split_k=split_k,
+                                                 cut_limit=cut_limit),
                tp.make_exec(write_counts=counts, write_owner=owner, checked=checked))
     info = tp.tp_partition_query(p)
     tp.tp_partition_destroy(p)
@@ -105,7 +106,7 @@ def test_mapped_partition_coverage(ctx, P, group_m, stages, bm):
     assert ogemm.rel_frobenius(c.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 1e-2
     # without cutting the last round, the owners are exactly the strided map's
     c1, counts1, owner1, info1 = _gemm(ctx, a, bt, bn=128, P=P, group_m=group_m, stages=stages, count=True, bm=bm,
-                                       split_k=1)
+                                       cut_limit=1)
     assert np.array_equal(owner1.cpu().numpy(),
                           opart.gemm_owner_map(m, n, bm, 128, info1["num_programs"], "strided", group_m))
     assert torch.equal(c1, c)
@@ -225,22 +226,131 @@ def test_last_round_cut_along_n(ctx, bm, limit):
     D, S = opart.gemm_cut_schedule(T, P, bn, 64 if bm == 256 else 32, limit or 4)
     assert S >= 2
     a, bt = _operands(m, n, k, seed=3, kind="int")
-    c, counts, owner, info = _gemm(ctx, a, bt, bn=bn, P=P, bm=bm, count=True, split_k=limit)
+    c, counts, owner, info = _gemm(ctx, a, bt, bn=bn, P=P, bm=bm, count=True, cut_limit=limit)
     assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(ogemm.gemm(a.cpu(), bt.cpu().t())))
     assert opart.check_counts(counts.cpu().numpy())["ok"]
     assert np.array_equal(owner.cpu().numpy(), opart.gemm_owner_map_cut(m, n, bm, bn, P, 1, limit or 4))
     a, bt = _operands(m, n, k, seed=4)
-    c1, _, _, _ = _gemm(ctx, a, bt, bn=bn, P=P, bm=bm, split_k=limit)
-    c0, _, _, _ = _gemm(ctx, a, bt, bn=bn, P=P, bm=bm, split_k=1)
+    c1, _, _, _ = _gemm(ctx, a, bt, bn=bn, P=P, bm=bm, cut_limit=limit)
+    c0, _, _, _ = _gemm(ctx, a, bt, bn=bn, P=P, bm=bm, cut_limit=1)
     assert torch.equal(c1, c0)
     assert ogemm.rel_frobenius(c1.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 5e-3
 
 
-def test_split_k_validation(ctx):
+def test_cut_limit_validation(ctx):
     a, bt = _operands(256, 256, 128)
     with pytest.raises(tp.TPError) as e:
-        _gemm(ctx, a, bt, bn=64, P=3, split_k=9)
+        _gemm(ctx, a, bt, bn=64, P=3, cut_limit=9)
     assert e.value.status == tp._lib.ERR_INVALID
+
+
+# ------------------------------------------------------------------ split-K
+@pytest.mark.parametrize("S,bn", [(2, 64), (2, 256), (4, 128), (4, 256), (8, 256)])
+@pytest.mark.parametrize("m,n,k", [(384, 512, 640), (300, 200, 1000), (1, 256, 4104), (129, 96, 520)])
+def test_split_k_parity(ctx, S, bn, m, n, k):
+    """split_k = S: each tile's K blocks are cut into S contiguous slices run
+    by the CTAs of one cluster and summed in slice order. Integer inputs are
+    exact in FP32 whatever the order, so C equals the exactly rounded product;
+    N(0,1) inputs stay within the BF16 gate; two runs are bit-identical."""
+    if (k + 63) // 64 < S:
+        pytest.skip("fewer K blocks than slices")
+    a, bt = _operands(m, n, k, seed=S + bn, kind="int")
+    c, counts, owner, info = _gemm(ctx, a, bt, bn=bn, kind=tp.MAP_IDENTITY, split_k=S, count=True)
+    assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(ogemm.gemm(a.cpu(), bt.cpu().t())))
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    assert np.array_equal(owner.cpu().numpy(), opart.gemm_owner_map(m, n, 128, bn))
+    a, bt = _operands(m, n, k, seed=S + bn + 1)
+    c1, _, _, _ = _gemm(ctx, a, bt, bn=bn, kind=tp.MAP_IDENTITY, split_k=S)
+    c2, _, _, _ = _gemm(ctx, a, bt, bn=bn, kind=tp.MAP_IDENTITY, split_k=S)
+    assert torch.equal(c1, c2)
+    assert ogemm.rel_frobenius(c1.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 5e-3
+
+
+@pytest.mark.parametrize("S", [2, 4])
+def test_split_k_strided_and_checked(ctx, S):
+    """A strided map with one tile per program (P = tiles, band raster) and the
+    checked launch give the same C as the identity map, each element stored
+    once by the program the map names."""
+    m, n, k = 512, 768, 384
+    a, bt = _operands(m, n, k, seed=31 + S)
+    ref, _, _, _ = _gemm(ctx, a, bt, bn=256, kind=tp.MAP_IDENTITY, split_k=S)
+    c, counts, owner, info = _gemm(ctx, a, bt, bn=256, kind=tp.MAP_STRIDED, group_m=2, split_k=S, count=True)
+    assert torch.equal(c, ref)
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    assert np.array_equal(owner.cpu().numpy(),
+                          opart.gemm_owner_map(m, n, 128, 256, info["num_programs"], "strided", 2))
+    chk, counts, _, _ = _gemm(ctx, a, bt, bn=256, kind=tp.MAP_STRIDED, group_m=2, split_k=S, checked=True,
+                              count=True)
+    assert torch.equal(chk, ref)
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    rel, _, _, _ = _gemm(ctx, a, bt, bn=256, kind=tp.MAP_STRIDED, group_m=2, split_k=S, checked=True)
+    assert torch.equal(rel, ref)
+
+
+def test_split_k_in_a_graph(ctx):
+    a, bt = _operands(256, 512, 2048, seed=41)
+    c = torch.zeros(256, 512, device="cuda", dtype=torch.bfloat16)
+    p = tp.tp_partition_create(ctx, c, (128, 256))
+    s = torch.cuda.Stream()
+    g = tp.tp_graph_begin(ctx, s)
+    tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=128, bn=256, split_k=8), tp.make_exec(tp.CAPTURE, s))
+    tp.tp_graph_end(g)
+    for _ in range(3):
+        tp.tp_graph_replay(g, tp.make_exec(stream=s))
+    ref, _, _, _ = _gemm(ctx, a, bt, bn=256, kind=tp.MAP_IDENTITY, split_k=8)
+    assert torch.equal(c, ref)
+    assert ogemm.rel_frobenius(c.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 5e-3
+    tp.tp_graph_destroy(g)
+    tp.tp_partition_destroy(p)
+
+
+@pytest.mark.parametrize("kw,status", [(dict(bm=256, bn=256, split_k=2), "ERR_UNSUPPORTED"),
+                                       (dict(bn=256, split_k=3), "ERR_INVALID"),
+                                       (dict(bn=256, split_k=16), "ERR_INVALID"),
+                                       (dict(bn=64, split_k=4), "ERR_UNSUPPORTED"),      # 64 / 4 < 32 columns
+                                       (dict(bn=256, split_k=8, k=448), "ERR_UNSUPPORTED"),  # 7 K blocks
+                                       (dict(bn=128, split_k=2, P=3), "ERR_UNSUPPORTED")])   # tiles > programs
+def test_split_k_validation(ctx, kw, status):
+    kw = dict(kw)
+    k = kw.pop("k", 512)
+    a, bt = _operands(512, 512, k)
+    with pytest.raises(tp.TPError) as e:
+        _gemm(ctx, a, bt, **kw)
+    assert e.value.status == getattr(tp._lib, status)
+
+
+def test_split_k_resident_programs(ctx):
+    one = tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=128, bn=256))
+    for S in (2, 4, 8):
+        n = tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=128, bn=256, split_k=S))
+        assert 0 < n * S <= one
+
+
+# ------------------------------------------------------- TMA-store epilogue
+@pytest.mark.parametrize("bm", [128, 256])
+@pytest.mark.parametrize("m,n,k", [(129, 72, 200), (300, 200, 136), (1, 32, 8), (130, 1000, 8), (65, 65, 72)])
+def test_epilogue_stays_inside_c(ctx, bm, m, n, k):
+    """C is a view inside a guarded allocation: the epilogue (TMA stores
+    clipped at C's bounds when rows are 16-byte aligned, plain stores
+    otherwise) writes every element of C and nothing around it."""
+    a, bt = _operands(m, n, k, seed=m * 7 + n)
+    guard = 4096
+    buf = torch.full((guard + m * n + guard,), 3.0, device="cuda", dtype=torch.bfloat16)
+    c = buf[guard:guard + m * n].view(m, n)
+    c.fill_(float("nan"))
+    _gemm(ctx, a, bt, bn=64, bm=bm, P=3, out=c)
+    assert torch.all(buf[:guard] == 3.0) and torch.all(buf[guard + m * n:] == 3.0)
+    assert ogemm.rel_frobenius(c.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 1e-2
+
+
+def test_plain_and_staged_epilogues_agree(ctx):
+    """256 x 256 tiles on CTA pairs: a 7-stage ring leaves no room for the
+    staging area (plain stores), the default 6-stage ring stages C for TMA
+    stores; both round the same FP32 sums, so C is bit-identical."""
+    a, bt = _operands(1024, 768, 1024, seed=51)
+    c6, _, _, _ = _gemm(ctx, a, bt, bn=256, bm=256, P=5)
+    c7, _, _, _ = _gemm(ctx, a, bt, bn=256, bm=256, P=5, stages=7)
+    assert torch.equal(c6, c7)
 
 
 @pytest.mark.parametrize("bm,P", [(128, 0), (128, 7), (256, 0), (256, 5)])

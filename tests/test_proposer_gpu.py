@@ -11,6 +11,7 @@ import torch
 
 import paper_2606_15991_gb300 as tp
 import synth
+from oracle import gemm as ogemm
 from oracle import mlp as omlp
 from paper_2606_15991_gb300 import proposer
 
@@ -98,17 +99,20 @@ def test_features_targets_and_save_load(ctx, tmp_path):
 @pytest.mark.parametrize("dtype", ["bf16", "fp8"])
 def test_autotune_table_cache_and_numerics(ctx, dtype, tmp_path):
     space = tp.tp_autotune_space(dtype)
-    assert len(space) == C
+    assert len(space) == 37
+    assert sum(cfg.split_k > 1 for cfg in space) == 5
     M, N, K = 700, 900, 1024
     best, table, best_tf = tp.tp_autotune(ctx, M, N, K, dtype)
-    assert len(table) == C and all(t > 0 for t in table)
+    assert len(table) == len(space) and all(t > 0 for t in table)
     assert best_tf == max(table) or best_tf >= 0.99 * max(table)
     assert tp.tp_autotune_lookup(ctx, M, N, K, dtype).bn == best.bn
     path = os.path.join(tmp_path, "cache.txt")
     tp.tp_autotune_save(ctx, path)
     tp.tp_autotune_load(ctx, path)
-    # every config computes the same C (each element is summed over K in the
-    # same order by one program): a proposal never changes numerics
+    # every config without split-K computes the same C (each element is
+    # summed over K in the same order by one program), so such a proposal
+    # never changes numerics; split-K configs sum K slices in a fixed order
+    # of their own (deterministic, within the BF16 gate)
     if dtype == "bf16":
         a = synth.to_bf16(synth.normal(M * K, 1)).reshape(M, K).cuda()
         bt = synth.to_bf16(synth.normal(N * K, 2)).reshape(N, K).cuda()
@@ -120,7 +124,9 @@ def test_autotune_table_cache_and_numerics(ctx, dtype, tmp_path):
             tp.tp_partition_map(p, tp.MAP_STRIDED, min(tiles, ctx.sm_count * 128 // cfg.bm))
             tp.tp_gemm(ctx, p, a, bt.t(), cfg)
             tp.tp_partition_destroy(p)
-            if ref is None:
+            if cfg.split_k > 1:
+                assert ogemm.rel_frobenius(c.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 5e-3
+            elif ref is None:
                 ref = c
             else:
                 assert torch.equal(c, ref)
