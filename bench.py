@@ -712,9 +712,10 @@ def grouped_row(tp, ctx, dev, stream, peaks):
 
 
 def run_proposer(args):
-    """The learned-proposer experiment: ~20k autotuner measurements (625
-    shapes x 32 configs, BF16 and FP8) for training, 2000 held-out shapes tuned
-    exhaustively for evaluation; prints one JSON line."""
+    """The learned-proposer experiment: ~21k autotuner measurements (625
+    shapes x 37 configs, BF16 and FP8, less the split-K configs a shape's
+    tiles rule out) for training, 2000 held-out shapes tuned exhaustively for
+    evaluation, proposals made by tp_propose; prints one JSON line."""
     import numpy as np
     import torch
 
@@ -738,20 +739,20 @@ def run_proposer(args):
     Xt, Tt, Vt, TFt = proposer.collect(ctx, test_shapes, log=log)
     t_exh = (time.perf_counter() - t0) / len(test_shapes)
     dflt = proposer.default_config(T, V)
-    r = proposer.evaluate(mlp, Xt, TFt, dflt)
     t0 = time.perf_counter()
-    for m, n, k, dt in test_shapes[:200]:
-        tp.tp_propose(ctx, mlp, m, n, k, dt, min_score=-1e9)
-    t_prop = (time.perf_counter() - t0) / min(200, len(test_shapes))
+    prop = proposer.propose_indices(ctx, mlp, test_shapes)
+    t_prop = (time.perf_counter() - t0) / len(test_shapes)
+    r = proposer.evaluate(mlp, Xt, TFt, dflt, prop=prop)
+    r_argmax = proposer.evaluate(mlp, Xt, TFt, dflt)
     big = np.array([m * n * k >= 2 ** 33 for m, n, k, _ in test_shapes])
-    S = proposer.scores(mlp, Xt)
-    reg = 1 - TFt[np.arange(len(TFt)), S.argmax(1)] / TFt.max(1)
+    reg = 1 - TFt[np.arange(len(TFt)), prop] / TFt.max(1)
     reg_d = 1 - TFt[:, dflt] / TFt.max(1)
     space = tp.tp_autotune_space("bf16")
     print(json.dumps({
         "case": "learned tile proposer", "train_shapes": len(train_shapes),
         "train_measurements": int(V.sum()), "test_shapes": len(test_shapes), "configs": int(T.shape[1]),
-        **r, "default_config": {n: getattr(space[dflt], n) for n in ("bm", "bn", "stages", "group_m")},
+        **r, "median_regret_plain_argmax": r_argmax["median_regret"], "mean_regret_plain_argmax": r_argmax["mean_regret"],
+        "default_config": {n: getattr(space[dflt], n) for n in ("bm", "bn", "stages", "group_m", "split_k")},
         "large_shapes": int(big.sum()),
         "large_mean_regret": float(reg[big].mean()) if big.any() else None,
         "large_mean_regret_default": float(reg_d[big].mean()) if big.any() else None,

@@ -507,14 +507,18 @@ tp_status tp_mlp_save(const tp_mlp* mlp, const char* path);
 tp_status tp_mlp_load(tp_mlp* mlp, const char* path);
 /* Proposer features of a shape: [log2 M, log2 N, log2 K, BF16?, FP8?] (host). */
 tp_status tp_mlp_features(int64_t M, int64_t N, int64_t K, int32_t dtype, float* out);
-/* Training targets of one autotuner table: target_i = tflops_i / max tflops,
- * mask_i = 1 where config i ran (tflops_i > 0) (host arrays of `count`). */
+/* Training targets of one autotuner table: target_i = max(tflops_i, 0) /
+ * max tflops and mask_i = 1 (a config that did not run scores 0), or all
+ * masked (0) when no config ran (host arrays of `count`). */
 tp_status tp_mlp_targets(const float* tflops, int32_t count, float* target, float* mask);
 /* Proposes a config for (M, N, K, dtype): the MLP's arg-max over the
- * autotuner's space (ties: lowest index). Falls back to the exhaustive
+ * configs of the autotuner's space that it would try on this shape (split-K
+ * configs only where the tiles x split_k fit two waves of clusters and K has
+ * split_k blocks; ties: lowest index). Falls back to the exhaustive
  * autotuner (cached) when the best score is below min_score or a dimension
- * exceeds 16384 (outside the trained range); *used_fallback tells which. A
- * proposal only selects among configs that compute the same C. */
+ * exceeds 16384 (outside the trained range); *used_fallback tells which.
+ * Configs without split-K compute the same C; split-K configs sum K slices
+ * in an order of their own (bit-reproducible, within the BF16 gate). */
 tp_status tp_propose(tp_ctx* ctx, tp_mlp* mlp, int64_t M, int64_t N, int64_t K, int32_t dtype, float min_score,
                      tp_gemm_config* out, float* score, int32_t* used_fallback);
 

@@ -73,6 +73,21 @@ std::vector<tp_gemm_config> space() {
   return v;
 }
 
+}  // namespace
+
+// Whether config c of the space is tried on an M x N x K problem: a split
+// program holds one tile and needs at least split_k K blocks, and past two
+// waves of clusters it cannot win.
+bool autotune_config_runs(const tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype,
+                          const tp_gemm_config& c) {
+  if (c.split_k <= 1) return true;
+  const int64_t tiles = ((M + c.bm - 1) / c.bm) * ((N + c.bn - 1) / c.bn);
+  const int64_t kblk = dtype == TP_F8E4M3 ? 128 : 64;
+  return (K + kblk - 1) / kblk >= c.split_k && tiles * c.split_k <= 2 * (int64_t)ctx->sm_count;
+}
+
+namespace {
+
 // Fills a workspace with finite values that exercise the tensor cores the
 // way real data does (a hash of the index, small magnitudes).
 __global__ void fill_kernel(uint16_t* p, int64_t n16, int fp8) {
@@ -208,9 +223,8 @@ tp_status tp_autotune(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtyp
     part.kind = TP_MAP_STRIDED;
     part.num_programs = std::min<int64_t>(part.num_tiles, cap);
     float tf = 0.f;
-    // a split program holds one tile; past two waves of clusters it cannot win
-    const bool skip = c.split_k > 1 && part.num_tiles * c.split_k > 2 * (int64_t)ctx->sm_count;
-    if (c.split_k > 1) part.num_programs = part.num_tiles;
+    const bool skip = !autotune_config_runs(ctx, M, N, K, dtype, c);
+    if (c.split_k > 1) part.num_programs = part.num_tiles;  // a split program holds one tile
     tp_status ls = skip ? TP_ERR_UNSUPPORTED : launch_gemm_tc_impl(ctx, &part, &a, &b, &c, &ex, st->stream, esize, one, one);
     if (ls == TP_OK) {
       delay_kernel<<<1, 32, 0, st->stream>>>(20000ull + 30000ull * (uint64_t)r);

@@ -372,10 +372,11 @@ tp_status tp_mlp_targets(const float* tflops, int32_t count, float* target, floa
   if (!tflops || !target || !mask || count < 1) return fail(TP_ERR_INVALID, "null argument or empty table");
   float best = 0.f;
   for (int i = 0; i < count; ++i) best = std::max(best, tflops[i]);
+  // a config that did not run on the shape is its worst proposal: target 0,
+  // still trained (an untrained output could otherwise win the arg-max)
   for (int i = 0; i < count; ++i) {
-    const bool ok = tflops[i] > 0.f && best > 0.f;
-    mask[i] = ok ? 1.f : 0.f;
-    target[i] = ok ? tflops[i] / best : 0.f;
+    mask[i] = best > 0.f ? 1.f : 0.f;
+    target[i] = best > 0.f ? std::max(tflops[i], 0.f) / best : 0.f;
   }
   return TP_OK;
 }
@@ -400,9 +401,11 @@ tp_status tp_propose(tp_ctx* ctx, tp_mlp* n, int64_t M, int64_t N, int64_t K, in
   std::vector<float> y(count);
   e = cudaMemcpy(y.data(), n->y, count * sizeof(float), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "proposer scores");
-  int best = 0;
-  for (int i = 1; i < count; ++i)
-    if (y[i] > y[best]) best = i;  // ties keep the lower index
+  // arg-max over the configs the autotuner would try on this shape (ties
+  // keep the lower index; configs without split-K always qualify)
+  int best = -1;
+  for (int i = 0; i < count; ++i)
+    if (autotune_config_runs(ctx, M, N, K, dtype, cfgs[i]) && (best < 0 || y[i] > y[best])) best = i;
   const bool in_range = M <= 16384 && N <= 16384 && K <= 16384;
   if (score) *score = y[best];
   if (y[best] >= min_score && in_range) {

@@ -6,7 +6,8 @@
    library's forward, backward and Adam kernels), mini-batches drawn in a
    seeded order.
 3. evaluate: on held-out shapes that were tuned exhaustively, the proposal
-   (arg-max of the MLP's scores) is charged its measured TFLOP/s; regret =
+   (tp_propose: the arg-max of the MLP's scores over the configs the
+   autotuner would try on the shape) is charged its measured TFLOP/s; regret =
    1 - TFLOP/s(proposal) / TFLOP/s(best). The method without the MLP is a fixed
    default config (the best on average over the training shapes).
 
@@ -106,11 +107,30 @@ def scores(mlp, X) -> np.ndarray:
     return out.cpu().numpy()
 
 
-def evaluate(mlp, X, TF, default_index: int, min_score: float = 0.0) -> dict:
-    """Regret of the MLP's proposals and of the fixed default config."""
+def config_index(space, cfg) -> int:
+    """Position of a proposed config in the autotuner's space."""
+    key = (cfg.bm, cfg.bn, cfg.stages, cfg.group_m, cfg.split_k)
+    for i, c in enumerate(space):
+        if (c.bm, c.bn, c.stages, c.group_m, c.split_k) == key:
+            return i
+    raise ValueError(f"config {key} is not in the space")
+
+
+def propose_indices(ctx, mlp, shapes) -> np.ndarray:
+    """tp_propose's choice (no fallback) for each (M, N, K, dtype), as space indices."""
+    from . import tp_propose
+    space = tp_autotune_space("bf16")
+    return np.array([config_index(space, tp_propose(ctx, mlp, m, n, k, dt, min_score=-1e9)[0])
+                     for m, n, k, dt in shapes])
+
+
+def evaluate(mlp, X, TF, default_index: int, min_score: float = 0.0, prop=None) -> dict:
+    """Regret of the MLP's proposals (the given space indices, else the plain
+    arg-max of its scores) and of the fixed default config."""
     S = scores(mlp, X)
     best = TF.max(axis=1)
-    prop = S.argmax(axis=1)
+    if prop is None:
+        prop = S.argmax(axis=1)
     reg = 1.0 - TF[np.arange(len(TF)), prop] / best
     reg_def = 1.0 - TF[:, default_index] / best
     fallback = S.max(axis=1) < min_score

@@ -84,8 +84,11 @@ def test_mlp_learns_separable_toy_on_gpu(ctx):
 
 def test_features_targets_and_save_load(ctx, tmp_path):
     assert tp.tp_mlp_features(1024, 3, 16384, "fp8") == pytest.approx(list(omlp.features(1024, 3, 16384, 1)))
+    # a config that did not run (0 TFLOP/s) is trained towards score 0
     tg, mk = tp.tp_mlp_targets([2.0, 0.0, 4.0, 1.0])
-    assert tg == [0.5, 0.0, 1.0, 0.25] and mk == [1.0, 0.0, 1.0, 1.0]
+    assert tg == [0.5, 0.0, 1.0, 0.25] and mk == [1.0, 1.0, 1.0, 1.0]
+    tg, mk = tp.tp_mlp_targets([0.0, 0.0])
+    assert tg == [0.0, 0.0] and mk == [0.0, 0.0]
     p0 = proposer.init_params(F, H, C, seed=9)
     m = tp.tp_mlp_create(ctx, F, H, C, 8, p0)
     path = os.path.join(tmp_path, "mlp.txt")
@@ -149,7 +152,8 @@ def test_small_end_to_end_gain(ctx):
     t_exhaustive = (time.perf_counter() - t0) / len(test_shapes)
     r = proposer.evaluate(mlp, Xt, TFt, proposer.default_config(T, V))
     assert r["median_regret"] <= 0.05
-    untrained = tp.tp_mlp_create(ctx, F, H, C, 256, proposer.init_params(F, H, C, seed=0))
+    NC = len(tp.tp_autotune_space("bf16"))
+    untrained = tp.tp_mlp_create(ctx, F, H, NC, 256, proposer.init_params(F, H, NC, seed=0))
     r0 = proposer.evaluate(untrained, Xt, TFt, 0)
     assert r["mean_regret"] < r0["mean_regret"]
     t0 = time.perf_counter()
@@ -162,3 +166,25 @@ def test_small_end_to_end_gain(ctx):
     assert fb and cfg.bm in (128, 256)
     tp.tp_mlp_destroy(mlp)
     tp.tp_mlp_destroy(untrained)
+
+
+def test_propose_skips_split_configs_that_cannot_run(ctx):
+    """An MLP whose scores favour every split-K config: tp_propose takes one
+    on a shape with few tiles and long K, and never on a shape whose tiles x
+    split_k exceed two waves of clusters (the autotuner would not try it)."""
+    space = tp.tp_autotune_space("bf16")
+    NC = len(space)
+    params = proposer.init_params(F, H, NC, seed=3)
+    b3 = params[-NC:]
+    for i, cfg in enumerate(space):
+        b3[i] = 100.0 + i if cfg.split_k > 1 else 0.0
+    m = tp.tp_mlp_create(ctx, F, H, NC, 8, params)
+    cfg, _, fb = tp.tp_propose(ctx, m, 128, 256, 4096, "bf16", min_score=-1e9)
+    assert not fb and cfg.split_k > 1
+    tiles = -(-128 // cfg.bm) * -(-256 // cfg.bn)
+    assert tiles * cfg.split_k <= 2 * ctx.sm_count
+    cfg, _, fb = tp.tp_propose(ctx, m, 8192, 8192, 8192, "bf16", min_score=-1e9)
+    assert not fb and cfg.split_k <= 1
+    cfg, _, fb = tp.tp_propose(ctx, m, 128, 256, 64, "bf16", min_score=-1e9)    # one K block
+    assert not fb and cfg.split_k <= 1
+    tp.tp_mlp_destroy(m)
