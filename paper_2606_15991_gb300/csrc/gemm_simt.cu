@@ -35,10 +35,19 @@ __device__ __forceinline__ void raster(int64_t s, int64_t gm, int64_t gn, int64_
   *tn = r / rows;
 }
 
+// Each of the 256 threads owns a 4 x 4 block of the tile: rows 4*ty..4*ty+3
+// and columns 4*tx..4*tx+3 (ty = tid / 16, tx = tid % 16). Shared memory
+// holds the A slice K-major (As[k][m]) and the B slice as stored (Bs[k][n]),
+// rows padded by 4 floats, so one 16-byte load gives a thread its 4 A or 4 B
+// values of a k step. The next K slice is loaded into registers while the
+// current one is multiplied (register-staged double buffering), so the
+// global-memory latency overlaps the FFMAs.
 template <int BK, bool COUNT>
-__global__ void __launch_bounds__(TH) gemm_f32_kernel(const __grid_constant__ SimtArgs p) {
-  __shared__ float As[2][BK][BM + 4];
-  __shared__ float Bs[2][BK][BN + 4];
+__global__ void __launch_bounds__(TH, 1) gemm_f32_kernel(const __grid_constant__ SimtArgs p) {
+  constexpr int PA = BM * BK / TH;  // A elements per thread per K slice
+  constexpr int PB = BK * BN / TH;
+  __shared__ __align__(16) float As[2][BK][BM + 4];
+  __shared__ __align__(16) float Bs[2][BK][BN + 4];
   __shared__ int64_t slot;
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
@@ -55,51 +64,78 @@ __global__ void __launch_bounds__(TH) gemm_f32_kernel(const __grid_constant__ Si
     const int64_t m0 = tm * BM, n0 = tn * BN;
     float acc[4][4] = {};
     const int64_t nk = (p.K + BK - 1) / BK;
-    auto load = [&](int buf, int64_t k0) {
-      for (int i = tid; i < BM * BK; i += TH) {
-        const int r = i / BK, kk = i % BK;
-        const int64_t gm_ = m0 + r, gk = k0 + kk;
-        As[buf][kk][r] = (gm_ < p.M && gk < p.K) ? p.a[gm_ * p.sam + gk * p.sak] : 0.f;
+    float ra[PA], rb[PB];
+    // element e of this thread's share: A (row e*TH/BK + tid/BK, k tid%BK),
+    // B (k e*TH/BN + tid/BN, column tid%BN): consecutive threads read
+    // consecutive k of A and consecutive n of B
+    auto fetch = [&](int64_t k0) {
+#pragma unroll
+      for (int e = 0; e < PA; ++e) {
+        const int i = e * TH + tid;
+        const int64_t gm_ = m0 + i / BK, gk = k0 + i % BK;
+        ra[e] = (gm_ < p.M && gk < p.K) ? p.a[gm_ * p.sam + gk * p.sak] : 0.f;
       }
-      for (int i = tid; i < BK * BN; i += TH) {
-        const int kk = i / BN, c = i % BN;
-        const int64_t gk = k0 + kk, gn_ = n0 + c;
-        Bs[buf][kk][c] = (gk < p.K && gn_ < p.N) ? p.b[gk * p.sbk + gn_ * p.sbn] : 0.f;
+#pragma unroll
+      for (int e = 0; e < PB; ++e) {
+        const int i = e * TH + tid;
+        const int64_t gk = k0 + i / BN, gn_ = n0 + i % BN;
+        rb[e] = (gk < p.K && gn_ < p.N) ? p.b[gk * p.sbk + gn_ * p.sbn] : 0.f;
       }
     };
-    if (nk > 0) load(0, 0);
+    auto stash = [&](int buf) {
+#pragma unroll
+      for (int e = 0; e < PA; ++e) {
+        const int i = e * TH + tid;
+        As[buf][i % BK][i / BK] = ra[e];
+      }
+#pragma unroll
+      for (int e = 0; e < PB; ++e) {
+        const int i = e * TH + tid;
+        Bs[buf][i / BN][i % BN] = rb[e];
+      }
+    };
+    if (nk > 0) {
+      fetch(0);
+      stash(0);
+    }
     __syncthreads();
     for (int64_t kt = 0; kt < nk; ++kt) {
       const int buf = kt & 1;
-      if (kt + 1 < nk) load(buf ^ 1, (kt + 1) * BK);
+      if (kt + 1 < nk) fetch((kt + 1) * BK);
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        float av[4], bv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) av[i] = As[buf][kk][ty + 16 * i];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) bv[j] = Bs[buf][kk][tx + 16 * j];
+        const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * ty]);
+        const float4 b4 = *reinterpret_cast<const float4*>(&Bs[buf][kk][4 * tx]);
+        const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+        const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
           for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
       }
+      if (kt + 1 < nk) stash(buf ^ 1);  // the other buffer's readers passed the barrier below last step
       __syncthreads();
     }
+    const bool vec = (p.N % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.c) & 15) == 0);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int64_t r = m0 + ty + 16 * i;
+      const int64_t r = m0 + 4 * ty + i;
       if (r >= p.M) continue;
+      const int64_t c0 = n0 + 4 * tx;
+      if (vec && c0 + 4 <= p.N) {
+        *reinterpret_cast<float4*>(p.c + r * p.N + c0) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int64_t c = n0 + tx + 16 * j;
-        if (c < p.N) {
-          p.c[r * p.N + c] = acc[i][j];
-          if constexpr (COUNT) {
-            atomicAdd(p.counts + r * p.N + c, 1u);
-            p.owner[r * p.N + c] = (int32_t)blockIdx.x;
+        for (int j = 0; j < 4; ++j)
+          if (c0 + j < p.N) p.c[r * p.N + c0 + j] = acc[i][j];
+      }
+      if constexpr (COUNT) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (c0 + j < p.N) {
+            atomicAdd(p.counts + r * p.N + c0 + j, 1u);
+            p.owner[r * p.N + c0 + j] = (int32_t)blockIdx.x;
           }
-        }
       }
     }
     if (p.kind == TP_MAP_IDENTITY) break;
@@ -152,7 +188,7 @@ tp_status launch_gemm_simt(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, con
   p.owner = ex->write_owner;
   if (p.M == 0 || p.N == 0) return TP_OK;
   const int64_t grid = c->kind == TP_MAP_IDENTITY ? c->num_tiles : c->num_programs;
-  const int bk = (cfg && cfg->bk > 0) ? cfg->bk : 16;
+  const int bk = (cfg && cfg->bk > 0) ? cfg->bk : 32;  // 32: fewest barriers per K (fastest at 512^3)
   const bool count = p.counts != nullptr;
   cudaError_t e;
   switch (bk) {
