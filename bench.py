@@ -520,9 +520,12 @@ def secondary_rows(tp, ctx, dev, stream, peaks):
     b = torch.from_numpy(synth.uniform(512 * 512, seed=1)).reshape(512, 512).to(dev)
     c = torch.empty(512, 512, device=dev)
     p = tp.tp_partition_create(ctx, c, (64, 64))
-    ms = _graph_time(tp, ctx, stream, lambda ex: tp.tp_gemm(ctx, p, a, b, None, ex), reps=50)
+    f32cfg = tp.gemm_config(bk=32, split_k=2)
+    ms = _graph_time(tp, ctx, stream, lambda ex: tp.tp_gemm(ctx, p, a, b, f32cfg, ex), reps=50)
     rows["gemm_f32_512"] = {"tflops": 2 * 512 ** 3 / (ms * 1e-3) / 1e12, "ms": ms, "programs": 64,
-                            "note": "64 tile programs on 152 SMs: latency-bound FFMA"}
+                            "split_k": 2, "bk": 32,
+                            "note": "64 tile programs, each a cluster of 2 CTAs splitting K (128 of 152 SMs): "
+                                    "latency-bound FFMA"}
     tp.tp_partition_destroy(p)
     del a, b, c
 

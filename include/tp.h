@@ -170,7 +170,10 @@ typedef struct tp_gemm_config {
                         * one writer and C is bit-reproducible (its rounding
                         * differs from split_k = 1). Needs at most one tile
                         * per program (an identity map, or a strided map with
-                        * num_programs >= tiles). SIMT GEMM: ignored.         */
+                        * num_programs >= tiles). FP32 SIMT GEMM: 0, 1, 2
+                        * or 4 CTAs per 64 x 64 tile program (not with a
+                        * queue map); CTA r stores rows [r*64/S, +64/S) of
+                        * the tile after adding the S partials in order.     */
   int32_t cut_limit;   /* tensor-core GEMM on a strided map with T tiles and P
                         * programs (split_k <= 1): each of the R = T mod P
                         * tiles of the last, partial round may be cut along N

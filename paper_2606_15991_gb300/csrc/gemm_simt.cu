@@ -3,6 +3,7 @@
 // launch one program per tile; mapped partitions launch persistent programs
 // that walk their tiles (strided slots or a device queue), slots being turned
 // into tiles by the band raster shared with the tensor-core GEMM.
+#include "sm100_ptx.cuh"
 #include "tp_internal.h"
 
 namespace tp {
@@ -18,6 +19,7 @@ struct SimtArgs {
   int64_t sam, sak, sbk, sbn;  // element strides of A (m, k) and B (k, n)
   int64_t gm, gn;              // tile grid
   int32_t kind, group_m;
+  int32_t split;               // K slices per tile (cluster size); 1 = none
   unsigned* queue;
   uint32_t* counts;
   int32_t* owner;
@@ -42,17 +44,30 @@ __device__ __forceinline__ void raster(int64_t s, int64_t gm, int64_t gn, int64_
 // values of a k step. The next K slice is loaded into registers while the
 // current one is multiplied (register-staged double buffering), so the
 // global-memory latency overlaps the FFMAs.
+// With split = S > 1 a tile program is a cluster of S CTAs: CTA r runs the
+// K slices [r*nk/S, (r+1)*nk/S) and keeps its partial 64 x 64 block in
+// shared memory; after a cluster barrier CTA r adds, for rows
+// [r*64/S, (r+1)*64/S), the S partials in slice order 0..S-1 (reading the
+// others through distributed shared memory) and stores them, so every
+// element still has one writer and C is bit-reproducible.
 template <int BK, bool COUNT>
 __global__ void __launch_bounds__(TH, 1) gemm_f32_kernel(const __grid_constant__ SimtArgs p) {
   constexpr int PA = BM * BK / TH;  // A elements per thread per K slice
   constexpr int PB = BK * BN / TH;
-  __shared__ __align__(16) float As[2][BK][BM + 4];
-  __shared__ __align__(16) float Bs[2][BK][BN + 4];
+  // the operand buffers; a split program's partial block overlays them once
+  // its K loop has ended
+  constexpr int kAB = 2 * BK * (BM + 4) + 2 * BK * (BN + 4);
+  __shared__ __align__(16) float raw[kAB > BM * BN ? kAB : BM * BN];
+  auto As = reinterpret_cast<float(*)[BK][BM + 4]>(raw);
+  auto Bs = reinterpret_cast<float(*)[BK][BN + 4]>(raw + 2 * BK * (BM + 4));
+  auto Ps = reinterpret_cast<float(*)[BN]>(raw);
   __shared__ int64_t slot;
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int64_t T = p.gm * p.gn;
-  int64_t s = blockIdx.x;
+  const int S = p.split;
+  const uint32_t r = S > 1 ? sm100::cluster_ctarank() : 0u;
+  int64_t s = S > 1 ? (int64_t)(blockIdx.x / S) : (int64_t)blockIdx.x;
   if (p.kind == TP_MAP_QUEUE) {
     if (tid == 0) slot = atomicAdd(p.queue, 1u);
     __syncthreads();
@@ -63,7 +78,9 @@ __global__ void __launch_bounds__(TH, 1) gemm_f32_kernel(const __grid_constant__
     raster(s, p.gm, p.gn, p.group_m, &tm, &tn);
     const int64_t m0 = tm * BM, n0 = tn * BN;
     float acc[4][4] = {};
-    const int64_t nk = (p.K + BK - 1) / BK;
+    const int64_t nk_all = (p.K + BK - 1) / BK;
+    const int64_t kt0 = (int64_t)r * nk_all / S, kt1 = (int64_t)(r + 1) * nk_all / S;
+    const int64_t nk = kt1 - kt0;
     float ra[PA], rb[PB];
     // element e of this thread's share: A (row e*TH/BK + tid/BK, k tid%BK),
     // B (k e*TH/BN + tid/BN, column tid%BN): consecutive threads read
@@ -95,13 +112,13 @@ __global__ void __launch_bounds__(TH, 1) gemm_f32_kernel(const __grid_constant__
       }
     };
     if (nk > 0) {
-      fetch(0);
+      fetch(kt0 * BK);
       stash(0);
     }
     __syncthreads();
     for (int64_t kt = 0; kt < nk; ++kt) {
       const int buf = kt & 1;
-      if (kt + 1 < nk) fetch((kt + 1) * BK);
+      if (kt + 1 < nk) fetch((kt0 + kt + 1) * BK);
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
         const float4 a4 = *reinterpret_cast<const float4*>(&As[buf][kk][4 * ty]);
@@ -116,9 +133,43 @@ __global__ void __launch_bounds__(TH, 1) gemm_f32_kernel(const __grid_constant__
       if (kt + 1 < nk) stash(buf ^ 1);  // the other buffer's readers passed the barrier below last step
       __syncthreads();
     }
+    bool mine = true;  // this thread's rows are stored by this CTA
+    if (S > 1) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        *reinterpret_cast<float4*>(&Ps[4 * ty + i][4 * tx]) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      sm100::cluster_sync();  // every CTA's partial is in its shared memory
+      mine = (4 * ty) / (BM / S) == (int)r;
+      if (mine) {
+        float sum[4][4];
+        for (int src = 0; src < S; ++src) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            float4 v;
+            if (src == (int)r) {
+              v = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            } else {
+              const uint32_t at = sm100::mapa(sm100::smem_u32(&Ps[4 * ty + i][4 * tx]), (uint32_t)src);
+              asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                           : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                           : "r"(at)
+                           : "memory");
+            }
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sum[i][j] = src == 0 ? vv[j] : sum[i][j] + vv[j];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = sum[i][j];
+      }
+      sm100::cluster_sync();  // the peers' reads of this CTA's partial are done
+    }
     const bool vec = (p.N % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.c) & 15) == 0);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 4 && mine; ++i) {
       const int64_t r = m0 + 4 * ty + i;
       if (r >= p.M) continue;
       const int64_t c0 = n0 + 4 * tx;
@@ -134,13 +185,13 @@ __global__ void __launch_bounds__(TH, 1) gemm_f32_kernel(const __grid_constant__
         for (int j = 0; j < 4; ++j)
           if (c0 + j < p.N) {
             atomicAdd(p.counts + r * p.N + c0 + j, 1u);
-            p.owner[r * p.N + c0 + j] = (int32_t)blockIdx.x;
+            p.owner[r * p.N + c0 + j] = (int32_t)(blockIdx.x / S);
           }
       }
     }
     if (p.kind == TP_MAP_IDENTITY) break;
     if (p.kind == TP_MAP_STRIDED) {
-      s += gridDim.x;
+      s += gridDim.x / S;
     } else {
       __syncthreads();
       if (tid == 0) slot = atomicAdd(p.queue, 1u);
@@ -152,9 +203,19 @@ __global__ void __launch_bounds__(TH, 1) gemm_f32_kernel(const __grid_constant__
 
 template <int BK>
 cudaError_t launch_bk(const SimtArgs& p, bool count, int64_t grid, cudaStream_t st) {
-  if (count) gemm_f32_kernel<BK, true><<<(unsigned)grid, TH, 0, st>>>(p);
-  else gemm_f32_kernel<BK, false><<<(unsigned)grid, TH, 0, st>>>(p);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(grid * p.split));
+  cfg.blockDim = dim3(TH);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)p.split;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return count ? cudaLaunchKernelEx(&cfg, gemm_f32_kernel<BK, true>, p)
+               : cudaLaunchKernelEx(&cfg, gemm_f32_kernel<BK, false>, p);
 }
 
 }  // namespace
@@ -189,6 +250,11 @@ tp_status launch_gemm_simt(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, con
   if (p.M == 0 || p.N == 0) return TP_OK;
   const int64_t grid = c->kind == TP_MAP_IDENTITY ? c->num_tiles : c->num_programs;
   const int bk = (cfg && cfg->bk > 0) ? cfg->bk : 32;  // 32: fewest barriers per K (fastest at 512^3)
+  p.split = (cfg && cfg->split_k > 1) ? cfg->split_k : 1;
+  if (cfg && (cfg->split_k < 0 || cfg->split_k > 4 || (p.split & (p.split - 1))))
+    return fail(TP_ERR_INVALID, "FP32 GEMM split_k must be 0, 1, 2 or 4");
+  if (p.split > 1 && c->kind == TP_MAP_QUEUE)
+    return fail(TP_ERR_UNSUPPORTED, "FP32 GEMM split_k with a queue map (each CTA would dequeue its own tile)");
   const bool count = p.counts != nullptr;
   cudaError_t e;
   switch (bk) {

@@ -12,7 +12,7 @@ from oracle import partition as opart
 pytestmark = pytest.mark.gpu
 
 
-def _gemm(ctx, a, b, kind=tp.MAP_IDENTITY, P=0, group_m=1, count=False, bk=16):
+def _gemm(ctx, a, b, kind=tp.MAP_IDENTITY, P=0, group_m=1, count=False, bk=16, split_k=0):
     M, N = a.shape[0], b.shape[1]
     c = torch.full((M, N), float("nan"), device="cuda")
     p = tp.tp_partition_create(ctx, c, (64, 64))
@@ -22,7 +22,7 @@ def _gemm(ctx, a, b, kind=tp.MAP_IDENTITY, P=0, group_m=1, count=False, bk=16):
     if count:
         counts = torch.zeros(M * N, dtype=torch.int32, device="cuda")
         owner = torch.full((M * N,), -1, dtype=torch.int32, device="cuda")
-    tp.tp_gemm(ctx, p, a, b, tp.gemm_config(group_m=group_m, bk=bk),
+    tp.tp_gemm(ctx, p, a, b, tp.gemm_config(group_m=group_m, bk=bk, split_k=split_k),
                tp.make_exec(write_counts=counts, write_owner=owner))
     tp.tp_partition_destroy(p)
     return c, counts, owner
@@ -112,3 +112,43 @@ def test_gemm_shape_errors(ctx):
         tp.tp_gemm(ctx, p, torch.zeros(64, 64, device="cuda"), torch.zeros(64, 64, device="cuda"))
     assert e.value.status == tp._lib.ERR_UNSUPPORTED
     tp.tp_partition_destroy(p)
+
+
+@pytest.mark.parametrize("S", [2, 4])
+@pytest.mark.parametrize("bk", [8, 32])
+def test_split_k_programs(ctx, S, bk):
+    """split_k = S: each 64 x 64 tile program is a cluster of S CTAs that run
+    contiguous K slices; CTA r adds the S partials of rows [r*64/S, +64/S)
+    in slice order and stores them. Integer inputs are exact in FP32 in any
+    order; U[-1,1] inputs stay within 1e-5; every element is stored once, by
+    the program that owns its tile; two runs are bit-identical."""
+    a = torch.from_numpy(synth.integers(512 * 512, seed=13, lo=-4, hi=4)).reshape(512, 512).cuda()
+    b = torch.from_numpy(synth.integers(512 * 512, seed=14, lo=-4, hi=4)).reshape(512, 512).cuda()
+    c, counts, owner = _gemm(ctx, a, b, bk=bk, split_k=S, count=True)
+    assert np.array_equal(c.cpu().double().numpy(), ogemm.gemm(a.cpu(), b.cpu()))
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    assert np.array_equal(owner.cpu().numpy(), opart.gemm_owner_map(512, 512, 64, 64))
+    a = torch.from_numpy(synth.uniform(300 * 700, seed=15)).reshape(300, 700).cuda()
+    b = torch.from_numpy(synth.uniform(700 * 260, seed=16)).reshape(700, 260).cuda()
+    c1, _, _ = _gemm(ctx, a, b, bk=bk, split_k=S)
+    c2, counts, owner = _gemm(ctx, a, b, tp.MAP_STRIDED, 7, 2, bk=bk, split_k=S, count=True)
+    assert torch.equal(c1, c2)
+    assert ogemm.rel_frobenius(c1.cpu(), ogemm.gemm(a.cpu(), b.cpu())) <= 1e-5
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    assert np.array_equal(owner.cpu().numpy(), opart.gemm_owner_map(300, 260, 64, 64, 7, "strided", 2))
+
+
+def test_split_k_validation(ctx):
+    a = torch.ones(128, 64, device="cuda")
+    b = torch.ones(64, 128, device="cuda")
+    with pytest.raises(tp.TPError) as e:
+        _gemm(ctx, a, b, split_k=3)
+    assert e.value.status == tp._lib.ERR_INVALID
+    with pytest.raises(tp.TPError) as e:
+        _gemm(ctx, a, b, split_k=8)
+    assert e.value.status == tp._lib.ERR_INVALID
+    with pytest.raises(tp.TPError) as e:
+        _gemm(ctx, a, b, tp.MAP_QUEUE, 2, split_k=2)
+    assert e.value.status == tp._lib.ERR_UNSUPPORTED
+    c, _, _ = _gemm(ctx, a[:, :1], b[:1], split_k=4)     # one K slice: three CTAs add zero partials
+    assert torch.equal(c, torch.ones(128, 128, device="cuda"))
