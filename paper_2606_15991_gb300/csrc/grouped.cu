@@ -32,6 +32,7 @@ namespace tp {
 struct alignas(64) GroupedProblem {
   CUtensorMap map_x;      // MMA A operand: A_i (normal) or B_i stored N x K (swap), box 128 rows
   CUtensorMap map_y;      // MMA B operand: B_i (normal, box 256 rows) or A_i (swap, box bn rows)
+  CUtensorMap map_c;      // C_i as 32 x 32 boxes (64-byte swizzle) for the epilogue's TMA stores
   __nv_bfloat16* c;
   int64_t M, N, K;
   int64_t tiles_r, tiles_c;  // tile grid in MMA orientation (rows of 128, columns of bn)
@@ -39,6 +40,7 @@ struct alignas(64) GroupedProblem {
   int32_t swap, bn;       // bn = MMA N of every tile of this problem
   int32_t tile_rows;      // 128 (one CTA) or 256 (CTA pair), MMA orientation
   int32_t box_y;          // rows of the MMA B operand each CTA loads per stage
+  int32_t c_tma;          // 1: normal orientation with 16-byte aligned C rows (map_c is valid)
 };
 
 }  // namespace tp
@@ -72,6 +74,7 @@ template <bool kPair> struct Ring {
   static constexpr int kStages = kPair ? 6 : 4;
 };
 constexpr size_t kWordsBytes = 8 + 8 * kRing;
+constexpr uint32_t kStageC = 4u * 2u * 2048u;  // epilogue staging: 4 warps x 2 buffers x (32 rows x 64 B)
 
 struct GroupedArgs {
   const GroupedProblem* probs;
@@ -102,7 +105,8 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
 
   const uint32_t x0 = base;
   const uint32_t y0 = x0 + kStageX * kStages;
-  const uint32_t bars = y0 + kStageY * kStages;
+  const uint32_t cst = y0 + kStageY * kStages;  // epilogue staging
+  const uint32_t bars = cst + kStageC;
   auto full_bar = [&](int s) { return bars + 8u * s; };
   auto empty_bar = [&](int s) { return bars + 64u + 8u * s; };
   auto tfull_bar = [&](int b) { return bars + 128u + 8u * b; };
@@ -280,6 +284,8 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
   } else {
     const int quad = warp & 3;
     const int lane_row = (int)rank * 128 + quad * 32 + lane;  // tile row (MMA orientation) of this TMEM lane
+    const uint32_t stg = cst + (uint32_t)quad * 4096u;       // this warp's two 2 KB staging buffers
+    uint32_t nstaged = 0;
     for (int64_t j = 0;; ++j) {
       const int r = (int)(j % kRing);
       const bool got = ring_wait(rfull_bar(r), (uint32_t)((j / kRing) & 1));
@@ -303,7 +309,33 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
         tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * 256 + ch * 32), v);
         tmem_ld_wait();
         const int64_t c0 = tc * pr->bn + ch * 32;  // first column of the chunk (MMA orientation)
-        if (!pr->swap) {
+        if (!kCount && pr->c_tma) {
+          // the warp's 32 x 32 block: staged (16-byte piece u of row `lane`
+          // at piece u ^ ((lane >> 1) & 3)) and written by one TMA store,
+          // clipped to C_i's bounds by its tensor map
+          const int64_t row0 = rr - lane;
+          if (row0 >= M || c0 >= N) continue;  // warp-uniform
+          const uint32_t buf = stg + (nstaged & 1u) * 2048u;
+          if (lane == 0) bulk_wait_read<1>();  // the store issued from this buffer two blocks ago has read it
+          __syncwarp();
+          uint32_t w[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+            w[i] = *reinterpret_cast<uint32_t*>(&h);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            st_shared_v4(buf + (uint32_t)lane * 64u + ((uint32_t)(u ^ ((lane >> 1) & 3)) << 4), w[4 * u],
+                         w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
+          fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) {
+            tma_store_2d(&pr->map_c, buf, (int32_t)c0, (int32_t)row0);
+            bulk_commit();
+          }
+          ++nstaged;
+        } else if (!pr->swap) {
           if (rr >= M || c0 >= N) continue;
           __nv_bfloat16* crow = pr->c + rr * N;
           if ((N & 7) == 0 && c0 + 32 <= N) {
@@ -350,6 +382,8 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
         else mbar_arrive(tempty_bar(acc));
       }
     }
+    if (lane == 0) bulk_wait_all();  // C written before the CTA retires
+    __syncwarp();
   }
   tc_fence_before();
   if constexpr (kPair) cluster_sync();  // the peer no longer touches our shared memory / TMEM
@@ -371,6 +405,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encode() {
       fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
   }
   return fn;
+}
+
+// C_i (bf16, N columns, row stride N) as 32 x 32 boxes with the 64-byte
+// swizzle of the epilogue's staging layout.
+tp_status c_map(CUtensorMap* map, void* ptr, int64_t M, int64_t N) {
+  auto fn = encode();
+  if (!fn) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+  cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
+  cuuint64_t strides[1] = {(cuuint64_t)(N * 2)};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled (C) failed (" + std::to_string((int)r) + ")");
+  return TP_OK;
 }
 
 tp_status kmajor_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t k, int64_t ld, int box_rows) {
@@ -462,6 +511,10 @@ tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int3
       g.tiles_c = (N + 255) / 256;
       s = kmajor_map(&g.map_x, a.ptr, M, K, lda, 128);
       if (s == TP_OK) s = kmajor_map(&g.map_y, b.ptr, N, K, ldb, g.box_y);
+      if (s == TP_OK && N % 8 == 0 && ((uintptr_t)c.ptr & 15) == 0) {
+        s = c_map(&g.map_c, c.ptr, M, N);
+        g.c_tma = 1;
+      }
       tile_rows = trows;
       tile_cols = 256;
       cost[i] = 2.0 * trows * 256 * (double)K / (plan->pair ? 2.4e13 : 1.2e13);
@@ -614,10 +667,10 @@ tp_status tp_grouped_gemm(tp_ctx* ctx, tp_grouped_plan* plan, int32_t num_progra
     return cudaLaunchKernelEx(&lc, kernel, a);
   };
   if (pair) {
-    smem = 1024 + (kStageX + Ring<true>::kStageY) * Ring<true>::kStages + 232 + kWordsBytes;
+    smem = 1024 + (kStageX + Ring<true>::kStageY) * Ring<true>::kStages + kStageC + 232 + kWordsBytes;
     e = a.counts ? launch(grouped_kernel<true, true>, smem, 2) : launch(grouped_kernel<true, false>, smem, 2);
   } else {
-    smem = 1024 + (kStageX + Ring<false>::kStageY) * Ring<false>::kStages + 232 + kWordsBytes;
+    smem = 1024 + (kStageX + Ring<false>::kStageY) * Ring<false>::kStages + kStageC + 232 + kWordsBytes;
     e = a.counts ? launch(grouped_kernel<false, true>, smem, 1) : launch(grouped_kernel<false, false>, smem, 1);
   }
   return o.end(e);
