@@ -201,8 +201,11 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int32_t TS = p.total_slots;
   const int32_t step = p.kind == TP_MAP_IDENTITY ? p.gm * p.gn : nprog;
-  const int32_t kb0 = (int32_t)(((int64_t)kslice * p.nk) / S);
-  const int32_t kb1 = (int32_t)(((int64_t)(kslice + 1) * p.nk) / S);
+  // S is a power of two and kslice * nk < 2^31 (nk < 2^25), so the slice
+  // bounds are shifts rather than 64-bit divisions (hundreds of cycles)
+  const int lgS = __ffs(S) - 1;
+  const int32_t kb0 = ((int32_t)kslice * p.nk) >> lgS;
+  const int32_t kb1 = ((int32_t)(kslice + 1) * p.nk) >> lgS;
   // split programs: the tile this CTA accumulated and whether its partial sum is complete
   int32_t sp_tm = 0, sp_tn = 0;
   bool sp_have = false;
@@ -722,7 +725,7 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   if (K == 0) return fail(TP_ERR_UNSUPPORTED, "K = 0");
   const int64_t T = c->num_tiles;
   // slots (tiles, or narrow tiles: up to 8 per tile) are counted in 32 bits
-  if (T >= ((int64_t)1 << 28) || M >= ((int64_t)1 << 31) || N >= ((int64_t)1 << 31))
+  if (T >= ((int64_t)1 << 28) || M >= ((int64_t)1 << 31) || N >= ((int64_t)1 << 31) || K >= ((int64_t)1 << 31))
     return fail(TP_ERR_UNSUPPORTED, "tensor-core GEMM: 2^28 tiles or more, or an extent of 2^31");
   const int64_t progs = c->kind == TP_MAP_IDENTITY ? T : c->num_programs;
   const int kblk = 128 / esize;
