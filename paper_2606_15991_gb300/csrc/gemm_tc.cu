@@ -18,10 +18,11 @@
 //            accumulators and commits each consumed stage back to the producer;
 //   warps 2-5 epilogue: tcgen05.ld the finished accumulator (each warp owns the
 //            32 TMEM lanes = tile rows its warp index selects), scale, round to
-//            bf16 and store only inside this program's tile (32 x 32 blocks
-//            staged in shared memory and written by TMA stores, or per-row
-//            stores when C rows are not 16-byte aligned), while the MMA warp
-//            already fills the other accumulator.
+//            bf16 and store only inside this program's tile (32 x 64 blocks,
+//            or 32 x 32 for an odd last chunk, staged in shared memory and
+//            written by TMA stores, or per-row stores when C rows are not
+//            16-byte aligned), while the MMA warp already fills the other
+//            accumulator.
 // Every mbarrier wait is bounded; on timeout the kernel records an error,
 // drains its in-flight copies and MMAs, frees TMEM and returns. The checked
 // build (TP_EXEC_CHECKED) validates and claims every tile before storing it;
@@ -45,7 +46,7 @@ using namespace sm100;
 constexpr int BM = 128;
 constexpr int kThreads = 192;
 constexpr int kMaxStages = 8;
-constexpr uint32_t kStageC = 4u * 2u * 2048u;  // epilogue staging: 4 warps x 2 buffers x (32 rows x 64 B)
+constexpr uint32_t kStageC = 4u * 2u * 4096u;  // epilogue staging: 4 warps x 2 buffers x (32 rows x 128 B)
 
 struct TcArgs {
   int64_t M, N, K;
@@ -123,7 +124,7 @@ template <bool kF8, bool kPair, bool kCount, bool kChecked>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                    const __grid_constant__ CUtensorMap map_b_cut, const __grid_constant__ CUtensorMap map_c,
-                   const __grid_constant__ TcArgs p) {
+                   const __grid_constant__ CUtensorMap map_c64, const __grid_constant__ TcArgs p) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
@@ -178,7 +179,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     tma_prefetch_desc(&map_a);
     tma_prefetch_desc(&map_b);
     if (p.ncut > 1) tma_prefetch_desc(&map_b_cut);
-    if (p.stage_c) tma_prefetch_desc(&map_c);
+    if (p.stage_c) {
+      tma_prefetch_desc(&map_c);
+      tma_prefetch_desc(&map_c64);
+    }
   }
   if (warp == 1) {
     if constexpr (kPair) {
@@ -310,8 +314,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   const uint32_t tlane = (uint32_t)(quad * 32) << 16;         // TMEM lane offset of this warp
   // FP8 dequantisation factor 1 / (s_A * s_B), both steps in fp32
   const float scale = (p.scale_a && p.scale_b) ? 1.f / (*p.scale_a * *p.scale_b) : 1.f;
-  // this warp's two staging buffers of 32 rows x 64 bytes (64-byte swizzle)
-  const uint32_t stg = cst + (uint32_t)quad * 4096u;
+  // this warp's two 4 KB staging buffers: 32 rows x 128 bytes (128-byte
+  // swizzle) for a 64-column block, or 32 rows x 64 bytes (64-byte swizzle)
+  // for a 32-column block
+  const uint32_t stg = cst + (uint32_t)quad * 8192u;
   uint32_t nstaged = 0;
   // one row's 32 columns [c0, c0 + 32) of C from FP32 values f (plain stores)
   auto store_chunk = [&](const float* f, int64_t row, int64_t c0) {
@@ -344,8 +350,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto store_block = [&](const float* f, int64_t row0, int64_t c0) {
     if (!kCount && p.stage_c) {
       if (row0 >= p.M || c0 >= p.N) return;  // warp-uniform: the block lies outside C
-      const uint32_t buf = stg + (nstaged & 1u) * 2048u;
-      if (lane == 0) bulk_wait_read<1>();  // the store issued from this buffer two blocks ago has read it
+      const uint32_t buf = stg + (nstaged & 1u) * 4096u;
+      if (lane == 0 && nstaged >= 2) bulk_wait_read<1>();  // the store issued from this buffer two blocks ago has read it
       __syncwarp();
       uint32_t w[16];
 #pragma unroll
@@ -368,6 +374,34 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
       store_chunk(f, row0 + lane, c0);
     }
+  };
+  // the 32 x 64 block at rows [row0, +32), columns [c0, +64) from two TMEM
+  // chunks (lane i holds row row0 + i): staged with 16-byte piece u of row
+  // `lane` at piece u ^ (lane & 7) and written by one TMA store
+  auto store_block64 = [&](const uint32_t* r0, const uint32_t* r1, int64_t row0, int64_t c0) {
+    if (row0 >= p.M || c0 >= p.N) return;  // warp-uniform: the block lies outside C
+    const uint32_t buf = stg + (nstaged & 1u) * 4096u;
+    if (lane == 0 && nstaged >= 2) bulk_wait_read<1>();  // as in store_block
+    __syncwarp();
+    uint32_t w[32];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(__uint_as_float(r0[2 * i]) * scale, __uint_as_float(r0[2 * i + 1]) * scale);
+      w[i] = *reinterpret_cast<uint32_t*>(&h);
+      h = __floats2bfloat162_rn(__uint_as_float(r1[2 * i]) * scale, __uint_as_float(r1[2 * i + 1]) * scale);
+      w[16 + i] = *reinterpret_cast<uint32_t*>(&h);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      st_shared_v4(buf + (uint32_t)lane * 128u + ((uint32_t)(u ^ (lane & 7)) << 4), w[4 * u], w[4 * u + 1],
+                   w[4 * u + 2], w[4 * u + 3]);
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+      tma_store_2d(&map_c64, buf, (int32_t)c0, (int32_t)row0);
+      bulk_commit();
+    }
+    ++nstaged;
   };
   bool counted = false;
   // Checked launch: each epilogue warp counts itself done right after its
@@ -444,7 +478,18 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int64_t row0 = (int64_t)tm * tile_m + warp_row0;
       const int64_t col0 = (int64_t)tn * p.bn + u.col;
       const uint32_t tacc = tmem_base + tlane + (uint32_t)(acc * p.bn);
-      for (int ch = 0; ch < u.width / 32 && store_ok; ++ch) {
+      const int nch = u.width / 32;
+      int ch = 0;
+      if (!kCount && p.stage_c) {
+        for (; ch + 1 < nch && store_ok; ch += 2) {
+          uint32_t r0[32], r1[32];
+          tmem_ld32(tacc + (uint32_t)(ch * 32), r0);
+          tmem_ld32(tacc + (uint32_t)(ch * 32 + 32), r1);
+          tmem_ld_wait();
+          store_block64(r0, r1, row0, col0 + ch * 32);
+        }
+      }
+      for (; ch < nch && store_ok; ++ch) {
         uint32_t r[32];
         tmem_ld32(tacc + (uint32_t)(ch * 32), r);
         tmem_ld_wait();
@@ -571,9 +616,10 @@ tp_status make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t k, i
   return TP_OK;
 }
 
-// The tensor maps of a launch: A, B, B for narrow tiles, C (TMA stores).
+// The tensor maps of a launch: A, B, B for narrow tiles, C in 32- and
+// 64-column boxes (TMA stores).
 struct Maps {
-  CUtensorMap a, b, b_cut, c;
+  CUtensorMap a, b, b_cut, c, c64;
 };
 
 template <bool kF8, bool kPair, bool kCount, bool kChecked>
@@ -599,7 +645,7 @@ cudaError_t launch_kernel(const Maps& m, const TcArgs& p, int grid, int csize, s
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  return cudaLaunchKernelEx(&cfg, k, m.a, m.b, m.b_cut, m.c, p);
+  return cudaLaunchKernelEx(&cfg, k, m.a, m.b, m.b_cut, m.c, m.c64, p);
 }
 
 template <bool kF8, bool kPair>
@@ -680,18 +726,19 @@ tp_status plan_smem(bool pair, int bn, int split, int stages_req, bool want_stag
   return fail(TP_ERR_UNSUPPORTED, "shared memory too small for the requested stages");
 }
 
-// C (bf16, N columns, row stride N) as 32 x 32 boxes with the 64-byte swizzle
-// of the epilogue's staging layout.
-tp_status make_map_c(CUtensorMap* map, void* ptr, int64_t M, int64_t N) {
+// C (bf16, N columns, row stride N) as boxes of 32 rows x `cols` columns
+// (32: 64-byte swizzle, 64: 128-byte swizzle) matching the epilogue's
+// staging layouts.
+tp_status make_map_c(CUtensorMap* map, void* ptr, int64_t M, int64_t N, int cols) {
   auto fn = encode_fn();
   if (!fn) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
   cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
   cuuint64_t strides[1] = {(cuuint64_t)(N * 2)};
-  cuuint32_t box[2] = {32, 32};
+  cuuint32_t box[2] = {(cuuint32_t)cols, 32};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled (C) failed (" + std::to_string((int)r) + ")");
   return TP_OK;
 }
@@ -779,10 +826,11 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   p.body_bytes = (int32_t)plan.body;
   p.stage_c = plan.stage_c ? 1 : 0;
   if (plan.stage_c) {
-    s = make_map_c(&maps.c, c->t.ptr, M, N);
+    s = make_map_c(&maps.c, c->t.ptr, M, N, 32);
+    if (s == TP_OK) s = make_map_c(&maps.c64, c->t.ptr, M, N, 64);
     if (s != TP_OK) return s;
   } else {
-    maps.c = maps.a;  // unused
+    maps.c = maps.c64 = maps.a;  // unused
   }
   const int csize = pair ? 2 : split;
   const int64_t grid = progs * csize;
