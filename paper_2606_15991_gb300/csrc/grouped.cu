@@ -32,7 +32,7 @@ namespace tp {
 struct alignas(64) GroupedProblem {
   CUtensorMap map_x;      // MMA A operand: A_i (normal) or B_i stored N x K (swap), box 128 rows
   CUtensorMap map_y;      // MMA B operand: B_i (normal, box 256 rows) or A_i (swap, box bn rows)
-  CUtensorMap map_c;      // C_i as 32 x 32 boxes (64-byte swizzle) for the epilogue's TMA stores
+  CUtensorMap map_c;      // C_i as 32 x 64 boxes (128-byte swizzle) for the epilogue's TMA stores
   __nv_bfloat16* c;
   int64_t M, N, K;
   int64_t tiles_r, tiles_c;  // tile grid in MMA orientation (rows of 128, columns of bn)
@@ -74,7 +74,7 @@ template <bool kPair> struct Ring {
   static constexpr int kStages = kPair ? 6 : 4;
 };
 constexpr size_t kWordsBytes = 8 + 8 * kRing;
-constexpr uint32_t kStageC = 4u * 2u * 2048u;  // epilogue staging: 4 warps x 2 buffers x (32 rows x 64 B)
+constexpr uint32_t kStageC = 4u * 2u * 4096u;  // epilogue staging: 4 warps x 2 buffers x (32 rows x 128 B)
 
 struct GroupedArgs {
   const GroupedProblem* probs;
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
   } else {
     const int quad = warp & 3;
     const int lane_row = (int)rank * 128 + quad * 32 + lane;  // tile row (MMA orientation) of this TMEM lane
-    const uint32_t stg = cst + (uint32_t)quad * 4096u;       // this warp's two 2 KB staging buffers
+    const uint32_t stg = cst + (uint32_t)quad * 8192u;       // this warp's two 4 KB staging buffers
     uint32_t nstaged = 0;
     for (int64_t j = 0;; ++j) {
       const int r = (int)(j % kRing);
@@ -304,30 +304,35 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
       tc_fence_after();
       const int64_t N = pr->N, M = pr->M;
       const int64_t rr = tr * pr->tile_rows + lane_row;  // row of C (normal) or column of C (swap)
-      for (int ch = 0; ch < pr->bn / 32; ++ch) {
-        uint32_t v[32];
-        tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * 256 + ch * 32), v);
-        tmem_ld_wait();
-        const int64_t c0 = tc * pr->bn + ch * 32;  // first column of the chunk (MMA orientation)
-        if (!kCount && pr->c_tma) {
-          // the warp's 32 x 32 block: staged (16-byte piece u of row `lane`
-          // at piece u ^ ((lane >> 1) & 3)) and written by one TMA store,
-          // clipped to C_i's bounds by its tensor map
-          const int64_t row0 = rr - lane;
+      int ch0 = 0;
+      if (!kCount && pr->c_tma) {
+        // normal orientation, 16-byte aligned C rows: 32 x 64 blocks staged
+        // with 16-byte piece u of row `lane` at piece u ^ (lane & 7) and
+        // written by one TMA store each, clipped to C_i's bounds by its
+        // tensor map (bn = 256: four blocks per tile row slice)
+        const int64_t row0 = rr - lane;
+        for (; ch0 + 1 < pr->bn / 32; ch0 += 2) {
+          uint32_t v0[32], v1[32];
+          tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * 256 + ch0 * 32), v0);
+          tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * 256 + ch0 * 32 + 32), v1);
+          tmem_ld_wait();
+          const int64_t c0 = tc * pr->bn + ch0 * 32;
           if (row0 >= M || c0 >= N) continue;  // warp-uniform
-          const uint32_t buf = stg + (nstaged & 1u) * 2048u;
-          if (lane == 0) bulk_wait_read<1>();  // the store issued from this buffer two blocks ago has read it
+          const uint32_t buf = stg + (nstaged & 1u) * 4096u;
+          if (lane == 0 && nstaged >= 2) bulk_wait_read<1>();  // the store from this buffer two blocks ago has read it
           __syncwarp();
-          uint32_t w[16];
+          uint32_t w[32];
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            __nv_bfloat162 h = __floats2bfloat162_rn(__uint_as_float(v[2 * i]), __uint_as_float(v[2 * i + 1]));
+            __nv_bfloat162 h = __floats2bfloat162_rn(__uint_as_float(v0[2 * i]), __uint_as_float(v0[2 * i + 1]));
             w[i] = *reinterpret_cast<uint32_t*>(&h);
+            h = __floats2bfloat162_rn(__uint_as_float(v1[2 * i]), __uint_as_float(v1[2 * i + 1]));
+            w[16 + i] = *reinterpret_cast<uint32_t*>(&h);
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            st_shared_v4(buf + (uint32_t)lane * 64u + ((uint32_t)(u ^ ((lane >> 1) & 3)) << 4), w[4 * u],
-                         w[4 * u + 1], w[4 * u + 2], w[4 * u + 3]);
+          for (int u = 0; u < 8; ++u)
+            st_shared_v4(buf + (uint32_t)lane * 128u + ((uint32_t)(u ^ (lane & 7)) << 4), w[4 * u], w[4 * u + 1],
+                         w[4 * u + 2], w[4 * u + 3]);
           fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) {
@@ -335,7 +340,14 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
             bulk_commit();
           }
           ++nstaged;
-        } else if (!pr->swap) {
+        }
+      }
+      for (int ch = ch0; ch < pr->bn / 32; ++ch) {
+        uint32_t v[32];
+        tmem_ld32(tmem_base + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * 256 + ch * 32), v);
+        tmem_ld_wait();
+        const int64_t c0 = tc * pr->bn + ch * 32;  // first column of the chunk (MMA orientation)
+        if (!pr->swap) {
           if (rr >= M || c0 >= N) continue;
           __nv_bfloat16* crow = pr->c + rr * N;
           if ((N & 7) == 0 && c0 + 32 <= N) {
@@ -407,17 +419,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode() {
   return fn;
 }
 
-// C_i (bf16, N columns, row stride N) as 32 x 32 boxes with the 64-byte
+// C_i (bf16, N columns, row stride N) as 32 x 64 boxes with the 128-byte
 // swizzle of the epilogue's staging layout.
 tp_status c_map(CUtensorMap* map, void* ptr, int64_t M, int64_t N) {
   auto fn = encode();
   if (!fn) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
   cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
   cuuint64_t strides[1] = {(cuuint64_t)(N * 2)};
-  cuuint32_t box[2] = {32, 32};
+  cuuint32_t box[2] = {64, 32};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled (C) failed (" + std::to_string((int)r) + ")");
   return TP_OK;
 }
