@@ -46,7 +46,7 @@ def _gemm(ctx, a, bt, bn=128, kind=tp.MAP_STRIDED, P=None, group_m=1, stages=0, 
     return c, counts, owner, info
 
 
-@pytest.mark.parametrize("bm,bn", [(128, 32), (128, 64), (128, 128), (128, 192), (128, 256),
+@pytest.mark.parametrize("bm,bn", [(128, 32), (128, 64), (128, 96), (128, 128), (128, 160), (128, 192), (128, 256),
                                    (256, 64), (256, 128), (256, 192), (256, 256)])
 def test_random_within_tolerance(ctx, bm, bn):
     m, n, k = 384, 512, 640
@@ -383,3 +383,14 @@ def test_resident_programs(ctx):
     with pytest.raises(tp.TPError) as e:
         tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=64, bn=256))
     assert e.value.status == tp._lib.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("bn", [96, 160, 224])
+def test_epilogue_mixed_block_widths_bit_exact(ctx, bn):
+    """Tile widths that are odd multiples of 32 columns store 32 x 64 blocks
+    and one 32 x 32 block per 32-row slice; integer inputs make C exact, so
+    every element is checked, including ragged edges."""
+    m, n, k = 300, 3 * bn + 40, 256
+    a, bt = _operands(m, n, k, seed=bn, kind="int")
+    c, _, _, _ = _gemm(ctx, a, bt, bn=bn, P=5)
+    assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(ogemm.gemm(a.cpu(), bt.cpu().t())))
