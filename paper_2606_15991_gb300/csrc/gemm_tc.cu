@@ -542,7 +542,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
     if (warp >= 2 && tile) {
-      const bool got = mbar_wait(recv_bar, 0, abort_flag, p.err);
+      // not cut short by the abort flag: the peers' copies into this CTA's
+      // shared memory must land before it can retire (they are issued right
+      // after barrier (1), so the bounded wait ends well within its limit)
+      const bool got = mbar_wait(recv_bar, 0, nullptr, p.err);
       if (__all_sync(0xffffffffu, got) && sp_have) {
         const int64_t row0 = (int64_t)sp_tm * tile_m + warp_row0;
         const int64_t col0 = (int64_t)sp_tn * p.bn + (int64_t)kslice * w;
