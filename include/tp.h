@@ -120,7 +120,14 @@ enum {
    * bitmap and its finished-claimant counter are one per context: checked
    * launches of one context must not overlap in time (order them on one
    * stream), or they see each other's claims. */
-  TP_EXEC_CHECKED = 1
+  TP_EXEC_CHECKED = 1,
+  /* Failure-path test hook of tp_gemm on 128-row tensor-core tiles: the
+   * producer of every program leaves its first K block unloaded, so the MMA
+   * issuer's bounded wait (cut to 50 ms) runs out; the kernel drains its
+   * copies and MMAs, frees TMEM and returns, and the operation reports
+   * TP_ERR_TIMEOUT where it reports device errors. C is left partly
+   * written. Other operations, and 256-row tiles, return TP_ERR_UNSUPPORTED. */
+  TP_EXEC_INJECT_TIMEOUT = 2
 };
 
 /* How an operation is executed. */

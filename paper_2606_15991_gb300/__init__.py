@@ -211,14 +211,15 @@ def tp_graph_destroy(g: Graph) -> None:
 
 
 def make_exec(mode: int = SYNC, stream=None, event: Event | None = None, write_counts=None,
-              write_owner=None, checked: bool = False) -> tp_exec:
+              write_owner=None, checked: bool = False, inject_timeout: bool = False) -> tp_exec:
     """tp_exec for `mode` on `stream` (torch.cuda.Stream, raw handle, or None =
     torch's current stream). write_counts / write_owner: optional uint32 /
     int32 device tensors with one entry per output element. checked: the
-    device-checked launch (TP_EXEC_CHECKED)."""
+    device-checked launch (TP_EXEC_CHECKED). inject_timeout: the tensor-core
+    GEMM's failure-path test hook (TP_EXEC_INJECT_TIMEOUT)."""
     ex = tp_exec()
     ex.mode = mode
-    ex.flags = _lib.EXEC_CHECKED if checked else 0
+    ex.flags = (_lib.EXEC_CHECKED if checked else 0) | (_lib.EXEC_INJECT_TIMEOUT if inject_timeout else 0)
     ex.stream = _stream_handle(stream)
     ex.event = event.handle.value if event is not None else None
     ex.write_counts = write_counts.data_ptr() if write_counts is not None else None

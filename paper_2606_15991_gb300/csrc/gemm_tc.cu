@@ -63,6 +63,8 @@ struct TcArgs {
   int32_t stage_c;      // epilogue writes C by TMA stores of 32 x 32 blocks staged in shared memory
   int32_t body_bytes;   // shared memory before the staging area: max(ring, split receive buffer)
   int32_t parts;        // claim parts per tile: narrow tiles (ncut) or K slices (split)
+  int32_t inject;       // failure-path test: each program's first K block is never loaded
+  uint64_t wait_ns;     // limit of every bounded wait (ns)
   __nv_bfloat16* c;
   const float* scale_a; // optional (FP8): C = acc * 1 / (*scale_a * *scale_b)
   const float* scale_b;
@@ -235,7 +237,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int32_t arow = tm * tile_m + (int32_t)rank * BM;
         const int32_t brow = tn * p.bn + u.col + (int32_t)rank * ub_rows;
         for (int32_t kb = kb0; kb < kb1; ++kb) {
-          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err)) { ok = false; break; }
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err, p.wait_ns)) { ok = false; break; }
+          if (p.inject && s == prog && kb == kb0) {
+            // test hook: this stage is never armed or filled, so its
+            // consumer's bounded wait runs out
+            if (++stage == p.stages) { stage = 0; phase ^= 1u; }
+            continue;
+          }
           const int32_t kc = kb * p.kblk;
           if constexpr (kPair) {
             // both CTAs' copies complete on the even CTA's full barrier
@@ -274,11 +282,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t idesc = u.cut ? idesc_cut : idesc_full;
         const int acc = t & 1;
         const uint32_t use = (uint32_t)((t >> 1) & 1);
-        if (!mbar_wait(tempty_bar(acc), use ^ 1u, abort_flag, p.err)) { ok = false; break; }
+        if (!mbar_wait(tempty_bar(acc), use ^ 1u, abort_flag, p.err, p.wait_ns)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d = tmem_base + (uint32_t)(acc * p.bn);
         for (int32_t kb = kb0; kb < kb1; ++kb) {
-          if (!mbar_wait(full_bar(stage), phase, abort_flag, p.err)) { ok = false; break; }
+          if (!mbar_wait(full_bar(stage), phase, abort_flag, p.err, p.wait_ns)) { ok = false; break; }
           tc_fence_after();
           const uint64_t ad = desc_kmajor_sw128(a0 + a_stage * stage);
           const uint64_t bd = desc_kmajor_sw128(b0 + b_stage * stage);
@@ -465,7 +473,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         store_ok = claim(s, tm, tn, S > 1 ? (int32_t)kslice : u.part);
         if (s + step >= TS) finish_claims();
       }
-      const bool ready = mbar_wait(tfull_bar(acc), use, abort_flag, p.err);
+      const bool ready = mbar_wait(tfull_bar(acc), use, abort_flag, p.err, p.wait_ns);
       if (!__all_sync(0xffffffffu, ready)) break;  // leave together (tcgen05.ld is warp-collective)
       tc_fence_after();
       if (S > 1) {
@@ -545,7 +553,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // not cut short by the abort flag: the peers' copies into this CTA's
       // shared memory must land before it can retire (they are issued right
       // after barrier (1), so the bounded wait ends well within its limit)
-      const bool got = mbar_wait(recv_bar, 0, nullptr, p.err);
+      const bool got = mbar_wait(recv_bar, 0, nullptr, p.err, p.wait_ns);
       if (__all_sync(0xffffffffu, got) && sp_have) {
         const int64_t row0 = (int64_t)sp_tm * tile_m + warp_row0;
         const int64_t col0 = (int64_t)sp_tn * p.bn + (int64_t)kslice * w;
@@ -861,6 +869,12 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
     }
   }
   p.parts = p.ncut * split;
+  p.wait_ns = 2000000000ull;
+  if (ex->flags & TP_EXEC_INJECT_TIMEOUT) {
+    if (pair) return fail(TP_ERR_UNSUPPORTED, "TP_EXEC_INJECT_TIMEOUT applies to 128-row tiles");
+    p.inject = 1;
+    p.wait_ns = 50000000ull;
+  }
   if (checked) {
     p.claim_bits = T * p.parts * (pair ? 8 : 4);
     s = claims_for(ctx, p.claim_bits, &p.claims, &p.claim_done);

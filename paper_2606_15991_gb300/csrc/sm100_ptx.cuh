@@ -60,7 +60,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 // Bounded wait for phase `parity` of the barrier at `bar`. Gives up after
 // `limit_ns` of wall time or when another role has set *abort; on timeout it
 // sets *abort and the kernel's error word. Returns true when the phase
-// completed.
+// completed. abort and err may be null (a drain after a timeout waits on its
+// own limit only and reports nothing).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort, int* err,
                                           uint64_t limit_ns = 2000000000ull) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -68,9 +69,9 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((i & 63) == 0) {
-      if (*abort) return false;
+      if (abort && *abort) return false;
       if (global_timer_ns() - t0 > limit_ns) {
-        *abort = 1;
+        if (abort) *abort = 1;
         if (err) atomicExch(err, 1);
         return false;
       }
@@ -308,9 +309,9 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait_cluster(bar, parity)) return true;
     if ((i & 63) == 0) {
-      if (*abort) return false;
+      if (abort && *abort) return false;
       if (global_timer_ns() - t0 > limit_ns) {
-        *abort = 1;
+        if (abort) *abort = 1;
         if (err) atomicExch(err, 1);
         return false;
       }

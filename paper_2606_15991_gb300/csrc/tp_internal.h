@@ -157,6 +157,7 @@ struct Op {
   bool check_err = false;   // kernel may write the device error word
   bool marked = false;
   bool allow_checked = false;  // the op implements TP_EXEC_CHECKED (set before begin)
+  bool allow_inject = false;   // the op implements TP_EXEC_INJECT_TIMEOUT (set before begin)
   DeviceGuard device;          // the context's device is current while the op launches
 
   tp_status begin(tp_ctx* c, const tp_exec* e, std::initializer_list<tp_partition*> outputs,

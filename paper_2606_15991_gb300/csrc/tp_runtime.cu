@@ -224,9 +224,12 @@ tp_status Op::begin_impl(tp_ctx* c, const tp_exec* e, const std::vector<tp_parti
   if (!ex) return fail(TP_ERR_INVALID, "null tp_exec");
   if (ex->mode < TP_SYNC || ex->mode > TP_CAPTURE)
     return fail(TP_ERR_INVALID, "tp_exec.mode must be TP_SYNC, TP_ASYNC or TP_CAPTURE");
-  if (ex->flags & ~TP_EXEC_CHECKED) return fail(TP_ERR_INVALID, "undefined tp_exec.flags bits");
+  if (ex->flags & ~(TP_EXEC_CHECKED | TP_EXEC_INJECT_TIMEOUT))
+    return fail(TP_ERR_INVALID, "undefined tp_exec.flags bits");
   if ((ex->flags & TP_EXEC_CHECKED) && !allow_checked)
     return fail(TP_ERR_UNSUPPORTED, "this operation has no device-checked launch (TP_EXEC_CHECKED)");
+  if ((ex->flags & TP_EXEC_INJECT_TIMEOUT) && !allow_inject)
+    return fail(TP_ERR_UNSUPPORTED, "this operation has no injected-timeout hook (TP_EXEC_INJECT_TIMEOUT)");
   if (ex->mode == TP_ASYNC && !ex->event) return fail(TP_ERR_INVALID, "TP_ASYNC needs tp_exec.event");
   if (ex->mode == TP_ASYNC && ex->event->ctx != ctx)
     return fail(TP_ERR_INVALID, "event belongs to another context");
@@ -822,6 +825,7 @@ tp_status tp_gemm(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_ten
   if (!simt && !tc) return fail(TP_ERR_UNSUPPORTED, "tp_gemm supports F32xF32->F32 and BF16xBF16->BF16");
   Op o(__func__);
   o.allow_checked = tc;
+  o.allow_inject = tc;
   tp_status s = o.begin(ctx, ex, {c}, {a, b});
   if (s != TP_OK) return s;
   unsigned* q = nullptr;
