@@ -131,7 +131,7 @@ def test_rejections(ctx):
         tp.tp_permute_heads(ctx, p, s, 3, tp.make_exec(checked=True))
     assert e.value.status == tp._lib.ERR_UNSUPPORTED
     ex = tp.make_exec()
-    ex.flags = 2                                            # undefined bit
+    ex.flags = 4                                            # undefined bit
     with pytest.raises(tp.TPError) as e:
         tp.tp_permute_heads(ctx, p, s, 3, ex)
     assert e.value.status == tp._lib.ERR_INVALID
