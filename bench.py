@@ -208,6 +208,24 @@ def cpu_oracle_gemm_rows(seconds: float = 4.0) -> dict:
     out["gemm_bf16_8192"] = {"tflops": 2 * 128 * 128 * K / el / 1e12, "ms_extrapolated": el * 4096 * 1e3,
                              "kind": "oracle", "sample": f"{reps} 128x128 output tiles with K = 8192, "
                                                           "extrapolated to the 4096 tiles of 8192^3"}
+    # the 64-problem group: one output tile (128 x 128, or M x 128 for M <
+    # 128) per problem with that problem's full K, extrapolated to every
+    # tile of every problem
+    probs = synth.grouped_problems(64, seed=0)
+    t_total, flops, tiles_timed, t0_all = 0.0, 0.0, 0, time.perf_counter()
+    for i, (m, n, k) in enumerate(probs):
+        tm = min(m, 128)
+        at = synth.normal(tm * k, 10 + 2 * i).reshape(tm, k)
+        bt = synth.normal(k * 128, 11 + 2 * i).reshape(k, 128)
+        t0 = time.perf_counter()
+        ogemm.gemm(at, bt)
+        el = time.perf_counter() - t0
+        tiles_timed += 1
+        t_total += el * (-(-m // 128)) * (-(-n // 128))
+        flops += 2.0 * m * n * k
+    out["grouped_64"] = {"tflops": flops / t_total / 1e12, "ms_extrapolated": t_total * 1e3, "kind": "oracle",
+                         "sample": f"{tiles_timed} output tiles (one per problem, full K), extrapolated to every "
+                                   f"tile of the 64 problems; {time.perf_counter() - t0_all:.1f} s"}
     out["threads"] = "numpy's BLAS threads (all host cores unless limited)"
     return out
 
@@ -427,6 +445,8 @@ def run_ours(args):
         single = cpu_oracle_sample(seconds=args.cpu_seconds / 2)
         cpu["single_thread"] = {"value": single["value"], "unit": "TB/s", "sample": single["sample"]}
         cpu["rows"] = cpu_oracle_gemm_rows()
+        cpu["host"] = {"nproc": os.cpu_count(), "affinity_cpus": len(os.sched_getaffinity(0))
+                       if hasattr(os, "sched_getaffinity") else None}
 
     if rank == 0:
         print(json.dumps({
