@@ -188,3 +188,20 @@ def test_propose_skips_split_configs_that_cannot_run(ctx):
     cfg, _, fb = tp.tp_propose(ctx, m, 128, 256, 64, "bf16", min_score=-1e9)    # one K block
     assert not fb and cfg.split_k <= 1
     tp.tp_mlp_destroy(m)
+
+
+def test_autotune_cache_reads_v1_files(ctx, tmp_path):
+    """A v1 cache line has no split_k column: it loads as split_k = 0, and
+    a v2 save writes the column."""
+    path = os.path.join(tmp_path, "v1.txt")
+    with open(path, "w") as f:
+        f.write("tp-autotune-cache v1\n")
+        f.write("1111 2222 3344 1 256 128 3 8 76 1234.500\n")
+    tp.tp_autotune_load(ctx, path)
+    cfg = tp.tp_autotune_lookup(ctx, 1111, 2222, 3344, "bf16")
+    assert (cfg.bm, cfg.bn, cfg.stages, cfg.group_m, cfg.num_programs, cfg.split_k) == (256, 128, 3, 8, 76, 0)
+    out = os.path.join(tmp_path, "v2.txt")
+    tp.tp_autotune_save(ctx, out)
+    lines = open(out).read().splitlines()
+    assert lines[0] == "tp-autotune-cache v2"
+    assert any(line.split()[:10] == ["1111", "2222", "3344", "1", "256", "128", "3", "8", "76", "0"] for line in lines[1:])
