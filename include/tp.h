@@ -197,7 +197,10 @@ typedef struct tp_gemm_config {
 const char* tp_error_string(tp_status s);
 /* Reason for the last non-OK status returned on this thread ("" if none). */
 const char* tp_last_error_detail(void);
-/* Library version (major, minor). */
+/* Library version (major, minor). 0.2: tp_gemm_config has the cut_limit
+ * field (the last-round N-cut limit that split_k carried in 0.1) and
+ * split_k selects split-K programs; tp_exec.flags has
+ * TP_EXEC_INJECT_TIMEOUT. */
 tp_status tp_version(int32_t* major, int32_t* minor);
 
 /* --------------------------------------------------------------- context */

@@ -370,7 +370,7 @@ const char* tp_last_error_detail(void) { return g_detail.c_str(); }
 tp_status tp_version(int32_t* major, int32_t* minor) {
   if (!major || !minor) return fail(TP_ERR_INVALID, "null output");
   *major = 0;
-  *minor = 1;
+  *minor = 2;  // 0.2: tp_gemm_config gained cut_limit; split_k selects split-K programs
   return TP_OK;
 }
 

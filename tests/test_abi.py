@@ -32,7 +32,7 @@ def test_exports_every_declared_symbol(built_lib):
 def test_error_strings_and_version(built_lib):
     for s in range(11):
         assert built_lib.tp_error_string(s)
-    assert tp.tp_version() == (0, 1)
+    assert tp.tp_version() == (0, 2)
 
 
 def test_tensor_init_validation(built_lib):
