@@ -894,6 +894,27 @@ def run_kernel(args):
                 tp.tp_partition_destroy(pq)
             fn = lambda: tp.tp_gemm_fp8(ctx, p, qa, qb.t(), scale[0:1], scale[1:2], cfg)
         out["size"] = n
+    elif k == "gemm_f32":
+        # the 512^3 FP32 configuration as the benchmark row runs it: 64 tile
+        # programs, each a cluster of 2 CTAs splitting K
+        a = torch.from_numpy(synth.uniform(512 * 512, seed=0)).reshape(512, 512).to(dev)
+        b = torch.from_numpy(synth.uniform(512 * 512, seed=1)).reshape(512, 512).to(dev)
+        c = torch.empty(512, 512, device=dev)
+        p = tp.tp_partition_create(ctx, c, (64, 64))
+        cfg = tp.gemm_config(bk=32, split_k=2)
+        fn = lambda: tp.tp_gemm(ctx, p, a, b, cfg)
+        out["size"] = 512
+    elif k == "gemm_bf16_split":
+        # few tiles, long K: M = 128, N = 256 * (size / 1024), K = 4096 as
+        # split-K programs of 4 CTAs on 128 x 128 tiles
+        nn = 256 * max(1, n // 1024)
+        a = torch.randn(128, 4096, device=dev, generator=g).to(torch.bfloat16)
+        bt = torch.randn(nn, 4096, device=dev, generator=g).to(torch.bfloat16)
+        c = torch.empty(128, nn, device=dev, dtype=torch.bfloat16)
+        p = tp.tp_partition_create(ctx, c, (128, 128))
+        cfg = tp.gemm_config(bm=128, bn=128, split_k=4)
+        fn = lambda: tp.tp_gemm(ctx, p, a, bt.t(), cfg)
+        out["shape"] = [128, nn, 4096]
     elif k == "grouped":
         shapes = synth.grouped_problems(64, seed=0)[:args.group]
         probs = []
@@ -943,7 +964,8 @@ def main():
                          "exec_modes: execution-mode scaling; gemm_sweep: GEMM size sweep; "
                          "bimodal: bimodal GEMM queue")
     ap.add_argument("--kernel", default="map_axpy_f32",
-                    help="map_axpy_f32|map_axpy_bf16|map_gelu_f32|map_gelu_bf16|gemm_bf16|gemm_fp8|grouped|decode")
+                    help="map_axpy_f32|map_axpy_bf16|map_gelu_f32|map_gelu_bf16|gemm_f32|gemm_bf16|gemm_bf16_split|"
+                         "gemm_fp8|grouped|decode")
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--elements", type=int, default=1 << 26)
     ap.add_argument("--group", type=int, default=8)
