@@ -583,6 +583,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (!kCount && p.stage_c && lane == 0) bulk_wait_all();  // C written before the CTA retires
     __syncwarp();
   }
+  if constexpr (kPair) settle_after_abort(abort_flag);
   tc_fence_before();
   if constexpr (kPair) cluster_sync();  // the peer no longer touches our shared memory / TMEM
   else __syncthreads();

@@ -397,6 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
     if (lane == 0) bulk_wait_all();  // C written before the CTA retires
     __syncwarp();
   }
+  if constexpr (kPair) settle_after_abort(abort_flag);
   tc_fence_before();
   if constexpr (kPair) cluster_sync();  // the peer no longer touches our shared memory / TMEM
   else __syncthreads();

@@ -319,6 +319,15 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
   }
 }
 
+// After a role of this CTA gave up on a bounded wait: pause ~100 us so that
+// TMA copies already issued by either CTA of a pair land before the CTAs
+// retire (the odd CTA's copies complete on the even CTA's barriers, which
+// only the even CTA drains).
+__device__ __forceinline__ void settle_after_abort(volatile int* abort) {
+  if (*abort)
+    for (int i = 0; i < 100; ++i) __nanosleep(1000);
+}
+
 // 64-bit store into a peer CTA's shared memory (shared::cluster address).
 __device__ __forceinline__ void st_cluster_u64(uint32_t addr, int64_t v) {
   asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
