@@ -454,29 +454,58 @@ tp_status tp_decode_down_residual(tp_ctx* ctx, tp_partition* h, const tp_tensor*
 
 /* ------------------------------------------------------------ autotuner */
 /* Tile-configuration search for the tensor-core GEMM (§5.1 tunes tile shapes
- * once per size). The space (same order on every call; index i is the MLP
+ * once per size; the algorithm and its numerics stay fixed).
+ *
+ * Numerics classes. Every config with split_k <= 1 computes each C element
+ * as one FP32 accumulation over K, in K order, by the one program that owns
+ * its tile; tile rows, tile columns, stages, raster band and program count
+ * only decide where and when that happens. All such configs, and the default
+ * config (cfg NULL), therefore give bit-identical C: the single-pass class.
+ * A split-K config adds split_k slice partials in slice order instead:
+ * reproducible, but rounded differently. Searches cover the single-pass
+ * class unless the caller opts in to split-K with TP_TUNE_SPLIT_K, so a
+ * tuned or proposed config never changes C unless asked to. */
+enum {
+  TP_TUNE_SPLIT_K = 1  /* also search the split-K configs (changes C's rounding) */
+};
+/* The space (same order on every call; with flags = 0, index i is the MLP
  * proposer's output i): tile rows {128 (one CTA), 256 (CTA pair)} x tile
- * columns {64, 128, 192, 256} x stages {3, max} x raster bands {1, 8}, then
- * split-K programs of 128-row tiles: (bn 128, split_k 2 / 4) and (bn 256,
- * split_k 2 / 4 / 8), 37 configs. Split configs are skipped (0 TFLOP/s) when
- * the shape's tiles x split_k exceed twice the SM count.
- * Writes up to `cap` configs to `out` (may be NULL) and the size to *count. */
-tp_status tp_autotune_space(int32_t dtype, tp_gemm_config* out, int32_t cap, int32_t* count);
-/* Times every config of the space on an M x N x K problem of `dtype`
- * (TP_BF16 or TP_F8E4M3; K * element size a multiple of 16) held in a device
- * workspace the context owns (grown with cudaMalloc: not during capture,
- * TP_ERR_CAPTURE), `reps` back-to-back launches per config timed with CUDA
- * events (0 = 3). Returns the fastest config (ties within 1% keep the earlier
- * one), optionally the TFLOP/s of every config (space order) and the best
- * TFLOP/s, and caches the winner for (M, N, K, dtype). */
-tp_status tp_autotune(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, int32_t reps,
+ * columns {64, 128, 192, 256} x stages {3, max} x raster bands {1, 8}, the 32
+ * single-pass configs; with TP_TUNE_SPLIT_K followed by the split-K programs
+ * of 128-row tiles: (bn 128, split_k 2 / 4) and (bn 256, split_k 2 / 4 / 8),
+ * 37 configs. Writes up to `cap` configs to `out` (may be NULL) and the size
+ * to *count. Errors: TP_ERR_INVALID (undefined flag bits), TP_ERR_UNSUPPORTED
+ * (dtype). */
+tp_status tp_autotune_space(int32_t dtype, int32_t flags, tp_gemm_config* out, int32_t cap, int32_t* count);
+/* Times every config of tp_autotune_space(dtype, flags) on an M x N x K
+ * problem of `dtype` (TP_BF16 or TP_F8E4M3; K * element size a multiple of
+ * 16) held in a device workspace the context owns (grown with cudaMalloc:
+ * not during capture, TP_ERR_CAPTURE), `reps` back-to-back launches per
+ * config timed with CUDA events (0 = 2..10 by problem size). Split-K configs
+ * are skipped (0 TFLOP/s) when the shape's tiles x split_k exceed twice the
+ * SM count or K has fewer than split_k blocks. Returns the fastest config
+ * (ties within 1% keep the earlier one), optionally the TFLOP/s of every
+ * config (space order) and the best TFLOP/s, and caches the winner under
+ * (M, N, K, dtype, flags). */
+tp_status tp_autotune(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, int32_t reps, int32_t flags,
                       tp_gemm_config* best, float* tflops_per_config, float* best_tflops);
-/* Cached winner for (M, N, K, dtype): *found = 1 and *out filled, else 0. */
-tp_status tp_autotune_lookup(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, tp_gemm_config* out,
-                             int32_t* found);
-/* Persist / restore the cache (text, "tp-autotune-cache v2": one line per
- * entry, M N K dtype bm bn stages group_m num_programs split_k TFLOP/s;
- * load also reads v1 files, whose lines lack split_k). */
+/* Re-times one config on the autotuner's workspace problem of that shape:
+ * `repeats` (1..64) independent timings of `reps` back-to-back launches
+ * (0 = as tp_autotune), each after a delay kernel that lets the host queue
+ * them all; *tflops_median = the median TFLOP/s. A split-K cfg is timed as
+ * given. Errors as tp_autotune, plus the launch's own (a config that cannot
+ * run on the shape). */
+tp_status tp_autotune_time(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, const tp_gemm_config* cfg,
+                           int32_t reps, int32_t repeats, float* tflops_median);
+/* Cached winner of a search with `flags` for (M, N, K, dtype): *found = 1
+ * and *out filled, else 0. */
+tp_status tp_autotune_lookup(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, int32_t flags,
+                             tp_gemm_config* out, int32_t* found);
+/* Persist / restore the cache (text, "tp-autotune-cache v3": one line per
+ * entry, M N K dtype flags bm bn stages group_m num_programs split_k
+ * TFLOP/s). Load also reads v2 and v1 files (no flags column; v1 lines also
+ * lack split_k), whose searches covered the split-K configs: an entry is
+ * filed under TP_TUNE_SPLIT_K, and a single-pass winner under flags 0 too. */
 tp_status tp_autotune_save(tp_ctx* ctx, const char* path);
 tp_status tp_autotune_load(tp_ctx* ctx, const char* path);
 
@@ -525,13 +554,12 @@ tp_status tp_mlp_features(int64_t M, int64_t N, int64_t K, int32_t dtype, float*
  * masked (0) when no config ran (host arrays of `count`). */
 tp_status tp_mlp_targets(const float* tflops, int32_t count, float* target, float* mask);
 /* Proposes a config for (M, N, K, dtype): the MLP's arg-max over the
- * configs of the autotuner's space that it would try on this shape (split-K
- * configs only where the tiles x split_k fit two waves of clusters and K has
- * split_k blocks; ties: lowest index). Falls back to the exhaustive
- * autotuner (cached) when the best score is below min_score or a dimension
- * exceeds 16384 (outside the trained range); *used_fallback tells which.
- * Configs without split-K compute the same C; split-K configs sum K slices
- * in an order of their own (bit-reproducible, within the BF16 gate). */
+ * single-pass configs (tp_autotune_space with flags 0; ties: lowest index).
+ * Falls back to the exhaustive autotuner over the same class (cached; flags
+ * 0) when the best score is below min_score or a dimension exceeds 16384
+ * (outside the trained range); *used_fallback tells which. Proposal and
+ * fallback choose within one numerics class, so C is bit-identical to the
+ * default config's whichever they pick: a proposal never changes numerics. */
 tp_status tp_propose(tp_ctx* ctx, tp_mlp* mlp, int64_t M, int64_t N, int64_t K, int32_t dtype, float min_score,
                      tp_gemm_config* out, float* score, int32_t* used_fallback);
 
@@ -550,11 +578,13 @@ tp_status tp_diag_bounded_wait(tp_ctx* ctx, int64_t limit_ns, int32_t arrive, co
 
 /* ------------------------------------------------- allocation-free entry */
 /* Queue-mapped z = alpha * x + y that needs no context and allocates nothing.
- * The paper has no counterpart; it exists for callers that cannot call
- * cudaMalloc: code that runs while someone else is capturing the stream into
- * a CUDA graph (allocating there breaks or invalidates the capture), and code
- * inside a runtime whose device memory is wholly owned by its own arena
- * allocator. Such a caller passes only its inputs and output:
+ * The paper has no counterpart. It exists for callers that cannot call
+ * cudaMalloc: code inside a runtime or plugin whose device memory is wholly
+ * owned by the host application's arena allocator (an allocation of its own
+ * would bypass that budget, and fails once the arena holds the device), and
+ * code on a latency-critical path where cudaMalloc / cudaFree are not
+ * allowed because they can synchronise the device. Such a caller passes only
+ * its inputs and output:
  *   z, x, y       device pointers to n contiguous elements of `dtype`
  *                 (TP_F32 or TP_BF16); x and y must not overlap z.
  *   tile          elements per tile (>= 1); the output is split into
@@ -562,15 +592,17 @@ tp_status tp_diag_bounded_wait(tp_ctx* ctx, int64_t limit_ns, int32_t arrive, co
  *                 exactly once, to `num_programs` persistent programs
  *                 (1..number of tiles).
  *   stream        cudaStream_t (NULL = legacy stream); the call only enqueues.
- * The result equals tp_map_axpy on a TP_MAP_QUEUE partition.
+ * The result equals tp_map_axpy on a TP_MAP_QUEUE partition, bit for bit.
  * Scratch: the queue's one 32-bit tile counter, kept in a static device array
  * of 256 bytes that every GPU loading this library holds until exit. The
- * first call on a device looks up that array's device address with the
- * device current, so make the first call on each device before any stream
- * capture. Each call clears the counter on `stream` before its launch. All
- * calls share the counter: calls that overlap on the GPU (on different
- * streams without ordering between them) race on it and may skip or repeat
- * tiles, so order such calls with one stream or with events.
+ * first call on a device does that device's set-up with the device current:
+ * it looks up the array's device address and loads the kernels this entry
+ * point launches. Make that first call on each device before any stream
+ * capture. Each call clears the counter on `stream` before its launch, in
+ * stream order behind earlier work on that stream. All calls share the
+ * counter: calls that overlap on the GPU (on different streams without
+ * ordering between them) race on it and may skip or repeat tiles, so order
+ * such calls with one stream or with events.
  * Limit: at most 2^31 tiles (TP_ERR_INVALID beyond). Errors: TP_ERR_INVALID
  * (bad sizes, null pointers), TP_ERR_ALIAS, TP_ERR_UNSUPPORTED (dtype),
  * TP_ERR_CUDA. Calls cudaMalloc, cudaFree or any allocating routine never. */

@@ -18,7 +18,7 @@ from ._lib import (ASYNC, CAPTURE, MAP_IDENTITY, MAP_QUEUE, MAP_STRIDED, SYNC, T
 
 __all__ = [
     "TPError", "SYNC", "ASYNC", "CAPTURE", "MAP_IDENTITY", "MAP_STRIDED", "MAP_QUEUE",
-    "tensor_desc", "make_exec", "gemm_config",
+    "tensor_desc", "make_exec", "gemm_config", "TUNE_SPLIT_K",
     "tp_version", "tp_ctx_create", "tp_ctx_destroy", "tp_ctx_info", "tp_tensor_init", "tp_tensor_view",
     "tp_partition_create", "tp_partition_map", "tp_partition_query", "tp_partition_destroy",
     "tp_event_create", "tp_event_query", "tp_event_wait", "tp_event_destroy",
@@ -29,7 +29,7 @@ __all__ = [
     "tp_rmsnorm", "tp_gemv", "tp_silu_mul", "tp_residual_add", "tp_decode_norm_qkv_gu",
     "tp_decode_down_residual", "DecodeChain", "tp_permute_heads", "tp_permute_heads_unchecked",
     "tp_gemm_unchecked", "tp_diag_bounded_wait", "tp_gemm_resident_programs",
-    "tp_autotune_space", "tp_autotune", "tp_autotune_lookup", "tp_autotune_save", "tp_autotune_load",
+    "tp_autotune_space", "tp_autotune", "tp_autotune_time", "tp_autotune_lookup", "tp_autotune_save", "tp_autotune_load",
     "tp_mlp_create", "tp_mlp_destroy", "tp_mlp_num_params", "tp_mlp_get_params", "tp_mlp_set_params",
     "tp_mlp_forward", "tp_mlp_loss_grad", "tp_mlp_train_step", "tp_mlp_save", "tp_mlp_load",
     "tp_mlp_features", "tp_mlp_targets", "tp_propose",
@@ -443,31 +443,45 @@ def _cfg_dict(c: tp_gemm_config) -> dict:
     return {n: getattr(c, n) for n, _ in tp_gemm_config._fields_}
 
 
-def tp_autotune_space(dtype: str = "bf16") -> list:
-    """The autotuner's config space (index i = proposer output i)."""
+TUNE_SPLIT_K = 1
+
+
+def tp_autotune_space(dtype: str = "bf16", split_k: bool = False) -> list:
+    """The autotuner's config space: the single-pass configs (index i =
+    proposer output i), then, with split_k, the split-K configs."""
+    fl = TUNE_SPLIT_K if split_k else 0
     n = ctypes.c_int32()
-    call("tp_autotune_space", _DT_CODE[dtype], None, 0, ctypes.byref(n))
+    call("tp_autotune_space", _DT_CODE[dtype], fl, None, 0, ctypes.byref(n))
     arr = (tp_gemm_config * n.value)()
-    call("tp_autotune_space", _DT_CODE[dtype], arr, n.value, ctypes.byref(n))
+    call("tp_autotune_space", _DT_CODE[dtype], fl, arr, n.value, ctypes.byref(n))
     return [arr[i] for i in range(n.value)]
 
 
-def tp_autotune(ctx, M: int, N: int, K: int, dtype: str = "bf16", reps: int = 0):
+def tp_autotune(ctx, M: int, N: int, K: int, dtype: str = "bf16", reps: int = 0, split_k: bool = False):
     """Exhaustive search: returns (best config, [TFLOP/s per config], best TFLOP/s)."""
-    cnt = len(tp_autotune_space(dtype))
+    cnt = len(tp_autotune_space(dtype, split_k))
     best = tp_gemm_config()
     table = (ctypes.c_float * cnt)()
     bt = ctypes.c_float()
-    call("tp_autotune", ctx.handle, int(M), int(N), int(K), _DT_CODE[dtype], int(reps), ctypes.byref(best),
-         table, ctypes.byref(bt))
+    call("tp_autotune", ctx.handle, int(M), int(N), int(K), _DT_CODE[dtype], int(reps),
+         TUNE_SPLIT_K if split_k else 0, ctypes.byref(best), table, ctypes.byref(bt))
     return best, list(table), bt.value
 
 
-def tp_autotune_lookup(ctx, M: int, N: int, K: int, dtype: str = "bf16"):
+def tp_autotune_time(ctx, M: int, N: int, K: int, dtype: str, cfg: tp_gemm_config, reps: int = 0,
+                     repeats: int = 3) -> float:
+    """Median TFLOP/s of `repeats` independent timings of one config."""
+    out = ctypes.c_float()
+    call("tp_autotune_time", ctx.handle, int(M), int(N), int(K), _DT_CODE[dtype], ctypes.byref(cfg), int(reps),
+         int(repeats), ctypes.byref(out))
+    return out.value
+
+
+def tp_autotune_lookup(ctx, M: int, N: int, K: int, dtype: str = "bf16", split_k: bool = False):
     out = tp_gemm_config()
     found = ctypes.c_int32()
-    call("tp_autotune_lookup", ctx.handle, int(M), int(N), int(K), _DT_CODE[dtype], ctypes.byref(out),
-         ctypes.byref(found))
+    call("tp_autotune_lookup", ctx.handle, int(M), int(N), int(K), _DT_CODE[dtype], TUNE_SPLIT_K if split_k else 0,
+         ctypes.byref(out), ctypes.byref(found))
     return out if found.value else None
 
 

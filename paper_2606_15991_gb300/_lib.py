@@ -117,9 +117,10 @@ _PROTOS = {
     "tp_residual_add": [_VP, _VP, _PT, _PE],
     "tp_decode_norm_qkv_gu": [_VP, _VP, _VP, _PT, _PT, _PT, _PT, ctypes.c_float, _PE],
     "tp_decode_down_residual": [_VP, _VP, _PT, _PT, _PE],
-    "tp_autotune_space": [_I32, ctypes.POINTER(tp_gemm_config), _I32, _PI32],
-    "tp_autotune": [_VP, _I64, _I64, _I64, _I32, _I32, ctypes.POINTER(tp_gemm_config), _VP, _VP],
-    "tp_autotune_lookup": [_VP, _I64, _I64, _I64, _I32, ctypes.POINTER(tp_gemm_config), _PI32],
+    "tp_autotune_space": [_I32, _I32, ctypes.POINTER(tp_gemm_config), _I32, _PI32],
+    "tp_autotune": [_VP, _I64, _I64, _I64, _I32, _I32, _I32, ctypes.POINTER(tp_gemm_config), _VP, _VP],
+    "tp_autotune_time": [_VP, _I64, _I64, _I64, _I32, ctypes.POINTER(tp_gemm_config), _I32, _I32, _VP],
+    "tp_autotune_lookup": [_VP, _I64, _I64, _I64, _I32, _I32, ctypes.POINTER(tp_gemm_config), _PI32],
     "tp_autotune_save": [_VP, ctypes.c_char_p],
     "tp_autotune_load": [_VP, ctypes.c_char_p],
     "tp_mlp_create": [_VP, _I32, _I32, _I32, _I32, _VP, _PP],

@@ -3,8 +3,16 @@
 // rows (128 on one CTA, 256 on a CTA pair), tile columns, pipeline depth and
 // raster band height; each config is timed with CUDA events on a device
 // workspace of the requested shape and the fastest wins (ties within 1% go to
-// the earlier, smaller config). Results are cached per (M, N, K, dtype) and
-// can be saved to / loaded from a versioned text file.
+// the earlier, smaller config). Results are cached per (M, N, K, dtype,
+// search flags) and can be saved to / loaded from a versioned text file.
+//
+// Numerics classes. Every config without split-K computes each C element as
+// one accumulation over K, in K order, by the one program that owns its
+// tile, so all of them give bit-identical C: choosing among them is a pure
+// performance decision (§5.1 tunes only the tile shape). A split-K config
+// adds S slice partials in slice order: reproducible, but rounded
+// differently. The default search is therefore the single-pass class only;
+// split-K configs are timed only when the caller opts in (TP_TUNE_SPLIT_K).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -22,8 +30,9 @@ namespace {
 struct TuneKey {
   int64_t m, n, k;
   int32_t dtype;
+  int32_t flags;  // TP_TUNE_* bits of the search that produced the entry
   bool operator<(const TuneKey& o) const {
-    return std::tie(m, n, k, dtype) < std::tie(o.m, o.n, o.k, o.dtype);
+    return std::tie(m, n, k, dtype, flags) < std::tie(o.m, o.n, o.k, o.dtype, o.flags);
   }
 };
 
@@ -45,7 +54,9 @@ TuneState* state(tp_ctx* ctx) {
   return s;
 }
 
-std::vector<tp_gemm_config> space() {
+// The single-pass configs (one numerics class), then, with TP_TUNE_SPLIT_K,
+// the split-K configs.
+std::vector<tp_gemm_config> space(int32_t flags) {
   std::vector<tp_gemm_config> v;
   for (int bm : {128, 256})
     for (int bn : {64, 128, 192, 256})
@@ -58,6 +69,7 @@ std::vector<tp_gemm_config> space() {
           c.group_m = gm;
           v.push_back(c);
         }
+  if (!(flags & TP_TUNE_SPLIT_K)) return v;
   // split-K programs (128-row tiles; a cluster of split_k CTAs per tile) for
   // shapes with fewer tiles than SMs
   for (int bn : {128, 256})
@@ -73,8 +85,6 @@ std::vector<tp_gemm_config> space() {
   return v;
 }
 
-}  // namespace
-
 // Whether config c of the space is tried on an M x N x K problem: a split
 // program holds one tile and needs at least split_k K blocks, and past two
 // waves of clusters it cannot win.
@@ -85,8 +95,6 @@ bool autotune_config_runs(const tp_ctx* ctx, int64_t M, int64_t N, int64_t K, in
   const int64_t kblk = dtype == TP_F8E4M3 ? 128 : 64;
   return (K + kblk - 1) / kblk >= c.split_k && tiles * c.split_k <= 2 * (int64_t)ctx->sm_count;
 }
-
-namespace {
 
 // Fills a workspace with finite values that exercise the tensor cores the
 // way real data does (a hash of the index, small magnitudes).
@@ -130,117 +138,168 @@ tp_status ensure_ws(tp_ctx* ctx, TuneState* st, size_t bytes) {
 }  // namespace
 }  // namespace tp
 
+namespace tp {
+namespace {
+
+// The autotuner's problem of one shape: A (M x K, row-major) and B (stored
+// N x K, viewed as K x N) in the context's workspace, C behind them; FP8
+// scales of 1 in the context's scratch.
+struct TuneProblem {
+  int64_t M = 0, N = 0, K = 0;
+  int esize = 2;
+  tp_tensor a{}, b{};
+  void* c = nullptr;
+  float* one = nullptr;
+  tp_exec ex{};
+};
+
+tp_status prepare(tp_ctx* ctx, TuneState* st, int64_t M, int64_t N, int64_t K, int32_t dtype, TuneProblem* pb) {
+  if (!st->stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&st->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune stream");
+  }
+  pb->M = M;
+  pb->N = N;
+  pb->K = K;
+  pb->esize = dtype == TP_BF16 ? 2 : 1;
+  const int esize = pb->esize;
+  auto align = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t ab = align((size_t)M * K * esize), bb = align((size_t)N * K * esize), cb = align((size_t)M * N * 2);
+  tp_status s = ensure_ws(ctx, st, ab + bb + cb);
+  if (s != TP_OK) return s;
+  char* ws = static_cast<char*>(st->ws);
+  pb->a.ptr = ws;
+  pb->a.dtype = dtype;
+  pb->a.rank = 2;
+  pb->a.shape[0] = M;
+  pb->a.shape[1] = K;
+  pb->a.strides[0] = K;
+  pb->a.strides[1] = 1;
+  pb->b.ptr = ws + ab;  // stored N x K, viewed as K x N
+  pb->b.dtype = dtype;
+  pb->b.rank = 2;
+  pb->b.shape[0] = K;
+  pb->b.shape[1] = N;
+  pb->b.strides[0] = 1;
+  pb->b.strides[1] = K;
+  pb->c = ws + ab + bb;
+  pb->ex = tp_exec{};
+  pb->ex.stream = st->stream;
+  pb->one = nullptr;
+  if (dtype == TP_F8E4M3) {
+    const float ones[2] = {1.f, 1.f};
+    cudaError_t e = cudaMemcpy(ctx->d_scratch, ones, sizeof(ones), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "fp8 unit scales");
+    pb->one = ctx->d_scratch;
+  }
+  return TP_OK;
+}
+
+// Launches per timing: enough that the timed span is well above the event
+// resolution.
+int default_reps(int64_t M, int64_t N, int64_t K) {
+  const double est_us = 2.0 * (double)M * (double)N * (double)K / 1.0e9;  // at 1 PFLOP/s
+  return est_us > 2000 ? 2 : est_us > 200 ? 4 : 10;
+}
+
+// One timing of config c: `r` back-to-back launches queued behind a delay
+// kernel and bracketed by CUDA events. *tf = TFLOP/s, 0 when the config
+// cannot run on the shape (the returned status says why) or did not run.
+tp_status time_config(tp_ctx* ctx, TuneState* st, const TuneProblem& pb, const tp_gemm_config& c, int r,
+                      cudaEvent_t e0, cudaEvent_t e1, float* tf) {
+  *tf = 0.f;
+  tp_partition part{};
+  part.ctx = ctx;
+  part.t.ptr = pb.c;
+  part.t.dtype = TP_BF16;
+  part.t.rank = 2;
+  part.t.shape[0] = pb.M;
+  part.t.shape[1] = pb.N;
+  part.t.strides[0] = pb.N;
+  part.t.strides[1] = 1;
+  part.rank = 2;
+  part.shape[0] = pb.M;
+  part.shape[1] = pb.N;
+  part.tile[0] = c.bm;
+  part.tile[1] = c.bn;
+  part.grid[0] = (pb.M + c.bm - 1) / c.bm;
+  part.grid[1] = (pb.N + c.bn - 1) / c.bn;
+  part.num_tiles = part.grid[0] * part.grid[1];
+  const int64_t cap = (int64_t)ctx->sm_count * 128 / c.bm;
+  part.kind = TP_MAP_STRIDED;
+  part.num_programs = std::min<int64_t>(part.num_tiles, cap);
+  if (c.num_programs > 0) part.num_programs = std::min<int64_t>(part.num_tiles, c.num_programs);
+  if (c.split_k > 1) part.num_programs = part.num_tiles;  // a split program holds one tile
+  tp_status ls = launch_gemm_tc_impl(ctx, &part, &pb.a, &pb.b, &c, &pb.ex, st->stream, pb.esize, pb.one, pb.one);
+  if (ls != TP_OK) return ls;
+  delay_kernel<<<1, 32, 0, st->stream>>>(20000ull + 30000ull * (uint64_t)r);
+  cudaEventRecord(e0, st->stream);
+  for (int j = 0; j < r && ls == TP_OK; ++j)
+    ls = launch_gemm_tc_impl(ctx, &part, &pb.a, &pb.b, &c, &pb.ex, st->stream, pb.esize, pb.one, pb.one);
+  cudaEventRecord(e1, st->stream);
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  if (ls == TP_OK && ms > 0.f) *tf = (float)(2.0 * (double)pb.M * (double)pb.N * (double)pb.K * r / (ms * 1e-3) / 1e12);
+  return ls;
+}
+
+tp_status check_args(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, int32_t flags) {
+  if (!ctx) return fail(TP_ERR_INVALID, "null context");
+  if (dtype != TP_BF16 && dtype != TP_F8E4M3) return fail(TP_ERR_UNSUPPORTED, "dtype must be BF16 or F8E4M3");
+  if (flags & ~TP_TUNE_SPLIT_K) return fail(TP_ERR_INVALID, "undefined TP_TUNE_* flag bits");
+  const int esize = dtype == TP_BF16 ? 2 : 1;
+  if (M < 1 || N < 1 || K < 1 || (K * esize) % 16) return fail(TP_ERR_SHAPE, "need M, N, K >= 1 and K*esize % 16 == 0");
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (ctx->capturing) return fail(TP_ERR_CAPTURE, "autotuning allocates and synchronises: not during capture");
+  return TP_OK;
+}
+
+}  // namespace
+}  // namespace tp
+
 using namespace tp;
 
 extern "C" {
 
-tp_status tp_autotune_space(int32_t dtype, tp_gemm_config* out, int32_t cap, int32_t* count) {
+tp_status tp_autotune_space(int32_t dtype, int32_t flags, tp_gemm_config* out, int32_t cap, int32_t* count) {
   if (!count) return fail(TP_ERR_INVALID, "null count");
   if (dtype != TP_BF16 && dtype != TP_F8E4M3) return fail(TP_ERR_UNSUPPORTED, "dtype must be BF16 or F8E4M3");
-  auto v = space();
+  if (flags & ~TP_TUNE_SPLIT_K) return fail(TP_ERR_INVALID, "undefined TP_TUNE_* flag bits");
+  auto v = space(flags);
   *count = (int32_t)v.size();
   if (out)
     for (int i = 0; i < (int)v.size() && i < cap; ++i) out[i] = v[i];
   return TP_OK;
 }
 
-tp_status tp_autotune(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, int32_t reps,
+tp_status tp_autotune(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, int32_t reps, int32_t flags,
                       tp_gemm_config* best, float* tflops_per_config, float* best_tflops) {
-  if (!ctx) return fail(TP_ERR_INVALID, "null context");
+  tp_status s = check_args(ctx, M, N, K, dtype, flags);
+  if (s != TP_OK) return s;
   DeviceGuard guard(ctx);
-  if (dtype != TP_BF16 && dtype != TP_F8E4M3) return fail(TP_ERR_UNSUPPORTED, "dtype must be BF16 or F8E4M3");
-  const int esize = dtype == TP_BF16 ? 2 : 1;
-  if (M < 1 || N < 1 || K < 1 || (K * esize) % 16) return fail(TP_ERR_SHAPE, "need M, N, K >= 1 and K*esize % 16 == 0");
-  {
-    std::lock_guard<std::mutex> lk(ctx->mu);
-    if (ctx->capturing) return fail(TP_ERR_CAPTURE, "autotuning allocates and synchronises: not during capture");
-  }
   TuneState* st = state(ctx);
   std::lock_guard<std::mutex> lk(st->mu);
-  if (!st->stream) {
-    cudaError_t e = cudaStreamCreateWithFlags(&st->stream, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return cuda_fail(e, "autotune stream");
-  }
-  auto align = [](size_t b) { return (b + 255) & ~size_t(255); };
-  const size_t ab = align((size_t)M * K * esize), bb = align((size_t)N * K * esize), cb = align((size_t)M * N * 2);
-  tp_status s = ensure_ws(ctx, st, ab + bb + cb);
+  TuneProblem pb;
+  s = prepare(ctx, st, M, N, K, dtype, &pb);
   if (s != TP_OK) return s;
-  char* ws = static_cast<char*>(st->ws);
-  tp_tensor a{}, b{};
-  a.ptr = ws;
-  a.dtype = dtype;
-  a.rank = 2;
-  a.shape[0] = M;
-  a.shape[1] = K;
-  a.strides[0] = K;
-  a.strides[1] = 1;
-  b.ptr = ws + ab;  // stored N x K, viewed as K x N
-  b.dtype = dtype;
-  b.rank = 2;
-  b.shape[0] = K;
-  b.shape[1] = N;
-  b.strides[0] = 1;
-  b.strides[1] = K;
-  tp_exec ex{};
-  ex.stream = st->stream;
-  float* one = nullptr;  // fp8 scales: the context's scratch holds 1.0f at [0] and [1]
-  if (dtype == TP_F8E4M3) {
-    const float ones[2] = {1.f, 1.f};
-    cudaError_t e = cudaMemcpy(ctx->d_scratch, ones, sizeof(ones), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(e, "fp8 unit scales");
-    one = ctx->d_scratch;
-  }
-  auto cfgs = space();
+  auto cfgs = space(flags);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const double flops = 2.0 * (double)M * (double)N * (double)K;
-  // enough launches that the timed span is well above event resolution
-  const double est_us = flops / 1.0e9;  // at 1 PFLOP/s
-  const int r = reps > 0 ? reps : (est_us > 2000 ? 2 : est_us > 200 ? 4 : 10);
+  const int r = reps > 0 ? reps : default_reps(M, N, K);
   int best_i = -1;
   float best_tf = 0.f;
   for (size_t i = 0; i < cfgs.size(); ++i) {
-    const tp_gemm_config& c = cfgs[i];
-    tp_partition part{};
-    part.ctx = ctx;
-    part.t.ptr = ws + ab + bb;
-    part.t.dtype = TP_BF16;
-    part.t.rank = 2;
-    part.t.shape[0] = M;
-    part.t.shape[1] = N;
-    part.t.strides[0] = N;
-    part.t.strides[1] = 1;
-    part.rank = 2;
-    part.shape[0] = M;
-    part.shape[1] = N;
-    part.tile[0] = c.bm;
-    part.tile[1] = c.bn;
-    part.grid[0] = (M + c.bm - 1) / c.bm;
-    part.grid[1] = (N + c.bn - 1) / c.bn;
-    part.num_tiles = part.grid[0] * part.grid[1];
-    const int64_t cap = (int64_t)ctx->sm_count * 128 / c.bm;
-    part.kind = TP_MAP_STRIDED;
-    part.num_programs = std::min<int64_t>(part.num_tiles, cap);
     float tf = 0.f;
-    const bool skip = !autotune_config_runs(ctx, M, N, K, dtype, c);
-    if (c.split_k > 1) part.num_programs = part.num_tiles;  // a split program holds one tile
-    tp_status ls = skip ? TP_ERR_UNSUPPORTED : launch_gemm_tc_impl(ctx, &part, &a, &b, &c, &ex, st->stream, esize, one, one);
-    if (ls == TP_OK) {
-      delay_kernel<<<1, 32, 0, st->stream>>>(20000ull + 30000ull * (uint64_t)r);
-      cudaEventRecord(e0, st->stream);
-      for (int j = 0; j < r && ls == TP_OK; ++j)
-        ls = launch_gemm_tc_impl(ctx, &part, &a, &b, &c, &ex, st->stream, esize, one, one);
-      cudaEventRecord(e1, st->stream);
-      cudaError_t e = cudaEventSynchronize(e1);
-      if (e != cudaSuccess) {
+    if (autotune_config_runs(ctx, M, N, K, dtype, cfgs[i])) {
+      s = time_config(ctx, st, pb, cfgs[i], r, e0, e1, &tf);
+      if (s == TP_ERR_CUDA) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        return cuda_fail(e, "autotune timing");
+        return s;
       }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ls == TP_OK && ms > 0.f) tf = (float)(flops * r / (ms * 1e-3) / 1e12);
     }
     if (tflops_per_config) tflops_per_config[i] = tf;
     if (tf > best_tf * 1.01f) {
@@ -253,18 +312,47 @@ tp_status tp_autotune(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtyp
   tp_status es = read_device_error(ctx);
   if (es != TP_OK) return es;
   if (best_i < 0) return fail(TP_ERR_CUDA, "no configuration ran");
-  st->cache[TuneKey{M, N, K, dtype}] = {cfgs[best_i], best_tf};
+  st->cache[TuneKey{M, N, K, dtype, flags}] = {cfgs[best_i], best_tf};
   if (best) *best = cfgs[best_i];
   if (best_tflops) *best_tflops = best_tf;
   return TP_OK;
 }
 
-tp_status tp_autotune_lookup(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, tp_gemm_config* out,
-                             int32_t* found) {
-  if (!ctx || !found) return fail(TP_ERR_INVALID, "null argument");
+tp_status tp_autotune_time(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, const tp_gemm_config* cfg,
+                           int32_t reps, int32_t repeats, float* tflops_median) {
+  if (!cfg || !tflops_median) return fail(TP_ERR_INVALID, "null argument");
+  if (repeats < 1 || repeats > 64) return fail(TP_ERR_INVALID, "repeats must be 1..64");
+  tp_status s = check_args(ctx, M, N, K, dtype, cfg->split_k > 1 ? TP_TUNE_SPLIT_K : 0);
+  if (s != TP_OK) return s;
+  DeviceGuard guard(ctx);
   TuneState* st = state(ctx);
   std::lock_guard<std::mutex> lk(st->mu);
-  auto it = st->cache.find(TuneKey{M, N, K, dtype});
+  TuneProblem pb;
+  s = prepare(ctx, st, M, N, K, dtype, &pb);
+  if (s != TP_OK) return s;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int r = reps > 0 ? reps : default_reps(M, N, K);
+  std::vector<float> tf(repeats, 0.f);
+  for (int i = 0; i < repeats && s == TP_OK; ++i) s = time_config(ctx, st, pb, *cfg, r, e0, e1, &tf[i]);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != TP_OK) return s;
+  tp_status es = read_device_error(ctx);
+  if (es != TP_OK) return es;
+  std::sort(tf.begin(), tf.end());
+  *tflops_median = repeats % 2 ? tf[repeats / 2] : 0.5f * (tf[repeats / 2 - 1] + tf[repeats / 2]);
+  return TP_OK;
+}
+
+tp_status tp_autotune_lookup(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, int32_t flags,
+                             tp_gemm_config* out, int32_t* found) {
+  if (!ctx || !found) return fail(TP_ERR_INVALID, "null argument");
+  if (flags & ~TP_TUNE_SPLIT_K) return fail(TP_ERR_INVALID, "undefined TP_TUNE_* flag bits");
+  TuneState* st = state(ctx);
+  std::lock_guard<std::mutex> lk(st->mu);
+  auto it = st->cache.find(TuneKey{M, N, K, dtype, flags});
   *found = it != st->cache.end();
   if (*found && out) *out = it->second.first;
   return TP_OK;
@@ -276,12 +364,12 @@ tp_status tp_autotune_save(tp_ctx* ctx, const char* path) {
   std::lock_guard<std::mutex> lk(st->mu);
   FILE* f = std::fopen(path, "w");
   if (!f) return fail(TP_ERR_INVALID, std::string("cannot write ") + path);
-  std::fprintf(f, "tp-autotune-cache v2\n");
+  std::fprintf(f, "tp-autotune-cache v3\n");
   for (auto& kv : st->cache) {
     const auto& c = kv.second.first;
-    std::fprintf(f, "%lld %lld %lld %d %d %d %d %d %d %d %.3f\n", (long long)kv.first.m, (long long)kv.first.n,
-                 (long long)kv.first.k, kv.first.dtype, c.bm, c.bn, c.stages, c.group_m, c.num_programs, c.split_k,
-                 kv.second.second);
+    std::fprintf(f, "%lld %lld %lld %d %d %d %d %d %d %d %d %.3f\n", (long long)kv.first.m, (long long)kv.first.n,
+                 (long long)kv.first.k, kv.first.dtype, kv.first.flags, c.bm, c.bn, c.stages, c.group_m,
+                 c.num_programs, c.split_k, kv.second.second);
   }
   std::fclose(f);
   return TP_OK;
@@ -291,25 +379,37 @@ tp_status tp_autotune_load(tp_ctx* ctx, const char* path) {
   if (!ctx || !path) return fail(TP_ERR_INVALID, "null argument");
   FILE* f = std::fopen(path, "r");
   if (!f) return fail(TP_ERR_INVALID, std::string("cannot read ") + path);
-  // v1 lines lack the split_k column
+  // v3 lines carry the search flags; v2 and v1 entries came from searches
+  // that included split-K (v1 lines also lack the split_k column)
   char magic[64] = {};
   const bool ok = std::fgets(magic, sizeof magic, f) != nullptr;
-  const bool v2 = ok && std::string(magic).rfind("tp-autotune-cache v2", 0) == 0;
-  if (!v2 && !(ok && std::string(magic).rfind("tp-autotune-cache v1", 0) == 0)) {
+  auto is = [&](const char* m) { return ok && std::string(magic).rfind(m, 0) == 0; };
+  const int ver = is("tp-autotune-cache v3") ? 3 : is("tp-autotune-cache v2") ? 2 : is("tp-autotune-cache v1") ? 1 : 0;
+  if (!ver) {
     std::fclose(f);
-    return fail(TP_ERR_INVALID, "not an autotune cache (v1 or v2)");
+    return fail(TP_ERR_INVALID, "not an autotune cache (v1, v2 or v3)");
   }
   TuneState* st = state(ctx);
   std::lock_guard<std::mutex> lk(st->mu);
   long long m, n, k;
-  int dt, bm, bn, stages, gm, np, sk = 0;
+  int dt, fl = TP_TUNE_SPLIT_K, bm, bn, stages, gm, np, sk = 0;
   float tf;
   for (;;) {
-    const int got = v2 ? std::fscanf(f, "%lld %lld %lld %d %d %d %d %d %d %d %f", &m, &n, &k, &dt, &bm, &bn, &stages,
-                                     &gm, &np, &sk, &tf)
-                       : std::fscanf(f, "%lld %lld %lld %d %d %d %d %d %d %f", &m, &n, &k, &dt, &bm, &bn, &stages,
-                                     &gm, &np, &tf);
-    if (got != (v2 ? 11 : 10)) break;
+    int got, want;
+    if (ver == 3) {
+      got = std::fscanf(f, "%lld %lld %lld %d %d %d %d %d %d %d %d %f", &m, &n, &k, &dt, &fl, &bm, &bn, &stages, &gm,
+                        &np, &sk, &tf);
+      want = 12;
+    } else if (ver == 2) {
+      got = std::fscanf(f, "%lld %lld %lld %d %d %d %d %d %d %d %f", &m, &n, &k, &dt, &bm, &bn, &stages, &gm, &np,
+                        &sk, &tf);
+      want = 11;
+    } else {
+      got = std::fscanf(f, "%lld %lld %lld %d %d %d %d %d %d %f", &m, &n, &k, &dt, &bm, &bn, &stages, &gm, &np, &tf);
+      want = 10;
+    }
+    if (got != want) break;
+    if ((fl & ~TP_TUNE_SPLIT_K) || (sk > 1 && !(fl & TP_TUNE_SPLIT_K))) continue;  // not a winner of such a search
     tp_gemm_config c{};
     c.bm = bm;
     c.bn = bn;
@@ -317,7 +417,10 @@ tp_status tp_autotune_load(tp_ctx* ctx, const char* path) {
     c.group_m = gm;
     c.num_programs = np;
     c.split_k = sk;
-    st->cache[TuneKey{m, n, k, dt}] = {c, tf};
+    st->cache[TuneKey{m, n, k, dt, fl}] = {c, tf};
+    // an older search over the whole space that picked a single-pass config
+    // also holds the single-pass class's winner
+    if (ver < 3 && sk <= 1) st->cache[TuneKey{m, n, k, dt, 0}] = {c, tf};
   }
   std::fclose(f);
   return TP_OK;

@@ -1,11 +1,14 @@
 // Learned tile proposer: a 3-layer ReLU MLP that scores every configuration
-// of the GEMM autotuner's space for a shape (features: log2 M, log2 N, log2 K
-// and a one-hot dtype), trained on the GPU by this file's kernels on the
-// autotuner's own measurements (target: TFLOP/s of the config over the best
-// TFLOP/s of the shape). The proposal is the arg-max config; the exhaustive
-// autotuner stays the fallback for low scores and shapes outside the trained
-// range. A proposal only picks among configurations that compute the same
-// result, so it never changes numerics.
+// of the GEMM autotuner's single-pass class for a shape (features: log2 M,
+// log2 N, log2 K and a one-hot dtype), trained on the GPU by this file's
+// kernels on the autotuner's own measurements (target: TFLOP/s of the config
+// over the best TFLOP/s of the shape). The proposal is the arg-max config;
+// the exhaustive autotuner over the same class stays the fallback for low
+// scores and shapes outside the trained range. Every config of that class
+// computes each C element as one K-ordered accumulation by one program, so
+// whichever config the proposal or its fallback picks, C is bit-identical:
+// the proposal never changes numerics. Split-K configs, which round
+// differently, are outside the class and never proposed.
 //
 //   h1 = relu(W1 x + b1), h2 = relu(W2 h1 + b2), y = W3 h2 + b3
 //   L  = sum V (y - T)^2 / max(1, sum V)      (V masks invalid configs)
@@ -386,11 +389,11 @@ tp_status tp_propose(tp_ctx* ctx, tp_mlp* n, int64_t M, int64_t N, int64_t K, in
   if (!ctx || !n || !out) return fail(TP_ERR_INVALID, "null argument");
   if (n->in != 5) return fail(TP_ERR_SHAPE, "the proposer takes 5 features");
   int32_t count = 0;
-  tp_status s = tp_autotune_space(dtype, nullptr, 0, &count);
+  tp_status s = tp_autotune_space(dtype, 0, nullptr, 0, &count);
   if (s != TP_OK) return s;
-  if (count != n->out) return fail(TP_ERR_SHAPE, "MLP outputs differ from the autotuner's config count");
+  if (count != n->out) return fail(TP_ERR_SHAPE, "MLP outputs differ from the autotuner's single-pass config count");
   std::vector<tp_gemm_config> cfgs(count);
-  tp_autotune_space(dtype, cfgs.data(), count, &count);
+  tp_autotune_space(dtype, 0, cfgs.data(), count, &count);
   float x[5];
   s = tp_mlp_features(M, N, K, dtype, x);
   if (s != TP_OK) return s;
@@ -401,11 +404,10 @@ tp_status tp_propose(tp_ctx* ctx, tp_mlp* n, int64_t M, int64_t N, int64_t K, in
   std::vector<float> y(count);
   e = cudaMemcpy(y.data(), n->y, count * sizeof(float), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "proposer scores");
-  // arg-max over the configs the autotuner would try on this shape (ties
-  // keep the lower index; configs without split-K always qualify)
-  int best = -1;
-  for (int i = 0; i < count; ++i)
-    if (autotune_config_runs(ctx, M, N, K, dtype, cfgs[i]) && (best < 0 || y[i] > y[best])) best = i;
+  // arg-max over the single-pass configs (ties keep the lower index)
+  int best = 0;
+  for (int i = 1; i < count; ++i)
+    if (y[i] > y[best]) best = i;
   const bool in_range = M <= 16384 && N <= 16384 && K <= 16384;
   if (score) *score = y[best];
   if (y[best] >= min_score && in_range) {
@@ -415,9 +417,9 @@ tp_status tp_propose(tp_ctx* ctx, tp_mlp* n, int64_t M, int64_t N, int64_t K, in
   }
   if (used_fallback) *used_fallback = 1;
   int32_t found = 0;
-  s = tp_autotune_lookup(ctx, M, N, K, dtype, out, &found);
+  s = tp_autotune_lookup(ctx, M, N, K, dtype, 0, out, &found);
   if (s != TP_OK || found) return s;
-  return tp_autotune(ctx, M, N, K, dtype, 0, out, nullptr, nullptr);
+  return tp_autotune(ctx, M, N, K, dtype, 0, 0, out, nullptr, nullptr);
 }
 
 }  // extern "C"

@@ -6,10 +6,16 @@
    library's forward, backward and Adam kernels), mini-batches drawn in a
    seeded order.
 3. evaluate: on held-out shapes that were tuned exhaustively, the proposal
-   (tp_propose: the arg-max of the MLP's scores over the configs the
-   autotuner would try on the shape) is charged its measured TFLOP/s; regret =
+   (tp_propose: the arg-max of the MLP's scores over the autotuner's
+   single-pass configs) is charged its measured TFLOP/s; regret =
    1 - TFLOP/s(proposal) / TFLOP/s(best). The method without the MLP is a fixed
    default config (the best on average over the training shapes).
+   `retimed_regret` re-times the proposal, the exhaustive pick and the default
+   (median of independent timings), so that regret is not measured against
+   the maximum of one noisy sample per config.
+
+The space is the autotuner's single-pass class: every config in it computes
+C bit-identically, so neither a proposal nor its fallback changes numerics.
 
 Shapes: M, N, K log-uniform on [1, 16384]; K is rounded up to a multiple of 16
 so TMA rows are 16-byte multiples in both BF16 and FP8.
@@ -24,8 +30,8 @@ import torch
 
 import synth
 
-from . import (tp_autotune, tp_autotune_space, tp_mlp_create, tp_mlp_forward, tp_mlp_features, tp_mlp_targets,
-               tp_mlp_train_step)
+from . import (tp_autotune, tp_autotune_space, tp_autotune_time, tp_mlp_create, tp_mlp_forward, tp_mlp_features,
+               tp_mlp_targets, tp_mlp_train_step)
 
 DTYPES = ("bf16", "fp8")
 HIDDEN = 64
@@ -141,6 +147,29 @@ def evaluate(mlp, X, TF, default_index: int, min_score: float = 0.0, prop=None) 
             "mean_regret_default": float(reg_def.mean()),
             "fallback_rate": float(fallback.mean()), "median_regret_with_fallback": float(np.median(reg_fb)),
             "exact_pick_rate": float((reg <= 1e-6).mean()), "shapes": int(len(TF))}
+
+
+def retimed_regret(ctx, shapes, TF, prop, default_index: int, repeats: int = 3) -> dict:
+    """Regret from re-timed configs. For each shape the proposal, the
+    exhaustive pick (arg-max of its table) and the default config are each
+    timed `repeats` times (tp_autotune_time, median); the reference is the
+    fastest of them, so regret = 1 - TFLOP/s(config) / TFLOP/s(reference)."""
+    space = tp_autotune_space("bf16")
+    reg, reg_def, beat = [], [], 0
+    for i, (m, n, k, dt) in enumerate(shapes):
+        best = int(np.argmax(TF[i]))
+        idx = {int(prop[i]), best, int(default_index)}
+        t = {j: tp_autotune_time(ctx, m, n, k, dt, space[j], repeats=repeats) for j in sorted(idx)}
+        ref = max(t.values())
+        reg.append(1.0 - t[int(prop[i])] / ref)
+        reg_def.append(1.0 - t[int(default_index)] / ref)
+        beat += int(t[int(prop[i])] > t[best])
+    reg, reg_def = np.array(reg), np.array(reg_def)
+    return {"median_regret": float(np.median(reg)), "p90_regret": float(np.percentile(reg, 90)),
+            "mean_regret": float(reg.mean()),
+            "median_regret_default": float(np.median(reg_def)), "p90_regret_default": float(np.percentile(reg_def, 90)),
+            "mean_regret_default": float(reg_def.mean()), "repeats": repeats, "shapes": len(shapes),
+            "proposal_faster_than_exhaustive_pick": beat}
 
 
 def default_config(T, V) -> int:
