@@ -370,6 +370,10 @@ static __device__ __align__(256) unsigned int g_noalloc_tile_queue[1];
 void* g_noalloc_queue_addr[kNoallocMaxDevices] = {};
 std::mutex g_noalloc_mu;
 
+// Set-up of a device, on the entry point's first call there: the scratch
+// array's device address, and every kernel instance the entry point can
+// launch loaded now (with lazy module loading a kernel is otherwise loaded
+// at its first launch), so later calls only enqueue work.
 tp_status noalloc_queue_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -377,6 +381,15 @@ tp_status noalloc_queue_address(void** out) {
   if (dev < 0 || dev >= kNoallocMaxDevices) return fail(TP_ERR_UNSUPPORTED, "device index above 63");
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_queue_addr[dev]) {
+    const void* kernels[4] = {reinterpret_cast<const void*>(map_vec_kernel<kMapAxpy, float, false, false>),
+                              reinterpret_cast<const void*>(map_vec_kernel<kMapAxpy, __nv_bfloat16, false, false>),
+                              reinterpret_cast<const void*>(map_generic_kernel<kMapAxpy, float, false>),
+                              reinterpret_cast<const void*>(map_generic_kernel<kMapAxpy, __nv_bfloat16, false>)};
+    for (const void* k : kernels) {
+      cudaFuncAttributes fa;
+      e = cudaFuncGetAttributes(&fa, k);
+      if (e != cudaSuccess) return cuda_fail(e, "loading the queue-mapped axpy kernels");
+    }
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_tile_queue);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the tile-queue scratch");

@@ -95,6 +95,16 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// Prefetch of the box at (c0, c1) from global memory into L2 (no shared
+// memory, no completion to wait for: a hint that turns a later tma_load_2d of
+// the same box into an L2 hit).
+__device__ __forceinline__ void tma_prefetch_l2_2d(const CUtensorMap* map, int32_t c0, int32_t c1) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(c0), "r"(c1)
+               : "memory");
+}
+
 // L2 eviction-priority policies for cache_hint operands.
 __device__ __forceinline__ uint64_t policy_evict_last() {
   uint64_t p;
@@ -319,13 +329,22 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity,
   }
 }
 
-// After a role of this CTA gave up on a bounded wait: pause ~100 us so that
-// TMA copies already issued by either CTA of a pair land before the CTAs
-// retire (the odd CTA's copies complete on the even CTA's barriers, which
-// only the even CTA drains).
+// After a role of this CTA gave up on a bounded wait, before the pair's final
+// cluster barrier: TMA copies issued by either CTA of a pair must land before
+// either CTA retires. The even CTA's producer drains, by bounded waits on its
+// full barriers, every stage it armed; those phases complete only once both
+// CTAs' halves have landed. A copy the odd CTA issued for a stage the even
+// CTA never armed cannot be waited for (it completes on the even CTA's
+// barrier, and mbarrier waits are CTA-local), but the odd CTA only gives up
+// after a bounded wait of its own (its producer on an empty barrier, or its
+// epilogue on an accumulator that never fills), which starts after its last
+// copy was issued. This pause, a minimum of 200 us of wall time on
+// %globaltimer, is the backstop for that path: both CTAs take it before the
+// final cluster barrier, so neither retires within 200 us of giving up.
 __device__ __forceinline__ void settle_after_abort(volatile int* abort) {
-  if (*abort)
-    for (int i = 0; i < 100; ++i) __nanosleep(1000);
+  if (!*abort) return;
+  const uint64_t t0 = global_timer_ns();
+  while (global_timer_ns() - t0 < 200000ull) __nanosleep(1000);
 }
 
 // 64-bit store into a peer CTA's shared memory (shared::cluster address).
