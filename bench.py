@@ -434,7 +434,7 @@ def run_ours(args):
 
     rows = {}
     if not args.skip_rows and rank == 0:
-        rows = secondary_rows(tp, ctx, dev, stream, peaks)
+        rows = secondary_rows(tp, ctx, dev, stream, peaks, args)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.skip_cpu:
@@ -527,7 +527,7 @@ def _graph_time(tp, ctx, stream, record, reps: int, replays: int = 3) -> float:
     return experiments.graph_time_ms(ctx, stream, record, reps, replays)
 
 
-def secondary_rows(tp, ctx, dev, stream, peaks):
+def secondary_rows(tp, ctx, dev, stream, peaks, args):
     """Other hot-path configurations. Each op is captured back to back into
     a CUDA graph and replayed; per-op time = replay time / ops (CUDA events)."""
     import torch
@@ -601,6 +601,8 @@ def secondary_rows(tp, ctx, dev, stream, peaks):
     torch.cuda.empty_cache()
     rows["grouped_64"] = grouped_row(tp, ctx, dev, stream, peaks)
     rows["decode_64"] = decode_row(tp, ctx, dev, stream, peaks)
+    if not args.skip_proposer:
+        rows["proposer"] = proposer_row(tp, ctx, args.train_shapes, args.test_shapes, args.epochs)
     return rows
 
 
@@ -658,10 +660,13 @@ def decode_row(tp, ctx, dev, stream, peaks):
     del layers
     torch.cuda.empty_cache()
     return {"ms_graph_fused": ms_graph, "ms_plain_sync_unfused": ms_plain, "ms_sync_fused": ms_fused_sync,
-            "speedup_vs_plain": ms_plain / ms_graph, "weight_gb": wbytes / 1e9,
+            "speedup_vs_plain": ms_plain / ms_graph, "speedup_vs_sync_fused": ms_fused_sync / ms_graph,
+            "speedup_bound_vs_plain": ms_plain / roof, "weight_gb": wbytes / 1e9,
             "weight_gbs_graph": wbytes / (ms_graph * 1e-3) / 1e9, "roofline_ms": roof,
             "frac_of_roofline": roof / ms_graph, "launches_graph": 2 * L, "launches_plain": 6 * L,
-            "note": "plain = 6 kernels per layer, each launched and synchronised on its own (per-call sync)"}
+            "note": "plain = 6 kernels per layer, each launched and synchronised on its own (per-call sync); "
+                    "speedup_bound_vs_plain = plain time / HBM roofline time, the largest speed-up any "
+                    "implementation streaming the weights once could reach against it"}
 
 
 def grouped_row(tp, ctx, dev, stream, peaks):
@@ -706,8 +711,24 @@ def grouped_row(tp, ctx, dev, stream, peaks):
             tp.tp_gemm(ctx, p, a, b, cfg, async_ex)
         tp.tp_event_wait(ev)
 
+    # plain per-call on each problem's autotuned config (single-pass class)
+    from paper_2606_15991_gb300 import experiments
+
+    tuned = []
+    for (a, b, c), (m, n, k) in zip(probs, shapes):
+        best, _, _ = tp.tp_autotune(ctx, m, n, k, "bf16")
+        p = tp.tp_partition_create(ctx, c, (best.bm, best.bn))
+        tiles = tp.tp_partition_query(p)["num_tiles"]
+        cfg = experiments.tuned_config(ctx, best, tiles)
+        tp.tp_partition_map(p, tp.MAP_STRIDED, cfg.num_programs)
+        tuned.append((p, cfg))
+
+    def tuned_sync():
+        for (a, b, c), (p, cfg) in zip(probs, tuned):
+            tp.tp_gemm(ctx, p, a, b, cfg, sync_ex)
+
     res = {}
-    for name, fn in (("plain_sync", plain_sync), ("plain_chained", plain_chained)):
+    for name, fn in (("plain_sync", plain_sync), ("plain_chained", plain_chained), ("tuned_sync", tuned_sync)):
         fn()
         torch.cuda.synchronize()
         ts = []
@@ -717,46 +738,58 @@ def grouped_row(tp, ctx, dev, stream, peaks):
             torch.cuda.synchronize()
             ts.append((time.perf_counter() - t0) * 1e3)
         res[name] = min(ts)
-    for p, _ in parts:
+    for p, _ in parts + tuned:
         tp.tp_partition_destroy(p)
     tp.tp_event_destroy(ev)
     tp.tp_grouped_plan_destroy(plan)
-    t_roof = sum(max(2.0 * m * n * k / (peaks["bf16_tflops"] * 1e12),
-                     2.0 * (m * k + k * n + m * n) / (peaks["hbm_gbs"] * 1e9)) for m, n, k in shapes) * 1e3
+    # overlap roofline: the launch can overlap HBM-bound and tensor-bound
+    # tiles, so its bound is max(total flops / tensor peak, total bytes / HBM
+    # peak); the sum of per-problem bounds (no overlap) is kept beside it
+    t_overlap = max(flops / (peaks["bf16_tflops"] * 1e12), bytes_ / (peaks["hbm_gbs"] * 1e9)) * 1e3
+    sust = peaks.get("bf16_tflops_sustained") or peaks["bf16_tflops"]
+    t_overlap_sust = max(flops / (sust * 1e12), bytes_ / (peaks["hbm_gbs"] * 1e9)) * 1e3
+    t_sum = sum(max(2.0 * m * n * k / (peaks["bf16_tflops"] * 1e12),
+                    2.0 * (m * k + k * n + m * n) / (peaks["hbm_gbs"] * 1e9)) for m, n, k in shapes) * 1e3
     del probs
     torch.cuda.empty_cache()
     return {"ms_grouped": ms_grouped, "ms_plain_sync": res["plain_sync"], "ms_plain_chained": res["plain_chained"],
+            "ms_tuned_sync": res["tuned_sync"],
             "speedup_vs_plain_sync": res["plain_sync"] / ms_grouped,
             "speedup_vs_plain_chained": res["plain_chained"] / ms_grouped,
+            "speedup_vs_tuned_sync": res["tuned_sync"] / ms_grouped,
             "tflops_grouped": flops / (ms_grouped * 1e-3) / 1e12, "gflop": flops / 1e9, "gbytes": bytes_ / 1e9,
             "tiles": total_tiles, "swapped_problems": int(sum(swapped)),
-            "roofline_ms": t_roof, "frac_of_roofline": t_roof / ms_grouped,
-            "note": "roofline = sum over problems of max(flops / bf16 peak, bytes / HBM peak), measured peaks"}
+            "roofline_ms": t_overlap, "frac_of_roofline": t_overlap / ms_grouped,
+            "roofline_peaks": f"{peaks['src']}: bf16 burst {peaks['bf16_tflops']} TFLOP/s, HBM {peaks['hbm_gbs']} GB/s",
+            "roofline_ms_sustained": t_overlap_sust, "frac_of_roofline_sustained": t_overlap_sust / ms_grouped,
+            "roofline_ms_per_problem_sum": t_sum, "frac_of_per_problem_sum": t_sum / ms_grouped,
+            "note": "roofline = max(sum flops / bf16 peak, sum bytes / HBM peak) over the group (the launch overlaps "
+                    "HBM-bound swap-AB tiles with tensor-bound tiles); _sustained uses the sustained bf16 peak; "
+                    "per_problem_sum = sum over problems of max(flops / bf16 peak, bytes / HBM peak); "
+                    "plain = one tp_gemm per problem on (128|256) x 256 tiles, group_m 8; tuned = one tp_gemm per "
+                    "problem on its autotuned config; _sync = each call synchronised"}
 
 
-def run_proposer(args):
-    """The learned-proposer experiment: ~21k autotuner measurements (625
-    shapes x 37 configs, BF16 and FP8, less the split-K configs a shape's
-    tiles rule out) for training, 2000 held-out shapes tuned exhaustively for
-    evaluation, proposals made by tp_propose; prints one JSON line."""
+def proposer_row(tp, ctx, train_n: int, test_n: int, epochs: int, log=None) -> dict:
+    """The learned-proposer experiment: exhaustive tables of `train_n` shapes
+    (BF16 and FP8, x 32 single-pass configs: ~20k autotuner measurements at
+    625 shapes) for training on the GPU, `test_n` held-out shapes tuned
+    exhaustively as the judge, proposals made by tp_propose. Regret is
+    reported twice: against the judge's one timing per config, and with the
+    proposal, the exhaustive pick and the fixed default re-timed (median of 3
+    independent timings each) so that the reference is not the maximum of
+    noisy samples."""
     import numpy as np
-    import torch
 
-    from paper_2606_15991_gb300 import build as _build
-
-    _build.build()
-    import paper_2606_15991_gb300 as tp
     from paper_2606_15991_gb300 import proposer
 
-    ctx = tp.tp_ctx_create(0)
-    log = (lambda m: print(m, file=sys.stderr, flush=True))
-    train_shapes = proposer.sample_shapes(args.train_shapes, seed=1)
-    test_shapes = proposer.sample_shapes(args.test_shapes, seed=2)
+    train_shapes = proposer.sample_shapes(train_n, seed=1)
+    test_shapes = proposer.sample_shapes(test_n, seed=2)
     t0 = time.perf_counter()
     X, T, V, TF = proposer.collect(ctx, train_shapes, log=log)
     t_collect = time.perf_counter() - t0
     t0 = time.perf_counter()
-    mlp, hist = proposer.train(ctx, X, T, V, epochs=args.epochs, batch=256, lr=3e-3, log=log)
+    mlp, hist = proposer.train(ctx, X, T, V, epochs=epochs, batch=256, lr=3e-3, log=log)
     t_train = time.perf_counter() - t0
     t0 = time.perf_counter()
     Xt, Tt, Vt, TFt = proposer.collect(ctx, test_shapes, log=log)
@@ -766,22 +799,38 @@ def run_proposer(args):
     prop = proposer.propose_indices(ctx, mlp, test_shapes)
     t_prop = (time.perf_counter() - t0) / len(test_shapes)
     r = proposer.evaluate(mlp, Xt, TFt, dflt, prop=prop)
-    r_argmax = proposer.evaluate(mlp, Xt, TFt, dflt)
+    t0 = time.perf_counter()
+    rt = proposer.retimed_regret(ctx, test_shapes, TFt, prop, dflt, repeats=3)
+    t_retime = time.perf_counter() - t0
     big = np.array([m * n * k >= 2 ** 33 for m, n, k, _ in test_shapes])
     reg = 1 - TFt[np.arange(len(TFt)), prop] / TFt.max(1)
     reg_d = 1 - TFt[:, dflt] / TFt.max(1)
     space = tp.tp_autotune_space("bf16")
-    print(json.dumps({
-        "case": "learned tile proposer", "train_shapes": len(train_shapes),
-        "train_measurements": int(V.sum()), "test_shapes": len(test_shapes), "configs": int(T.shape[1]),
-        **r, "median_regret_plain_argmax": r_argmax["median_regret"], "mean_regret_plain_argmax": r_argmax["mean_regret"],
+    tp.tp_mlp_destroy(mlp)
+    return {
+        "space": "single-pass configs (bit-identical C; split-K excluded)", "configs": int(T.shape[1]),
+        "train_shapes": len(train_shapes), "train_measurements": int(V.sum()), "test_shapes": len(test_shapes),
+        "judge_single_timing": r, "retimed_median_of_3": rt,
         "default_config": {n: getattr(space[dflt], n) for n in ("bm", "bn", "stages", "group_m", "split_k")},
         "large_shapes": int(big.sum()),
         "large_mean_regret": float(reg[big].mean()) if big.any() else None,
         "large_mean_regret_default": float(reg_d[big].mean()) if big.any() else None,
         "ms_exhaustive_per_shape": t_exh * 1e3, "ms_propose_per_shape": t_prop * 1e3,
         "tuning_time_saved_x": t_exh / t_prop, "loss_first_last": [hist[0], hist[-1]],
-        "s_collect_train": t_collect, "s_train": t_train}))
+        "s_collect_train": t_collect, "s_train": t_train, "s_retime": t_retime}
+
+
+def run_proposer(args):
+    """The learned-proposer experiment alone; prints one JSON line."""
+    from paper_2606_15991_gb300 import build as _build
+
+    _build.build()
+    import paper_2606_15991_gb300 as tp
+
+    ctx = tp.tp_ctx_create(0)
+    log = (lambda m: print(m, file=sys.stderr, flush=True))
+    print(json.dumps({"case": "learned tile proposer",
+                      **proposer_row(tp, ctx, args.train_shapes, args.test_shapes, args.epochs, log)}))
 
 
 def run_exec_modes(args):
@@ -957,6 +1006,7 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-rows", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-proposer", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--case", default="maps", choices=["maps", "proposer", "kernel", "exec_modes", "gemm_sweep", "bimodal"],
                     help="maps: the benchmark step (default); proposer: the learned-proposer experiment; "
