@@ -147,9 +147,10 @@ def test_autotune_table_cache_and_numerics(ctx, dtype, tmp_path):
 
 @pytest.fixture(scope="module")
 def trained(ctx):
-    """A proposer trained on 384 exhaustively tuned shapes (both dtypes,
-    dimensions up to 8192), with its training tables."""
-    shapes = proposer.sample_shapes(384, seed=1, hi=8192)
+    """A proposer trained on 512 exhaustively tuned shapes (both dtypes,
+    dimensions log-uniform on [1, 16384], the benchmark's range), with its
+    training tables."""
+    shapes = proposer.sample_shapes(512, seed=1)
     X, T, V, TF = proposer.collect(ctx, shapes)
     mlp, hist = proposer.train(ctx, X, T, V, epochs=400, batch=64, lr=3e-3)
     yield mlp, hist, T, V
@@ -157,19 +158,20 @@ def trained(ctx):
 
 
 def test_small_end_to_end_gain(ctx, trained):
-    """Evaluate the trained proposer on 160 held-out shapes. It must reach the
-    stated median regret (<= 5% of the exhaustive best) and lose less than the
-    same network untrained. Against the best fixed config (the method
-    without it: the config with the best mean relative speed over the
-    training shapes) it must lose less in mean and in p90 regret, with the
+    """Evaluate the trained proposer on 200 held-out shapes of the same range.
+    It must reach the stated median regret (<= 5% of the exhaustive best) and
+    lose less than the same network untrained. Against the best fixed config
+    (the method without it: the config with the best mean relative speed over
+    the training shapes) it must lose less in mean and in p90 regret, with the
     proposal, the exhaustive pick and the default re-timed (median of 3
-    timings) so that one noisy sample decides nothing. It must also choose a
-    config far faster than exhaustive tuning of the shape."""
+    timings) so that one noisy sample decides nothing; the single-pass
+    configs differ most on large shapes, where the fixed config loses most.
+    It must also choose a config far faster than exhaustive tuning."""
     import time
 
     mlp, hist, T, V = trained
     assert hist[-1] < 0.5 * hist[0]
-    test_shapes = proposer.sample_shapes(160, seed=2, hi=8192)
+    test_shapes = proposer.sample_shapes(200, seed=2)
     t0 = time.perf_counter()
     Xt, Tt, Vt, TFt = proposer.collect(ctx, test_shapes)
     t_exhaustive = (time.perf_counter() - t0) / len(test_shapes)
