@@ -10,6 +10,13 @@
 // the MMA's N (rounded up to 32). Its tile is a 128-column slab of C; one pass
 // streams the matching 128 rows of B_i from HBM exactly once.
 //
+// On CTA pairs, a larger problem whose last 256-row band is partial (M mod
+// 256 <= 192) runs that band the same way: its tail rows become a swap
+// problem of their own (A, C and the write counts offset to the band's first
+// row), whose tile for column slab j is queued right after the normal tiles
+// of column j, while their B slab is still in L2. The tail then costs MMA
+// columns for its rows rounded up to 32 instead of a full 256-row tile.
+//
 // Roles per CTA (192 threads): warp 0 dequeues slots, publishes them through
 // a 4-entry shared-memory ring and streams the tile's K slices with TMA;
 // warp 1 issues tcgen05.mma into two TMEM accumulators; warps 2-5 drain TMEM
@@ -41,6 +48,7 @@ struct alignas(64) GroupedProblem {
   int32_t tile_rows;      // 128 (one CTA) or 256 (CTA pair), MMA orientation
   int32_t box_y;          // rows of the MMA B operand each CTA loads per stage
   int32_t c_tma;          // 1: normal orientation with 16-byte aligned C rows (map_c is valid)
+  int32_t stream_x;       // swap tile whose B slab no other tile reads (loaded evict-first)
 };
 
 }  // namespace tp
@@ -75,6 +83,12 @@ template <bool kPair> struct Ring {
 };
 constexpr size_t kWordsBytes = 8 + 8 * kRing;
 constexpr uint32_t kStageC = 4u * 2u * 4096u;  // epilogue staging: 4 warps x 2 buffers x (32 rows x 128 B)
+// Longest partial last 256-row band of a normal problem that CTA pairs run
+// as a swap-AB tail (0 = never)
+#ifndef TP_GROUPED_TAIL_MAX
+#define TP_GROUPED_TAIL_MAX 192
+#endif
+constexpr int64_t kTailMax = TP_GROUPED_TAIL_MAX;
 
 struct GroupedArgs {
   const GroupedProblem* probs;
@@ -212,8 +226,8 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
         for (int64_t kb = 0; kb < nk; ++kb) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err)) { ok = false; break; }
           const int32_t kc = (int32_t)(kb * 64);
-          // swap: x = B_i slab (read once), y = A_i (reused by every tile)
-          const uint64_t px = pr->swap ? pol_stream : pol_keep;
+          // streamed swap: x = B_i slab (read once), y = A_i (reused by every tile)
+          const uint64_t px = pr->stream_x ? pol_stream : pol_keep;
           if constexpr (kPair) {
             const uint32_t fb = mapa(full_bar(stage), 0);  // both halves complete on the even CTA's barrier
             if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * tx);
@@ -469,7 +483,11 @@ tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int3
     if (ctx->capturing) return fail(TP_ERR_CAPTURE, "a plan allocates device memory: build it before capture");
   }
   std::vector<GroupedProblem> host(n);
+  host.reserve(2 * (size_t)n);  // tails are appended: no reallocation under the references below
   std::vector<double> cost(n);
+  // tails[j] = (parent problem, table entry); tail entries follow the n
+  // problems in the device table
+  std::vector<std::pair<int, int>> tails;
   auto* plan = new tp_grouped_plan();
   plan->ctx = ctx;
   plan->n = n;
@@ -478,6 +496,24 @@ tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int3
   auto cleanup = [&](tp_status s) {
     for (auto* q : plan->outs) tp_partition_destroy(q);
     delete plan;
+    return s;
+  };
+  // a swap-orientation entry: C rows [0, M) of `c` (row stride N) from A rows
+  // of `a` (row stride lda) and B (N x K, row stride ldb)
+  auto make_swap = [&](GroupedProblem& g, const void* a, const void* b, void* c, int64_t M, int64_t N, int64_t K,
+                       int64_t lda, int64_t ldb) {
+    g.c = static_cast<__nv_bfloat16*>(c);
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.swap = 1;
+    g.tile_rows = trows;
+    g.bn = (int32_t)(((M + 31) / 32) * 32);
+    g.box_y = plan->pair ? g.bn / 2 : g.bn;
+    g.tiles_r = (N + trows - 1) / trows;
+    g.tiles_c = 1;
+    tp_status s = kmajor_map(&g.map_x, b, N, K, ldb, 128);
+    if (s == TP_OK) s = kmajor_map(&g.map_y, a, M, K, lda, g.box_y);
     return s;
   };
   int64_t elems = 0;
@@ -499,41 +535,54 @@ tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int3
       return cleanup(fail(TP_ERR_ALIGN, "TMA needs 16-byte aligned bases and row strides (K % 8 == 0)"));
     GroupedProblem& g = host[i];
     std::memset(&g, 0, sizeof(g));
-    g.c = static_cast<__nv_bfloat16*>(c.ptr);
-    g.M = M;
-    g.N = N;
-    g.K = K;
-    g.swap = M <= swap_max_m ? 1 : 0;
     tp_status s;
     int64_t tile_rows, tile_cols;
-    g.tile_rows = trows;
-    if (g.swap) {
-      g.bn = (int32_t)(((M + 31) / 32) * 32);
-      g.box_y = plan->pair ? g.bn / 2 : g.bn;
-      g.tiles_r = (N + trows - 1) / trows;
-      g.tiles_c = 1;
-      s = kmajor_map(&g.map_x, b.ptr, N, K, ldb, 128);
-      if (s == TP_OK) s = kmajor_map(&g.map_y, a.ptr, M, K, lda, g.box_y);
+    if (M <= swap_max_m) {
+      s = make_swap(g, a.ptr, b.ptr, c.ptr, M, N, K, lda, ldb);
+      g.stream_x = 1;
       tile_rows = M;
       tile_cols = trows;
       cost[i] = trows * (double)K * 2.0 / 44e9 + 2.0 * trows * g.bn * K / 1.2e13;
     } else {
+      // on CTA pairs, a partial last band of at most 192 rows runs as a swap
+      // tail (below); the normal tiles cover the whole bands above it
+      const int64_t tail = plan->pair ? M % 256 : 0;
+      const bool split = tail > 0 && tail <= kTailMax;
+      const int64_t M0 = split ? M - tail : M;
+      g.c = static_cast<__nv_bfloat16*>(c.ptr);
+      g.M = M0;
+      g.N = N;
+      g.K = K;
+      g.swap = 0;
+      g.tile_rows = trows;
       g.bn = 256;
       g.box_y = plan->pair ? 128 : 256;
-      g.tiles_r = (M + trows - 1) / trows;
+      g.tiles_r = (M0 + trows - 1) / trows;
       g.tiles_c = (N + 255) / 256;
-      s = kmajor_map(&g.map_x, a.ptr, M, K, lda, 128);
+      s = kmajor_map(&g.map_x, a.ptr, M0, K, lda, 128);
       if (s == TP_OK) s = kmajor_map(&g.map_y, b.ptr, N, K, ldb, g.box_y);
       if (s == TP_OK && N % 8 == 0 && ((uintptr_t)c.ptr & 15) == 0) {
-        s = c_map(&g.map_c, c.ptr, M, N);
+        s = c_map(&g.map_c, c.ptr, M0, N);
         g.c_tma = 1;
       }
       tile_rows = trows;
       tile_cols = 256;
       cost[i] = 2.0 * trows * 256 * (double)K / (plan->pair ? 2.4e13 : 1.2e13);
+      if (s == TP_OK && split) {
+        GroupedProblem t;
+        std::memset(&t, 0, sizeof(t));
+        const char* a_tail = static_cast<const char*>(a.ptr) + M0 * lda * 2;
+        char* c_tail = static_cast<char*>(c.ptr) + M0 * N * 2;
+        s = make_swap(t, a_tail, b.ptr, c_tail, tail, N, K, lda, ldb);
+        t.stream_x = 0;  // its B slab was just read by the normal tiles of that column
+        t.count_base = elems + M0 * N;
+        tails.push_back({i, (int)(n + tails.size())});
+        host.push_back(t);
+        cost.push_back(2.0 * trows * t.bn * (double)K / 2.4e13);
+      }
     }
     if (s != TP_OK) return cleanup(s);
-    g.count_base = elems;
+    host[i].count_base = elems;
     elems += M * N;
     tp_partition* part = nullptr;
     int64_t tile[2] = {tile_rows, tile_cols};
@@ -548,19 +597,28 @@ tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int3
     plan->ins.push_back(a);
     plan->ins.push_back(b);
   }
+  std::vector<int> tail_of(n, -1);
+  for (auto& t : tails) tail_of[t.first] = t.second;
   // Queue order. Tiles of swapped problems stream B from HBM, the others are
   // tensor-core bound; each stream is ordered most expensive problem first
   // (longest processing time first) and the two are merged in proportion to
   // their total cost, so that tiles running at the same time use both HBM
-  // and the tensor cores.
+  // and the tensor cores. A normal problem's tiles go column by column, each
+  // column followed by its tail tile.
   std::vector<int> mem_p, comp_p;
   for (int i = 0; i < n; ++i) (host[i].swap ? mem_p : comp_p).push_back(i);
   auto by_cost = [&](int x, int y) { return cost[x] > cost[y]; };
   std::stable_sort(mem_p.begin(), mem_p.end(), by_cost);
   std::stable_sort(comp_p.begin(), comp_p.end(), by_cost);
   auto expand = [&](const std::vector<int>& ps, std::vector<std::pair<int64_t, double>>& out) {
-    for (int i : ps)
-      for (int64_t t = 0; t < host[i].tiles_r * host[i].tiles_c; ++t) out.push_back({((int64_t)i << 32) | t, cost[i]});
+    for (int i : ps) {
+      const GroupedProblem& g = host[i];
+      for (int64_t tc = 0; tc < g.tiles_c; ++tc) {
+        for (int64_t tr = 0; tr < g.tiles_r; ++tr) out.push_back({((int64_t)i << 32) | (tc * g.tiles_r + tr), cost[i]});
+        const int t = tail_of[i];
+        if (t >= 0) out.push_back({((int64_t)t << 32) | tc, cost[t]});
+      }
+    }
   };
   std::vector<std::pair<int64_t, double>> mem_t, comp_t;
   expand(mem_p, mem_t);
@@ -590,9 +648,9 @@ tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int3
   plan->total_tiles = slot;
   plan->total_elems = elems;
   if (slot >= (int64_t(1) << 31)) return cleanup(fail(TP_ERR_UNSUPPORTED, "more than 2^31 tiles in a group"));
-  cudaError_t e = cudaMalloc(&plan->d_probs, sizeof(GroupedProblem) * n);
+  cudaError_t e = cudaMalloc(&plan->d_probs, sizeof(GroupedProblem) * ordered.size());
   if (e == cudaSuccess)
-    e = cudaMemcpy(plan->d_probs, ordered.data(), sizeof(GroupedProblem) * n, cudaMemcpyHostToDevice);
+    e = cudaMemcpy(plan->d_probs, ordered.data(), sizeof(GroupedProblem) * ordered.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&plan->d_slots, sizeof(int64_t) * std::max<int64_t>(slot, 1));
   if (e == cudaSuccess)
     e = cudaMemcpy(plan->d_slots, slots.data(), sizeof(int64_t) * slot, cudaMemcpyHostToDevice);

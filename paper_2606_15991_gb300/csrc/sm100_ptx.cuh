@@ -95,16 +95,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-// Prefetch of the box at (c0, c1) from global memory into L2 (no shared
-// memory, no completion to wait for: a hint that turns a later tma_load_2d of
-// the same box into an L2 hit).
-__device__ __forceinline__ void tma_prefetch_l2_2d(const CUtensorMap* map, int32_t c0, int32_t c1) {
-  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
-                   reinterpret_cast<uint64_t>(map)),
-               "r"(c0), "r"(c1)
-               : "memory");
-}
-
 // L2 eviction-priority policies for cache_hint operands.
 __device__ __forceinline__ uint64_t policy_evict_last() {
   uint64_t p;

@@ -1,6 +1,7 @@
 """GPU parity of the grouped persistent BF16 GEMM (one launch, device tile
-queue, swap-AB for small M) against the FP64 oracle, and queue coverage
-(every element of every C_i written exactly once)."""
+queue, swap-AB for small M and for the partial last band of larger M on CTA
+pairs) against the FP64 oracle, and queue coverage (every element of every
+C_i written exactly once)."""
 import numpy as np
 import pytest
 import torch
@@ -14,8 +15,11 @@ from oracle import partition as opart
 
 pytestmark = pytest.mark.gpu
 
+# (257, ...), (300, ...) and (448, ...) have a partial last 256-row band of
+# at most 192 rows, which CTA pairs run as a swap-AB tail; (449, ...) and
+# (1000, ...) have longer partial bands, run as normal tiles
 SMALL = [(1, 300, 64), (17, 128, 136), (256, 520, 72), (257, 384, 128), (300, 1000, 200), (64, 96, 4104),
-         (33, 2048, 512), (1000, 256, 64)]
+         (33, 2048, 512), (1000, 256, 64), (448, 600, 96), (449, 520, 64)]
 
 
 def _problems(shapes, kind="normal", seed=0):
