@@ -772,8 +772,8 @@ def grouped_row(tp, ctx, dev, stream, peaks):
 
 def proposer_row(tp, ctx, train_n: int, test_n: int, epochs: int, log=None) -> dict:
     """The learned-proposer experiment: exhaustive tables of `train_n` shapes
-    (BF16 and FP8, x 32 single-pass configs: ~20k autotuner measurements at
-    625 shapes) for training on the GPU, `test_n` held-out shapes tuned
+    (BF16 and FP8, x 48 single-pass configs: ~20k autotuner measurements at
+    417 shapes) for training on the GPU, `test_n` held-out shapes tuned
     exhaustively as the judge, proposals made by tp_propose. Regret is
     reported twice: against the judge's one timing per config, and with the
     proposal, the exhaustive pick and the fixed default re-timed (median of 3
@@ -1019,7 +1019,7 @@ def main():
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--elements", type=int, default=1 << 26)
     ap.add_argument("--group", type=int, default=8)
-    ap.add_argument("--train-shapes", type=int, default=625)
+    ap.add_argument("--train-shapes", type=int, default=417)
     ap.add_argument("--test-shapes", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=600)
     ap.add_argument("--reps", type=int, default=30)

@@ -114,7 +114,7 @@ enum {
    * device errors (SYNC: on return; ASYNC: from tp_event_query /
    * tp_event_wait; graph: from a SYNC replay or the replay's event).
    * Supported by the element-wise maps (tp_map_*), by tp_gemm and
-   * tp_gemm_fp8 on the tensor-core path (tiles of 128 or 256 rows) and by
+   * tp_gemm_fp8 on the tensor-core path (tiles of 64, 128 or 256 rows) and by
    * tp_permute_heads_unchecked, up to 2^23 tiles per launch; other
    * operations return TP_ERR_UNSUPPORTED when it is set. The
    * bitmap and its finished-claimant counter are one per context: checked
@@ -159,7 +159,8 @@ typedef struct tp_partition_info {
 
 /* GEMM tile configuration (§5.1: tile shapes tuned per size). 0 = default. */
 typedef struct tp_gemm_config {
-  int32_t bm;          /* 128 (one CTA) or 256 (CTA pair, cta_group::2)        */
+  int32_t bm;          /* tensor-core GEMM: 64 or 128 (one CTA), or 256 (CTA
+                        * pair, cta_group::2); SIMT GEMM: 64                   */
   int32_t bn;          /* 32..256, multiple of 32 (tensor-core paths)          */
   int32_t bk;          /* K per stage: 64 (bf16) / 128 (fp8); SIMT: 8/16/32     */
   int32_t stages;      /* shared-memory ring depth                              */
@@ -337,7 +338,10 @@ tp_status tp_permute_heads_unchecked(tp_ctx* ctx, void* dst, const void* src, in
  *   M x K) and B K-major (stored N x K); base addresses 16-byte aligned and
  *   K a multiple of 8 (TMA rows are 16-byte multiples), else TP_ERR_ALIGN.
  *   FP32 accumulation in tensor memory; C rounded to bf16 (nearest even).
- *   c's tile must be (cfg.bm, cfg.bn) or (128, bn) for the default config.
+ *   Tiles of 64 or 128 rows run on one CTA (64: tcgen05 M = 64, for short
+ *   M), 256 rows on a CTA pair; columns 32..256, a multiple of 32 (64 for
+ *   256 rows). c's tile must be (cfg.bm, cfg.bn) or (128, bn) for the
+ *   default config.
  * cfg may be NULL (defaults). The partition may be plain or mapped
  * (TP_MAP_STRIDED: persistent programs). Errors: TP_ERR_SHAPE, TP_ERR_ALIGN,
  * TP_ERR_ALIAS, TP_ERR_BUSY, TP_ERR_UNSUPPORTED, TP_ERR_TIMEOUT, TP_ERR_CUDA. */
@@ -345,7 +349,8 @@ tp_status tp_gemm(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_ten
                   const tp_gemm_config* cfg, const tp_exec* ex);
 
 /* How many programs of the tensor-core GEMM can be resident on the device at
- * once for `cfg` (bm 128 or 256, bn, stages; 0 fields take the defaults): CTA pairs for 256-row tiles, CTAs for 128-row tiles. A
+ * once for `cfg` (bm 64, 128 or 256, bn, stages; 0 fields take the
+ * defaults): CTA pairs for 256-row tiles, CTAs otherwise. A
  * persistent launch with more programs than this runs the extra ones after
  * others finish. With split_k > 1 the count is of split programs (clusters
  * of split_k CTAs). Errors: TP_ERR_INVALID, TP_ERR_UNSUPPORTED, TP_ERR_CUDA. */
@@ -354,7 +359,7 @@ tp_status tp_gemm_resident_programs(tp_ctx* ctx, const tp_gemm_config* cfg, int3
 /* The BF16 tensor-core GEMM against a raw output pointer: the unchecked
  * baseline of §5.1 (the same schedule with manual raw-pointer output access).
  * `c` is a contiguous BF16 M x N device buffer; A and B as for tp_gemm.
- * cfg->bm (128 or 256) and cfg->bn give the tile; cfg->num_programs > 0
+ * cfg->bm (64, 128 or 256) and cfg->bn give the tile; cfg->num_programs > 0
  * maps tiles strided over that many programs (CTA pairs for bm = 256), 0
  * launches one program per tile; cfg->stages and cfg->group_m as for tp_gemm.
  * No partition is involved: nothing is checked against aliasing or work in
@@ -469,11 +474,11 @@ enum {
   TP_TUNE_SPLIT_K = 1  /* also search the split-K configs (changes C's rounding) */
 };
 /* The space (same order on every call; with flags = 0, index i is the MLP
- * proposer's output i): tile rows {128 (one CTA), 256 (CTA pair)} x tile
- * columns {64, 128, 192, 256} x stages {3, max} x raster bands {1, 8}, the 32
+ * proposer's output i): tile rows {64, 128 (one CTA), 256 (CTA pair)} x tile
+ * columns {64, 128, 192, 256} x stages {3, max} x raster bands {1, 8}, the 48
  * single-pass configs; with TP_TUNE_SPLIT_K followed by the split-K programs
  * of 128-row tiles: (bn 128, split_k 2 / 4) and (bn 256, split_k 2 / 4 / 8),
- * 37 configs. Writes up to `cap` configs to `out` (may be NULL) and the size
+ * 53 configs. Writes up to `cap` configs to `out` (may be NULL) and the size
  * to *count. Errors: TP_ERR_INVALID (undefined flag bits), TP_ERR_UNSUPPORTED
  * (dtype). */
 tp_status tp_autotune_space(int32_t dtype, int32_t flags, tp_gemm_config* out, int32_t cap, int32_t* count);

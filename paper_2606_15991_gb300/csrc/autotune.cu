@@ -58,7 +58,7 @@ TuneState* state(tp_ctx* ctx) {
 // the split-K configs.
 std::vector<tp_gemm_config> space(int32_t flags) {
   std::vector<tp_gemm_config> v;
-  for (int bm : {128, 256})
+  for (int bm : {64, 128, 256})
     for (int bn : {64, 128, 192, 256})
       for (int stages : {3, 0})
         for (int gm : {1, 8}) {
@@ -225,7 +225,7 @@ tp_status time_config(tp_ctx* ctx, TuneState* st, const TuneProblem& pb, const t
   part.grid[0] = (pb.M + c.bm - 1) / c.bm;
   part.grid[1] = (pb.N + c.bn - 1) / c.bn;
   part.num_tiles = part.grid[0] * part.grid[1];
-  const int64_t cap = (int64_t)ctx->sm_count * 128 / c.bm;
+  const int64_t cap = c.bm == 256 ? ctx->sm_count / 2 : ctx->sm_count;  // CTA pairs, or CTAs
   part.kind = TP_MAP_STRIDED;
   part.num_programs = std::min<int64_t>(part.num_tiles, cap);
   if (c.num_programs > 0) part.num_programs = std::min<int64_t>(part.num_tiles, c.num_programs);

@@ -1,8 +1,8 @@
 // Tensor-core GEMM for sm_103a: C (bf16) = A . B with BF16 (kind::f16) or
 // FP8-E4M3 (kind::f8f6f4) operands and FP32 accumulation in TMEM.
 //
-// One output tile of 128 x BN (one CTA) or 256 x BN (a CTA pair running
-// cta_group::2 MMAs) per tile program step, with a K loop (§3.6, Listing 6:
+// One output tile of 64 x BN or 128 x BN (one CTA) or 256 x BN (a CTA pair
+// running cta_group::2 MMAs) per tile program step, with a K loop (§3.6, Listing 6:
 // the program walks its mapped sequence of output tiles and, for each,
 // accumulates mma over the K tiles). On a strided map the tiles of the last,
 // partial round may be cut along N into narrow tiles for programs that would
@@ -17,7 +17,9 @@
 //   warp 1   MMA issuer: one thread issues tcgen05.mma into one of two TMEM
 //            accumulators and commits each consumed stage back to the producer;
 //   warps 2-5 epilogue: tcgen05.ld the finished accumulator (each warp owns the
-//            32 TMEM lanes = tile rows its warp index selects), scale, round to
+//            32 TMEM lanes its warp index selects: tile rows 32q..32q+31 of a
+//            128-row MMA, or in lanes 0-15 rows 16q..16q+15 of a 64-row MMA,
+//            whose D rows occupy lanes 32(r/16) + r%16), scale, round to
 //            bf16 and store only inside this program's tile (32 x 64 blocks,
 //            or 32 x 32 for an odd last chunk, staged in shared memory and
 //            written by TMA stores, or per-row stores when C rows are not
@@ -45,12 +47,13 @@ using namespace sm100;
 
 constexpr int BM = 128;
 constexpr int kThreads = 192;
-constexpr int kMaxStages = 8;
+constexpr int kMaxStages = 16;
 constexpr uint32_t kStageC = 4u * 2u * 4096u;  // epilogue staging: 4 warps x 2 buffers x (32 rows x 128 B)
 
 struct TcArgs {
   int64_t M, N, K;
   int32_t gm, gn;       // tile grid (gm * gn < 2^31)
+  int32_t rows;         // tile rows of one CTA: 64 or 128 (a CTA pair: 128 each, 256 per tile)
   int32_t bn;           // tile columns (32..256, multiple of 32)
   int32_t stages;
   int32_t kind;         // tp_map_kind (IDENTITY or STRIDED)
@@ -146,24 +149,24 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int32_t csize = kPair ? 2 : S;
   const int32_t prog = (int32_t)blockIdx.x / csize;
   const int32_t nprog = (int32_t)gridDim.x / csize;
-  const int tile_m = kPair ? 2 * BM : BM;
+  const int tile_m = kPair ? 2 * BM : p.rows;
   const int b_rows = kPair ? p.bn / 2 : p.bn;
-  const uint32_t a_stage = BM * 128;
+  const uint32_t a_stage = (uint32_t)(kPair ? BM : p.rows) * 128;
   const uint32_t b_stage = (uint32_t)b_rows * 128;
   const uint32_t a0 = base;
   const uint32_t b0 = base + a_stage * p.stages;
   const uint32_t cst = base + (uint32_t)p.body_bytes;           // epilogue staging
   const uint32_t bars = cst + (p.stage_c ? kStageC : 0u);
-  // barrier block: full[8], empty[8], tfull[2], tempty[2], drain, two
+  // barrier block: full[16], empty[16], tfull[2], tempty[2], drain, two
   // words, recv (split-K)
   auto full_bar = [&](int s) { return bars + 8u * s; };
-  auto empty_bar = [&](int s) { return bars + 64u + 8u * s; };
-  auto tfull_bar = [&](int b) { return bars + 128u + 8u * b; };
-  auto tempty_bar = [&](int b) { return bars + 144u + 8u * b; };
-  const uint32_t drain_bar = bars + 160u;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + (bars - base) + 168u);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + (bars - base) + 172u);
-  const uint32_t recv_bar = bars + 176u;
+  auto empty_bar = [&](int s) { return bars + 128u + 8u * s; };
+  auto tfull_bar = [&](int b) { return bars + 256u + 8u * b; };
+  auto tempty_bar = [&](int b) { return bars + 272u + 8u * b; };
+  const uint32_t drain_bar = bars + 288u;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + (bars - base) + 296u);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + (bars - base) + 300u);
+  const uint32_t recv_bar = bars + 304u;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) {
@@ -318,7 +321,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   // ------------------------------------------------------------ epilogue
   // (warps 2..5 -> TMEM lane quadrants 2,3,0,1)
   const int quad = warp & 3;
-  const int32_t warp_row0 = (int32_t)rank * BM + quad * 32;  // first tile row of this warp
+  // rows of this warp: 32 of a 128-row MMA, 16 (in lanes 0-15) of a 64-row one
+  const int wrows = (kPair || p.rows == BM) ? 32 : 16;
+  const int32_t warp_row0 = (int32_t)rank * BM + quad * wrows;  // first tile row of this warp
   const uint32_t tlane = (uint32_t)(quad * 32) << 16;         // TMEM lane offset of this warp
   // FP8 dequantisation factor 1 / (s_A * s_B), both steps in fp32
   const float scale = (p.scale_a && p.scale_b) ? 1.f / (*p.scale_a * *p.scale_b) : 1.f;
@@ -352,9 +357,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     }
   };
-  // the 32 x 32 block of C at rows [row0, +32), columns [c0, +32): lane i
-  // holds row row0 + i in f. Staged in shared memory and written by one TMA
-  // store (clipped to C's bounds by the tensor map), or by per-row stores.
+  // the wrows x 32 block of C at rows [row0, +wrows), columns [c0, +32):
+  // lane i < wrows holds row row0 + i in f. Staged in shared memory and
+  // written by one TMA store (the tensor map's box has wrows rows and is
+  // clipped to C's bounds), or by per-row stores.
   auto store_block = [&](const float* f, int64_t row0, int64_t c0) {
     if (!kCount && p.stage_c) {
       if (row0 >= p.M || c0 >= p.N) return;  // warp-uniform: the block lies outside C
@@ -380,12 +386,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       ++nstaged;
     } else {
-      store_chunk(f, row0 + lane, c0);
+      if (lane < wrows) store_chunk(f, row0 + lane, c0);
     }
   };
-  // the 32 x 64 block at rows [row0, +32), columns [c0, +64) from two TMEM
-  // chunks (lane i holds row row0 + i): staged with 16-byte piece u of row
-  // `lane` at piece u ^ (lane & 7) and written by one TMA store
+  // the wrows x 64 block at rows [row0, +wrows), columns [c0, +64) from two
+  // TMEM chunks (lane i holds row row0 + i): staged with 16-byte piece u of
+  // row `lane` at piece u ^ (lane & 7) and written by one TMA store (lanes
+  // past wrows stage rows that the store's box leaves out)
   auto store_block64 = [&](const uint32_t* r0, const uint32_t* r1, int64_t row0, int64_t c0) {
     if (row0 >= p.M || c0 >= p.N) return;  // warp-uniform: the block lies outside C
     const uint32_t buf = stg + (nstaged & 1u) * 4096u;
@@ -711,14 +718,14 @@ struct SmemPlan {
   size_t smem = 0;
 };
 
-constexpr size_t kSmemFixed = 1024 + 256;  // alignment slack + barriers
+constexpr size_t kSmemFixed = 1024 + 320;  // alignment slack + barriers (312 bytes)
 constexpr size_t kSmemBudget = 232448;     // 227 KB opt-in
 
 // stages_req = 0 asks for the deepest ring that fits beside the staging
 // area. The staging area is dropped (per-row stores) when an explicitly
 // requested ring leaves no room for it.
-tp_status plan_smem(bool pair, int bn, int split, int stages_req, bool want_stage_c, SmemPlan* out) {
-  const size_t stage_bytes = (size_t)BM * 128 + (size_t)(pair ? bn / 2 : bn) * 128;
+tp_status plan_smem(bool pair, int rows, int bn, int split, int stages_req, bool want_stage_c, SmemPlan* out) {
+  const size_t stage_bytes = (size_t)rows * 128 + (size_t)(pair ? bn / 2 : bn) * 128;
   // split-K: receive and send areas of (split - 1) slice partials each
   const size_t recv = split > 1 ? 2 * (size_t)(split - 1) * 128 * (size_t)(bn / split) * 4 : 0;
   for (int stage_c = want_stage_c ? 1 : 0; stage_c >= 0; --stage_c) {
@@ -738,15 +745,15 @@ tp_status plan_smem(bool pair, int bn, int split, int stages_req, bool want_stag
   return fail(TP_ERR_UNSUPPORTED, "shared memory too small for the requested stages");
 }
 
-// C (bf16, N columns, row stride N) as boxes of 32 rows x `cols` columns
-// (32: 64-byte swizzle, 64: 128-byte swizzle) matching the epilogue's
-// staging layouts.
-tp_status make_map_c(CUtensorMap* map, void* ptr, int64_t M, int64_t N, int cols) {
+// C (bf16, N columns, row stride N) as boxes of `rows` (16 or 32) rows x
+// `cols` columns (32: 64-byte swizzle, 64: 128-byte swizzle) matching the
+// epilogue's staging layouts.
+tp_status make_map_c(CUtensorMap* map, void* ptr, int64_t M, int64_t N, int cols, int rows) {
   auto fn = encode_fn();
   if (!fn) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
   cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
   cuuint64_t strides[1] = {(cuuint64_t)(N * 2)};
-  cuuint32_t box[2] = {(cuuint32_t)cols, 32};
+  cuuint32_t box[2] = {(cuuint32_t)cols, (cuuint32_t)rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ptr, dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
@@ -766,9 +773,10 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
     return fail(TP_ERR_INVALID, "write_counts and write_owner must be given together");
   if (c->kind == TP_MAP_QUEUE) return fail(TP_ERR_UNSUPPORTED, "the tensor-core GEMM maps tiles by slot (identity/strided)");
   const int bm = (int)c->tile[0], bn = (int)c->tile[1];
-  if (bm != BM && bm != 2 * BM)
-    return fail(TP_ERR_UNSUPPORTED, "tensor-core GEMM tiles have 128 rows (one CTA) or 256 rows (CTA pair)");
+  if (bm != BM / 2 && bm != BM && bm != 2 * BM)
+    return fail(TP_ERR_UNSUPPORTED, "tensor-core GEMM tiles have 64 or 128 rows (one CTA) or 256 rows (CTA pair)");
   const bool pair = bm == 2 * BM;
+  const int rows = pair ? BM : bm;  // A rows per CTA and stage
   if (bn < 32 || bn > 256 || bn % 32 || (pair && bn % 64))
     return fail(TP_ERR_UNSUPPORTED, "tile columns must be 32..256, a multiple of 32 (of 64 for 256-row tiles)");
   if (cfg && cfg->bm && cfg->bm != bm) return fail(TP_ERR_SHAPE, "cfg.bm differs from the partition's tile");
@@ -793,7 +801,7 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   if (cfg && (cfg->split_k < 0 || cfg->split_k > 8 || (split > 1 && (split & (split - 1)))))
     return fail(TP_ERR_INVALID, "split_k must be 0, 1, 2, 4 or 8");
   if (split > 1) {
-    if (pair) return fail(TP_ERR_UNSUPPORTED, "split_k applies to 128-row tiles (one CTA per K slice)");
+    if (bm != BM) return fail(TP_ERR_UNSUPPORTED, "split_k applies to 128-row tiles (one CTA per K slice)");
     if (bn % (32 * split)) return fail(TP_ERR_UNSUPPORTED, "split_k needs tile columns a multiple of 32 * split_k");
     if (nk < split) return fail(TP_ERR_UNSUPPORTED, "split_k exceeds the number of K blocks");
     if (progs < T) return fail(TP_ERR_UNSUPPORTED, "split_k needs at most one tile per program");
@@ -803,7 +811,7 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   const bool count = ex->write_counts != nullptr;
   const bool checked = (ex->flags & TP_EXEC_CHECKED) != 0;
   Maps maps;
-  tp_status s = make_map(&maps.a, a->ptr, M, K, lda, esize, BM);
+  tp_status s = make_map(&maps.a, a->ptr, M, K, lda, esize, rows);
   if (s != TP_OK) return s;
   s = make_map(&maps.b, b->ptr, N, K, ldb, esize, pair ? bn / 2 : bn);
   if (s != TP_OK) return s;
@@ -814,6 +822,7 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   p.K = K;
   p.gm = (int32_t)c->grid[0];
   p.gn = (int32_t)c->grid[1];
+  p.rows = rows;
   p.bn = bn;
   p.kind = c->kind;
   p.group_m = (c->kind != TP_MAP_IDENTITY && cfg && cfg->group_m > 0) ? cfg->group_m : 1;
@@ -832,14 +841,15 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   while (cols < 2 * bn) cols *= 2;
   p.tmem_cols = cols;
   SmemPlan plan;
-  s = plan_smem(pair, bn, split, cfg ? cfg->stages : 0, p.c_vec && !count, &plan);
+  s = plan_smem(pair, rows, bn, split, cfg ? cfg->stages : 0, p.c_vec && !count, &plan);
   if (s != TP_OK) return s;
   p.stages = plan.stages;
   p.body_bytes = (int32_t)plan.body;
   p.stage_c = plan.stage_c ? 1 : 0;
   if (plan.stage_c) {
-    s = make_map_c(&maps.c, c->t.ptr, M, N, 32);
-    if (s == TP_OK) s = make_map_c(&maps.c64, c->t.ptr, M, N, 64);
+    const int store_rows = rows == BM / 2 ? 16 : 32;  // rows of C one epilogue warp holds
+    s = make_map_c(&maps.c, c->t.ptr, M, N, 32, store_rows);
+    if (s == TP_OK) s = make_map_c(&maps.c64, c->t.ptr, M, N, 64, store_rows);
     if (s != TP_OK) return s;
   } else {
     maps.c = maps.c64 = maps.a;  // unused
@@ -889,13 +899,13 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
 
 tp_status gemm_tc_resident(tp_ctx* ctx, const tp_gemm_config* cfg, int32_t* programs) {
   const int bm = cfg->bm ? cfg->bm : BM, bn = cfg->bn ? cfg->bn : 256;
-  if (bm != BM && bm != 2 * BM) return fail(TP_ERR_UNSUPPORTED, "tiles have 128 or 256 rows");
+  if (bm != BM / 2 && bm != BM && bm != 2 * BM) return fail(TP_ERR_UNSUPPORTED, "tiles have 64, 128 or 256 rows");
   const bool pair = bm == 2 * BM;
   const int split = cfg->split_k > 1 ? cfg->split_k : 1;
   if (split > 8 || (split & (split - 1))) return fail(TP_ERR_INVALID, "split_k must be 0, 1, 2, 4 or 8");
-  if (split > 1 && pair) return fail(TP_ERR_UNSUPPORTED, "split_k applies to 128-row tiles");
+  if (split > 1 && bm != BM) return fail(TP_ERR_UNSUPPORTED, "split_k applies to 128-row tiles");
   SmemPlan plan;
-  tp_status s = plan_smem(pair, bn, split, cfg->stages, true, &plan);
+  tp_status s = plan_smem(pair, pair ? BM : bm, bn, split, cfg->stages, true, &plan);
   if (s != TP_OK) return s;
   (void)ctx;
   const int csize = pair ? 2 : split;

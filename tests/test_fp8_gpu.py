@@ -84,7 +84,8 @@ def _fp8_gemm(ctx, a, bt, bm=128, bn=128, P=None, group_m=1, count=False, checke
     c = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
     p = tp.tp_partition_create(ctx, c, (bm, bn))
     tiles = tp.tp_partition_query(p)["num_tiles"]
-    tp.tp_partition_map(p, tp.MAP_STRIDED, tiles if split_k > 1 else min(P or (ctx.sm_count * 128 // bm), tiles))
+    default = ctx.sm_count // 2 if bm == 256 else ctx.sm_count
+    tp.tp_partition_map(p, tp.MAP_STRIDED, tiles if split_k > 1 else min(P or default, tiles))
     counts = owner = None
     if count:
         counts = torch.zeros(m * n, dtype=torch.int32, device="cuda")
@@ -97,7 +98,7 @@ def _fp8_gemm(ctx, a, bt, bm=128, bn=128, P=None, group_m=1, count=False, checke
 
 
 @pytest.mark.parametrize("checked", [False, True])
-@pytest.mark.parametrize("bm", [128, 256])
+@pytest.mark.parametrize("bm", [64, 128, 256])
 def test_integer_inputs_exact(ctx, bm, checked):
     """Entries in [-7, 7] with amax 7: s = 64 (a power of two), every code and
     partial sum is exact, so C is the bf16 rounding of the exact product."""
@@ -133,7 +134,7 @@ def test_split_k_integer_inputs_exact(ctx, S):
     assert ogemm.rel_frobenius(c.cpu(), ref_fp8) <= 5e-3
 
 
-@pytest.mark.parametrize("bm,bn", [(128, 128), (128, 256), (256, 256), (256, 128)])
+@pytest.mark.parametrize("bm,bn", [(64, 128), (64, 256), (128, 128), (128, 256), (256, 256), (256, 128)])
 def test_random_errors(ctx, bm, bn):
     m, n, k = 384, 512, 640
     a = _x(m * k, 11, "bf16").reshape(m, k)

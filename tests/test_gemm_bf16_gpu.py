@@ -1,5 +1,6 @@
 """GPU parity of the BF16 tcgen05 GEMM (TMA -> shared-memory ring -> tcgen05.mma
--> TMEM -> bf16 epilogue) against the FP64 oracle, and its tile coverage."""
+-> TMEM -> bf16 epilogue) against the FP64 oracle, and its tile coverage, for
+64-row tiles (tcgen05 M = 64), 128-row tiles and 256-row tiles on CTA pairs."""
 import numpy as np
 import pytest
 import torch
@@ -32,7 +33,7 @@ def _gemm(ctx, a, bt, bn=128, kind=tp.MAP_STRIDED, P=None, group_m=1, stages=0, 
     p = tp.tp_partition_create(ctx, c, (bm, bn))
     if kind != tp.MAP_IDENTITY:
         tiles = tp.tp_partition_query(p)["num_tiles"]
-        default = ctx.sm_count if bm == 128 else ctx.sm_count // 2
+        default = ctx.sm_count // 2 if bm == 256 else ctx.sm_count
         tp.tp_partition_map(p, kind, tiles if split_k > 1 and P is None else min(P or default, tiles))
     counts = owner = None
     if count:
@@ -46,7 +47,8 @@ def _gemm(ctx, a, bt, bn=128, kind=tp.MAP_STRIDED, P=None, group_m=1, stages=0, 
     return c, counts, owner, info
 
 
-@pytest.mark.parametrize("bm,bn", [(128, 32), (128, 64), (128, 96), (128, 128), (128, 160), (128, 192), (128, 256),
+@pytest.mark.parametrize("bm,bn", [(64, 32), (64, 64), (64, 96), (64, 128), (64, 192), (64, 256),
+                                   (128, 32), (128, 64), (128, 96), (128, 128), (128, 160), (128, 192), (128, 256),
                                    (256, 64), (256, 128), (256, 192), (256, 256)])
 def test_random_within_tolerance(ctx, bm, bn):
     m, n, k = 384, 512, 640
@@ -58,7 +60,7 @@ def test_random_within_tolerance(ctx, bm, bn):
     assert err <= 5e-3          # expected ~2e-3: bf16 output rounding dominates
 
 
-@pytest.mark.parametrize("bm", [128, 256])
+@pytest.mark.parametrize("bm", [64, 128, 256])
 @pytest.mark.parametrize("kind", [tp.MAP_IDENTITY, tp.MAP_STRIDED])
 def test_integer_inputs_bit_exact(ctx, kind, bm):
     """Integer entries in [-4, 4]: every partial sum is exact in FP32, so C must
@@ -83,7 +85,7 @@ def test_identity_and_permutation_bit_exact(ctx):
     assert torch.equal(c, bt.t()[perm.cuda()])
 
 
-@pytest.mark.parametrize("bm", [128, 256])
+@pytest.mark.parametrize("bm", [64, 128, 256])
 @pytest.mark.parametrize("m,n,k", [(1, 32, 8), (129, 65, 72), (300, 200, 136), (130, 1000, 8), (7, 8, 4104)])
 def test_ragged_shapes(ctx, m, n, k, bm):
     a, bt = _operands(m, n, k, seed=m + n)
@@ -94,7 +96,7 @@ def test_ragged_shapes(ctx, m, n, k, bm):
     assert np.array_equal(owner.cpu().numpy(), opart.gemm_owner_map_cut(m, n, bm, 64, info["num_programs"], 1))
 
 
-@pytest.mark.parametrize("bm", [128, 256])
+@pytest.mark.parametrize("bm", [64, 128, 256])
 @pytest.mark.parametrize("P,group_m,stages", [(7, 2, 0), (148, 8, 3), (1, 1, 2), (64, 4, 6)])
 def test_mapped_partition_coverage(ctx, P, group_m, stages, bm):
     m, n, k = 1024, 1280, 256
@@ -112,7 +114,7 @@ def test_mapped_partition_coverage(ctx, P, group_m, stages, bm):
     assert torch.equal(c1, c)
 
 
-@pytest.mark.parametrize("bm", [128, 256])
+@pytest.mark.parametrize("bm", [64, 128, 256])
 def test_plain_partition_one_program_per_tile(ctx, bm):
     m, n, k = 512, 768, 128
     a, bt = _operands(m, n, k, seed=9)
@@ -136,7 +138,7 @@ def test_layout_and_alignment_errors(ctx):
         tp.tp_gemm(ctx, p, a2, b_rowmajor)
     assert e.value.status == tp._lib.ERR_UNSUPPORTED
     tp.tp_partition_destroy(p)
-    p = tp.tp_partition_create(ctx, c, (64, 128))
+    p = tp.tp_partition_create(ctx, c, (96, 128))             # tiles have 64, 128 or 256 rows
     with pytest.raises(tp.TPError) as e:
         tp.tp_gemm(ctx, p, a2, b_rowmajor.t())
     assert e.value.status == tp._lib.ERR_UNSUPPORTED
@@ -168,7 +170,7 @@ def test_8192_cubed_sampled_tiles(ctx):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("bm", [128, 256])
+@pytest.mark.parametrize("bm", [64, 128, 256])
 @pytest.mark.parametrize("kind,P,group_m", [(tp.MAP_IDENTITY, None, 1), (tp.MAP_STRIDED, 7, 1),
                                             (tp.MAP_STRIDED, None, 8)])
 @pytest.mark.parametrize("m,n,k", [(384, 512, 640), (300, 200, 136), (1, 96, 64)])
@@ -212,15 +214,15 @@ def test_checked_flag_rejected_where_unsupported(ctx):
     tp.tp_partition_destroy(p)
 
 
-@pytest.mark.parametrize("bm", [128, 256])
+@pytest.mark.parametrize("bm", [64, 128, 256])
 @pytest.mark.parametrize("limit", [0, 2, 3, 8])
 def test_last_round_cut_along_n(ctx, bm, limit):
     """The tiles of the last, partial round cut along N into narrow tiles run
     by otherwise idle programs: every element is stored once, by the program
     the oracle's schedule names, and C is bit-identical to the uncut run
     (integer inputs: the exact product rounded once)."""
-    m, n, k = 1024, 640, 512            # 128-row tiles: 8 x 5 = 40 tiles of 128 columns; 256-row: 20
-    P = 13 if bm == 128 else 9          # 40 mod 13 = 1 and 20 mod 9 = 2 tiles in the last round
+    m, n, k = 1024, 640, 512            # 128-row tiles: 8 x 5 = 40 tiles of 128 columns; 64-row: 80; 256-row: 20
+    P = 9 if bm == 256 else 13          # 40 mod 13 = 1, 80 mod 13 = 2 and 20 mod 9 = 2 tiles in the last round
     bn = 128
     T = (m // bm) * (n // bn)
     D, S = opart.gemm_cut_schedule(T, P, bn, 64 if bm == 256 else 32, limit or 4)
@@ -327,7 +329,7 @@ def test_split_k_resident_programs(ctx):
 
 
 # ------------------------------------------------------- TMA-store epilogue
-@pytest.mark.parametrize("bm", [128, 256])
+@pytest.mark.parametrize("bm", [64, 128, 256])
 @pytest.mark.parametrize("m,n,k", [(129, 72, 200), (300, 200, 136), (1, 32, 8), (130, 1000, 8), (65, 65, 72)])
 def test_epilogue_stays_inside_c(ctx, bm, m, n, k):
     """C is a view inside a guarded allocation: the epilogue (TMA stores
@@ -353,7 +355,7 @@ def test_plain_and_staged_epilogues_agree(ctx):
     assert torch.equal(c6, c7)
 
 
-@pytest.mark.parametrize("bm,P", [(128, 0), (128, 7), (256, 0), (256, 5)])
+@pytest.mark.parametrize("bm,P", [(64, 0), (64, 9), (128, 0), (128, 7), (256, 0), (256, 5)])
 def test_unchecked_raw_pointer_gemm_matches_partitioned(ctx, bm, P):
     """tp_gemm_unchecked runs the same schedule on a raw C pointer: C is
     bit-identical to tp_gemm on the equivalent partition (plain for
@@ -369,19 +371,20 @@ def test_unchecked_raw_pointer_gemm_matches_partitioned(ctx, bm, P):
     assert torch.equal(c, ref)
     assert ogemm.rel_frobenius(c.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 1e-2
     with pytest.raises(tp.TPError) as e:
-        tp.tp_gemm_unchecked(ctx, c, a, bt.t(), tp.gemm_config(bm=64, bn=128), s)
+        tp.tp_gemm_unchecked(ctx, c, a, bt.t(), tp.gemm_config(bm=96, bn=128), s)
     assert e.value.status == tp._lib.ERR_INVALID
 
 
 def test_resident_programs(ctx):
     """The resident-program query: CTA pairs for 256-row tiles, CTAs for
-    128-row tiles, never more than the SMs allow."""
+    64- and 128-row tiles, never more than the SMs allow."""
     pairs = tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=256, bn=256))
     ctas = tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=128, bn=256))
-    print(f"resident: {ctas} CTAs, {pairs} CTA pairs")
-    assert 0 < pairs <= ctx.sm_count // 2 and 0 < ctas <= ctx.sm_count
+    ctas64 = tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=64, bn=64))
+    print(f"resident: {ctas} CTAs, {pairs} CTA pairs, {ctas64} CTAs of 64 x 64 tiles")
+    assert 0 < pairs <= ctx.sm_count // 2 and 0 < ctas <= ctx.sm_count and 0 < ctas64 <= ctx.sm_count
     with pytest.raises(tp.TPError) as e:
-        tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=64, bn=256))
+        tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=96, bn=256))
     assert e.value.status == tp._lib.ERR_UNSUPPORTED
 
 
@@ -394,3 +397,21 @@ def test_epilogue_mixed_block_widths_bit_exact(ctx, bn):
     a, bt = _operands(m, n, k, seed=bn, kind="int")
     c, _, _, _ = _gemm(ctx, a, bt, bn=bn, P=5)
     assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(ogemm.gemm(a.cpu(), bt.cpu().t())))
+
+
+@pytest.mark.parametrize("m", [1, 16, 64, 65, 100])
+def test_64_row_tiles_equal_128_row_tiles(ctx, m):
+    """A 64-row tile (tcgen05 M = 64: D row r in TMEM lane 32(r/16) + r%16)
+    accumulates each C element over K in the same order as a 128-row tile,
+    so C is bit-identical, and both equal the exact integer product rounded
+    once when every partial sum is exact."""
+    n, k = 640, 1032
+    a, bt = _operands(m, n, k, seed=m)
+    c64, counts, owner, info = _gemm(ctx, a, bt, bn=128, bm=64, P=7, count=True)
+    c128, _, _, _ = _gemm(ctx, a, bt, bn=128, bm=128, P=7)
+    assert torch.equal(c64, c128)
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    assert np.array_equal(owner.cpu().numpy(), opart.gemm_owner_map_cut(m, n, 64, 128, info["num_programs"], 1))
+    ai, bi = _operands(m, n, k, seed=m + 1, kind="int")
+    c, _, _, _ = _gemm(ctx, ai, bi, bn=64, bm=64, P=5)
+    assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(ogemm.gemm(ai.cpu(), bi.cpu().t())))

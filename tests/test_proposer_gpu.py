@@ -104,7 +104,7 @@ def test_features_targets_and_save_load(ctx, tmp_path):
 @pytest.mark.parametrize("dtype", ["bf16", "fp8"])
 def test_autotune_table_cache_and_numerics(ctx, dtype, tmp_path):
     space = tp.tp_autotune_space(dtype)
-    assert len(space) == 32 and all(cfg.split_k <= 1 for cfg in space)
+    assert len(space) == 48 and all(cfg.split_k <= 1 for cfg in space)
     M, N, K = 700, 900, 1024
     best, table, best_tf = tp.tp_autotune(ctx, M, N, K, dtype)
     assert len(table) == len(space) and all(t > 0 for t in table)
@@ -112,9 +112,9 @@ def test_autotune_table_cache_and_numerics(ctx, dtype, tmp_path):
     assert best.split_k <= 1
     assert tp.tp_autotune_lookup(ctx, M, N, K, dtype).bn == best.bn
     assert tp.tp_autotune_lookup(ctx, M, N, K, dtype, split_k=True) is None     # that search has not run
-    # the split-K opt-in times the same 32 configs plus the split ones
+    # the split-K opt-in times the same 48 configs plus the split ones
     best_s, table_s, _ = tp.tp_autotune(ctx, M, N, K, dtype, split_k=True)
-    assert len(table_s) == 37 and all(t > 0 for t in table_s[:32])
+    assert len(table_s) == 53 and all(t > 0 for t in table_s[:48])
     assert tp.tp_autotune_lookup(ctx, M, N, K, dtype, split_k=True) is not None
     t = tp.tp_autotune_time(ctx, M, N, K, dtype, best, repeats=3)
     assert 0.5 * best_tf < t < 2.0 * best_tf
@@ -134,7 +134,7 @@ def test_autotune_table_cache_and_numerics(ctx, dtype, tmp_path):
             c = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
             p = tp.tp_partition_create(ctx, c, (cfg.bm, cfg.bn))
             tiles = tp.tp_partition_query(p)["num_tiles"]
-            tp.tp_partition_map(p, tp.MAP_STRIDED, min(tiles, ctx.sm_count * 128 // cfg.bm))
+            tp.tp_partition_map(p, tp.MAP_STRIDED, min(tiles, ctx.sm_count // (2 if cfg.bm == 256 else 1)))
             tp.tp_gemm(ctx, p, a, bt.t(), cfg)
             tp.tp_partition_destroy(p)
             if cfg.split_k > 1:
@@ -219,7 +219,7 @@ def test_proposals_equal_exhaustive_pick_bit_for_bit(ctx, trained):
             c = torch.full((m, n), float("nan"), dtype=torch.bfloat16, device="cuda")
             p = tp.tp_partition_create(ctx, c, (cfg.bm, cfg.bn))
             tiles = tp.tp_partition_query(p)["num_tiles"]
-            tp.tp_partition_map(p, tp.MAP_STRIDED, min(tiles, ctx.sm_count * 128 // cfg.bm))
+            tp.tp_partition_map(p, tp.MAP_STRIDED, min(tiles, ctx.sm_count // (2 if cfg.bm == 256 else 1)))
             tp.tp_gemm(ctx, p, a, bt.t(), cfg)
             tp.tp_partition_destroy(p)
             outs.append(c)
@@ -243,10 +243,10 @@ def test_split_k_is_opt_in_only(ctx):
     cfg, _, fb = tp.tp_propose(ctx, m, 128, 256, 4096, "bf16", min_score=1e9)   # forced fallback
     assert fb and cfg.split_k <= 1
     best, table, _ = tp.tp_autotune(ctx, 128, 256, 4096, "bf16", split_k=True)
-    assert len(table) == 37 and max(table[32:]) > 0
+    assert len(table) == 53 and max(table[48:]) > 0
     tp.tp_mlp_destroy(m)
     # an MLP whose output count is the split-inclusive space is refused
-    bad = tp.tp_mlp_create(ctx, F, H, 37, 8, proposer.init_params(F, H, 37, seed=3))
+    bad = tp.tp_mlp_create(ctx, F, H, 53, 8, proposer.init_params(F, H, 53, seed=3))
     with pytest.raises(tp.TPError):
         tp.tp_propose(ctx, bad, 128, 256, 4096, "bf16", min_score=-1e9)
     tp.tp_mlp_destroy(bad)
