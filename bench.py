@@ -811,7 +811,7 @@ def proposer_row(tp, ctx, train_n: int, test_n: int, epochs: int, log=None) -> d
         "space": "single-pass configs (bit-identical C; split-K excluded)", "configs": int(T.shape[1]),
         "train_shapes": len(train_shapes), "train_measurements": int(V.sum()), "test_shapes": len(test_shapes),
         "judge_single_timing": r, "retimed_median_of_3": rt,
-        "default_config": {n: getattr(space[dflt], n) for n in ("bm", "bn", "stages", "group_m", "split_k")},
+        "default_config": {n: getattr(space[dflt], n) for n in ("bm", "bn", "bk", "stages", "group_m", "split_k")},
         "large_shapes": int(big.sum()),
         "large_mean_regret": float(reg[big].mean()) if big.any() else None,
         "large_mean_regret_default": float(reg_d[big].mean()) if big.any() else None,

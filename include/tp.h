@@ -162,7 +162,16 @@ typedef struct tp_gemm_config {
   int32_t bm;          /* tensor-core GEMM: 64 or 128 (one CTA), or 256 (CTA
                         * pair, cta_group::2); SIMT GEMM: 64                   */
   int32_t bn;          /* 32..256, multiple of 32 (tensor-core paths)          */
-  int32_t bk;          /* K per stage: 64 (bf16) / 128 (fp8); SIMT: 8/16/32     */
+  int32_t bk;          /* tensor-core GEMM: K per ring stage, 1, 2 or 4 K blocks
+                        * of 128 bytes (64 bf16 / 128 fp8 elements; 0 = one).
+                        * With more than one, each operand arrives as one 3-D
+                        * TMA box per stage: fewer, larger copies (a copy
+                        * costs about the same time whatever its size). The
+                        * largest count up to bk that leaves room for two
+                        * stages is used, and one block per stage when K is
+                        * not a multiple of the K block or split_k > 1. The
+                        * MMAs and their K order do not change, so C does
+                        * not. SIMT GEMM: 8, 16 or 32.                       */
   int32_t stages;      /* shared-memory ring depth                              */
   int32_t group_m;     /* raster band height in tiles (L2 reuse)                */
   int32_t num_programs;/* persistent programs; 0 = number of SMs (or pairs)     */
@@ -463,8 +472,8 @@ tp_status tp_decode_down_residual(tp_ctx* ctx, tp_partition* h, const tp_tensor*
  *
  * Numerics classes. Every config with split_k <= 1 computes each C element
  * as one FP32 accumulation over K, in K order, by the one program that owns
- * its tile; tile rows, tile columns, stages, raster band and program count
- * only decide where and when that happens. All such configs, and the default
+ * its tile; tile rows, tile columns, K per stage, stages, raster band and
+ * program count only decide where and when that happens. All such configs, and the default
  * config (cfg NULL), therefore give bit-identical C: the single-pass class.
  * A split-K config adds split_k slice partials in slice order instead:
  * reproducible, but rounded differently. Searches cover the single-pass
@@ -475,10 +484,10 @@ enum {
 };
 /* The space (same order on every call; with flags = 0, index i is the MLP
  * proposer's output i): tile rows {64, 128 (one CTA), 256 (CTA pair)} x tile
- * columns {64, 128, 192, 256} x stages {3, max} x raster bands {1, 8}, the 48
- * single-pass configs; with TP_TUNE_SPLIT_K followed by the split-K programs
- * of 128-row tiles: (bn 128, split_k 2 / 4) and (bn 256, split_k 2 / 4 / 8),
- * 53 configs. Writes up to `cap` configs to `out` (may be NULL) and the size
+ * columns {64, 128, 192, 256} x K per stage {1, 2, 4} K blocks (bk; the
+ * deepest ring that fits) x raster bands {1, 8}, the 72 single-pass configs;
+ * with TP_TUNE_SPLIT_K followed by the split-K programs of 128-row tiles:
+ * (bn 128, split_k 2 / 4) and (bn 256, split_k 2 / 4 / 8), 77 configs. Writes up to `cap` configs to `out` (may be NULL) and the size
  * to *count. Errors: TP_ERR_INVALID (undefined flag bits), TP_ERR_UNSUPPORTED
  * (dtype). */
 tp_status tp_autotune_space(int32_t dtype, int32_t flags, tp_gemm_config* out, int32_t cap, int32_t* count);
@@ -506,11 +515,12 @@ tp_status tp_autotune_time(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t
  * and *out filled, else 0. */
 tp_status tp_autotune_lookup(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, int32_t flags,
                              tp_gemm_config* out, int32_t* found);
-/* Persist / restore the cache (text, "tp-autotune-cache v3": one line per
- * entry, M N K dtype flags bm bn stages group_m num_programs split_k
- * TFLOP/s). Load also reads v2 and v1 files (no flags column; v1 lines also
- * lack split_k), whose searches covered the split-K configs: an entry is
- * filed under TP_TUNE_SPLIT_K, and a single-pass winner under flags 0 too. */
+/* Persist / restore the cache (text, "tp-autotune-cache v4": one line per
+ * entry, M N K dtype flags bm bn bk stages group_m num_programs split_k
+ * TFLOP/s). Load also reads v3 files (no bk column: bk 0) and v2 and v1
+ * files (no flags column; v1 lines also lack split_k), whose searches
+ * covered the split-K configs: an entry is filed under TP_TUNE_SPLIT_K, and
+ * a single-pass winner under flags 0 too. */
 tp_status tp_autotune_save(tp_ctx* ctx, const char* path);
 tp_status tp_autotune_load(tp_ctx* ctx, const char* path);
 

@@ -1,7 +1,7 @@
 // Exhaustive autotuner for the tensor-core GEMM (§5.1 tunes tile shapes once
 // per size; here the search is automatic). The config space enumerates tile
-// rows (128 on one CTA, 256 on a CTA pair), tile columns, pipeline depth and
-// raster band height; each config is timed with CUDA events on a device
+// rows (64 or 128 on one CTA, 256 on a CTA pair), tile columns, K blocks per
+// ring stage and raster band height; each config is timed with CUDA events on a device
 // workspace of the requested shape and the fastest wins (ties within 1% go to
 // the earlier, smaller config). Results are cached per (M, N, K, dtype,
 // search flags) and can be saved to / loaded from a versioned text file.
@@ -55,17 +55,19 @@ TuneState* state(tp_ctx* ctx) {
 }
 
 // The single-pass configs (one numerics class), then, with TP_TUNE_SPLIT_K,
-// the split-K configs.
-std::vector<tp_gemm_config> space(int32_t flags) {
+// the split-K configs. K per stage is 1, 2 or 4 K blocks of 128 bytes (64
+// bf16 / 128 fp8 elements), the deepest ring that fits.
+std::vector<tp_gemm_config> space(int32_t dtype, int32_t flags) {
   std::vector<tp_gemm_config> v;
+  const int kblk = dtype == TP_F8E4M3 ? 128 : 64;
   for (int bm : {64, 128, 256})
     for (int bn : {64, 128, 192, 256})
-      for (int stages : {3, 0})
+      for (int kb : {1, 2, 4})
         for (int gm : {1, 8}) {
           tp_gemm_config c{};
           c.bm = bm;
           c.bn = bn;
-          c.stages = stages;
+          c.bk = kb * kblk;
           c.group_m = gm;
           v.push_back(c);
         }
@@ -267,7 +269,7 @@ tp_status tp_autotune_space(int32_t dtype, int32_t flags, tp_gemm_config* out, i
   if (!count) return fail(TP_ERR_INVALID, "null count");
   if (dtype != TP_BF16 && dtype != TP_F8E4M3) return fail(TP_ERR_UNSUPPORTED, "dtype must be BF16 or F8E4M3");
   if (flags & ~TP_TUNE_SPLIT_K) return fail(TP_ERR_INVALID, "undefined TP_TUNE_* flag bits");
-  auto v = space(flags);
+  auto v = space(dtype, flags);
   *count = (int32_t)v.size();
   if (out)
     for (int i = 0; i < (int)v.size() && i < cap; ++i) out[i] = v[i];
@@ -284,7 +286,7 @@ tp_status tp_autotune(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtyp
   TuneProblem pb;
   s = prepare(ctx, st, M, N, K, dtype, &pb);
   if (s != TP_OK) return s;
-  auto cfgs = space(flags);
+  auto cfgs = space(dtype, flags);
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -364,11 +366,11 @@ tp_status tp_autotune_save(tp_ctx* ctx, const char* path) {
   std::lock_guard<std::mutex> lk(st->mu);
   FILE* f = std::fopen(path, "w");
   if (!f) return fail(TP_ERR_INVALID, std::string("cannot write ") + path);
-  std::fprintf(f, "tp-autotune-cache v3\n");
+  std::fprintf(f, "tp-autotune-cache v4\n");
   for (auto& kv : st->cache) {
     const auto& c = kv.second.first;
-    std::fprintf(f, "%lld %lld %lld %d %d %d %d %d %d %d %d %.3f\n", (long long)kv.first.m, (long long)kv.first.n,
-                 (long long)kv.first.k, kv.first.dtype, kv.first.flags, c.bm, c.bn, c.stages, c.group_m,
+    std::fprintf(f, "%lld %lld %lld %d %d %d %d %d %d %d %d %d %.3f\n", (long long)kv.first.m, (long long)kv.first.n,
+                 (long long)kv.first.k, kv.first.dtype, kv.first.flags, c.bm, c.bn, c.bk, c.stages, c.group_m,
                  c.num_programs, c.split_k, kv.second.second);
   }
   std::fclose(f);
@@ -379,24 +381,33 @@ tp_status tp_autotune_load(tp_ctx* ctx, const char* path) {
   if (!ctx || !path) return fail(TP_ERR_INVALID, "null argument");
   FILE* f = std::fopen(path, "r");
   if (!f) return fail(TP_ERR_INVALID, std::string("cannot read ") + path);
-  // v3 lines carry the search flags; v2 and v1 entries came from searches
-  // that included split-K (v1 lines also lack the split_k column)
+  // v4 lines carry the search flags and bk; v3 lines lack bk; v2 and v1
+  // entries came from searches that included split-K (v1 lines also lack
+  // the split_k column)
   char magic[64] = {};
   const bool ok = std::fgets(magic, sizeof magic, f) != nullptr;
   auto is = [&](const char* m) { return ok && std::string(magic).rfind(m, 0) == 0; };
-  const int ver = is("tp-autotune-cache v3") ? 3 : is("tp-autotune-cache v2") ? 2 : is("tp-autotune-cache v1") ? 1 : 0;
+  const int ver = is("tp-autotune-cache v4")   ? 4
+                  : is("tp-autotune-cache v3") ? 3
+                  : is("tp-autotune-cache v2") ? 2
+                  : is("tp-autotune-cache v1") ? 1
+                                               : 0;
   if (!ver) {
     std::fclose(f);
-    return fail(TP_ERR_INVALID, "not an autotune cache (v1, v2 or v3)");
+    return fail(TP_ERR_INVALID, "not an autotune cache (v1 to v4)");
   }
   TuneState* st = state(ctx);
   std::lock_guard<std::mutex> lk(st->mu);
   long long m, n, k;
-  int dt, fl = TP_TUNE_SPLIT_K, bm, bn, stages, gm, np, sk = 0;
+  int dt, fl = TP_TUNE_SPLIT_K, bm, bn, bk = 0, stages, gm, np, sk = 0;
   float tf;
   for (;;) {
     int got, want;
-    if (ver == 3) {
+    if (ver == 4) {
+      got = std::fscanf(f, "%lld %lld %lld %d %d %d %d %d %d %d %d %d %f", &m, &n, &k, &dt, &fl, &bm, &bn, &bk,
+                        &stages, &gm, &np, &sk, &tf);
+      want = 13;
+    } else if (ver == 3) {
       got = std::fscanf(f, "%lld %lld %lld %d %d %d %d %d %d %d %d %f", &m, &n, &k, &dt, &fl, &bm, &bn, &stages, &gm,
                         &np, &sk, &tf);
       want = 12;
@@ -413,6 +424,7 @@ tp_status tp_autotune_load(tp_ctx* ctx, const char* path) {
     tp_gemm_config c{};
     c.bm = bm;
     c.bn = bn;
+    c.bk = bk;
     c.stages = stages;
     c.group_m = gm;
     c.num_programs = np;

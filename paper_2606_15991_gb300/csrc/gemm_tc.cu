@@ -60,8 +60,9 @@ struct TcArgs {
   int32_t group_m;
   int32_t tmem_cols;    // allocated TMEM columns (2 * bn rounded to a power of two)
   int32_t c_vec;        // C rows are 16-byte aligned (N % 8 == 0, aligned base)
-  int32_t kblk;         // K elements per stage (64 bf16 / 128 fp8)
+  int32_t kblk;         // K elements per K block: 128 bytes (64 bf16 / 128 fp8)
   int32_t nk;           // K blocks per tile: ceil(K / kblk)
+  int32_t kc;           // K blocks per ring stage; > 1: each operand arrives as one 3-D box per stage
   int32_t split;        // K slices per tile (cluster size of a split program); 1 = none
   int32_t stage_c;      // epilogue writes C by TMA stores of 32 x 32 blocks staged in shared memory
   int32_t body_bytes;   // shared memory before the staging area: max(ring, split receive buffer)
@@ -151,8 +152,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int32_t nprog = (int32_t)gridDim.x / csize;
   const int tile_m = kPair ? 2 * BM : p.rows;
   const int b_rows = kPair ? p.bn / 2 : p.bn;
-  const uint32_t a_stage = (uint32_t)(kPair ? BM : p.rows) * 128;
-  const uint32_t b_stage = (uint32_t)b_rows * 128;
+  // a stage holds kc K blocks of each operand, stacked: block j of A at
+  // j * a_blk, of B at j * (its box rows * 128), each a 128-byte-swizzled
+  // K-major tile
+  const uint32_t a_blk = (uint32_t)(kPair ? BM : p.rows) * 128;
+  const uint32_t a_stage = a_blk * (uint32_t)p.kc;
+  const uint32_t b_stage = (uint32_t)b_rows * 128 * (uint32_t)p.kc;
   const uint32_t a0 = base;
   const uint32_t b0 = base + a_stage * p.stages;
   const uint32_t cst = base + (uint32_t)p.body_bytes;           // epilogue staging
@@ -236,10 +241,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         // box has that many rows
         const int ub_rows = kPair ? u.width / 2 : u.width;
         const CUtensorMap* mb = u.cut ? &map_b_cut : &map_b;
-        const uint32_t utx = a_stage + (uint32_t)ub_rows * 128;
+        const uint32_t utx = a_stage + (uint32_t)ub_rows * 128 * (uint32_t)p.kc;
         const int32_t arow = tm * tile_m + (int32_t)rank * BM;
         const int32_t brow = tn * p.bn + u.col + (int32_t)rank * ub_rows;
-        for (int32_t kb = kb0; kb < kb1; ++kb) {
+        for (int32_t kb = kb0; kb < kb1; kb += p.kc) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err, p.wait_ns)) { ok = false; break; }
           if (p.inject && s == prog && kb == kb0) {
             // test hook: this stage is never armed or filled, so its
@@ -247,17 +252,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (++stage == p.stages) { stage = 0; phase ^= 1u; }
             continue;
           }
-          const int32_t kc = kb * p.kblk;
+          // 2-D boxes take K at element kb * kblk; 3-D boxes take K block kb
+          // (blocks past the last one are zero-filled and never multiplied)
+          const int32_t kx = p.kc > 1 ? 0 : kb * p.kblk;
           if constexpr (kPair) {
             // both CTAs' copies complete on the even CTA's full barrier
             const uint32_t fb = mapa(full_bar(stage), 0);
             if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * utx);
-            tma_load_2d_pair(a0 + a_stage * stage, &map_a, kc, arow, fb, pol_a);
-            tma_load_2d_pair(b0 + b_stage * stage, mb, kc, brow, fb, pol_b);
+            if (p.kc > 1) {
+              tma_load_3d_pair(a0 + a_stage * stage, &map_a, 0, arow, kb, fb, pol_a);
+              tma_load_3d_pair(b0 + b_stage * stage, mb, 0, brow, kb, fb, pol_b);
+            } else {
+              tma_load_2d_pair(a0 + a_stage * stage, &map_a, kx, arow, fb, pol_a);
+              tma_load_2d_pair(b0 + b_stage * stage, mb, kx, brow, fb, pol_b);
+            }
           } else {
             mbar_arrive_expect_tx(full_bar(stage), utx);
-            tma_load_2d(a0 + a_stage * stage, &map_a, kc, arow, full_bar(stage), pol_a);
-            tma_load_2d(b0 + b_stage * stage, mb, kc, brow, full_bar(stage), pol_b);
+            if (p.kc > 1) {
+              tma_load_3d(a0 + a_stage * stage, &map_a, 0, arow, kb, full_bar(stage), pol_a);
+              tma_load_3d(b0 + b_stage * stage, mb, 0, brow, kb, full_bar(stage), pol_b);
+            } else {
+              tma_load_2d(a0 + a_stage * stage, &map_a, kx, arow, full_bar(stage), pol_a);
+              tma_load_2d(b0 + b_stage * stage, mb, kx, brow, full_bar(stage), pol_b);
+            }
           }
           fills[stage]++;
           if (++stage == p.stages) { stage = 0; phase ^= 1u; }
@@ -283,23 +300,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int32_t s = prog; s < TS && ok; s += step, ++t) {
         const Unit u = unit_of(s, p);
         const uint32_t idesc = u.cut ? idesc_cut : idesc_full;
+        const uint32_t b_blk = (uint32_t)(kPair ? u.width / 2 : u.width) * 128;  // B box rows * 128
         const int acc = t & 1;
         const uint32_t use = (uint32_t)((t >> 1) & 1);
         if (!mbar_wait(tempty_bar(acc), use ^ 1u, abort_flag, p.err, p.wait_ns)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d = tmem_base + (uint32_t)(acc * p.bn);
-        for (int32_t kb = kb0; kb < kb1; ++kb) {
+        for (int32_t kb = kb0; kb < kb1; kb += p.kc) {
           if (!mbar_wait(full_bar(stage), phase, abort_flag, p.err, p.wait_ns)) { ok = false; break; }
           tc_fence_after();
-          const uint64_t ad = desc_kmajor_sw128(a0 + a_stage * stage);
-          const uint64_t bd = desc_kmajor_sw128(b0 + b_stage * stage);
-          // 128-byte K slice = 4 MMAs of K = 16 (bf16) or K = 32 (fp8), 32 bytes
-          // apart inside the swizzle atom (start address advances by 32 >> 4).
+          // the stage's K blocks in K order, the same MMAs as one block per
+          // stage (blocks past the tile's last are not multiplied)
+          for (int32_t j = 0; j < p.kc && kb + j < kb1; ++j) {
+            const uint64_t ad = desc_kmajor_sw128(a0 + a_stage * stage + a_blk * (uint32_t)j);
+            const uint64_t bd = desc_kmajor_sw128(b0 + b_stage * stage + b_blk * (uint32_t)j);
+            // 128-byte K slice = 4 MMAs of K = 16 (bf16) or K = 32 (fp8), 32
+            // bytes apart inside the swizzle atom (start address advances by 32 >> 4).
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const uint32_t accum = (kb > kb0 || k > 0) ? 1u : 0u;
-            if constexpr (kPair) mma_pair<kF8>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accum);
-            else mma<kF8>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accum);
+            for (int k = 0; k < 4; ++k) {
+              const uint32_t accum = (kb + j > kb0 || k > 0) ? 1u : 0u;
+              if constexpr (kPair) mma_pair<kF8>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accum);
+              else mma<kF8>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accum);
+            }
           }
           if constexpr (kPair) mma_commit_pair(empty_bar(stage), 0x3);
           else mma_commit(empty_bar(stage));
@@ -635,6 +657,27 @@ tp_status make_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t k, i
   return TP_OK;
 }
 
+// K-major operand seen as 3-D {K block element, row, K block}: a box of
+// {128 bytes, box_rows, kc} brings kc consecutive K blocks of box_rows rows
+// in one copy, stacked in shared memory as kc 128-byte-swizzled K-major
+// tiles. Needs k a multiple of the K block (128 bytes).
+tp_status make_map3(CUtensorMap* map, const void* ptr, int64_t rows, int64_t k, int64_t ld, int esize, int box_rows,
+                    int kc) {
+  auto fn = encode_fn();
+  if (!fn) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+  const int kblk = 128 / esize;
+  cuuint64_t dims[3] = {(cuuint64_t)kblk, (cuuint64_t)rows, (cuuint64_t)(k / kblk)};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * esize), 128};
+  cuuint32_t box[3] = {(cuuint32_t)kblk, (cuuint32_t)box_rows, (cuuint32_t)kc};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 3,
+                  const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled (3-D) failed (" + std::to_string((int)r) + ")");
+  return TP_OK;
+}
+
 // The tensor maps of a launch: A, B, B for narrow tiles, C in 32- and
 // 64-column boxes (TMA stores).
 struct Maps {
@@ -712,6 +755,7 @@ int max_active_clusters(int csize, size_t smem) {
 // epilogue staging (the ring, or the larger split-K receive buffer), whether
 // the epilogue stages C blocks, and the dynamic size requested.
 struct SmemPlan {
+  int kc = 1;  // K blocks per stage
   int stages = 0;
   size_t body = 0;
   bool stage_c = false;
@@ -724,23 +768,30 @@ constexpr size_t kSmemBudget = 232448;     // 227 KB opt-in
 // stages_req = 0 asks for the deepest ring that fits beside the staging
 // area. The staging area is dropped (per-row stores) when an explicitly
 // requested ring leaves no room for it.
-tp_status plan_smem(bool pair, int rows, int bn, int split, int stages_req, bool want_stage_c, SmemPlan* out) {
-  const size_t stage_bytes = (size_t)rows * 128 + (size_t)(pair ? bn / 2 : bn) * 128;
+// kc_req: K blocks per stage asked for; the plan takes the largest count up
+// to it that leaves room for two stages, preferring a plan that keeps the
+// epilogue's staging area.
+tp_status plan_smem(bool pair, int rows, int bn, int kc_req, int split, int stages_req, bool want_stage_c,
+                    SmemPlan* out) {
   // split-K: receive and send areas of (split - 1) slice partials each
   const size_t recv = split > 1 ? 2 * (size_t)(split - 1) * 128 * (size_t)(bn / split) * 4 : 0;
   for (int stage_c = want_stage_c ? 1 : 0; stage_c >= 0; --stage_c) {
     const size_t stg = stage_c ? kStageC : 0;
-    int stages = stages_req > 0 ? stages_req : (int)((kSmemBudget - kSmemFixed - stg) / stage_bytes);
-    stages = stages > kMaxStages ? kMaxStages : stages;
-    if (stages < 2) continue;
-    size_t body = std::max((size_t)stages * stage_bytes, recv);
-    body = (body + 1023) & ~(size_t)1023;
-    if (kSmemFixed + body + stg > kSmemBudget) continue;
-    out->stages = stages;
-    out->body = body;
-    out->stage_c = stage_c != 0;
-    out->smem = kSmemFixed + body + stg;
-    return TP_OK;
+    for (int kc = kc_req; kc >= 1; kc /= 2) {
+      const size_t stage_bytes = ((size_t)rows * 128 + (size_t)(pair ? bn / 2 : bn) * 128) * (size_t)kc;
+      int stages = stages_req > 0 ? stages_req : (int)((kSmemBudget - kSmemFixed - stg) / stage_bytes);
+      stages = stages > kMaxStages ? kMaxStages : stages;
+      if (stages < 2) continue;
+      size_t body = std::max((size_t)stages * stage_bytes, recv);
+      body = (body + 1023) & ~(size_t)1023;
+      if (kSmemFixed + body + stg > kSmemBudget) continue;
+      out->kc = kc;
+      out->stages = stages;
+      out->body = body;
+      out->stage_c = stage_c != 0;
+      out->smem = kSmemFixed + body + stg;
+      return TP_OK;
+    }
   }
   return fail(TP_ERR_UNSUPPORTED, "shared memory too small for the requested stages");
 }
@@ -806,16 +857,22 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
     if (nk < split) return fail(TP_ERR_UNSUPPORTED, "split_k exceeds the number of K blocks");
     if (progs < T) return fail(TP_ERR_UNSUPPORTED, "split_k needs at most one tile per program");
   }
+  // K blocks per stage from cfg->bk (a multiple of the K block); one block
+  // per stage (2-D boxes) when K is not a multiple of the K block or the
+  // program splits K
+  int32_t kc = 1;
+  if (cfg && cfg->bk > 0) {
+    if (cfg->bk % kblk || (cfg->bk / kblk != 1 && cfg->bk / kblk != 2 && cfg->bk / kblk != 4))
+      return fail(TP_ERR_INVALID, "bk must be 1, 2 or 4 K blocks (64 bf16 / 128 fp8 elements each)");
+    kc = cfg->bk / kblk;
+  }
+  if (K % kblk || split > 1) kc = 1;
   const int32_t limit = (cfg && cfg->cut_limit > 0) ? cfg->cut_limit : 4;
   if (cfg && (cfg->cut_limit < 0 || cfg->cut_limit > 8)) return fail(TP_ERR_INVALID, "cut_limit must be 0..8");
   const bool count = ex->write_counts != nullptr;
   const bool checked = (ex->flags & TP_EXEC_CHECKED) != 0;
   Maps maps;
-  tp_status s = make_map(&maps.a, a->ptr, M, K, lda, esize, rows);
-  if (s != TP_OK) return s;
-  s = make_map(&maps.b, b->ptr, N, K, ldb, esize, pair ? bn / 2 : bn);
-  if (s != TP_OK) return s;
-  maps.b_cut = maps.b;
+  tp_status s = TP_OK;
   TcArgs p{};
   p.M = M;
   p.N = N;
@@ -829,6 +886,7 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   if (p.group_m > p.gm) p.group_m = p.gm;
   p.kblk = kblk;
   p.nk = (int32_t)nk;
+
   p.split = split;
   p.c_vec = (N % 8 == 0) && (((uintptr_t)c->t.ptr & 15) == 0);
   p.c = static_cast<__nv_bfloat16*>(c->t.ptr);
@@ -841,8 +899,18 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   while (cols < 2 * bn) cols *= 2;
   p.tmem_cols = cols;
   SmemPlan plan;
-  s = plan_smem(pair, rows, bn, split, cfg ? cfg->stages : 0, p.c_vec && !count, &plan);
+  s = plan_smem(pair, rows, bn, kc, split, cfg ? cfg->stages : 0, p.c_vec && !count, &plan);
   if (s != TP_OK) return s;
+  kc = plan.kc;
+  p.kc = kc;
+  auto operand_map = [&](CUtensorMap* m, const void* ptr, int64_t rws, int64_t ld, int box_rows) {
+    return kc > 1 ? make_map3(m, ptr, rws, K, ld, esize, box_rows, kc) : make_map(m, ptr, rws, K, ld, esize, box_rows);
+  };
+  s = operand_map(&maps.a, a->ptr, M, lda, rows);
+  if (s != TP_OK) return s;
+  s = operand_map(&maps.b, b->ptr, N, ldb, pair ? bn / 2 : bn);
+  if (s != TP_OK) return s;
+  maps.b_cut = maps.b;
   p.stages = plan.stages;
   p.body_bytes = (int32_t)plan.body;
   p.stage_c = plan.stage_c ? 1 : 0;
@@ -875,7 +943,7 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
       p.bn_cut = (int32_t)(bn / S);
       p.dp_slots = (int32_t)(T - R);
       p.total_slots = (int32_t)(T - R + R * S);
-      s = make_map(&maps.b_cut, b->ptr, N, K, ldb, esize, pair ? p.bn_cut / 2 : p.bn_cut);
+      s = operand_map(&maps.b_cut, b->ptr, N, ldb, pair ? p.bn_cut / 2 : p.bn_cut);
       if (s != TP_OK) return s;
     }
   }
@@ -905,7 +973,8 @@ tp_status gemm_tc_resident(tp_ctx* ctx, const tp_gemm_config* cfg, int32_t* prog
   if (split > 8 || (split & (split - 1))) return fail(TP_ERR_INVALID, "split_k must be 0, 1, 2, 4 or 8");
   if (split > 1 && bm != BM) return fail(TP_ERR_UNSUPPORTED, "split_k applies to 128-row tiles");
   SmemPlan plan;
-  tp_status s = plan_smem(pair, pair ? BM : bm, bn, split, cfg->stages, true, &plan);
+  const int kc = cfg->bk >= 256 ? 4 : cfg->bk >= 128 ? 2 : 1;  // K blocks per stage (bf16 K blocks of 64)
+  tp_status s = plan_smem(pair, pair ? BM : bm, bn, kc, split, cfg->stages, true, &plan);
   if (s != TP_OK) return s;
   (void)ctx;
   const int csize = pair ? 2 : split;

@@ -49,6 +49,7 @@ struct alignas(64) GroupedProblem {
   int32_t box_y;          // rows of the MMA B operand each CTA loads per stage
   int32_t c_tma;          // 1: normal orientation with 16-byte aligned C rows (map_c is valid)
   int32_t stream_x;       // swap tile whose B slab no other tile reads (loaded evict-first)
+  int32_t kc;             // K blocks per ring stage: the ring's count (3-D maps) when K % 64 == 0, else 1
 };
 
 }  // namespace tp
@@ -75,11 +76,19 @@ constexpr int kThreads = 192;
 constexpr int kRing = 4;
 constexpr int kMaxProblems = 1 << 16;
 constexpr uint32_t kStageX = 128 * 128;   // 128 rows x 128 bytes per CTA
-// B-operand rows per CTA and stage count: one CTA holds up to 256 rows
-// (4 stages of 48 KB); a CTA of a pair holds up to 128 (6 stages of 32 KB).
+// B-operand rows per CTA, K blocks per stage and stage count: one CTA holds
+// up to 256 rows, one K block per stage (4 stages of 48 KB); a CTA of a pair
+// holds up to 128 rows, two K blocks per stage (3 stages of 64 KB), so each
+// operand arrives as one 3-D TMA box of two K blocks. A TMA copy costs about
+// the same time whatever its size, so a swap tile streams its B slab in
+// 32 KB copies at twice the rate of 16 KB ones.
+#ifndef TP_GROUPED_PAIR_KC
+#define TP_GROUPED_PAIR_KC 2
+#endif
 template <bool kPair> struct Ring {
-  static constexpr uint32_t kStageY = kPair ? 128 * 128 : 256 * 128;
-  static constexpr int kStages = kPair ? 6 : 4;
+  static constexpr uint32_t kStageY = kPair ? 128 * 128 : 256 * 128;  // per K block
+  static constexpr int kKc = kPair ? TP_GROUPED_PAIR_KC : 1;
+  static constexpr int kStages = kPair ? 6 / TP_GROUPED_PAIR_KC : 4;
 };
 constexpr size_t kWordsBytes = 8 + 8 * kRing;
 constexpr uint32_t kStageC = 4u * 2u * 4096u;  // epilogue staging: 4 warps x 2 buffers x (32 rows x 128 B)
@@ -103,7 +112,9 @@ struct GroupedArgs {
 
 template <bool kPair, bool kCount>
 __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_constant__ GroupedArgs p) {
-  constexpr uint32_t kStageY = Ring<kPair>::kStageY;
+  constexpr int kKc = Ring<kPair>::kKc;
+  constexpr uint32_t kStageY = Ring<kPair>::kStageY * kKc;  // a stage: kKc K blocks of each operand
+  constexpr uint32_t kStageXs = kStageX * kKc;
   constexpr int kStages = Ring<kPair>::kStages;
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -118,7 +129,7 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
   const int32_t prog = kPair ? (int32_t)(blockIdx.x / 2) : (int32_t)blockIdx.x;
 
   const uint32_t x0 = base;
-  const uint32_t y0 = x0 + kStageX * kStages;
+  const uint32_t y0 = x0 + kStageXs * kStages;
   const uint32_t cst = y0 + kStageY * kStages;  // epilogue staging
   const uint32_t bars = cst + kStageC;
   auto full_bar = [&](int s) { return bars + 8u * s; };
@@ -221,22 +232,30 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
         decode(g, &pr, &tr, &tc);
         const int32_t xrow = (int32_t)(tr * pr->tile_rows + rank * 128);
         const int32_t yrow = (int32_t)(tc * pr->bn + rank * pr->box_y);
-        const uint32_t tx = kStageX + (uint32_t)pr->box_y * 128u;
+        const int32_t pkc = pr->kc;
+        const uint32_t tx = (kStageX + (uint32_t)pr->box_y * 128u) * (uint32_t)pkc;
         const int64_t nk = (pr->K + 63) / 64;
-        for (int64_t kb = 0; kb < nk; ++kb) {
+        for (int64_t kb = 0; kb < nk; kb += pkc) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err)) { ok = false; break; }
-          const int32_t kc = (int32_t)(kb * 64);
+          // 2-D maps take K at element kb * 64; 3-D maps take K block kb (a
+          // block past the last is zero-filled and never multiplied)
+          const int32_t kx = pkc > 1 ? 0 : (int32_t)(kb * 64);
           // streamed swap: x = B_i slab (read once), y = A_i (reused by every tile)
           const uint64_t px = pr->stream_x ? pol_stream : pol_keep;
           if constexpr (kPair) {
             const uint32_t fb = mapa(full_bar(stage), 0);  // both halves complete on the even CTA's barrier
             if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * tx);
-            tma_load_2d_pair(x0 + kStageX * stage, &pr->map_x, kc, xrow, fb, px);
-            tma_load_2d_pair(y0 + kStageY * stage, &pr->map_y, kc, yrow, fb, pol_keep);
+            if (pkc > 1) {
+              tma_load_3d_pair(x0 + kStageXs * stage, &pr->map_x, 0, xrow, (int32_t)kb, fb, px);
+              tma_load_3d_pair(y0 + kStageY * stage, &pr->map_y, 0, yrow, (int32_t)kb, fb, pol_keep);
+            } else {
+              tma_load_2d_pair(x0 + kStageXs * stage, &pr->map_x, kx, xrow, fb, px);
+              tma_load_2d_pair(y0 + kStageY * stage, &pr->map_y, kx, yrow, fb, pol_keep);
+            }
           } else {
             mbar_arrive_expect_tx(full_bar(stage), tx);
-            tma_load_2d(x0 + kStageX * stage, &pr->map_x, kc, xrow, full_bar(stage), px);
-            tma_load_2d(y0 + kStageY * stage, &pr->map_y, kc, yrow, full_bar(stage), pol_keep);
+            tma_load_2d(x0 + kStageXs * stage, &pr->map_x, kx, xrow, full_bar(stage), px);
+            tma_load_2d(y0 + kStageY * stage, &pr->map_y, kx, yrow, full_bar(stage), pol_keep);
           }
           fills[stage]++;
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
@@ -269,16 +288,21 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
         const uint32_t idesc = idesc_f32acc(kPair ? 256 : 128, (uint32_t)pr->bn, false);
         const uint32_t d = tmem_base + (uint32_t)(acc * 256);
         const int64_t nk = (pr->K + 63) / 64;
-        for (int64_t kb = 0; kb < nk; ++kb) {
+        const int32_t pkc = pr->kc;
+        const uint32_t y_blk = (uint32_t)pr->box_y * 128u;  // one K block of the B operand
+        for (int64_t kb = 0; kb < nk; kb += pkc) {
           if (!mbar_wait(full_bar(stage), phase, abort_flag, p.err)) { ok = false; break; }
           tc_fence_after();
-          const uint64_t ad = desc_kmajor_sw128(x0 + kStageX * stage);
-          const uint64_t bd = desc_kmajor_sw128(y0 + kStageY * stage);
+          // the stage's K blocks in K order (blocks past the last are not multiplied)
+          for (int32_t jb = 0; jb < pkc && kb + jb < nk; ++jb) {
+            const uint64_t ad = desc_kmajor_sw128(x0 + kStageXs * stage + kStageX * (uint32_t)jb);
+            const uint64_t bd = desc_kmajor_sw128(y0 + kStageY * stage + y_blk * (uint32_t)jb);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            const uint32_t accum = (kb > 0 || k > 0) ? 1u : 0u;
-            if constexpr (kPair) mma_pair<false>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accum);
-            else mma<false>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accum);
+            for (int k = 0; k < 4; ++k) {
+              const uint32_t accum = (kb + jb > 0 || k > 0) ? 1u : 0u;
+              if constexpr (kPair) mma_pair<false>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accum);
+              else mma<false>(d, ad + (uint64_t)(2 * k), bd + (uint64_t)(2 * k), idesc, accum);
+            }
           }
           if constexpr (kPair) mma_commit_pair(empty_bar(stage), 0x3);
           else mma_commit(empty_bar(stage));
@@ -449,14 +473,25 @@ tp_status c_map(CUtensorMap* map, void* ptr, int64_t M, int64_t N) {
   return TP_OK;
 }
 
-tp_status kmajor_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t k, int64_t ld, int box_rows) {
+// K-major bf16 operand, boxes of box_rows rows x 64 elements (128 bytes,
+// 128-byte swizzle); with kc > 1 (K a multiple of 64) seen as 3-D {64, rows,
+// K / 64} so that one box brings kc consecutive K blocks, stacked in shared
+// memory as kc K-major tiles.
+tp_status kmajor_map(CUtensorMap* map, const void* ptr, int64_t rows, int64_t k, int64_t ld, int box_rows, int kc) {
   auto fn = encode();
   if (!fn) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
-  cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
-  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+  const cuuint32_t rank = kc > 1 ? 3 : 2;
+  cuuint64_t dims[3] = {(cuuint64_t)k, (cuuint64_t)rows, 1};
+  cuuint64_t strides[2] = {(cuuint64_t)(ld * 2), 0};
+  cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+  if (kc > 1) {
+    dims[0] = 64;
+    dims[2] = (cuuint64_t)(k / 64);
+    strides[1] = 128;
+    box[2] = (cuuint32_t)kc;
+  }
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(ptr), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
@@ -498,6 +533,10 @@ tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int3
     delete plan;
     return s;
   };
+  // K blocks per ring stage of a problem: the ring's count when K is a
+  // multiple of the 64-element K block (3-D maps), else one
+  const int ring_kc = plan->pair ? Ring<true>::kKc : Ring<false>::kKc;
+  auto kc_of = [&](int64_t K) { return K % 64 == 0 ? ring_kc : 1; };
   // a swap-orientation entry: C rows [0, M) of `c` (row stride N) from A rows
   // of `a` (row stride lda) and B (N x K, row stride ldb)
   auto make_swap = [&](GroupedProblem& g, const void* a, const void* b, void* c, int64_t M, int64_t N, int64_t K,
@@ -512,8 +551,9 @@ tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int3
     g.box_y = plan->pair ? g.bn / 2 : g.bn;
     g.tiles_r = (N + trows - 1) / trows;
     g.tiles_c = 1;
-    tp_status s = kmajor_map(&g.map_x, b, N, K, ldb, 128);
-    if (s == TP_OK) s = kmajor_map(&g.map_y, a, M, K, lda, g.box_y);
+    g.kc = kc_of(K);
+    tp_status s = kmajor_map(&g.map_x, b, N, K, ldb, 128, g.kc);
+    if (s == TP_OK) s = kmajor_map(&g.map_y, a, M, K, lda, g.box_y, g.kc);
     return s;
   };
   int64_t elems = 0;
@@ -559,8 +599,9 @@ tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int3
       g.box_y = plan->pair ? 128 : 256;
       g.tiles_r = (M0 + trows - 1) / trows;
       g.tiles_c = (N + 255) / 256;
-      s = kmajor_map(&g.map_x, a.ptr, M0, K, lda, 128);
-      if (s == TP_OK) s = kmajor_map(&g.map_y, b.ptr, N, K, ldb, g.box_y);
+      g.kc = kc_of(K);
+      s = kmajor_map(&g.map_x, a.ptr, M0, K, lda, 128, g.kc);
+      if (s == TP_OK) s = kmajor_map(&g.map_y, b.ptr, N, K, ldb, g.box_y, g.kc);
       if (s == TP_OK && N % 8 == 0 && ((uintptr_t)c.ptr & 15) == 0) {
         s = c_map(&g.map_c, c.ptr, M0, N);
         g.c_tma = 1;
@@ -738,10 +779,12 @@ tp_status tp_grouped_gemm(tp_ctx* ctx, tp_grouped_plan* plan, int32_t num_progra
     return cudaLaunchKernelEx(&lc, kernel, a);
   };
   if (pair) {
-    smem = 1024 + (kStageX + Ring<true>::kStageY) * Ring<true>::kStages + kStageC + 232 + kWordsBytes;
+    smem = 1024 + (kStageX + Ring<true>::kStageY) * Ring<true>::kKc * Ring<true>::kStages + kStageC + 232 +
+           kWordsBytes;
     e = a.counts ? launch(grouped_kernel<true, true>, smem, 2) : launch(grouped_kernel<true, false>, smem, 2);
   } else {
-    smem = 1024 + (kStageX + Ring<false>::kStageY) * Ring<false>::kStages + kStageC + 232 + kWordsBytes;
+    smem = 1024 + (kStageX + Ring<false>::kStageY) * Ring<false>::kKc * Ring<false>::kStages + kStageC + 232 +
+           kWordsBytes;
     e = a.counts ? launch(grouped_kernel<false, true>, smem, 1) : launch(grouped_kernel<false, false>, smem, 1);
   }
   return o.end(e);

@@ -114,10 +114,11 @@ def scores(mlp, X) -> np.ndarray:
 
 
 def config_index(space, cfg) -> int:
-    """Position of a proposed config in the autotuner's space."""
-    key = (cfg.bm, cfg.bn, cfg.stages, cfg.group_m, cfg.split_k)
+    """Position of a proposed config in the autotuner's space (of its dtype:
+    BF16 and FP8 configs differ in bk, K blocks of 64 or 128 elements)."""
+    key = (cfg.bm, cfg.bn, cfg.bk, cfg.stages, cfg.group_m, cfg.split_k)
     for i, c in enumerate(space):
-        if (c.bm, c.bn, c.stages, c.group_m, c.split_k) == key:
+        if (c.bm, c.bn, c.bk, c.stages, c.group_m, c.split_k) == key:
             return i
     raise ValueError(f"config {key} is not in the space")
 
@@ -125,8 +126,8 @@ def config_index(space, cfg) -> int:
 def propose_indices(ctx, mlp, shapes) -> np.ndarray:
     """tp_propose's choice (no fallback) for each (M, N, K, dtype), as space indices."""
     from . import tp_propose
-    space = tp_autotune_space("bf16")
-    return np.array([config_index(space, tp_propose(ctx, mlp, m, n, k, dt, min_score=-1e9)[0])
+    spaces = {dt: tp_autotune_space(dt) for dt in DTYPES}
+    return np.array([config_index(spaces[dt], tp_propose(ctx, mlp, m, n, k, dt, min_score=-1e9)[0])
                      for m, n, k, dt in shapes])
 
 
@@ -154,12 +155,12 @@ def retimed_regret(ctx, shapes, TF, prop, default_index: int, repeats: int = 3) 
     exhaustive pick (arg-max of its table) and the default config are each
     timed `repeats` times (tp_autotune_time, median); the reference is the
     fastest of them, so regret = 1 - TFLOP/s(config) / TFLOP/s(reference)."""
-    space = tp_autotune_space("bf16")
+    spaces = {dt: tp_autotune_space(dt) for dt in DTYPES}
     reg, reg_def, beat = [], [], 0
     for i, (m, n, k, dt) in enumerate(shapes):
         best = int(np.argmax(TF[i]))
         idx = {int(prop[i]), best, int(default_index)}
-        t = {j: tp_autotune_time(ctx, m, n, k, dt, space[j], repeats=repeats) for j in sorted(idx)}
+        t = {j: tp_autotune_time(ctx, m, n, k, dt, spaces[dt][j], repeats=repeats) for j in sorted(idx)}
         ref = max(t.values())
         reg.append(1.0 - t[int(prop[i])] / ref)
         reg_def.append(1.0 - t[int(default_index)] / ref)

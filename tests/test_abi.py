@@ -138,22 +138,26 @@ def test_missing_library_fails_loudly(monkeypatch):
 
 
 def test_autotune_space_and_targets_on_the_host(built_lib):
-    """The autotuner's space (host data): by default the 48 single-pass
-    configs (rows 64, 128 or 256, columns 64..256, stages 3 or max, raster
-    bands 1 or 8), which all compute C bit-identically; with the split-K
-    opt-in the same 48 followed by the split-K configs, each with 128-row tiles and a
-    column slice of at least 32 per K slice. BF16 and FP8 share it, and
-    undefined flag bits are refused. Training targets train a config that
-    did not run towards 0."""
+    """The autotuner's space (host data): by default the 72 single-pass
+    configs (rows 64, 128 or 256, columns 64..256, 1, 2 or 4 K blocks per
+    stage, raster bands 1 or 8), which all compute C bit-identically; with
+    the split-K opt-in the same 72 followed by the split-K configs, each
+    with 128-row tiles and a column slice of at least 32 per K slice. BF16
+    and FP8 share the layout, with K blocks of 64 and 128 elements; undefined
+    flag bits are refused. Training targets train a config that did not run
+    towards 0."""
     whole = tp.tp_autotune_space("bf16")
-    assert len(whole) == 48 and len(tp.tp_autotune_space("fp8")) == 48
-    assert {(c.bm, c.bn, c.stages, c.group_m) for c in whole} == {
-        (bm, bn, st, g) for bm in (64, 128, 256) for bn in (64, 128, 192, 256) for st in (3, 0) for g in (1, 8)}
-    assert all(c.split_k == 0 for c in whole)
+    assert len(whole) == 72 and len(tp.tp_autotune_space("fp8")) == 72
+    assert {(c.bm, c.bn, c.bk, c.group_m) for c in whole} == {
+        (bm, bn, 64 * kb, g) for bm in (64, 128, 256) for bn in (64, 128, 192, 256) for kb in (1, 2, 4)
+        for g in (1, 8)}
+    assert [c.bk for c in tp.tp_autotune_space("fp8")] == [2 * c.bk for c in whole]
+    assert all(c.split_k == 0 and c.stages == 0 for c in whole)
     full = tp.tp_autotune_space("bf16", split_k=True)
-    assert len(full) == 53 and len(tp.tp_autotune_space("fp8", split_k=True)) == 53
-    assert [(c.bm, c.bn, c.stages, c.group_m) for c in full[:48]] == [(c.bm, c.bn, c.stages, c.group_m) for c in whole]
-    split = full[48:]
+    assert len(full) == 77 and len(tp.tp_autotune_space("fp8", split_k=True)) == 77
+    key = lambda c: (c.bm, c.bn, c.bk, c.stages, c.group_m)
+    assert [key(c) for c in full[:72]] == [key(c) for c in whole]
+    split = full[72:]
     assert [(c.bn, c.split_k) for c in split] == [(128, 2), (128, 4), (256, 2), (256, 4), (256, 8)]
     assert all(c.bm == 128 and c.bn % (32 * c.split_k) == 0 for c in split)
     n = ctypes.c_int32()

@@ -172,3 +172,26 @@ def test_8192_cubed_sampled_tiles(ctx):
     assert ogemm.rel_frobenius(got, np.stack(ref_in)) <= 5e-2
     del a, bt, c, qa, qbt
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("bm,bn,bk", [(64, 128, 256), (128, 256, 256), (256, 256, 256), (128, 128, 512)])
+def test_multi_block_stages_bit_identical(ctx, bm, bn, bk):
+    """FP8 stages of 2 or 4 K blocks of 128 codes (one 3-D TMA box per operand
+    and stage): the same MMAs in the same K order, so C is bit-identical to
+    one block per stage; integer inputs give the exact product."""
+    m, n, k = 320, 512, 1152
+    a = synth.tensor(synth.integers(m * k, 21, -7, 7), "bf16").reshape(m, k)
+    bt = synth.tensor(synth.integers(n * k, 22, -7, 7), "bf16").reshape(n, k)
+    a[0, 0], bt[0, 0] = 7, -7
+    qa, _, sa, _, _ = _quantize(ctx, a.cuda(), 16)
+    qbt, _, sb, _, _ = _quantize(ctx, bt.cuda(), 16)
+    out = []
+    for kk in (0, bk):
+        c = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
+        p = tp.tp_partition_create(ctx, c, (bm, bn))
+        tp.tp_partition_map(p, tp.MAP_STRIDED, min(9, tp.tp_partition_query(p)["num_tiles"]))
+        tp.tp_gemm_fp8(ctx, p, qa, qbt.t(), sa, sb, tp.gemm_config(bm=bm, bn=bn, bk=kk))
+        tp.tp_partition_destroy(p)
+        out.append(c)
+    assert torch.equal(out[0], out[1])
+    assert np.array_equal(out[1].cpu().double().numpy(), lowp.round_bf16(ogemm.gemm(a, bt.t())))

@@ -27,7 +27,7 @@ def _operands(m, n, k, seed=0, kind="normal"):
 
 
 def _gemm(ctx, a, bt, bn=128, kind=tp.MAP_STRIDED, P=None, group_m=1, stages=0, count=False, bm=128,
-          checked=False, split_k=0, cut_limit=0, out=None):
+          checked=False, split_k=0, cut_limit=0, out=None, bk=0):
     m, n = a.shape[0], bt.shape[0]
     c = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16) if out is None else out
     p = tp.tp_partition_create(ctx, c, (bm, bn))
@@ -40,7 +40,7 @@ def _gemm(ctx, a, bt, bn=128, kind=tp.MAP_STRIDED, P=None, group_m=1, stages=0, 
         counts = torch.zeros(m * n, dtype=torch.int32, device="cuda")
         owner = torch.full((m * n,), -1, dtype=torch.int32, device="cuda")
     tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=bm, bn=bn, group_m=group_m, stages=stages, split_k=split_k,
-                                                 cut_limit=cut_limit),
+                                                 cut_limit=cut_limit, bk=bk),
                tp.make_exec(write_counts=counts, write_owner=owner, checked=checked))
     info = tp.tp_partition_query(p)
     tp.tp_partition_destroy(p)
@@ -415,3 +415,49 @@ def test_64_row_tiles_equal_128_row_tiles(ctx, m):
     ai, bi = _operands(m, n, k, seed=m + 1, kind="int")
     c, _, _, _ = _gemm(ctx, ai, bi, bn=64, bm=64, P=5)
     assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(ogemm.gemm(ai.cpu(), bi.cpu().t())))
+
+
+@pytest.mark.parametrize("bm,bn", [(64, 64), (128, 128), (128, 256), (256, 256)])
+@pytest.mark.parametrize("bk", [128, 256])
+@pytest.mark.parametrize("m,n,k", [(300, 520, 1024), (129, 200, 448), (64, 256, 192), (257, 96, 4160)])
+def test_multi_block_stages_bit_identical(ctx, bm, bn, bk, m, n, k):
+    """Stages of 2 or 4 K blocks (each operand one 3-D TMA box per stage;
+    K-block counts that do not fill the last stage leave zero-filled blocks
+    that are not multiplied) issue the same MMAs in the same K order as one
+    block per stage: C is bit-identical, every element stored once, and the
+    integer product exact."""
+    if bm == 256 and bn % 64:
+        pytest.skip("256-row tiles take multiples of 64 columns")
+    a, bt = _operands(m, n, k, seed=k + bm)
+    ref, _, _, _ = _gemm(ctx, a, bt, bn=bn, bm=bm, P=7)
+    c = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
+    p = tp.tp_partition_create(ctx, c, (bm, bn))
+    tp.tp_partition_map(p, tp.MAP_STRIDED, min(7, tp.tp_partition_query(p)["num_tiles"]))
+    counts = torch.zeros(m * n, dtype=torch.int32, device="cuda")
+    owner = torch.full((m * n,), -1, dtype=torch.int32, device="cuda")
+    tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=bm, bn=bn, bk=bk), tp.make_exec(write_counts=counts,
+                                                                                    write_owner=owner))
+    tp.tp_partition_destroy(p)
+    assert torch.equal(c, ref)
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    ai, bi = _operands(m, n, k, seed=k + bm + 1, kind="int")
+    c2 = torch.empty(m, n, device="cuda", dtype=torch.bfloat16)
+    p = tp.tp_partition_create(ctx, c2, (bm, bn))
+    tp.tp_partition_map(p, tp.MAP_STRIDED, min(5, tp.tp_partition_query(p)["num_tiles"]))
+    tp.tp_gemm(ctx, p, ai, bi.t(), tp.gemm_config(bm=bm, bn=bn, bk=bk))
+    tp.tp_partition_destroy(p)
+    assert np.array_equal(c2.cpu().double().numpy(), lowp.round_bf16(ogemm.gemm(ai.cpu(), bi.cpu().t())))
+
+
+def test_multi_block_stages_fallback_and_validation(ctx):
+    """K not a multiple of the 64-element K block runs one block per stage
+    (same C); bk values other than 1, 2 or 4 K blocks are refused."""
+    m, n, k = 200, 256, 520
+    a, bt = _operands(m, n, k, seed=77)
+    ref, _, _, _ = _gemm(ctx, a, bt, bn=128, bm=128, P=3)
+    c, _, _, _ = _gemm(ctx, a, bt, bn=128, bm=128, P=3, bk=256)
+    assert torch.equal(c, ref)
+    for bad in (96, 192, 512):
+        with pytest.raises(tp.TPError) as e:
+            _gemm(ctx, a, bt, bn=128, bm=128, P=3, bk=bad)
+        assert e.value.status == tp._lib.ERR_INVALID

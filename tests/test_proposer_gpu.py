@@ -104,7 +104,7 @@ def test_features_targets_and_save_load(ctx, tmp_path):
 @pytest.mark.parametrize("dtype", ["bf16", "fp8"])
 def test_autotune_table_cache_and_numerics(ctx, dtype, tmp_path):
     space = tp.tp_autotune_space(dtype)
-    assert len(space) == 48 and all(cfg.split_k <= 1 for cfg in space)
+    assert len(space) == 72 and all(cfg.split_k <= 1 for cfg in space)
     M, N, K = 700, 900, 1024
     best, table, best_tf = tp.tp_autotune(ctx, M, N, K, dtype)
     assert len(table) == len(space) and all(t > 0 for t in table)
@@ -112,9 +112,9 @@ def test_autotune_table_cache_and_numerics(ctx, dtype, tmp_path):
     assert best.split_k <= 1
     assert tp.tp_autotune_lookup(ctx, M, N, K, dtype).bn == best.bn
     assert tp.tp_autotune_lookup(ctx, M, N, K, dtype, split_k=True) is None     # that search has not run
-    # the split-K opt-in times the same 48 configs plus the split ones
+    # the split-K opt-in times the same 72 configs plus the split ones
     best_s, table_s, _ = tp.tp_autotune(ctx, M, N, K, dtype, split_k=True)
-    assert len(table_s) == 53 and all(t > 0 for t in table_s[:48])
+    assert len(table_s) == 77 and all(t > 0 for t in table_s[:72])
     assert tp.tp_autotune_lookup(ctx, M, N, K, dtype, split_k=True) is not None
     t = tp.tp_autotune_time(ctx, M, N, K, dtype, best, repeats=3)
     assert 0.5 * best_tf < t < 2.0 * best_tf
@@ -211,7 +211,7 @@ def test_proposals_equal_exhaustive_pick_bit_for_bit(ctx, trained):
         prop, _, fb = tp.tp_propose(ctx, mlp, m, n, k, "bf16", min_score=-1e9)
         assert not fb and prop.split_k <= 1
         exh, _, _ = tp.tp_autotune(ctx, m, n, k, "bf16")
-        differ += (prop.bm, prop.bn, prop.stages, prop.group_m) != (exh.bm, exh.bn, exh.stages, exh.group_m)
+        differ += (prop.bm, prop.bn, prop.bk, prop.group_m) != (exh.bm, exh.bn, exh.bk, exh.group_m)
         a = synth.to_bf16(synth.normal(m * k, 100 + i)).reshape(m, k).cuda()
         bt = synth.to_bf16(synth.normal(n * k, 200 + i)).reshape(n, k).cuda()
         outs = []
@@ -243,26 +243,27 @@ def test_split_k_is_opt_in_only(ctx):
     cfg, _, fb = tp.tp_propose(ctx, m, 128, 256, 4096, "bf16", min_score=1e9)   # forced fallback
     assert fb and cfg.split_k <= 1
     best, table, _ = tp.tp_autotune(ctx, 128, 256, 4096, "bf16", split_k=True)
-    assert len(table) == 53 and max(table[48:]) > 0
+    assert len(table) == 77 and max(table[72:]) > 0
     tp.tp_mlp_destroy(m)
     # an MLP whose output count is the split-inclusive space is refused
-    bad = tp.tp_mlp_create(ctx, F, H, 53, 8, proposer.init_params(F, H, 53, seed=3))
+    bad = tp.tp_mlp_create(ctx, F, H, 77, 8, proposer.init_params(F, H, 77, seed=3))
     with pytest.raises(tp.TPError):
         tp.tp_propose(ctx, bad, 128, 256, 4096, "bf16", min_score=-1e9)
     tp.tp_mlp_destroy(bad)
 
 
-def test_autotune_cache_reads_v1_and_v2_files(ctx, tmp_path):
+def test_autotune_cache_reads_older_files(ctx, tmp_path):
     """v1 and v2 cache lines (no flags column) came from searches that
     included split-K: a single-pass winner loads under both searches, a
-    split winner only under the split-K search; v3 saves write the flags."""
+    split winner only under the split-K search; v3 lines lack bk (0); v4
+    saves write the flags and bk."""
     path = os.path.join(tmp_path, "v1.txt")
     with open(path, "w") as f:
         f.write("tp-autotune-cache v1\n")
         f.write("1111 2222 3344 1 256 128 3 8 76 1234.500\n")
     tp.tp_autotune_load(ctx, path)
     cfg = tp.tp_autotune_lookup(ctx, 1111, 2222, 3344, "bf16")
-    assert (cfg.bm, cfg.bn, cfg.stages, cfg.group_m, cfg.num_programs, cfg.split_k) == (256, 128, 3, 8, 76, 0)
+    assert (cfg.bm, cfg.bn, cfg.bk, cfg.stages, cfg.group_m, cfg.num_programs, cfg.split_k) == (256, 128, 0, 3, 8, 76, 0)
     assert tp.tp_autotune_lookup(ctx, 1111, 2222, 3344, "bf16", split_k=True).bn == 128
     path2 = os.path.join(tmp_path, "v2.txt")
     with open(path2, "w") as f:
@@ -270,11 +271,23 @@ def test_autotune_cache_reads_v1_and_v2_files(ctx, tmp_path):
         f.write("128 256 4096 1 128 256 0 1 0 4 300.0\n")
     tp.tp_autotune_load(ctx, path2)
     assert tp.tp_autotune_lookup(ctx, 128, 256, 4096, "bf16", split_k=True).split_k == 4
-    out = os.path.join(tmp_path, "v3.txt")
+    path3 = os.path.join(tmp_path, "v3.txt")
+    with open(path3, "w") as f:
+        f.write("tp-autotune-cache v3\n")
+        f.write("333 444 512 1 0 64 128 0 1 0 0 99.0\n")
+    tp.tp_autotune_load(ctx, path3)
+    assert (tp.tp_autotune_lookup(ctx, 333, 444, 512, "bf16").bm, tp.tp_autotune_lookup(ctx, 333, 444, 512).bk) == (64, 0)
+    tp.tp_autotune(ctx, 640, 384, 512, "bf16")
+    best = tp.tp_autotune_lookup(ctx, 640, 384, 512, "bf16")
+    out = os.path.join(tmp_path, "v4.txt")
     tp.tp_autotune_save(ctx, out)
     lines = open(out).read().splitlines()
-    assert lines[0] == "tp-autotune-cache v3"
-    assert any(line.split()[:11] == ["1111", "2222", "3344", "1", "0", "256", "128", "3", "8", "76", "0"]
+    assert lines[0] == "tp-autotune-cache v4"
+    assert any(line.split()[:12] == ["1111", "2222", "3344", "1", "0", "256", "128", "0", "3", "8", "76", "0"]
                for line in lines[1:])
-    assert not any(line.split()[:5] == ["128", "256", "4096", "1", "0"] and line.split()[10] == "4"
+    assert not any(line.split()[:5] == ["128", "256", "4096", "1", "0"] and line.split()[11] == "4"
                    for line in lines[1:])
+    assert any(line.split()[:8] == ["640", "384", "512", "1", "0", str(best.bm), str(best.bn), str(best.bk)]
+               for line in lines[1:])
+    tp.tp_autotune_load(ctx, out)
+    assert tp.tp_autotune_lookup(ctx, 640, 384, 512, "bf16").bk == best.bk
