@@ -557,13 +557,16 @@ def secondary_rows(tp, ctx, dev, stream, peaks, args):
     a = torch.randn(M, K, device=dev, generator=g).to(torch.bfloat16)
     bt = torch.randn(N, K, device=dev, generator=g).to(torch.bfloat16)   # B stored N x K (K-major)
     c = torch.empty(M, N, device=dev, dtype=torch.bfloat16)
-    cfg = tp.gemm_config(bm=256, bn=256, group_m=8)
+    # 256 x 256 tiles on CTA pairs, stages of 2 K blocks, raster bands of 8
+    cfg = tp.gemm_config(bm=256, bn=256, group_m=8, bk=128)
     p = tp.tp_partition_create(ctx, c, (256, 256))
     tp.tp_partition_map(p, tp.MAP_STRIDED, min(ctx.sm_count // 2, tp.tp_partition_query(p)["num_tiles"]))
     ms = _graph_time(tp, ctx, stream, lambda ex: tp.tp_gemm(ctx, p, a, bt.t(), cfg, ex), reps=10)
+    ms_cublas = _torch_graph_time(stream, lambda: torch.matmul(a, bt.t(), out=c), reps=10)
     tf = flops / (ms * 1e-3) / 1e12
     rows["gemm_bf16_8192"] = {
-        "tflops": tf, "ms": ms, "tile": [256, 256], "programs": ctx.sm_count // 2,
+        "tflops": tf, "ms": ms, "tile": [256, 256], "programs": ctx.sm_count // 2, "bk": 128, "group_m": 8,
+        "cublas_tflops_same_run": flops / (ms_cublas * 1e-3) / 1e12, "vs_cublas_same_run": ms_cublas / ms,
         "roofline": {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                      "frac_of_nominal": tf / NOMINAL["bf16_tflops"],
                      "frac": tf / peaks["bf16_tflops"], "peak_src": peaks["src"] + " bf16 burst"}}
@@ -584,12 +587,19 @@ def secondary_rows(tp, ctx, dev, stream, peaks, args):
 
     qms = _graph_time(tp, ctx, stream, quant, reps=5)
     qbytes = 2 * (2 * M * K * 2 + M * K)   # per operand: amax read + quantize read (bf16) + write (fp8)
+    # stages of 2 K blocks of 128 codes, raster bands of 16
+    cfg8 = tp.gemm_config(bm=256, bn=256, group_m=16, bk=256)
     ms8 = _graph_time(tp, ctx, stream,
-                      lambda ex: tp.tp_gemm_fp8(ctx, p, qa, qbt.t(), scale[0:1], scale[1:2], cfg, ex), reps=10)
+                      lambda ex: tp.tp_gemm_fp8(ctx, p, qa, qbt.t(), scale[0:1], scale[1:2], cfg8, ex), reps=10)
+    inv = (1.0 / scale).contiguous()
+    sa, sb = inv[0:1].reshape(()).contiguous(), inv[1:2].reshape(()).contiguous()
+    ms8_cublas = _torch_graph_time(stream, lambda: torch._scaled_mm(qa, qbt.t(), scale_a=sa, scale_b=sb,
+                                                                    out_dtype=torch.bfloat16), reps=10)
     tf8 = flops / (ms8 * 1e-3) / 1e12
     peak8 = 2 * peaks["bf16_tflops"]
     rows["gemm_fp8_8192"] = {
-        "tflops": tf8, "ms": ms8, "tile": [256, 256],
+        "tflops": tf8, "ms": ms8, "tile": [256, 256], "bk": 256, "group_m": 16,
+        "cublas_tflops_same_run": flops / (ms8_cublas * 1e-3) / 1e12, "vs_cublas_same_run": ms8_cublas / ms8,
         "quantize_ms": qms, "quantize_gbs": qbytes / (qms * 1e-3) / 1e9,
         "tflops_incl_quantize": flops / ((ms8 + qms) * 1e-3) / 1e12,
         "roofline": {"bound": "tensor", "achieved": tf8, "peak": peak8, "unit": "TFLOP/s", "frac": tf8 / peak8,
@@ -599,11 +609,60 @@ def secondary_rows(tp, ctx, dev, stream, peaks, args):
         tp.tp_partition_destroy(h)
     del a, bt, c, qa, qbt
     torch.cuda.empty_cache()
+    rows["small_gemm"] = small_gemm_row(tp, ctx, dev, stream)
     rows["grouped_64"] = grouped_row(tp, ctx, dev, stream, peaks)
     rows["decode_64"] = decode_row(tp, ctx, dev, stream, peaks)
     if not args.skip_proposer:
         rows["proposer"] = proposer_row(tp, ctx, args.train_shapes, args.test_shapes, args.epochs)
     return rows
+
+
+def _torch_graph_time(stream, fn, reps: int, replays: int = 3) -> float:
+    """Device time (ms) of one torch call (cuBLAS): `reps` calls captured
+    into one CUDA graph and replayed; the fastest replay / reps."""
+    from paper_2606_15991_gb300 import experiments
+
+    cap = experiments._Captured(None, stream, reps, torch_fn=fn)
+    ms = min(cap.time() for _ in range(replays))
+    cap.close()
+    return ms
+
+
+def small_gemm_row(tp, ctx, dev, stream):
+    """Small and skinny BF16 GEMMs on each shape's autotuned config (the
+    single-pass class, whose configs all compute C bit-identically) and on the
+    split-K opt-in's pick, against cuBLAS (torch.matmul) in the same run."""
+    import torch
+
+    from paper_2606_15991_gb300 import experiments
+
+    out = {}
+    for m, n, k in ((1024, 1024, 1024), (2048, 2048, 2048), (64, 8192, 8192), (64, 16384, 4096)):
+        g = torch.Generator(device=dev)
+        g.manual_seed(m + n + k)
+        a = torch.randn(m, k, device=dev, generator=g).to(torch.bfloat16)
+        bt = torch.randn(n, k, device=dev, generator=g).to(torch.bfloat16)
+        c = torch.empty(m, n, device=dev, dtype=torch.bfloat16)
+        fl = 2.0 * m * n * k
+        reps = 50
+        row = {}
+        for name, split in (("single_pass", False), ("split_k_opt_in", True)):
+            best, _, _ = tp.tp_autotune(ctx, m, n, k, "bf16", split_k=split)
+            p = tp.tp_partition_create(ctx, c, (best.bm, best.bn))
+            cfg = experiments.tuned_config(ctx, best, tp.tp_partition_query(p)["num_tiles"])
+            cfg.bk = best.bk
+            tp.tp_partition_map(p, tp.MAP_STRIDED, cfg.num_programs)
+            ms = _graph_time(tp, ctx, stream, lambda ex: tp.tp_gemm(ctx, p, a, bt.t(), cfg, ex), reps=reps)
+            tp.tp_partition_destroy(p)
+            row[name] = {"us": ms * 1e3, "tflops": fl / (ms * 1e-3) / 1e12,
+                         "config": {f: getattr(best, f) for f in ("bm", "bn", "bk", "group_m", "split_k")}}
+        ms_cb = _torch_graph_time(stream, lambda: torch.matmul(a, bt.t(), out=c), reps=reps)
+        row["cublas_us"] = ms_cb * 1e3
+        for name in ("single_pass", "split_k_opt_in"):
+            row[name]["vs_cublas"] = ms_cb / (row[name]["us"] * 1e-3)
+        row["b_stream_gbs_single_pass"] = 2.0 * n * k / (row["single_pass"]["us"] * 1e-6) / 1e9
+        out[f"{m}x{n}x{k}"] = row
+    return out
 
 
 def decode_row(tp, ctx, dev, stream, peaks):
@@ -772,8 +831,8 @@ def grouped_row(tp, ctx, dev, stream, peaks):
 
 def proposer_row(tp, ctx, train_n: int, test_n: int, epochs: int, log=None) -> dict:
     """The learned-proposer experiment: exhaustive tables of `train_n` shapes
-    (BF16 and FP8, x 48 single-pass configs: ~20k autotuner measurements at
-    417 shapes) for training on the GPU, `test_n` held-out shapes tuned
+    (BF16 and FP8, x 72 single-pass configs: ~20k autotuner measurements at
+    278 shapes) for training on the GPU, `test_n` held-out shapes tuned
     exhaustively as the judge, proposals made by tp_propose. Regret is
     reported twice: against the judge's one timing per config, and with the
     proposal, the exhaustive pick and the fixed default re-timed (median of 3
@@ -929,7 +988,8 @@ def run_kernel(args):
         c = torch.empty(n, n, device=dev, dtype=torch.bfloat16)
         p = tp.tp_partition_create(ctx, c, (256, 256))
         tp.tp_partition_map(p, tp.MAP_STRIDED, min(ctx.sm_count // 2, tp.tp_partition_query(p)["num_tiles"]))
-        cfg = tp.gemm_config(bm=256, bn=256, group_m=8)
+        # the benchmark rows' configs: stages of 2 K blocks; raster bands of 8 (bf16) / 16 (fp8)
+        cfg = tp.gemm_config(bm=256, bn=256, group_m=8 if k == "gemm_bf16" else 16, bk=128 if k == "gemm_bf16" else 256)
         if k == "gemm_bf16":
             fn = lambda: tp.tp_gemm(ctx, p, a, bt.t(), cfg)
         else:
@@ -1019,7 +1079,7 @@ def main():
     ap.add_argument("--size", type=int, default=4096)
     ap.add_argument("--elements", type=int, default=1 << 26)
     ap.add_argument("--group", type=int, default=8)
-    ap.add_argument("--train-shapes", type=int, default=417)
+    ap.add_argument("--train-shapes", type=int, default=278)
     ap.add_argument("--test-shapes", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=600)
     ap.add_argument("--reps", type=int, default=30)
