@@ -650,7 +650,6 @@ def small_gemm_row(tp, ctx, dev, stream):
             best, _, _ = tp.tp_autotune(ctx, m, n, k, "bf16", split_k=split)
             p = tp.tp_partition_create(ctx, c, (best.bm, best.bn))
             cfg = experiments.tuned_config(ctx, best, tp.tp_partition_query(p)["num_tiles"])
-            cfg.bk = best.bk
             tp.tp_partition_map(p, tp.MAP_STRIDED, cfg.num_programs)
             ms = _graph_time(tp, ctx, stream, lambda ex: tp.tp_gemm(ctx, p, a, bt.t(), cfg, ex), reps=reps)
             tp.tp_partition_destroy(p)
@@ -848,7 +847,7 @@ def proposer_row(tp, ctx, train_n: int, test_n: int, epochs: int, log=None) -> d
     X, T, V, TF = proposer.collect(ctx, train_shapes, log=log)
     t_collect = time.perf_counter() - t0
     t0 = time.perf_counter()
-    mlp, hist = proposer.train(ctx, X, T, V, epochs=epochs, batch=256, lr=3e-3, log=log)
+    mlp, hist = proposer.train(ctx, X, T, V, epochs=epochs, batch=64, lr=3e-3, log=log)
     t_train = time.perf_counter() - t0
     t0 = time.perf_counter()
     Xt, Tt, Vt, TFt = proposer.collect(ctx, test_shapes, log=log)

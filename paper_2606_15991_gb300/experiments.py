@@ -196,8 +196,8 @@ def tuned_config(ctx, best, tiles: int):
         progs = tiles
     else:
         progs = min(best.num_programs or (ctx.sm_count // (2 if best.bm == 256 else 1)), tiles)
-    return gemm_config(bm=best.bm, bn=best.bn, stages=best.stages, group_m=best.group_m, num_programs=progs,
-                       split_k=best.split_k)
+    return gemm_config(bm=best.bm, bn=best.bn, bk=best.bk, stages=best.stages, group_m=best.group_m,
+                       num_programs=progs, split_k=best.split_k)
 
 
 class _Captured:
@@ -335,7 +335,7 @@ def gemm_size_sweep(ctx, sizes=(1024, 2048, 4096, 8192, 16384, 32768), target_ms
         bT = bt.t()
         chk = make_exec(CAPTURE, stream, checked=True)
         ucfg = tuned_config(ctx, best, tiles)
-        pcfg = gemm_config(bm=best.bm, bn=best.bn, stages=best.stages, split_k=best.split_k)
+        pcfg = gemm_config(bm=best.bm, bn=best.bn, bk=best.bk, stages=best.stages, split_k=best.split_k)
         variants = {
             "safe": _Captured(ctx, stream, reps, record=lambda ex: tp_gemm(ctx, p, a, bT, cfg, ex)),
             "checked": _Captured(ctx, stream, reps, record=lambda ex: tp_gemm(ctx, p, a, bT, cfg, chk)),
