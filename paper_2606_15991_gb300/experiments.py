@@ -351,7 +351,7 @@ def gemm_size_sweep(ctx, sizes=(1024, 2048, 4096, 8192, 16384, 32768), target_ms
             v.close()
         if with_cublas:
             del c2
-        row = {"n": n, "tile": [best.bm, best.bn], "stages": best.stages, "group_m": best.group_m,
+        row = {"n": n, "tile": [best.bm, best.bn], "bk": best.bk, "stages": best.stages, "group_m": best.group_m,
                "split_k": best.split_k,
                "programs": progs, "tiles": tiles, "reps": reps, "tune_s": t_tune,
                "ms": ms, "tflops": {k: flops / (v * 1e-3) / 1e12 for k, v in ms.items()}}
