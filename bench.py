@@ -631,7 +631,8 @@ def _torch_graph_time(stream, fn, reps: int, replays: int = 3) -> float:
 def small_gemm_row(tp, ctx, dev, stream):
     """Small and skinny BF16 GEMMs on each shape's autotuned config (the
     single-pass class, whose configs all compute C bit-identically) and on the
-    split-K opt-in's pick, against cuBLAS (torch.matmul) in the same run."""
+    split-K opt-in's pick, against cuBLAS (torch.matmul) in the same run; for
+    M <= 256 also swap-AB through the grouped kernel (one-problem group)."""
     import torch
 
     from paper_2606_15991_gb300 import experiments
@@ -655,6 +656,15 @@ def small_gemm_row(tp, ctx, dev, stream):
             tp.tp_partition_destroy(p)
             row[name] = {"us": ms * 1e3, "tflops": fl / (ms * 1e-3) / 1e12,
                          "config": {f: getattr(best, f) for f in ("bm", "bn", "bk", "group_m", "split_k")}}
+        if m <= 256:
+            # the same product computed swap-AB (C^T = B^T A^T: 128 or 256 N rows
+            # per MMA, N = M) by the grouped kernel as a one-problem group
+            for pair in (True, False):
+                plan = tp.tp_grouped_plan_create(ctx, [(a, bt.t(), c)], -1, pair)
+                ms = _graph_time(tp, ctx, stream, lambda ex: tp.tp_grouped_gemm(ctx, plan, 0, ex), reps=reps)
+                tp.tp_grouped_plan_destroy(plan)
+                row["swap_ab_pairs" if pair else "swap_ab_single_ctas"] = {"us": ms * 1e3,
+                                                                          "tflops": fl / (ms * 1e-3) / 1e12}
         ms_cb = _torch_graph_time(stream, lambda: torch.matmul(a, bt.t(), out=c), reps=reps)
         row["cublas_us"] = ms_cb * 1e3
         for name in ("single_pass", "split_k_opt_in"):
