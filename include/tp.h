@@ -282,6 +282,10 @@ tp_status tp_graph_end(tp_graph* g);
  * pipeline). The replay is itself an operation with a mode (SYNC or ASYNC,
  * §3.2): the partitions recorded into the graph are busy while it runs. */
 tp_status tp_graph_replay(tp_graph* g, const tp_exec* ex);
+/* *count = the kernel nodes of an ended graph (each replay launches that many
+ * kernels). TP_ERR_INVALID before tp_graph_end; TP_ERR_CUDA if the graph
+ * cannot be walked. */
+tp_status tp_graph_kernel_count(tp_graph* g, int64_t* count);
 tp_status tp_graph_destroy(tp_graph* g);
 
 /* ----------------------------------------------------- element-wise maps */

@@ -22,7 +22,7 @@ __all__ = [
     "tp_version", "tp_ctx_create", "tp_ctx_destroy", "tp_ctx_info", "tp_tensor_init", "tp_tensor_view",
     "tp_partition_create", "tp_partition_map", "tp_partition_query", "tp_partition_destroy",
     "tp_event_create", "tp_event_query", "tp_event_wait", "tp_event_destroy",
-    "tp_graph_begin", "tp_graph_end", "tp_graph_replay", "tp_graph_destroy",
+    "tp_graph_begin", "tp_graph_end", "tp_graph_replay", "tp_graph_kernel_count", "tp_graph_destroy",
     "tp_map_axpy", "tp_map_gelu_mul", "tp_map_scale", "tp_map_add_accum", "tp_gemm",
     "tp_amax", "tp_quantize_fp8", "tp_gemm_fp8",
     "tp_grouped_plan_create", "tp_grouped_plan_info", "tp_grouped_plan_destroy", "tp_grouped_gemm",
@@ -202,6 +202,12 @@ def tp_graph_end(g: Graph) -> None:
 
 def tp_graph_replay(g: Graph, ex: tp_exec | None = None) -> None:
     call("tp_graph_replay", g.handle, ctypes.byref(ex if ex is not None else make_exec(stream=g.stream)))
+
+
+def tp_graph_kernel_count(g: Graph) -> int:
+    n = ctypes.c_int64()
+    call("tp_graph_kernel_count", g.handle, ctypes.byref(n))
+    return n.value
 
 
 def tp_graph_destroy(g: Graph) -> None:

@@ -98,6 +98,7 @@ _PROTOS = {
     "tp_graph_begin": [_VP, _VP, _PP],
     "tp_graph_end": [_VP],
     "tp_graph_replay": [_VP, _PE],
+    "tp_graph_kernel_count": [_VP, _PI64],
     "tp_graph_destroy": [_VP],
     "tp_map_axpy": [_VP, _VP, ctypes.c_float, _PT, _PT, _PE],
     "tp_map_gelu_mul": [_VP, _VP, _PT, _PT, _PE],

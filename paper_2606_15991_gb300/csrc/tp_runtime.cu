@@ -736,6 +736,26 @@ tp_status tp_graph_replay(tp_graph* g, const tp_exec* ex) {
   return TP_OK;
 }
 
+tp_status tp_graph_kernel_count(tp_graph* g, int64_t* count) {
+  if (!g || !count) return fail(TP_ERR_INVALID, "null argument");
+  if (!g->ended || !g->graph) return fail(TP_ERR_INVALID, "graph not ended");
+  size_t n = 0;
+  cudaError_t e = cudaGraphGetNodes(g->graph, nullptr, &n);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphGetNodes");
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n > 0) e = cudaGraphGetNodes(g->graph, nodes.data(), &n);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGraphGetNodes");
+  int64_t k = 0;
+  for (size_t i = 0; i < n; ++i) {
+    cudaGraphNodeType t;
+    e = cudaGraphNodeGetType(nodes[i], &t);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphNodeGetType");
+    k += t == cudaGraphNodeTypeKernel;
+  }
+  *count = k;
+  return TP_OK;
+}
+
 tp_status tp_graph_destroy(tp_graph* g) {
   if (!g) return fail(TP_ERR_INVALID, "null graph");
   {

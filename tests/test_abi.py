@@ -106,6 +106,9 @@ def test_ops_reject_missing_context(built_lib):
     assert _status("tp_map_axpy", None, h, ctypes.c_float(1.0), ctypes.byref(x), ctypes.byref(x),
                    ctypes.byref(ex)) == _lib.ERR_INVALID
     _status("tp_partition_destroy", h)
+    n = ctypes.c_int64(-1)
+    assert _status("tp_graph_kernel_count", None, ctypes.byref(n)) == _lib.ERR_INVALID
+    assert n.value == -1
 
 
 def test_ctx_create_without_gpu_fails_cleanly(built_lib):
