@@ -15,10 +15,23 @@
 // Fused kernels (the graph-replayed path): norm + QKV + gate/up with SiLU*mul
 // in the epilogue, and down projection + residual add. Unfused kernels (one
 // per step, the plain per-call path): rmsnorm, gemv, silu_mul, residual_add.
+//
+// The fused path streams the weights through TMA (gemv_stream_kernel): a
+// producer thread copies blocks of 32 rows x 256 columns (16 KB per box)
+// into a ring of shared-memory stages, and eight consumer warps take four
+// rows each; every lane multiplies 8 consecutive weights of a row by the
+// matching 8 entries of x (read from global memory, L2-resident) into four
+// fixed-order accumulators. A TMA copy into one SM costs about the same time
+// whatever its size, so a few large copies keep a stream going at the DRAM
+// read rate, above what per-lane 16-byte loads reach here.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 
+#include "sm100_ptx.cuh"
 #include "tp_internal.h"
 
 namespace tp {
@@ -209,6 +222,10 @@ template <bool kCount>
 __global__ void __launch_bounds__(kThreads) residual_finish_kernel(float* __restrict__ h, const float* __restrict__ partial,
                                                                    int64_t rows, int parts, uint32_t* counts,
                                                                    int32_t* owner) {
+  // launched as a programmatic dependent of the kernel that wrote the partial
+  // sums: let the next kernel be scheduled at once, then wait for them
+  sm100::allow_dependents();
+  sm100::grid_dependency_wait();
   const int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x;
   if (r >= rows) return;
   float s = 0.f;
@@ -217,6 +234,275 @@ __global__ void __launch_bounds__(kThreads) residual_finish_kernel(float* __rest
   if constexpr (kCount) {
     atomicAdd(counts + r, 1u);
     owner[r] = (int32_t)blockIdx.x;
+  }
+}
+
+// ------------------------------------------------ TMA-fed matrix-vector products
+constexpr int kSCols = 256;                       // columns per stage (512 bytes of bf16)
+constexpr int kSRows = 32;                        // rows of a plain unit (one 16 KB box)
+constexpr int kSPairRows = 16;                    // row pairs of a SiLU unit (one 16 KB 3-D box)
+constexpr int kSStage = kSRows * kSCols * 2;      // 16 KB per stage
+constexpr int kSConsumers = 8;                    // consumer warps
+constexpr int kSThreads = (kSConsumers + 1) * 32; // + the producer warp
+constexpr int kSStages = 12;
+constexpr int kSMaxXCols = 8192;                  // x (or a slice of it) kept in shared memory, fp32
+
+// Units of equal work (32 rows x one K slice): a plain unit is 32 rows of its
+// problem, a SiLU-pair unit 16 rows g = [r0, +16) of the first half of its
+// weight matrix and their partners u, the same rows of the second half. Problem 0 has units0
+// units, problem 1 the rest. With slices > 1 (long rows) a unit is (row
+// block, K slice), its dot products go to partial[slice * rows + r], and the
+// producer brings each unit's slice of x into one of two x buffers.
+struct StreamArgs {
+  int64_t k;                // columns (x length)
+  int32_t slices;           // K slices (1, or > 1 with partial sums)
+  int64_t slice_cols;       // columns per slice, a multiple of kSCols, <= kSMaxXCols
+  int64_t units0, units;    // units of problem 0, total units
+  int64_t rows0, rows1;
+  int32_t epi0, epi1;       // kPlain / kSiluPair / kResidual (partial sums when slices > 1)
+  float* y0;
+  float* y1;
+  float* partial;
+  const float* x;           // 16-byte aligned
+  int32_t norm;             // x = rmsnorm(x) * gamma (slices == 1 only)
+  float eps;
+  const float* gamma;
+  int* err;
+  uint64_t wait_ns;
+  uint32_t* counts;
+  int32_t* owner;
+};
+
+template <bool kCount>
+__global__ void __launch_bounds__(kSThreads, 1)
+    gemv_stream_kernel(const __grid_constant__ CUtensorMap map0, const __grid_constant__ CUtensorMap map1,
+                       const __grid_constant__ StreamArgs p) {
+  using namespace sm100;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* gbase = smem_raw + (base - raw);
+  // [ring: kSStages x 16 KB][x: one buffer of slice_cols floats, two when sliced][barriers]
+  const uint32_t xcols = (uint32_t)p.slice_cols;
+  const int xbufs = p.slices > 1 ? 2 : 1;
+  const uint32_t xs0 = base + (uint32_t)kSStage * kSStages;
+  float* xsp = reinterpret_cast<float*>(gbase + (size_t)kSStage * kSStages);
+  const uint32_t bars = xs0 + 4u * xcols * (uint32_t)xbufs;
+  auto full_bar = [&](int s) { return bars + 8u * s; };
+  auto empty_bar = [&](int s) { return bars + 8u * (kSStages + s); };
+  auto xfull_bar = [&](int b) { return bars + 8u * (2 * kSStages + b); };
+  auto xempty_bar = [&](int b) { return bars + 8u * (2 * kSStages + 2 + b); };
+  const uint32_t words = 8u * (2 * kSStages + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + (bars - base) + words);
+  float* red = reinterpret_cast<float*>(gbase + (bars - base) + words + 16u);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kSStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), kSConsumers);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(xfull_bar(b), 1);
+      mbar_init(xempty_bar(b), kSConsumers);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+    if (p.units0 > 0) tma_prefetch_desc(&map0);
+    if (p.units > p.units0) tma_prefetch_desc(&map1);
+  }
+  __syncthreads();
+  // Programmatic dependent launch: the weights do not depend on the grids
+  // before this one, so the producer streams them at once, overlapping the
+  // previous kernel's tail; x (written by the previous kernels) is read only
+  // after the dependency wait (consumers; the producer before its first copy
+  // of an x slice).
+  allow_dependents();
+  // consumers only (warps 0-7): named barrier 1
+  auto consumers_sync = [] { asm volatile("bar.sync 1, %0;" ::"n"(kSConsumers * 32) : "memory"); };
+  if (warp < kSConsumers) {
+    grid_dependency_wait();
+    if (p.slices == 1) {
+      // the whole of x (normalised) in shared memory, zero past its end
+      float scale = 1.f;
+      if (p.norm) {
+        float sq = 0.f;
+        for (int64_t i = threadIdx.x; i < p.k; i += kSConsumers * 32) sq = fmaf(p.x[i], p.x[i], sq);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) red[warp] = sq;
+        consumers_sync();
+        float t = 0.f;
+        for (int w = 0; w < kSConsumers; ++w) t += red[w];  // fixed order
+        scale = rsqrtf(t / (float)p.k + p.eps);
+      }
+      for (uint32_t i = threadIdx.x; i < xcols; i += kSConsumers * 32) {
+        float v = i < p.k ? p.x[i] : 0.f;
+        if (p.norm && i < p.k) v = v * scale * (p.gamma ? p.gamma[i] : 1.f);
+        xsp[i] = v;
+      }
+      consumers_sync();
+    }
+  }
+  const int64_t stages_per_unit = (p.slice_cols + kSCols - 1) / kSCols;
+  // unit u -> problem, row block, K slice
+  auto decode_unit = [&](int64_t u, bool* second, int64_t* rb, int32_t* slice) {
+    *second = u >= p.units0;
+    const int64_t ub = *second ? u - p.units0 : u;
+    *rb = p.slices > 1 ? ub / p.slices : ub;
+    *slice = p.slices > 1 ? (int32_t)(ub % p.slices) : 0;
+  };
+  if (warp == kSConsumers) {
+    // ---------------- producer: one thread issues every copy
+    if (lane == 0) {
+      uint32_t fills[kSStages] = {};
+      uint32_t xfills[2] = {};
+      int stage = 0;
+      uint32_t phase = 0;
+      int64_t t = 0;  // units taken by this CTA (x buffer = t & 1)
+      bool ok = true;
+      const uint64_t pol = policy_evict_first();  // weights are read once
+      bool waited = false;
+      for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++t) {
+        bool second;
+        int64_t rb;
+        int32_t slice;
+        decode_unit(u, &second, &rb, &slice);
+        if (p.slices > 1) {
+          if (!waited) {
+            grid_dependency_wait();  // x is the previous kernels' output
+            waited = true;
+          }
+          // this unit's slice of x (whole 8-float pieces: k is a multiple of 8)
+          const int xb = (int)(t & 1);
+          if (!mbar_wait(xempty_bar(xb), (uint32_t)(((t >> 1) & 1) ^ 1), abort_flag, p.err, p.wait_ns)) {
+            ok = false;
+            break;
+          }
+          const int64_t c0 = (int64_t)slice * p.slice_cols;
+          const uint32_t bytes = (uint32_t)(min(p.slice_cols, p.k - c0) * 4);
+          mbar_arrive_expect_tx(xfull_bar(xb), bytes);
+          bulk_copy_g2s(xs0 + 4u * xcols * (uint32_t)xb, p.x + c0, bytes, xfull_bar(xb));
+          xfills[xb]++;
+        }
+        const bool pair = (second ? p.epi1 : p.epi0) == kSiluPair;
+        const CUtensorMap* m = second ? &map1 : &map0;
+        const int32_t r0 = (int32_t)(rb * (pair ? kSPairRows : kSRows));
+        for (int64_t st = 0; st < stages_per_unit; ++st) {
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err, p.wait_ns)) { ok = false; break; }
+          const int32_t c0 = (int32_t)(slice * p.slice_cols + st * kSCols);  // 512-byte aligned
+          const uint32_t dst = base + (uint32_t)kSStage * stage;
+          mbar_arrive_expect_tx(full_bar(stage), (uint32_t)kSStage);
+          if (pair) tma_load_3d(dst, m, c0, r0, 0, full_bar(stage), pol);  // g rows, then their u rows
+          else tma_load_2d(dst, m, c0, r0, full_bar(stage), pol);
+          fills[stage]++;
+          if (++stage == kSStages) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (!ok) {
+        // every copy this thread issued lands before the CTA retires
+        for (int s2 = 0; s2 < kSStages; ++s2)
+          if (fills[s2]) mbar_wait(full_bar(s2), (fills[s2] - 1u) & 1u, nullptr, nullptr, 200000000ull);
+        for (int b = 0; b < 2; ++b)
+          if (xfills[b]) mbar_wait(xfull_bar(b), (xfills[b] - 1u) & 1u, nullptr, nullptr, 200000000ull);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---------------- consumers: warp w owns rows [4w, 4w + 4) of a plain
+    // unit, or row pairs [2w, 2w + 2) of a SiLU-pair unit (g in the stage's
+    // first half, u in its second)
+    int stage = 0;
+    uint32_t phase = 0;
+    int64_t t = 0;
+    bool ok = true;
+    for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++t) {
+      bool second;
+      int64_t rb;
+      int32_t slice;
+      decode_unit(u, &second, &rb, &slice);
+      const int epi = second ? p.epi1 : p.epi0;
+      const bool pair = epi == kSiluPair;
+      const int xb = p.slices > 1 ? (int)(t & 1) : 0;
+      const float* xs = xsp + (size_t)xcols * xb;
+      const int64_t lim = min(p.k - (int64_t)slice * p.slice_cols, p.slice_cols);  // valid x in this slice
+      if (p.slices > 1) {
+        const bool got = mbar_wait(xfull_bar(xb), (uint32_t)((t >> 1) & 1), abort_flag, p.err, p.wait_ns);
+        if (!__all_sync(0xffffffffu, got)) break;
+      }
+      // acc[q][j]: q = row (plain) or 2 * half + pair (SiLU); j = lane slot
+      float acc[4][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[q][j] = 0.f;
+      for (int64_t st = 0; st < stages_per_unit; ++st) {
+        // this lane's 8 columns of x (zero past the valid part of the buffer)
+        const int64_t cx = st * kSCols + lane * 8;
+        float xv[8];
+        if (cx + 8 <= lim) {
+          const float4 a = *reinterpret_cast<const float4*>(xs + cx);
+          const float4 b = *reinterpret_cast<const float4*>(xs + cx + 4);
+          xv[0] = a.x; xv[1] = a.y; xv[2] = a.z; xv[3] = a.w;
+          xv[4] = b.x; xv[5] = b.y; xv[6] = b.z; xv[7] = b.w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) xv[j] = cx + j < lim ? xs[cx + j] : 0.f;
+        }
+        const bool got = mbar_wait(full_bar(stage), phase, abort_flag, p.err, p.wait_ns);
+        if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+        const uint32_t src = base + (uint32_t)kSStage * stage;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          // smem row of slot q: plain row 4w + q; SiLU half q / 2, pair 2w + q % 2
+          const uint32_t row = pair ? (uint32_t)((q >> 1) * kSPairRows + 2 * warp + (q & 1)) : (uint32_t)(4 * warp + q);
+          uint32_t w4[4];
+          ld_shared_v4(src + row * (kSCols * 2) + (uint32_t)lane * 16u, w4);
+          const __nv_bfloat162* w2 = reinterpret_cast<const __nv_bfloat162*>(w4);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const float2 f = __bfloat1622float2(w2[j]);
+            acc[q][j] = fmaf(f.x, xv[2 * j], acc[q][j]);
+            acc[q][j] = fmaf(f.y, xv[2 * j + 1], acc[q][j]);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty_bar(stage));
+        if (++stage == kSStages) { stage = 0; phase ^= 1u; }
+      }
+      if (p.slices > 1 && ok) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(xempty_bar(xb));  // this warp is done with the x buffer
+      }
+      if (!ok) break;
+      // fixed-order reductions: the lane's four slots, then a butterfly
+      float sum[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float tq = (acc[q][0] + acc[q][1]) + (acc[q][2] + acc[q][3]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tq += __shfl_xor_sync(0xffffffffu, tq, o);
+        sum[q] = tq;
+      }
+      if (lane == 0) {
+        const int64_t rows = second ? p.rows1 : p.rows0;
+        float* y = second ? p.y1 : p.y0;
+        const int nout = pair ? 2 : 4;
+        for (int q = 0; q < nout; ++q) {
+          const int64_t r = pair ? rb * kSPairRows + 2 * warp + q : rb * kSRows + 4 * warp + q;
+          if (r >= rows) continue;
+          if (p.slices > 1) {
+            p.partial[(int64_t)slice * rows + r] = sum[q];
+            continue;
+          }
+          y[r] = pair ? silu(sum[q]) * sum[2 + q] : (epi == kResidual ? y[r] + sum[q] : sum[q]);
+          if constexpr (kCount) {
+            const int64_t e = second ? p.rows0 + r : r;
+            atomicAdd(p.counts + e, 1u);
+            p.owner[e] = (int32_t)blockIdx.x;
+          }
+        }
+      }
+    }
   }
 }
 
@@ -279,6 +565,80 @@ int gemv_grid(tp_ctx* ctx, int64_t k) {
   const int per_sm = smem > 110 * 1024 ? 1 : (smem > 70 * 1024 ? 2 : 4);
   return ctx->sm_count * per_sm;
 }
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+// Weights [rows, k] bf16 (row stride ld) as boxes of 32 rows x 256 columns,
+// no swizzle (each row's 512 bytes contiguous in shared memory), zero fill
+// past the edges. A SiLU-pair matrix ([2 n, k]: g rows, then u rows) is seen
+// as 3-D {k, n, 2} and boxed {256, 16, 2}, so one copy brings 16 g rows and
+// their 16 u partners (16 KB, g first).
+tp_status weight_map(CUtensorMap* map, const tp_tensor* w, bool pair) {
+  auto fn = encode_fn();
+  if (!fn) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled unavailable from the driver");
+  const int64_t half = w->shape[0] / 2;
+  cuuint64_t dims[3] = {(cuuint64_t)w->shape[1], (cuuint64_t)(pair ? half : w->shape[0]), 2};
+  cuuint64_t strides[2] = {(cuuint64_t)(w->strides[0] * 2), (cuuint64_t)(half * w->strides[0] * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)kSCols, (cuuint32_t)(pair ? kSPairRows : kSRows), 2};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, pair ? 3 : 2, w->ptr, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(TP_ERR_CUDA, "cuTensorMapEncodeTiled (weights) failed (" + std::to_string((int)r) + ")");
+  return TP_OK;
+}
+
+// The streaming kernel on w0 (problem 0) and w1 (problem 1, may equal w0):
+// one persistent CTA per SM, or one per unit when there are fewer units.
+tp_status launch_stream(tp_ctx* ctx, StreamArgs a, const tp_tensor* w0, bool pair0, const tp_tensor* w1, bool pair1,
+                        cudaStream_t st) {
+  // a problem without units has no map (and its descriptor is never touched)
+  CUtensorMap m0 = {}, m1 = {};
+  tp_status s = a.units0 > 0 ? weight_map(&m0, w0, pair0) : TP_OK;
+  if (s == TP_OK && a.units > a.units0) s = weight_map(&m1, w1, pair1);
+  if (s != TP_OK) return s;
+  a.err = ctx->d_err;
+  a.wait_ns = 2000000000ull;
+  const size_t xbytes = (size_t)a.slice_cols * 4 * (a.slices > 1 ? 2 : 1);
+  const size_t smem = 1024 + (size_t)kSStage * kSStages + xbytes + 8 * (2 * kSStages + 4) + 16 + 64;
+  auto k = a.counts ? gemv_stream_kernel<true> : gemv_stream_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(e, "streaming matrix-vector kernel attributes");
+  const int grid = (int)std::min<int64_t>(a.units, ctx->sm_count);
+  if (grid > 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kSThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k, m0, m1, a);
+    if (e != cudaSuccess) return cuda_fail(e, "streaming matrix-vector kernel launch");
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "streaming matrix-vector kernel launch");
+  return TP_OK;
+}
+
+// Whether the streaming kernel takes x: 16-byte aligned fp32 (copied to
+// shared memory in bulk, read in 16-byte pieces).
+bool stream_ok(const tp_tensor* x) { return ((uintptr_t)x->ptr & 15) == 0; }
 
 tp_status check_counts(const tp_exec* ex) {
   if ((ex->write_counts == nullptr) != (ex->write_owner == nullptr))
@@ -409,7 +769,37 @@ tp_status tp_decode_norm_qkv_gu(tp_ctx* ctx, tp_partition* qkv, tp_partition* a_
   a.counts = ex->write_counts;
   a.owner = ex->write_owner;
   cudaError_t e = cudaSuccess;
-  if (d > 0 && nq + ni > 0) e = launch_gemv<kPlain, 1, 4>(a, gemv_grid(ctx, d), o.stream);
+  if (d > 0 && nq + ni > 0) {
+    if (stream_ok(h) && d <= kSMaxXCols) {
+      // QKV rows in 32-row units, then gate/up pairs in 16-pair units
+      o.check_err = true;  // its waits are bounded: a timeout lands in the error word
+      StreamArgs sa{};
+      sa.k = d;
+      sa.slices = 1;
+      sa.slice_cols = d;
+      sa.units0 = (nq + kSRows - 1) / kSRows;
+      sa.units = sa.units0 + (ni + kSPairRows - 1) / kSPairRows;
+      sa.rows0 = nq;
+      sa.rows1 = ni;
+      sa.epi0 = kPlain;
+      sa.epi1 = kSiluPair;
+      sa.y0 = a.y;
+      sa.y1 = a.y2;
+      sa.x = a.x;
+      sa.norm = 1;
+      sa.eps = eps;
+      sa.gamma = a.gamma;
+      sa.counts = a.counts;
+      sa.owner = a.owner;
+      tp_status ls = launch_stream(ctx, sa, w_qkv, false, w_gu, true, o.stream);
+      if (ls != TP_OK) {
+        o.abort();
+        return ls;
+      }
+    } else {
+      e = launch_gemv<kPlain, 1, 4>(a, gemv_grid(ctx, d), o.stream);
+    }
+  }
   return o.end(e);
 }
 
@@ -434,6 +824,59 @@ tp_status tp_decode_down_residual(tp_ctx* ctx, tp_partition* h, const tp_tensor*
   a.counts = ex->write_counts;
   a.owner = ex->write_owner;
   cudaError_t e = cudaSuccess;
+  // streamed when x fits shared memory whole (short rows) or in slices of
+  // whole stages, about 16 of them, whose partial sums fit the context's
+  // scratch
+  int32_t slices = 1;
+  int64_t slice_cols = ni;
+  if (ni > 2048) {
+    slice_cols = std::min<int64_t>(((ni + 15) / 16 + kSCols - 1) / kSCols * kSCols, kSMaxXCols);
+    slices = (int32_t)((ni + slice_cols - 1) / slice_cols);
+  }
+  const bool streamed = stream_ok(a_in) && slice_cols <= kSMaxXCols && d * slices <= tp_ctx::kPartialFloats;
+  if (d > 0 && ni > 0 && streamed) {
+    o.check_err = true;  // the streaming kernel's waits are bounded
+    // 32-row units; with slices, a finish kernel adds the partial sums to h
+    // in slice order
+    StreamArgs sa{};
+    sa.k = ni;
+    sa.slices = slices;
+    sa.slice_cols = slice_cols;
+    sa.units0 = (d + kSRows - 1) / kSRows * sa.slices;
+    sa.units = sa.units0;
+    sa.rows0 = d;
+    sa.rows1 = d;
+    sa.epi0 = kResidual;
+    sa.epi1 = kResidual;
+    sa.y0 = a.y;
+    sa.y1 = a.y;
+    sa.partial = ctx->d_partial;
+    sa.x = a.x;
+    sa.counts = sa.slices > 1 ? nullptr : a.counts;
+    sa.owner = sa.slices > 1 ? nullptr : a.owner;
+    tp_status ls = launch_stream(ctx, sa, w_down, false, w_down, false, o.stream);
+    if (ls != TP_OK) {
+      o.abort();
+      return ls;
+    }
+    if (sa.slices > 1) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)((d + kThreads - 1) / kThreads));
+      cfg.blockDim = dim3(kThreads);
+      cfg.stream = o.stream;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      e = a.counts ? cudaLaunchKernelEx(&cfg, residual_finish_kernel<true>, a.y, (const float*)ctx->d_partial, d,
+                                        (int)sa.slices, a.counts, a.owner)
+                   : cudaLaunchKernelEx(&cfg, residual_finish_kernel<false>, a.y, (const float*)ctx->d_partial, d,
+                                        (int)sa.slices, (uint32_t*)nullptr, (int32_t*)nullptr);
+      if (e == cudaSuccess) e = cudaGetLastError();
+    }
+    return o.end(e);
+  }
   // few long rows: split K into 8 slices, one slice per CTA (so 4 CTAs fit
   // per SM); partial sums go to context scratch allocated once, and a
   // finish kernel adds them to h in slice order

@@ -137,7 +137,9 @@ def test_64_layer_chain_matches_oracle_and_replay_matches_eager(ctx):
     (each layer's three weight matrices copied to the host in turn) within
     1e-4 relative Frobenius error for h and for the last layer's qkv, and
     the captured graph replayed gives exactly the eager result, on every
-    replay."""
+    replay. The graph holds three kernels a layer: the fused norm + QKV +
+    gate/up product, the down product over K slices, and the finish kernel
+    adding the slices' partial sums to h."""
     d, nq, ni, L = 5120, 10240, 25600, 64
     g = torch.Generator(device="cuda")
     layers = []
@@ -165,6 +167,7 @@ def test_64_layer_chain_matches_oracle_and_replay_matches_eager(ctx):
     gr = tp.tp_graph_begin(ctx, s)
     ch.record_fused(tp.make_exec(mode=tp.CAPTURE, stream=s))
     tp.tp_graph_end(gr)
+    assert tp.tp_graph_kernel_count(gr) == 3 * L
     for _ in range(3):
         h.copy_(h0)
         torch.cuda.synchronize()
@@ -175,3 +178,48 @@ def test_64_layer_chain_matches_oracle_and_replay_matches_eager(ctx):
     ch.close()
     del layers
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("d,nq,ni", [(8, 1, 8), (264, 45, 40), (5000, 70, 24), (512, 96, 3000)])
+def test_streamed_layer_ragged_shapes(ctx, d, nq, ni):
+    """The TMA-fed matrix-vector kernels on ragged sizes: rows that do not
+    fill a 32-row (QKV, down) or 16-pair (gate/up) unit, columns that do not
+    fill a 256-column stage, and rows of 3000 (down projection) cut into K
+    slices whose partial sums a finish kernel adds; every output row written
+    once, h and qkv against the FP64 oracle."""
+    layers = _layers(d, nq, ni, 1, seed=d + ni)
+    h0 = _vec(d, 13)
+    h = h0.clone()
+    ch = tp.DecodeChain(ctx, h, layers)
+    counts = torch.zeros(nq + ni, dtype=torch.int32, device="cuda")
+    owner = torch.full((nq + ni,), -1, dtype=torch.int32, device="cuda")
+    w = layers[0]
+    tp.tp_decode_norm_qkv_gu(ctx, ch.p["qkv"], ch.p["a"], h, None, w[0], w[1], 1e-6,
+                             tp.make_exec(write_counts=counts, write_owner=owner))
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    dcounts = torch.zeros(d, dtype=torch.int32, device="cuda")
+    downer = torch.full((d,), -1, dtype=torch.int32, device="cuda")
+    tp.tp_decode_down_residual(ctx, ch.p["h"], w[2], ch.a, tp.make_exec(write_counts=dcounts, write_owner=downer))
+    assert opart.check_counts(dcounts.cpu().numpy())["ok"]
+    href, qref = odecode.chain(h0.cpu(), [(a.cpu(), b.cpu(), c.cpu()) for a, b, c in layers])
+    assert ogemm.rel_frobenius(h.cpu(), href) <= 1e-5
+    assert ogemm.rel_frobenius(ch.qkv.cpu(), qref) <= 1e-5
+    ch.close()
+
+
+def test_unaligned_input_takes_the_per_lane_kernel(ctx):
+    """An input vector that is not 16-byte aligned goes to the per-lane
+    kernel (the streaming kernel reads x in 16-byte pieces): same results
+    within the oracle's tolerance."""
+    d, nq, ni = 264, 40, 24
+    layers = _layers(d, nq, ni, 1, seed=91)
+    buf = torch.zeros(d + 1, device="cuda")
+    h = buf[1:]                                    # 4-byte offset
+    h.copy_(_vec(d, 14))
+    h0 = h.clone()
+    ch = tp.DecodeChain(ctx, h, layers)
+    ch.record_fused()
+    href, qref = odecode.chain(h0.cpu(), [(a.cpu(), b.cpu(), c.cpu()) for a, b, c in layers])
+    assert ogemm.rel_frobenius(h.cpu(), href) <= 1e-5
+    assert ogemm.rel_frobenius(ch.qkv.cpu(), qref) <= 1e-5
+    ch.close()
