@@ -17,13 +17,15 @@
 // per step, the plain per-call path): rmsnorm, gemv, silu_mul, residual_add.
 //
 // The fused path streams the weights through TMA (gemv_stream_kernel): a
-// producer thread copies blocks of 32 rows x 256 columns (16 KB per box)
-// into a ring of shared-memory stages, and eight consumer warps take four
-// rows each; every lane multiplies 8 consecutive weights of a row by the
-// matching 8 entries of x (read from global memory, L2-resident) into four
-// fixed-order accumulators. A TMA copy into one SM costs about the same time
-// whatever its size, so a few large copies keep a stream going at the DRAM
-// read rate, above what per-lane 16-byte loads reach here.
+// producer thread copies blocks of 32 rows x 256 columns (16 KB per box; a
+// 3-D box brings 16 gate rows with their 16 up partners) into a ring of
+// shared-memory stages, and eight consumer warps take four rows each; every
+// lane multiplies 8 consecutive weights of a row by the matching 8 entries of
+// x, which sits in shared memory (whole, or one K slice at a time brought by
+// bulk copies), into four fixed-order accumulators. A TMA copy into one SM
+// costs about the same time whatever its size, so a few large copies keep a
+// stream going at the DRAM read rate, above what per-lane 16-byte loads reach
+// here.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -244,18 +246,28 @@ constexpr int kSPairRows = 16;                    // row pairs of a SiLU unit (o
 constexpr int kSStage = kSRows * kSCols * 2;      // 16 KB per stage
 constexpr int kSConsumers = 8;                    // consumer warps
 constexpr int kSThreads = (kSConsumers + 1) * 32; // + the producer warp
-constexpr int kSStages = 12;
+constexpr int kSStages = 12;                      // ring stages at most (StreamArgs::stages)
 constexpr int kSMaxXCols = 8192;                  // x (or a slice of it) kept in shared memory, fp32
+constexpr int kSXVec = kSMaxXCols / (kSConsumers * 32 * 4);  // 16-byte pieces of x per consumer thread
+constexpr int kSMaxXBufs = 4;                     // x slice buffers (sliced mode)
+constexpr int kSOBuf = 32;                        // units whose outputs are held in shared memory
+constexpr size_t kSSmemMax = 232448;              // opt-in shared memory per CTA
+// shared memory beside the x buffers: alignment slack, ring, barriers, abort word, reduction scratch
+// alignment slack, barriers, abort word, reduction scratch, output buffer (+ the ring and x)
+constexpr size_t kSSmemFixed = 1024 + 8 * (2 * kSStages + 2 * kSMaxXBufs) + 16 + 64 + (size_t)kSOBuf * kSRows * 4;
 
 // Units of equal work (32 rows x one K slice): a plain unit is 32 rows of its
 // problem, a SiLU-pair unit 16 rows g = [r0, +16) of the first half of its
 // weight matrix and their partners u, the same rows of the second half. Problem 0 has units0
 // units, problem 1 the rest. With slices > 1 (long rows) a unit is (row
 // block, K slice), its dot products go to partial[slice * rows + r], and the
-// producer brings each unit's slice of x into one of two x buffers.
+// producer brings each unit's slice of x into one of xbufs x buffers (2-4,
+// as many as shared memory holds).
 struct StreamArgs {
   int64_t k;                // columns (x length)
   int32_t slices;           // K slices (1, or > 1 with partial sums)
+  int32_t xbufs;            // x slice buffers when slices > 1 (2..kSMaxXBufs)
+  int32_t stages;           // ring stages (2..kSStages)
   int64_t slice_cols;       // columns per slice, a multiple of kSCols, <= kSMaxXCols
   int64_t units0, units;    // units of problem 0, total units
   int64_t rows0, rows1;
@@ -282,26 +294,32 @@ __global__ void __launch_bounds__(kSThreads, 1)
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* gbase = smem_raw + (base - raw);
-  // [ring: kSStages x 16 KB][x: one buffer of slice_cols floats, two when sliced][barriers]
+  // [ring: stages x 16 KB][x: one buffer of slice_cols floats, xbufs when sliced][barriers]
+  const int nst = p.stages;
   const uint32_t xcols = (uint32_t)p.slice_cols;
-  const int xbufs = p.slices > 1 ? 2 : 1;
-  const uint32_t xs0 = base + (uint32_t)kSStage * kSStages;
-  float* xsp = reinterpret_cast<float*>(gbase + (size_t)kSStage * kSStages);
-  const uint32_t bars = xs0 + 4u * xcols * (uint32_t)xbufs;
+  const uint32_t xstride = (xcols + 3u) & ~3u;  // floats per x buffer: 16-byte multiples
+  const int xbufs = p.slices > 1 ? p.xbufs : 1;
+  const uint32_t xs0 = base + (uint32_t)kSStage * nst;
+  float* xsp = reinterpret_cast<float*>(gbase + (size_t)kSStage * nst);
+  const uint32_t bars = xs0 + 4u * xstride * (uint32_t)xbufs;
   auto full_bar = [&](int s) { return bars + 8u * s; };
   auto empty_bar = [&](int s) { return bars + 8u * (kSStages + s); };
   auto xfull_bar = [&](int b) { return bars + 8u * (2 * kSStages + b); };
-  auto xempty_bar = [&](int b) { return bars + 8u * (2 * kSStages + 2 + b); };
-  const uint32_t words = 8u * (2 * kSStages + 4);
+  auto xempty_bar = [&](int b) { return bars + 8u * (2 * kSStages + kSMaxXBufs + b); };
+  const uint32_t words = 8u * (2 * kSStages + 2 * kSMaxXBufs);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + (bars - base) + words);
   float* red = reinterpret_cast<float*>(gbase + (bars - base) + words + 16u);
+  // outputs of the last kSOBuf units: slot t mod kSOBuf holds unit t's 32
+  // values (warp w's at [4w, 4w + 4)), written to global memory kSOBuf units
+  // at a time and at the end
+  float* obuf = red + 16;
   const int warp = threadIdx.x / 32, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kSStages; ++s) {
+    for (int s = 0; s < nst; ++s) {
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), kSConsumers);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kSMaxXBufs; ++b) {
       mbar_init(xfull_bar(b), 1);
       mbar_init(xempty_bar(b), kSConsumers);
     }
@@ -322,11 +340,47 @@ __global__ void __launch_bounds__(kSThreads, 1)
   if (warp < kSConsumers) {
     grid_dependency_wait();
     if (p.slices == 1) {
-      // the whole of x (normalised) in shared memory, zero past its end
+      // The whole of x (normalised) in shared memory. Each consumer thread
+      // loads its 16-byte pieces of x (and of gamma) at once, up to
+      // kSXVec of them, so the prologue waits about one memory latency,
+      // not one per element.
+      constexpr int kT = kSConsumers * 32;
+      const int64_t n4 = p.k / 4;   // whole 16-byte pieces
+      const int tail = (int)(p.k - 4 * n4);
+      const float4* x4 = reinterpret_cast<const float4*>(p.x);
+      float4 xv[kSXVec];
+#pragma unroll
+      for (int j = 0; j < kSXVec; ++j) {
+        const int64_t i4 = threadIdx.x + (int64_t)j * kT;
+        xv[j] = i4 < n4 ? x4[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      const float xt = threadIdx.x < tail ? p.x[4 * n4 + threadIdx.x] : 0.f;
+      float gv[kSXVec][4];
+      float gt = 1.f;
+#pragma unroll
+      for (int j = 0; j < kSXVec; ++j)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) gv[j][c] = 1.f;
+      if (p.norm && p.gamma) {
+#pragma unroll
+        for (int j = 0; j < kSXVec; ++j) {
+          const int64_t i4 = threadIdx.x + (int64_t)j * kT;
+          if (i4 < n4)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) gv[j][c] = p.gamma[4 * i4 + c];
+        }
+        if (threadIdx.x < tail) gt = p.gamma[4 * n4 + threadIdx.x];
+      }
       float scale = 1.f;
       if (p.norm) {
-        float sq = 0.f;
-        for (int64_t i = threadIdx.x; i < p.k; i += kSConsumers * 32) sq = fmaf(p.x[i], p.x[i], sq);
+        float sq = xt * xt;
+#pragma unroll
+        for (int j = 0; j < kSXVec; ++j) {
+          sq = fmaf(xv[j].x, xv[j].x, sq);
+          sq = fmaf(xv[j].y, xv[j].y, sq);
+          sq = fmaf(xv[j].z, xv[j].z, sq);
+          sq = fmaf(xv[j].w, xv[j].w, sq);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
         if (lane == 0) red[warp] = sq;
@@ -335,11 +389,22 @@ __global__ void __launch_bounds__(kSThreads, 1)
         for (int w = 0; w < kSConsumers; ++w) t += red[w];  // fixed order
         scale = rsqrtf(t / (float)p.k + p.eps);
       }
-      for (uint32_t i = threadIdx.x; i < xcols; i += kSConsumers * 32) {
-        float v = i < p.k ? p.x[i] : 0.f;
-        if (p.norm && i < p.k) v = v * scale * (p.gamma ? p.gamma[i] : 1.f);
-        xsp[i] = v;
+      float4* xs4 = reinterpret_cast<float4*>(xsp);
+#pragma unroll
+      for (int j = 0; j < kSXVec; ++j) {
+        const int64_t i4 = threadIdx.x + (int64_t)j * kT;
+        if (i4 < n4) {
+          float4 v = xv[j];
+          if (p.norm) {
+            v.x = v.x * scale * gv[j][0];
+            v.y = v.y * scale * gv[j][1];
+            v.z = v.z * scale * gv[j][2];
+            v.w = v.w * scale * gv[j][3];
+          }
+          xs4[i4] = v;
+        }
       }
+      if (threadIdx.x < tail) xsp[4 * n4 + threadIdx.x] = p.norm ? xt * scale * gt : xt;
       consumers_sync();
     }
   }
@@ -352,57 +417,65 @@ __global__ void __launch_bounds__(kSThreads, 1)
     *slice = p.slices > 1 ? (int32_t)(ub % p.slices) : 0;
   };
   if (warp == kSConsumers) {
-    // ---------------- producer: one thread issues every copy
+    // ---------------- producer: one thread issues every copy. With K
+    // slices, unit t's x slice goes to buffer t mod xbufs; the first unit's
+    // weight stages (as many as the ring holds) are issued before the
+    // dependency wait, the x slices only after it.
     if (lane == 0) {
       uint32_t fills[kSStages] = {};
-      uint32_t xfills[2] = {};
+      uint32_t xfills[kSMaxXBufs] = {};
       int stage = 0;
       uint32_t phase = 0;
-      int64_t t = 0;  // units taken by this CTA (x buffer = t & 1)
+      int64_t t = 0;  // units taken by this CTA
       bool ok = true;
       const uint64_t pol = policy_evict_first();  // weights are read once
-      bool waited = false;
       for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++t) {
         bool second;
         int64_t rb;
         int32_t slice;
         decode_unit(u, &second, &rb, &slice);
-        if (p.slices > 1) {
-          if (!waited) {
-            grid_dependency_wait();  // x is the previous kernels' output
-            waited = true;
-          }
-          // this unit's slice of x (whole 8-float pieces: k is a multiple of 8)
-          const int xb = (int)(t & 1);
-          if (!mbar_wait(xempty_bar(xb), (uint32_t)(((t >> 1) & 1) ^ 1), abort_flag, p.err, p.wait_ns)) {
-            ok = false;
-            break;
-          }
-          const int64_t c0 = (int64_t)slice * p.slice_cols;
-          const uint32_t bytes = (uint32_t)(min(p.slice_cols, p.k - c0) * 4);
-          mbar_arrive_expect_tx(xfull_bar(xb), bytes);
-          bulk_copy_g2s(xs0 + 4u * xcols * (uint32_t)xb, p.x + c0, bytes, xfull_bar(xb));
-          xfills[xb]++;
-        }
         const bool pair = (second ? p.epi1 : p.epi0) == kSiluPair;
         const CUtensorMap* m = second ? &map1 : &map0;
         const int32_t r0 = (int32_t)(rb * (pair ? kSPairRows : kSRows));
-        for (int64_t st = 0; st < stages_per_unit; ++st) {
-          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err, p.wait_ns)) { ok = false; break; }
+        auto issue = [&](int64_t st) {
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err, p.wait_ns)) return false;
           const int32_t c0 = (int32_t)(slice * p.slice_cols + st * kSCols);  // 512-byte aligned
           const uint32_t dst = base + (uint32_t)kSStage * stage;
           mbar_arrive_expect_tx(full_bar(stage), (uint32_t)kSStage);
           if (pair) tma_load_3d(dst, m, c0, r0, 0, full_bar(stage), pol);  // g rows, then their u rows
           else tma_load_2d(dst, m, c0, r0, full_bar(stage), pol);
           fills[stage]++;
-          if (++stage == kSStages) { stage = 0; phase ^= 1u; }
+          if (++stage == nst) { stage = 0; phase ^= 1u; }
+          return true;
+        };
+        int64_t st = 0;
+        if (p.slices > 1) {
+          if (t == 0) {
+            // consumers start on x only after this copy, so at most a ring's
+            // worth of stages goes first
+            for (; st < stages_per_unit && st < nst && ok; ++st) ok = issue(st);
+            if (!ok) break;
+            grid_dependency_wait();  // x is the previous kernels' output
+          }
+          // this unit's slice of x (whole 8-float pieces: k is a multiple of 8)
+          const int xb = (int)(t % xbufs);
+          if (!mbar_wait(xempty_bar(xb), (uint32_t)(((t / xbufs) & 1) ^ 1), abort_flag, p.err, p.wait_ns)) {
+            ok = false;
+            break;
+          }
+          const int64_t c0 = (int64_t)slice * p.slice_cols;
+          const uint32_t bytes = (uint32_t)(min(p.slice_cols, p.k - c0) * 4);
+          mbar_arrive_expect_tx(xfull_bar(xb), bytes);
+          bulk_copy_g2s(xs0 + 4u * xstride * (uint32_t)xb, p.x + c0, bytes, xfull_bar(xb));
+          xfills[xb]++;
         }
+        for (; st < stages_per_unit && ok; ++st) ok = issue(st);
       }
       if (!ok) {
         // every copy this thread issued lands before the CTA retires
-        for (int s2 = 0; s2 < kSStages; ++s2)
+        for (int s2 = 0; s2 < nst; ++s2)
           if (fills[s2]) mbar_wait(full_bar(s2), (fills[s2] - 1u) & 1u, nullptr, nullptr, 200000000ull);
-        for (int b = 0; b < 2; ++b)
+        for (int b = 0; b < kSMaxXBufs; ++b)
           if (xfills[b]) mbar_wait(xfull_bar(b), (xfills[b] - 1u) & 1u, nullptr, nullptr, 200000000ull);
       }
     }
@@ -413,8 +486,44 @@ __global__ void __launch_bounds__(kSThreads, 1)
     // first half, u in its second)
     int stage = 0;
     uint32_t phase = 0;
-    int64_t t = 0;
+    int64_t t = 0, done = 0;
     bool ok = true;
+    // Writes this warp's outputs of the CTA's units [t0, t1) (at most kSOBuf),
+    // 8 units per round, lane l taking value l % 4 of unit t0 + l / 4 (a
+    // SiLU-pair unit has 2 values per warp, the others 4). Stores of a unit
+    // leave at once in a batch instead of holding up the next stage's
+    // release of its ring slot.
+    auto flush = [&](int64_t t0, int64_t t1) {
+      __syncwarp();
+      for (int64_t b0 = t0; b0 < t1; b0 += 8) {
+        const int64_t tt = b0 + lane / 4;
+        const int q = lane & 3;
+        if (tt >= t1) continue;
+        bool sec;
+        int64_t rbb;
+        int32_t sl;
+        decode_unit(blockIdx.x + tt * (int64_t)gridDim.x, &sec, &rbb, &sl);
+        const int ep = sec ? p.epi1 : p.epi0;
+        const bool pr = ep == kSiluPair;
+        if (pr && q >= 2) continue;
+        const int64_t rows = sec ? p.rows1 : p.rows0;
+        const int64_t r = pr ? rbb * kSPairRows + 2 * warp + q : rbb * kSRows + 4 * warp + q;
+        if (r >= rows) continue;
+        const float v = obuf[(tt % kSOBuf) * kSRows + 4 * warp + q];
+        if (p.slices > 1) {
+          p.partial[(int64_t)sl * rows + r] = v;
+          continue;
+        }
+        float* y = sec ? p.y1 : p.y0;
+        y[r] = ep == kResidual ? y[r] + v : v;
+        if constexpr (kCount) {
+          const int64_t e = sec ? p.rows0 + r : r;
+          atomicAdd(p.counts + e, 1u);
+          p.owner[e] = (int32_t)blockIdx.x;
+        }
+      }
+      __syncwarp();
+    };
     for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++t) {
       bool second;
       int64_t rb;
@@ -422,11 +531,11 @@ __global__ void __launch_bounds__(kSThreads, 1)
       decode_unit(u, &second, &rb, &slice);
       const int epi = second ? p.epi1 : p.epi0;
       const bool pair = epi == kSiluPair;
-      const int xb = p.slices > 1 ? (int)(t & 1) : 0;
-      const float* xs = xsp + (size_t)xcols * xb;
+      const int xb = p.slices > 1 ? (int)(t % xbufs) : 0;
+      const float* xs = xsp + (size_t)xstride * xb;
       const int64_t lim = min(p.k - (int64_t)slice * p.slice_cols, p.slice_cols);  // valid x in this slice
       if (p.slices > 1) {
-        const bool got = mbar_wait(xfull_bar(xb), (uint32_t)((t >> 1) & 1), abort_flag, p.err, p.wait_ns);
+        const bool got = mbar_wait(xfull_bar(xb), (uint32_t)((t / xbufs) & 1), abort_flag, p.err, p.wait_ns);
         if (!__all_sync(0xffffffffu, got)) break;
       }
       // acc[q][j]: q = row (plain) or 2 * half + pair (SiLU); j = lane slot
@@ -467,7 +576,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(empty_bar(stage));
-        if (++stage == kSStages) { stage = 0; phase ^= 1u; }
+        if (++stage == nst) { stage = 0; phase ^= 1u; }
       }
       if (p.slices > 1 && ok) {
         __syncwarp();
@@ -484,25 +593,19 @@ __global__ void __launch_bounds__(kSThreads, 1)
         sum[q] = tq;
       }
       if (lane == 0) {
-        const int64_t rows = second ? p.rows1 : p.rows0;
-        float* y = second ? p.y1 : p.y0;
-        const int nout = pair ? 2 : 4;
-        for (int q = 0; q < nout; ++q) {
-          const int64_t r = pair ? rb * kSPairRows + 2 * warp + q : rb * kSRows + 4 * warp + q;
-          if (r >= rows) continue;
-          if (p.slices > 1) {
-            p.partial[(int64_t)slice * rows + r] = sum[q];
-            continue;
-          }
-          y[r] = pair ? silu(sum[q]) * sum[2 + q] : (epi == kResidual ? y[r] + sum[q] : sum[q]);
-          if constexpr (kCount) {
-            const int64_t e = second ? p.rows0 + r : r;
-            atomicAdd(p.counts + e, 1u);
-            p.owner[e] = (int32_t)blockIdx.x;
-          }
+        float* ob = obuf + (t % kSOBuf) * kSRows + 4 * warp;
+        if (pair && p.slices == 1) {
+          ob[0] = silu(sum[0]) * sum[2];
+          ob[1] = silu(sum[1]) * sum[3];
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) ob[q] = sum[q];
         }
       }
+      done = t + 1;
+      if (done % kSOBuf == 0) flush(done - kSOBuf, done);
     }
+    if (ok && done % kSOBuf) flush(done - done % kSOBuf, done);
   }
 }
 
@@ -600,6 +703,19 @@ tp_status weight_map(CUtensorMap* map, const tp_tensor* w, bool pair) {
   return TP_OK;
 }
 
+// Ring depth of the streaming kernel: 10 stages of 16 KB per SM. Deeper
+// rings were measured slower (a 10240 x 5120 + 51200 x 5120 product: 89.4 us
+// at 10 stages, 92.6 at 12; 8 stages: 89.7), the DRAM queues fuller for no
+// more bandwidth.
+constexpr int kSRingStages = 10;
+int stream_stages() { return kSRingStages; }
+
+// The longest K slice (whole stages) of which two x buffers fit beside the ring.
+int64_t stream_max_slice_cols() {
+  const size_t fixed = kSSmemFixed + (size_t)kSStage * stream_stages();
+  return (int64_t)((kSSmemMax - fixed) / 8 / kSCols * kSCols);
+}
+
 // The streaming kernel on w0 (problem 0) and w1 (problem 1, may equal w0):
 // one persistent CTA per SM, or one per unit when there are fewer units.
 tp_status launch_stream(tp_ctx* ctx, StreamArgs a, const tp_tensor* w0, bool pair0, const tp_tensor* w1, bool pair1,
@@ -611,12 +727,23 @@ tp_status launch_stream(tp_ctx* ctx, StreamArgs a, const tp_tensor* w0, bool pai
   if (s != TP_OK) return s;
   a.err = ctx->d_err;
   a.wait_ns = 2000000000ull;
-  const size_t xbytes = (size_t)a.slice_cols * 4 * (a.slices > 1 ? 2 : 1);
-  const size_t smem = 1024 + (size_t)kSStage * kSStages + xbytes + 8 * (2 * kSStages + 4) + 16 + 64;
+  // x: one buffer, or with K slices as many (2..kSMaxXBufs) as fit
+  a.stages = stream_stages();
+  const size_t fixed = kSSmemFixed + (size_t)kSStage * a.stages;
+  const size_t xbuf = (size_t)((a.slice_cols + 3) & ~int64_t(3)) * 4;
+  a.xbufs = a.slices > 1 ? (int32_t)std::min<size_t>(kSMaxXBufs, (kSSmemMax - fixed) / xbuf) : 1;
+  if (a.slices > 1 && a.xbufs < 2) return fail(TP_ERR_INVALID, "streaming matrix-vector kernel: K slice too long");
+  const size_t smem = fixed + xbuf * (size_t)a.xbufs;
   auto k = a.counts ? gemv_stream_kernel<true> : gemv_stream_kernel<false>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(e, "streaming matrix-vector kernel attributes");
-  const int grid = (int)std::min<int64_t>(a.units, ctx->sm_count);
+  // the fewest CTAs (at most one per SM) that take as many units each as
+  // one per SM would: every CTA gets the same count, give or take one
+  int grid = (int)std::min<int64_t>(a.units, ctx->sm_count);
+  if (grid > 0) {
+    const int64_t per = (a.units + grid - 1) / grid;
+    grid = (int)((a.units + per - 1) / per);
+  }
   if (grid > 0) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -824,16 +951,21 @@ tp_status tp_decode_down_residual(tp_ctx* ctx, tp_partition* h, const tp_tensor*
   a.counts = ex->write_counts;
   a.owner = ex->write_owner;
   cudaError_t e = cudaSuccess;
-  // streamed when x fits shared memory whole (short rows) or in slices of
-  // whole stages, about 16 of them, whose partial sums fit the context's
-  // scratch
-  int32_t slices = 1;
-  int64_t slice_cols = ni;
-  if (ni > 2048) {
-    slice_cols = std::min<int64_t>(((ni + 15) / 16 + kSCols - 1) / kSCols * kSCols, kSMaxXCols);
-    slices = (int32_t)((ni + slice_cols - 1) / slice_cols);
-  }
-  const bool streamed = stream_ok(a_in) && slice_cols <= kSMaxXCols && d * slices <= tp_ctx::kPartialFloats;
+  // Streamed in K slices as long as two x buffers of one fit beside the
+  // ring, and more of them (down to 2048 columns) while the units (32-row
+  // block x slice) number under four per SM; slices of equal whole stages.
+  // Few long units beat many short ones (measured: a 5120 x 25600 product
+  // takes 43.4 us in 4 slices, 44.7 us in 10, 52 us in 15). One slice (x
+  // whole in shared memory, no finish kernel) when that is all it takes.
+  const int64_t row_blocks = (d + kSRows - 1) / kSRows;
+  const int64_t max_cols = stream_max_slice_cols();
+  int64_t slices64 = (ni + max_cols - 1) / max_cols;
+  while (row_blocks * slices64 < 4 * (int64_t)ctx->sm_count && ni / (slices64 + 1) >= 2048) ++slices64;
+  int32_t slices = (int32_t)slices64;
+  int64_t slice_cols = slices == 1 ? ni : ((ni + slices - 1) / slices + kSCols - 1) / kSCols * kSCols;
+  if (slices > 1) slices = (int32_t)((ni + slice_cols - 1) / slice_cols);
+  // (x slices arrive by bulk copies, whose sizes are multiples of 16 bytes)
+  const bool streamed = stream_ok(a_in) && (slices == 1 || ni % 4 == 0) && d * slices <= tp_ctx::kPartialFloats;
   if (d > 0 && ni > 0 && streamed) {
     o.check_err = true;  // the streaming kernel's waits are bounded
     // 32-row units; with slices, a finish kernel adds the partial sums to h

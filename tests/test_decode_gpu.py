@@ -223,3 +223,36 @@ def test_unaligned_input_takes_the_per_lane_kernel(ctx):
     assert ogemm.rel_frobenius(h.cpu(), href) <= 1e-5
     assert ogemm.rel_frobenius(ch.qkv.cpu(), qref) <= 1e-5
     ch.close()
+
+
+@pytest.mark.parametrize("d,nq,ni,pad", [(261, 40, 48, 3), (64, 8, 3001, 7), (64, 8, 3004, 4), (96, 8, 70000, 0)])
+def test_streamed_layer_padded_weights(ctx, d, nq, ni, pad):
+    """Weights that are views of wider matrices (row pitch a multiple of 8
+    elements, rows of any length): an odd input length for the fused norm +
+    QKV + gate/up kernel, a down projection whose input length is not a
+    multiple of 4 floats (no bulk copies of its slices: the per-lane kernel
+    runs it) or is one (ragged last slice), and rows of 70000 cut into
+    4096-column slices. h and qkv against the FP64 oracle, every output row
+    written once."""
+    def wpad(rows, k, seed):
+        kp = (k + pad + 7) // 8 * 8
+        return _w(rows, kp, seed)[:, :k]
+
+    layers = [(wpad(nq, d, 5), wpad(2 * ni, d, 6), wpad(d, ni, 7))]
+    h0 = _vec(d, 17)
+    h = h0.clone()
+    ch = tp.DecodeChain(ctx, h, layers)
+    counts = torch.zeros(nq + ni, dtype=torch.int32, device="cuda")
+    owner = torch.full((nq + ni,), -1, dtype=torch.int32, device="cuda")
+    w = layers[0]
+    tp.tp_decode_norm_qkv_gu(ctx, ch.p["qkv"], ch.p["a"], h, None, w[0], w[1], 1e-6,
+                             tp.make_exec(write_counts=counts, write_owner=owner))
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    dcounts = torch.zeros(d, dtype=torch.int32, device="cuda")
+    downer = torch.full((d,), -1, dtype=torch.int32, device="cuda")
+    tp.tp_decode_down_residual(ctx, ch.p["h"], w[2], ch.a, tp.make_exec(write_counts=dcounts, write_owner=downer))
+    assert opart.check_counts(dcounts.cpu().numpy())["ok"]
+    href, qref = odecode.chain(h0.cpu(), [tuple(t.cpu().contiguous() for t in lay) for lay in layers])
+    assert ogemm.rel_frobenius(h.cpu(), href) <= 1e-5
+    assert ogemm.rel_frobenius(ch.qkv.cpu(), qref) <= 1e-5
+    ch.close()
