@@ -614,7 +614,38 @@ def secondary_rows(tp, ctx, dev, stream, peaks, args):
     rows["decode_64"] = decode_row(tp, ctx, dev, stream, peaks)
     if not args.skip_proposer:
         rows["proposer"] = proposer_row(tp, ctx, args.train_shapes, args.test_shapes, args.epochs)
+    if not args.skip_experiments:
+        rows["experiments"] = experiment_rows(tp, ctx, peaks)
     return rows
+
+
+def experiment_rows(tp, ctx, peaks) -> dict:
+    """The paper's three measurement studies in short form, each run here in
+    full: the BF16 GEMM size sweep with safe / checked / unchecked / plain
+    launches and cuBLAS (§5.1), microseconds per op of the four execution
+    modes (§5.2), and the bimodal GEMM queue (Appendix B). About 45 s."""
+    from paper_2606_15991_gb300 import experiments
+
+    sweep = experiments.gemm_size_sweep(ctx, (1024, 2048, 4096, 8192, 16384, 32768))
+    modes = experiments.exec_mode_scaling(ctx, reps=30)
+    bim = experiments.bimodal_queue(ctx, reps=3)
+    us = modes["us_per_op"]
+    plateau = max(list(bim["threaded"].values()) + list(bim["async"].values()), key=lambda r: r["wu_per_ms"])
+    return {
+        "gemm_sweep": [{"n": r["n"], "tile": r["tile"], "bk": r["bk"],
+                        "tflops": {k: round(v, 1) for k, v in r["tflops"].items()},
+                        "checked_overhead": r["checked_overhead"], "unchecked_vs_safe": r["unchecked_vs_safe"],
+                        "safe_vs_cublas": r.get("safe_vs_cublas"),
+                        "frac_of_measured_bf16_safe": r["tflops"]["safe"] / peaks["bf16_tflops"]} for r in sweep],
+        "exec_modes_us_per_op": {m: {str(n): us[m][n]["min"] for n in (1, 10, 100, 1000) if n in us[m]}
+                                 for m in us},
+        "exec_modes_note": "minimum us per op of an N-launch chain (2048-element bf16 tile), host wall time",
+        "bimodal_wu_per_ms": {"serial": bim["serial"]["wu_per_ms"], "best_threads_or_streams": plateau["wu_per_ms"],
+                              "grouped": bim["grouped"]["wu_per_ms"]},
+        "paper_reference_numbers": {"rtx5090_us_per_op_at_1000": {"sync": 7.3, "chained": 3.4, "async": 3.4,
+                                                                  "graph": 0.8},
+                                    "b200_bimodal_wu_per_ms": {"serial": 37, "plateau_S8": 77}},
+    }
 
 
 def _torch_graph_time(stream, fn, reps: int, replays: int = 3) -> float:
@@ -1077,6 +1108,7 @@ def main():
     ap.add_argument("--skip-rows", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-proposer", action="store_true")
+    ap.add_argument("--skip-experiments", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--case", default="maps", choices=["maps", "proposer", "kernel", "exec_modes", "gemm_sweep", "bimodal"],
                     help="maps: the benchmark step (default); proposer: the learned-proposer experiment; "

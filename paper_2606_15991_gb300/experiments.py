@@ -246,19 +246,19 @@ class _Captured:
         self.torch_graph = None
 
 
-def _interleaved_best(variants: dict, rounds: int) -> dict:
-    """Best (lowest) ms per call of each captured variant over `rounds`
-    rounds (at least one per variant), each round replaying every variant
+def _interleaved(variants: dict, rounds: int) -> tuple:
+    """Median and lowest ms per call of each captured variant over `rounds`
+    rounds (at least two per variant), each round replaying every variant
     once in turn, the starting variant rotating from round to round, so that
     clock and power drift (and the burst after an idle gap) fall on all
     variants alike."""
     names = list(variants)
-    best = {k: None for k in names}
-    for r in range(max(rounds, len(names))):
+    ts = {k: [] for k in names}
+    for r in range(max(rounds, 2 * len(names))):
         for k in names[r % len(names):] + names[:r % len(names)]:
-            t = variants[k].time()
-            best[k] = t if best[k] is None else min(best[k], t)
-    return best
+            ts[k].append(variants[k].time())
+    med = {k: float(np.median(v)) for k, v in ts.items()}
+    return med, {k: min(v) for k, v in ts.items()}
 
 
 def _torch_graph_time_ms(fn, stream, reps: int, replays: int = 3) -> float:
@@ -306,8 +306,11 @@ def gemm_size_sweep(ctx, sizes=(1024, 2048, 4096, 8192, 16384, 32768), target_ms
       plain       tp_gemm on a plain partition (one program per tile);
       cublas      torch.matmul (cuBLAS) into a preallocated C, for context.
     Device time per GEMM from CUDA graphs of back-to-back launches (operands
-    stay L2/HBM-resident between launches, as in a loop of GEMMs), the best of
-    `rounds` interleaved rounds over the variants. Host
+    stay L2/HBM-resident between launches, as in a loop of GEMMs), the median
+    (`ms`, and the TFLOP/s from it) and the lowest (`ms_min`) of at least ten
+    interleaved rounds over the variants. safe and unchecked launch the same
+    kernel with the same arguments, so their gap is the spread of the
+    measurement. Host
     enqueue cost per call (safe vs unchecked, ctypes arguments built once) is
     reported for the smallest size."""
     from . import (tp_autotune, tp_gemm, tp_gemm_unchecked, tp_partition_map, tp_partition_query, gemm_config,
@@ -346,7 +349,7 @@ def gemm_size_sweep(ctx, sizes=(1024, 2048, 4096, 8192, 16384, 32768), target_ms
         if with_cublas:
             c2 = torch.empty_like(c)
             variants["cublas"] = _Captured(ctx, stream, reps, torch_fn=lambda: torch.matmul(a, bT, out=c2))
-        ms = _interleaved_best(variants, rounds)
+        ms, ms_min = _interleaved(variants, rounds)
         for v in variants.values():
             v.close()
         if with_cublas:
@@ -354,7 +357,7 @@ def gemm_size_sweep(ctx, sizes=(1024, 2048, 4096, 8192, 16384, 32768), target_ms
         row = {"n": n, "tile": [best.bm, best.bn], "bk": best.bk, "stages": best.stages, "group_m": best.group_m,
                "split_k": best.split_k,
                "programs": progs, "tiles": tiles, "reps": reps, "tune_s": t_tune,
-               "ms": ms, "tflops": {k: flops / (v * 1e-3) / 1e12 for k, v in ms.items()}}
+               "ms": ms, "ms_min": ms_min, "tflops": {k: flops / (v * 1e-3) / 1e12 for k, v in ms.items()}}
         row["checked_overhead"] = ms["checked"] / ms["safe"] - 1.0
         row["unchecked_vs_safe"] = ms["safe"] / ms["unchecked"]
         if with_cublas:
