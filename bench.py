@@ -544,8 +544,8 @@ def secondary_rows(tp, ctx, dev, stream, peaks, args):
     ms = _graph_time(tp, ctx, stream, lambda ex: tp.tp_gemm(ctx, p, a, b, f32cfg, ex), reps=50)
     rows["gemm_f32_512"] = {"tflops": 2 * 512 ** 3 / (ms * 1e-3) / 1e12, "ms": ms, "programs": 64,
                             "split_k": 2, "bk": 32,
-                            "note": "64 tile programs, each a cluster of 2 CTAs splitting K (128 of 152 SMs): "
-                                    "latency-bound FFMA"}
+                            "note": "64 tile programs, each a cluster of 2 CTAs splitting K (128 of 152 SMs), "
+                                    "operands fed by TMA into a ring of 32-wide K chunks"}
     tp.tp_partition_destroy(p)
     del a, b, c
 

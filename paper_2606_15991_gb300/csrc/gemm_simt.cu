@@ -3,6 +3,11 @@
 // launch one program per tile; mapped partitions launch persistent programs
 // that walk their tiles (strided slots or a device queue), slots being turned
 // into tiles by the band raster shared with the tensor-core GEMM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "sm100_ptx.cuh"
 #include "tp_internal.h"
 
@@ -218,12 +223,278 @@ cudaError_t launch_bk(const SimtArgs& p, bool count, int64_t grid, cudaStream_t 
                : cudaLaunchKernelEx(&cfg, gemm_f32_kernel<BK, false>, p);
 }
 
+// ------------------------------------------------ TMA-fed FP32 GEMM
+// The same tiles, thread blocking, K order and split-K reduction as
+// gemm_f32_kernel (so the same C bit for bit), with the operands brought by
+// TMA: a producer thread copies each 32-wide K chunk of the tile's A rows
+// (64 x 32 floats, 128-byte rows, 128-byte swizzle) and B columns (32 x 64
+// floats, 256-byte rows) into a ring of 16 KB stages while eight compute
+// warps multiply the chunks already landed; no register staging, no block
+// barrier per K step. Used for identity and strided maps with unit-stride,
+// 16-byte-aligned operands (and split-K only when each program holds one
+// tile); other launches take gemm_f32_kernel.
+constexpr int kFChunk = 32;
+constexpr int kFStages = 8;
+constexpr uint32_t kFChunkA = BM * kFChunk * 4;  // 8 KB
+constexpr uint32_t kFChunkB = kFChunk * BN * 4;  // 8 KB
+constexpr uint32_t kFStageBytes = kFChunkA + kFChunkB;
+constexpr int kFThreads = TH + 32;               // eight compute warps + the producer warp
+constexpr size_t kFSmem = 1024 + (size_t)kFStages * kFStageBytes + BM * BN * 4 + 8 * (2 * kFStages) + 16;
+
+struct F32TmaArgs {
+  float* c;
+  int64_t M, N, K;
+  int64_t gm, gn;
+  int32_t kind, group_m, split;
+  int32_t nchunks;  // K chunks of 32
+  uint32_t* counts;
+  int32_t* owner;
+  int* err;
+  uint64_t wait_ns;
+};
+
+template <bool COUNT>
+__global__ void __launch_bounds__(kFThreads, 1)
+    gemm_f32_tma_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
+                        const __grid_constant__ F32TmaArgs p) {
+  using namespace sm100;
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;  // 128-byte swizzle: 1024-byte aligned stages
+  uint8_t* gbase = smem_raw + (base - raw);
+  auto Ps = reinterpret_cast<float(*)[BN]>(gbase + (size_t)kFStages * kFStageBytes);
+  const uint32_t bars = base + kFStages * kFStageBytes + BM * BN * 4;
+  auto full_bar = [&](int s) { return bars + 8u * s; };
+  auto empty_bar = [&](int s) { return bars + 8u * (kFStages + s); };
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(gbase + (bars - base) + 8 * 2 * kFStages);
+  const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+  const int S = p.split;
+  const uint32_t r = S > 1 ? cluster_ctarank() : 0u;
+  if (tid == 0) {
+    for (int s = 0; s < kFStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), TH / 32);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+    tma_prefetch_desc(&map_a);
+    tma_prefetch_desc(&map_b);
+  }
+  __syncthreads();
+  // A and B may be the previous kernel's output, and C its input
+  grid_dependency_wait();
+  allow_dependents();
+  const int64_t T = p.gm * p.gn;
+  const int64_t s0 = (int64_t)(blockIdx.x / S);
+  const int64_t step = p.kind == TP_MAP_IDENTITY ? T : (int64_t)(gridDim.x / S);
+  const int32_t c0 = (int32_t)(((int64_t)r * p.nchunks) / S), c1 = (int32_t)(((int64_t)(r + 1) * p.nchunks) / S);
+  if (warp == TH / 32) {
+    // ---------------- producer
+    if (lane == 0) {
+      uint32_t fills[kFStages] = {};
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t s = s0; s < T && ok; s += step) {
+        int64_t tm, tn;
+        raster(s, p.gm, p.gn, p.group_m, &tm, &tn);
+        for (int32_t ch = c0; ch < c1; ++ch) {
+          if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err, p.wait_ns)) { ok = false; break; }
+          const uint32_t dst = base + kFStageBytes * (uint32_t)stage;
+          mbar_arrive_expect_tx(full_bar(stage), kFStageBytes);
+          tma_load_2d(dst, &map_a, ch * kFChunk, (int32_t)(tm * BM), full_bar(stage), policy_evict_last());
+          tma_load_2d(dst + kFChunkA, &map_b, (int32_t)(tn * BN), ch * kFChunk, full_bar(stage), policy_evict_last());
+          fills[stage]++;
+          if (++stage == kFStages) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (!ok)  // every copy this thread issued lands before the CTA retires
+        for (int s2 = 0; s2 < kFStages; ++s2)
+          if (fills[s2]) mbar_wait(full_bar(s2), (fills[s2] - 1u) & 1u, nullptr, nullptr, 200000000ull);
+    }
+    __syncwarp();
+    // split programs hold one tile: the producer warp joins the two
+    // cluster barriers of the epilogue below
+    if (S > 1) {
+      cluster_sync();
+      cluster_sync();
+    }
+    return;
+  }
+  // ---------------- compute warps: thread (tx, ty) owns rows 4ty..4ty+3 and
+  // columns 4tx..4tx+3 of the tile, as in gemm_f32_kernel
+  const int tx = tid % 16, ty = tid / 16;
+  int stage = 0;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int64_t s = s0; s < T || (S > 1 && s == s0); s += step) {
+    const bool have = s < T;  // a split cluster without a tile still joins the cluster barriers
+    int64_t tm = 0, tn = 0;
+    if (have) raster(s, p.gm, p.gn, p.group_m, &tm, &tn);
+    float acc[4][4] = {};
+    for (int32_t ch = c0; have && ok && ch < c1; ++ch) {
+      const bool got = mbar_wait(full_bar(stage), phase, abort_flag, p.err, p.wait_ns);
+      if (!__all_sync(0xffffffffu, got)) { ok = false; break; }
+      const uint32_t sa = base + kFStageBytes * (uint32_t)stage;
+      const uint32_t sb = sa + kFChunkA;
+#pragma unroll
+      for (int g = 0; g < kFChunk / 4; ++g) {
+        // A rows 4ty+i, k = 4g..4g+3 (16-byte piece g of a 128-byte row,
+        // stored at piece g ^ (row & 7)); B rows k = 4g+j, columns 4tx..
+        float av[4][4], bv[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const uint32_t row = (uint32_t)(4 * ty + i);
+          uint32_t w[4];
+          ld_shared_v4(sa + row * 128u + ((((uint32_t)g) ^ (row & 7u)) << 4), w);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) av[i][q] = __uint_as_float(w[q]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          uint32_t w[4];
+          ld_shared_v4(sb + (uint32_t)(4 * g + j) * 256u + (uint32_t)tx * 16u, w);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) bv[j][q] = __uint_as_float(w[q]);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][q] = fmaf(av[i][j], bv[j][q], acc[i][q]);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty_bar(stage));
+      if (++stage == kFStages) { stage = 0; phase ^= 1u; }
+    }
+    const int64_t m0 = tm * BM, n0 = tn * BN;
+    bool mine = have;  // this thread's rows are stored by this CTA
+    if (S > 1) {
+      // partial blocks in shared memory, summed in slice order by the CTA
+      // that owns the rows (peers read through distributed shared memory)
+      if (have) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          *reinterpret_cast<float4*>(&Ps[4 * ty + i][4 * tx]) =
+              make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      }
+      cluster_sync();
+      mine = have && (4 * ty) / (BM / S) == (int)r;
+      if (mine) {
+        float sum[4][4];
+        for (int src = 0; src < S; ++src) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            float4 v;
+            if (src == (int)r) {
+              v = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            } else {
+              const uint32_t at = mapa(smem_u32(&Ps[4 * ty + i][4 * tx]), (uint32_t)src);
+              asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                           : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                           : "r"(at)
+                           : "memory");
+            }
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sum[i][q] = src == 0 ? vv[q] : sum[i][q] + vv[q];
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[i][q] = sum[i][q];
+      }
+      cluster_sync();  // the peers' reads of this CTA's partial are done
+    }
+    if (!ok) mine = false;
+    const bool vec = (p.N % 4 == 0) && ((reinterpret_cast<uintptr_t>(p.c) & 15) == 0);
+#pragma unroll
+    for (int i = 0; i < 4 && mine; ++i) {
+      const int64_t row = m0 + 4 * ty + i;
+      if (row >= p.M) continue;
+      const int64_t col = n0 + 4 * tx;
+      if (vec && col + 4 <= p.N) {
+        *reinterpret_cast<float4*>(p.c + row * p.N + col) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (col + q < p.N) p.c[row * p.N + col + q] = acc[i][q];
+      }
+      if constexpr (COUNT) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (col + q < p.N) {
+            atomicAdd(p.counts + row * p.N + col + q, 1u);
+            p.owner[row * p.N + col + q] = (int32_t)(blockIdx.x / S);
+          }
+      }
+    }
+    if (S > 1 || !ok) break;
+  }
+}
+
+template <bool COUNT>
+cudaError_t launch_f32_tma(const CUtensorMap& ma, const CUtensorMap& mb, const F32TmaArgs& p, int64_t programs,
+                           cudaStream_t st) {
+  auto k = gemm_f32_tma_kernel<COUNT>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(programs * p.split));
+  cfg.blockDim = dim3(kFThreads);
+  cfg.dynamicSmemBytes = kFSmem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)p.split;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, k, ma, mb, p);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+// fp32 [rows, cols] row-major (row pitch ld floats) in boxes of box_cols x
+// box_rows, zero fill past the edges
+bool f32_map(CUtensorMap* map, const float* ptr, int64_t rows, int64_t cols, int64_t ld, int box_cols, int box_rows,
+             bool swizzle) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 4)};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 }  // namespace
 
 tp_status launch_gemm_simt(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_tensor* b,
                            const tp_gemm_config* cfg, const tp_exec* ex, cudaStream_t stream,
                            unsigned* queue) {
-  (void)ctx;
   if (c->tile[0] != BM || c->tile[1] != BN)
     return fail(TP_ERR_UNSUPPORTED, "the FP32 GEMM uses 64 x 64 output tiles");
   if ((ex->write_counts == nullptr) != (ex->write_owner == nullptr))
@@ -257,6 +528,36 @@ tp_status launch_gemm_simt(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, con
     return fail(TP_ERR_UNSUPPORTED, "FP32 GEMM split_k with a queue map (each CTA would dequeue its own tile)");
   const bool count = p.counts != nullptr;
   cudaError_t e;
+  // TMA-fed kernel: unit-stride rows 16-byte aligned, K chunks of 32 (the
+  // bk = 32 schedule), identity or strided maps, split programs one tile each
+  const int64_t T = p.gm * p.gn;
+  const bool tma_ok = bk == 32 && p.sak == 1 && p.sbn == 1 && p.sam % 4 == 0 && p.sbk % 4 == 0 &&
+                      ((reinterpret_cast<uintptr_t>(p.a) | reinterpret_cast<uintptr_t>(p.b)) & 15) == 0 &&
+                      p.K > 0 && p.K < ((int64_t)1 << 30) && p.M < ((int64_t)1 << 31) && p.N < ((int64_t)1 << 31) &&
+                      c->kind != TP_MAP_QUEUE && (p.split == 1 || grid >= T);
+  if (tma_ok) {
+    CUtensorMap ma, mb;
+    if (f32_map(&ma, p.a, p.M, p.K, p.sam, kFChunk, BM, true) && f32_map(&mb, p.b, p.K, p.N, p.sbk, BN, kFChunk, false)) {
+      F32TmaArgs t{};
+      t.c = p.c;
+      t.M = p.M;
+      t.N = p.N;
+      t.K = p.K;
+      t.gm = p.gm;
+      t.gn = p.gn;
+      t.kind = p.kind;
+      t.group_m = p.group_m;
+      t.split = p.split;
+      t.nchunks = (int32_t)((p.K + kFChunk - 1) / kFChunk);
+      t.counts = p.counts;
+      t.owner = p.owner;
+      t.err = ctx->d_err;
+      t.wait_ns = 2000000000ull;
+      e = count ? launch_f32_tma<true>(ma, mb, t, grid, stream) : launch_f32_tma<false>(ma, mb, t, grid, stream);
+      if (e != cudaSuccess) return cuda_fail(e, "FP32 GEMM launch");
+      return TP_OK;
+    }
+  }
   switch (bk) {
     case 8: e = launch_bk<8>(p, count, grid, stream); break;
     case 16: e = launch_bk<16>(p, count, grid, stream); break;
