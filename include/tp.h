@@ -346,7 +346,12 @@ tp_status tp_permute_heads_unchecked(tp_ctx* ctx, void* dst, const void* src, in
  * c: partition of a row-major M x N output whose tile is the GEMM tile.
  * a: M x K. b: K x N (its strides decide the layout: row stride 1 means B is
  * stored N x K, "K-major").
- * - F32 A, B, C: FFMA tiles (no TF32), any strides; tile 64 x 64 recommended.
+ * - F32 A, B, C: FFMA tiles of 64 x 64 (no TF32), any strides. With bk = 32
+ *   (the default), row-major A and B whose row pitches are multiples of 4
+ *   floats and whose bases are 16-byte aligned, and an identity or strided
+ *   map (split programs holding one tile each), the operands are brought by
+ *   TMA; otherwise each thread stages them through registers. Both give
+ *   the same C bit for bit.
  * - BF16 A, B, C: tcgen05 tensor-core path. A must be K-major (row-major
  *   M x K) and B K-major (stored N x K); base addresses 16-byte aligned and
  *   K a multiple of 8 (TMA rows are 16-byte multiples), else TP_ERR_ALIGN.
