@@ -423,11 +423,6 @@ def run_ours(args):
                 "per_map_gbs": {f"{o}_{d}": _map_bytes(d) / (t * 1e-3) / 1e9 for (o, d), t in per_kernel.items()}}
 
     # ---------------- end-to-end through the C ABI with pinned host buffers
-    # The inputs and outputs live in pinned host memory; the partitions are
-    # over the host output buffers, so each map kernel reads its operands from
-    # host memory and writes its result back over the host link inside the timed
-    # region (measured faster than staging through device copies: ~300 vs
-    # ~200 GB/s of host traffic on GB300).
     e2e = None
     if not args.skip_e2e:
         e2e = _e2e_leg(tp, ctx, ex, ev, inputs, tens, step_bytes, ws, dev, args)
@@ -464,12 +459,19 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+E2E_CHUNKS = 16   # pipeline chunks of the end-to-end step (2^24 elements each)
+
+
 def _e2e_leg(tp, ctx, ex, ev, inputs, tens, step_bytes, ws, dev, args):
-    """The maps step end to end: inputs and outputs in pinned host memory;
-    the partitions are over the host output buffers, so every map kernel
-    reads its operands from host memory and writes its result back over the
-    host link inside the timed region (measured faster than staging through
-    device copies: ~300 vs ~200 GB/s of host traffic on GB300)."""
+    """The maps step end to end through the C ABI, inputs and outputs in
+    pinned host memory. Every step copies its inputs (x and y of both dtypes)
+    to the device, runs the four maps and copies their results back, in
+    E2E_CHUNKS chunks pipelined over three streams (copies in, maps, copies
+    out), so both directions of the host link stay busy while the kernels
+    run; each input crosses the link once per step, as it would for a user
+    running the four maps on host data. (The maps reading and writing host
+    memory directly, each map fetching its own inputs over the link, ran at
+    0.30 TB/s on GB300, bound by the ~210 GB/s host-to-device direction.)"""
     import torch
 
     # every rank must hold its pinned buffers before any rank times (the
@@ -477,25 +479,46 @@ def _e2e_leg(tp, ctx, ex, ev, inputs, tens, step_bytes, ws, dev, args):
     err = None
     try:
         host_in = {dt: (x.cpu().pin_memory(), y.cpu().pin_memory()) for dt, (x, y) in inputs.items()}
-        host_out = {}
-        for op, dt in MAPS:
-            hz = torch.empty(N_ELEMS, dtype=inputs[dt][0].dtype).pin_memory()
-            host_out[(op, dt)] = (hz, tp.tp_partition_create(ctx, hz, (TILE,)))
+        host_out = {(op, dt): torch.empty(N_ELEMS, dtype=inputs[dt][0].dtype).pin_memory() for op, dt in MAPS}
     except (RuntimeError, MemoryError) as e:
         err = f"{type(e).__name__}: {str(e)[:200]}"
     if _all_ranks_ok(err is None, ws, dev) is False:
         return {"value": None, "unit": "TB/s", "unavailable": err or "pinned host buffers unavailable on another rank"}
+    L = N_ELEMS // E2E_CHUNKS
+    chunks = [slice(c * L, (c + 1) * L) for c in range(E2E_CHUNKS)]
+    parts = {(op, dt, c): tp.tp_partition_create(ctx, tens[(op, dt)][2][sl], (TILE,))
+             for op, dt in MAPS for c, sl in enumerate(chunks)}
+    s_in, s_map, s_out = (torch.cuda.Stream(device=dev) for _ in range(3))
+    ev_map = tp.tp_event_create(ctx)
+    ex_map = tp.make_exec(stream=s_map)
+    ex_map.mode = tp.ASYNC
+    ex_map.event = ev_map.handle.value
     e2e_steps = max(2, min(args.steps, 5))
 
     def e2e_step():
-        for op, dt in MAPS:
-            hx, hy = host_in[dt]
-            hz, hp = host_out[(op, dt)]
-            if op == "axpy":
-                tp.tp_map_axpy(ctx, hp, ALPHA, hx, hy, ex)
-            else:
-                tp.tp_map_gelu_mul(ctx, hp, hx, hy, ex)
-        tp.tp_event_wait(ev)
+        for c, sl in enumerate(chunks):
+            with torch.cuda.stream(s_in):
+                for dt, (hx, hy) in host_in.items():
+                    dx, dy = inputs[dt]
+                    dx[sl].copy_(hx[sl], non_blocking=True)
+                    dy[sl].copy_(hy[sl], non_blocking=True)
+            landed = torch.cuda.Event()
+            landed.record(s_in)
+            s_map.wait_event(landed)
+            for op, dt in MAPS:
+                dx, dy = inputs[dt]
+                if op == "axpy":
+                    tp.tp_map_axpy(ctx, parts[(op, dt, c)], ALPHA, dx[sl], dy[sl], ex_map)
+                else:
+                    tp.tp_map_gelu_mul(ctx, parts[(op, dt, c)], dx[sl], dy[sl], ex_map)
+            mapped = torch.cuda.Event()
+            mapped.record(s_map)
+            s_out.wait_event(mapped)
+            with torch.cuda.stream(s_out):
+                for op, dt in MAPS:
+                    host_out[(op, dt)][sl].copy_(tens[(op, dt)][2][sl], non_blocking=True)
+        tp.tp_event_wait(ev_map)
+        s_out.synchronize()
 
     e2e_step()
     torch.cuda.synchronize()
@@ -504,18 +527,24 @@ def _e2e_leg(tp, ctx, ex, ev, inputs, tens, step_bytes, ws, dev, args):
         e2e_step()
     t1 = time.perf_counter()
     e2e_ms = _barrier_max((t1 - t0) * 1e3 / e2e_steps, ws, dev)
-    # the result read back on the host: a strided sample of every output is
-    # compared with the device-resident run of the same maps
+    # the results read back on the host: a strided sample of every output is
+    # compared with a device-resident run of the same maps on the same inputs
     for op, dt in MAPS:
-        assert torch.equal(host_out[(op, dt)][0][::4097], tens[(op, dt)][2][::4097].cpu()), (op, dt)
-    h2d = sum(2 * ESIZE[dt] * N_ELEMS for _, dt in MAPS)
+        x, y, z, p = tens[(op, dt)]
+        if op == "axpy":
+            tp.tp_map_axpy(ctx, p, ALPHA, x, y)
+        else:
+            tp.tp_map_gelu_mul(ctx, p, x, y)
+        assert torch.equal(host_out[(op, dt)][::4097], z[::4097].cpu()), (op, dt)
+    h2d = sum(2 * ESIZE[dt] * N_ELEMS for dt in host_in)
     d2h = sum(ESIZE[dt] * N_ELEMS for _, dt in MAPS)
     e2e = {"value": weak_scaling_value(ws, step_bytes, e2e_ms), "unit": "TB/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e2e_steps,
-           "transfer": "zero-copy: the map kernels read pinned host inputs and write pinned host outputs"}
-    for _, hp in host_out.values():
-        tp.tp_partition_destroy(hp)
-
+           "transfer": f"pinned host inputs copied in and results copied out every step, in {E2E_CHUNKS} chunks "
+                       "pipelined with the maps over three streams (each input crosses the link once per step)"}
+    for p in parts.values():
+        tp.tp_partition_destroy(p)
+    tp.tp_event_destroy(ev_map)
     return e2e
 
 
