@@ -49,7 +49,8 @@ struct alignas(64) GroupedProblem {
   int32_t box_y;          // rows of the MMA B operand each CTA loads per stage
   int32_t c_tma;          // 1: normal orientation with 16-byte aligned C rows (map_c is valid)
   int32_t stream_x;       // swap tile whose B slab no other tile reads (loaded evict-first)
-  int32_t kc;             // K blocks per ring stage: the ring's count (3-D maps) when K % 64 == 0, else 1
+  int32_t kc;             // K blocks per ring stage: the ring's count (3-D maps) when K % 64 == 0, else 1;
+                          // 3 for a swap problem on pairs with at most 32 B-operand rows per CTA
 };
 
 }  // namespace tp
@@ -91,6 +92,7 @@ template <bool kPair> struct Ring {
   static constexpr int kStages = kPair ? 6 / TP_GROUPED_PAIR_KC : 4;
 };
 constexpr size_t kWordsBytes = 8 + 8 * kRing;
+constexpr int kWideKc = 3;  // K blocks per stage of a swap problem with few B rows (pairs)
 constexpr uint32_t kStageC = 4u * 2u * 4096u;  // epilogue staging: 4 warps x 2 buffers x (32 rows x 128 B)
 // Longest partial last 256-row band of a normal problem that CTA pairs run
 // as a swap-AB tail (0 = never)
@@ -128,9 +130,12 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
   const bool leader = rank == 0;
   const int32_t prog = kPair ? (int32_t)(blockIdx.x / 2) : (int32_t)blockIdx.x;
 
-  const uint32_t x0 = base;
-  const uint32_t y0 = x0 + kStageXs * kStages;
-  const uint32_t cst = y0 + kStageY * kStages;  // epilogue staging
+  // stage s: [A-operand K blocks][B-operand K blocks], the B blocks right
+  // after the problem's kc A blocks (so a swap problem with few B rows fits
+  // 3 K blocks of each in one stage)
+  constexpr uint32_t kStageBytes = kStageXs + kStageY;
+  auto stage_at = [&](int s) { return base + kStageBytes * (uint32_t)s; };
+  const uint32_t cst = base + kStageBytes * kStages;  // epilogue staging
   const uint32_t bars = cst + kStageC;
   auto full_bar = [&](int s) { return bars + 8u * s; };
   auto empty_bar = [&](int s) { return bars + 64u + 8u * s; };
@@ -246,16 +251,17 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
             const uint32_t fb = mapa(full_bar(stage), 0);  // both halves complete on the even CTA's barrier
             if (leader) mbar_arrive_expect_tx(full_bar(stage), 2 * tx);
             if (pkc > 1) {
-              tma_load_3d_pair(x0 + kStageXs * stage, &pr->map_x, 0, xrow, (int32_t)kb, fb, px);
-              tma_load_3d_pair(y0 + kStageY * stage, &pr->map_y, 0, yrow, (int32_t)kb, fb, pol_keep);
+              tma_load_3d_pair(stage_at(stage), &pr->map_x, 0, xrow, (int32_t)kb, fb, px);
+              tma_load_3d_pair(stage_at(stage) + kStageX * (uint32_t)pkc, &pr->map_y, 0, yrow, (int32_t)kb, fb,
+                               pol_keep);
             } else {
-              tma_load_2d_pair(x0 + kStageXs * stage, &pr->map_x, kx, xrow, fb, px);
-              tma_load_2d_pair(y0 + kStageY * stage, &pr->map_y, kx, yrow, fb, pol_keep);
+              tma_load_2d_pair(stage_at(stage), &pr->map_x, kx, xrow, fb, px);
+              tma_load_2d_pair(stage_at(stage) + kStageX, &pr->map_y, kx, yrow, fb, pol_keep);
             }
           } else {
             mbar_arrive_expect_tx(full_bar(stage), tx);
-            tma_load_2d(x0 + kStageXs * stage, &pr->map_x, kx, xrow, full_bar(stage), px);
-            tma_load_2d(y0 + kStageY * stage, &pr->map_y, kx, yrow, full_bar(stage), pol_keep);
+            tma_load_2d(stage_at(stage), &pr->map_x, kx, xrow, full_bar(stage), px);
+            tma_load_2d(stage_at(stage) + kStageX, &pr->map_y, kx, yrow, full_bar(stage), pol_keep);
           }
           fills[stage]++;
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
@@ -295,8 +301,8 @@ __global__ void __launch_bounds__(kThreads, 1) grouped_kernel(const __grid_const
           tc_fence_after();
           // the stage's K blocks in K order (blocks past the last are not multiplied)
           for (int32_t jb = 0; jb < pkc && kb + jb < nk; ++jb) {
-            const uint64_t ad = desc_kmajor_sw128(x0 + kStageXs * stage + kStageX * (uint32_t)jb);
-            const uint64_t bd = desc_kmajor_sw128(y0 + kStageY * stage + y_blk * (uint32_t)jb);
+            const uint64_t ad = desc_kmajor_sw128(stage_at(stage) + kStageX * (uint32_t)jb);
+            const uint64_t bd = desc_kmajor_sw128(stage_at(stage) + kStageX * (uint32_t)pkc + y_blk * (uint32_t)jb);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
               const uint32_t accum = (kb + jb > 0 || k > 0) ? 1u : 0u;
@@ -552,6 +558,12 @@ tp_status tp_grouped_plan_create(tp_ctx* ctx, const tp_gemm_problem* probs, int3
     g.tiles_r = (N + trows - 1) / trows;
     g.tiles_c = 1;
     g.kc = kc_of(K);
+    // few B rows (M <= 64 on a pair): a stage holds 3 K blocks of each
+    // operand (48 KB of the streamed slab instead of 32 KB), so the slab
+    // streams with more bytes in flight and fewer copies per byte
+    constexpr uint32_t kPairStage = (kStageX + Ring<true>::kStageY) * Ring<true>::kKc;
+    if (plan->pair && K % 64 == 0 && (uint32_t)kWideKc * (kStageX + (uint32_t)g.box_y * 128u) <= kPairStage)
+      g.kc = kWideKc;
     tp_status s = kmajor_map(&g.map_x, b, N, K, ldb, 128, g.kc);
     if (s == TP_OK) s = kmajor_map(&g.map_y, a, M, K, lda, g.box_y, g.kc);
     return s;
