@@ -154,15 +154,16 @@ def test_split_k_validation(ctx):
     assert torch.equal(c, torch.ones(128, 128, device="cuda"))
 
 
-@pytest.mark.parametrize("m,n,k,split,kind,P", [
-    (512, 512, 512, 2, tp.MAP_IDENTITY, 0),   # the benchmark configuration
-    (512, 512, 512, 4, tp.MAP_IDENTITY, 0),
-    (65, 132, 36, 1, tp.MAP_IDENTITY, 0),     # ragged tiles, a partial K chunk
-    (100, 4, 300, 1, tp.MAP_IDENTITY, 0),
-    (300, 200, 1000, 1, tp.MAP_STRIDED, 5),   # programs walking several tiles
-    (200, 300, 4104, 2, tp.MAP_STRIDED, 20),  # split programs, one tile each, long K
+@pytest.mark.parametrize("m,n,k,split,kind,P,group_m", [
+    (512, 512, 512, 2, tp.MAP_IDENTITY, 0, 1),   # the benchmark configuration
+    (512, 512, 512, 4, tp.MAP_IDENTITY, 0, 1),
+    (65, 132, 36, 1, tp.MAP_IDENTITY, 0, 1),     # ragged tiles, a partial K chunk
+    (100, 4, 300, 1, tp.MAP_IDENTITY, 0, 1),
+    (300, 200, 1000, 1, tp.MAP_STRIDED, 5, 1),   # programs walking several tiles
+    (450, 260, 520, 1, tp.MAP_STRIDED, 7, 3),    # ... in raster bands of 3 tile rows
+    (200, 300, 4104, 2, tp.MAP_STRIDED, 20, 2),  # split programs, one tile each, long K
 ])
-def test_tma_fed_kernel_equals_register_staged(ctx, m, n, k, split, kind, P):
+def test_tma_fed_kernel_equals_register_staged(ctx, m, n, k, split, kind, P, group_m):
     """With 32-wide K steps, unit-stride 16-byte-aligned operands and an
     identity or strided map, the FP32 GEMM runs the TMA-fed kernel; the same
     values with A 4 bytes off alignment run the register-staged kernel. Both
@@ -171,14 +172,14 @@ def test_tma_fed_kernel_equals_register_staged(ctx, m, n, k, split, kind, P):
     every element is written once by the oracle's owner."""
     a = torch.from_numpy(synth.uniform(m * k, seed=m + k)).reshape(m, k).cuda()
     b = torch.from_numpy(synth.uniform(k * n, seed=n + 7)).reshape(k, n).cuda()
-    c_tma, counts, owner = _gemm(ctx, a, b, kind, P, bk=32, split_k=split, count=True)
+    c_tma, counts, owner = _gemm(ctx, a, b, kind, P, group_m=group_m, bk=32, split_k=split, count=True)
     abuf = torch.empty(m * k + 1, device="cuda")
     a_off = abuf[1:].view(m, k)
     a_off.copy_(a)
-    c_reg, _, _ = _gemm(ctx, a_off, b, kind, P, bk=32, split_k=split)
+    c_reg, _, _ = _gemm(ctx, a_off, b, kind, P, group_m=group_m, bk=32, split_k=split)
     assert torch.equal(c_tma, c_reg)
     assert ogemm.rel_frobenius(c_tma.cpu(), ogemm.gemm(a.cpu(), b.cpu())) <= 1e-5
     assert opart.check_counts(counts.cpu().numpy())["ok"]
     expect = (opart.gemm_owner_map(m, n, 64, 64) if kind == tp.MAP_IDENTITY
-              else opart.gemm_owner_map(m, n, 64, 64, P, "strided"))
+              else opart.gemm_owner_map(m, n, 64, 64, P, "strided", group_m))
     assert np.array_equal(owner.cpu().numpy(), expect)
