@@ -522,10 +522,13 @@ def _e2e_leg(tp, ctx, ex, ev, inputs, tens, step_bytes, ws, dev, args):
 
     e2e_step()
     torch.cuda.synchronize()
+    each = []
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()
+        each.append(time.perf_counter())
     t1 = time.perf_counter()
+    each = [round((b - a) * 1e3, 2) for a, b in zip([t0] + each[:-1], each)]
     e2e_ms = _barrier_max((t1 - t0) * 1e3 / e2e_steps, ws, dev)
     # the results read back on the host: a strided sample of every output is
     # compared with a device-resident run of the same maps on the same inputs
@@ -539,7 +542,7 @@ def _e2e_leg(tp, ctx, ex, ev, inputs, tens, step_bytes, ws, dev, args):
     h2d = sum(2 * ESIZE[dt] * N_ELEMS for dt in host_in)
     d2h = sum(ESIZE[dt] * N_ELEMS for _, dt in MAPS)
     e2e = {"value": weak_scaling_value(ws, step_bytes, e2e_ms), "unit": "TB/s", "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "steps": e2e_steps,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms, "ms_each_step": each, "steps": e2e_steps,
            "transfer": f"pinned host inputs copied in and results copied out every step, in {E2E_CHUNKS} chunks "
                        "pipelined with the maps over three streams (each input crosses the link once per step)"}
     for p in parts.values():
