@@ -74,6 +74,22 @@ def test_integer_group_bit_exact(ctx, programs, pair):
 
 
 @pytest.mark.parametrize("pair", [True, False])
+def test_swap_problems_with_few_rows_bit_exact(ctx, pair):
+    """Swap problems of at most 64 rows take 3 K blocks per ring stage on CTA
+    pairs: K of 1, 3, 5, 8 and 10 blocks (the last stage full, holding 1 or
+    2 blocks, or a single stage), integer inputs, C equal to the rounded
+    exact product; the same problems on single CTAs too."""
+    shapes = [(1, 256, 64), (64, 384, 192), (17, 300, 320), (33, 2048, 512), (40, 520, 640)]
+    probs = _problems(shapes, kind="int", seed=9)
+    _, swapped, counts, _ = _run(ctx, probs, count=True, pair=pair)
+    assert all(swapped)
+    for a, b, c in probs:
+        exact = ogemm.gemm(a.cpu(), b.cpu())
+        assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(exact))
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+
+
+@pytest.mark.parametrize("pair", [True, False])
 def test_swap_threshold_and_single_problem(ctx, pair):
     probs = _problems([(200, 640, 256)])
     plan = tp.tp_grouped_plan_create(ctx, probs, swap_max_m=0, cta_pair=pair)   # force the normal orientation
