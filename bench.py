@@ -388,6 +388,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    # The timed steps are chained on one stream (§3.2's asynchronous
+    # pipeline: same-stream launches may rewrite a partition still held by
+    # the previous step); the event wait after the last step releases them.
     t_start.record(stream)
     for _ in range(args.steps):
         for op, dt in MAPS:
@@ -397,8 +400,8 @@ def run_ours(args):
             launch(op, dt)
             e1.record(stream)
             evs[(op, dt)].append((e0, e1))
-        tp.tp_event_wait(ev)
     t_end.record(stream)
+    tp.tp_event_wait(ev)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     el_ms = t_start.elapsed_time(t_end)
