@@ -856,7 +856,7 @@ tp_status tp_gemm(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_ten
       return s;
     }
   }
-  o.check_err = tc;
+  o.check_err = true;  // the tensor-core and TMA-fed FP32 kernels' waits are bounded
   s = simt ? launch_gemm_simt(ctx, c, a, b, cfg, ex, o.stream, q)
            : launch_gemm_tc(ctx, c, a, b, cfg, ex, o.stream, q);
   if (s != TP_OK) {
