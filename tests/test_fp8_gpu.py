@@ -77,7 +77,7 @@ def test_quantize_zero_tensor_and_strided_map(ctx):
     assert scale.item() == 1.0 and int(q.view(torch.uint8).max()) == 0
 
 
-def _fp8_gemm(ctx, a, bt, bm=128, bn=128, P=None, group_m=1, count=False, checked=False, split_k=0):
+def _fp8_gemm(ctx, a, bt, bm=128, bn=128, P=None, group_m=1, count=False, checked=False, split_k=0, bk=0):
     qa, _, sa, _, _ = _quantize(ctx, a, 16)
     qbt, _, sb, _, _ = _quantize(ctx, bt, 16)
     m, n = a.shape[0], bt.shape[0]
@@ -90,7 +90,7 @@ def _fp8_gemm(ctx, a, bt, bm=128, bn=128, P=None, group_m=1, count=False, checke
     if count:
         counts = torch.zeros(m * n, dtype=torch.int32, device="cuda")
         owner = torch.full((m * n,), -1, dtype=torch.int32, device="cuda")
-    tp.tp_gemm_fp8(ctx, p, qa, qbt.t(), sa, sb, tp.gemm_config(bm=bm, bn=bn, group_m=group_m, split_k=split_k),
+    tp.tp_gemm_fp8(ctx, p, qa, qbt.t(), sa, sb, tp.gemm_config(bm=bm, bn=bn, group_m=group_m, split_k=split_k, bk=bk),
                    tp.make_exec(write_counts=counts, write_owner=owner, checked=checked))
     info = tp.tp_partition_query(p)
     tp.tp_partition_destroy(p)
@@ -150,13 +150,14 @@ def test_random_errors(ctx, bm, bn):
 
 def test_8192_cubed_sampled_tiles(ctx):
     """8192^3 with N(0,1) bf16 inputs quantised per tensor, launched as the
-    benchmark launches it; errors over 64 sampled 128 x 128 tiles."""
+    benchmark launches it (76 CTA pairs, 256 x 256 tiles, stages of 2 K
+    blocks, raster bands of 16); errors over 64 sampled 128 x 128 tiles."""
     M = N = K = 8192
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
     a = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
     bt = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
-    c, qa, qbt, sa, sb, _, _, _ = _fp8_gemm(ctx, a, bt, bm=256, bn=256, group_m=16)
+    c, qa, qbt, sa, sb, _, _, _ = _fp8_gemm(ctx, a, bt, bm=256, bn=256, group_m=16, bk=256)
     inv = float(ogemm.fp8_dequant_factor(sa.item(), sb.item()))
     tiles = synth.sample_tiles(64, 64, 64, seed=0)
     got, ref_q, ref_in = [], [], []
