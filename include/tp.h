@@ -127,7 +127,16 @@ enum {
    * copies and MMAs, frees TMEM and returns, and the operation reports
    * TP_ERR_TIMEOUT where it reports device errors. C is left partly
    * written. Other operations, and 256-row tiles, return TP_ERR_UNSUPPORTED. */
-  TP_EXEC_INJECT_TIMEOUT = 2
+  TP_EXEC_INJECT_TIMEOUT = 2,
+  /* The decode products (tp_decode_norm_qkv_gu, tp_decode_down_residual):
+   * the caller promises that no work queued before the call on its stream,
+   * still running, writes the weight matrices (weights loaded once and
+   * kept, as in a decode loop). The streaming kernel then starts copying
+   * weights while the preceding kernels finish (this library's kernels let
+   * the next one start early); its inputs h and a are still read only after
+   * them. Without the flag every read waits for the preceding work. Other
+   * operations return TP_ERR_UNSUPPORTED when it is set. */
+  TP_EXEC_STATIC_WEIGHTS = 4
 };
 
 /* How an operation is executed. */

@@ -217,15 +217,19 @@ def tp_graph_destroy(g: Graph) -> None:
 
 
 def make_exec(mode: int = SYNC, stream=None, event: Event | None = None, write_counts=None,
-              write_owner=None, checked: bool = False, inject_timeout: bool = False) -> tp_exec:
+              write_owner=None, checked: bool = False, inject_timeout: bool = False,
+              static_weights: bool = False) -> tp_exec:
     """tp_exec for `mode` on `stream` (torch.cuda.Stream, raw handle, or None =
     torch's current stream). write_counts / write_owner: optional uint32 /
     int32 device tensors with one entry per output element. checked: the
     device-checked launch (TP_EXEC_CHECKED). inject_timeout: the tensor-core
-    GEMM's failure-path test hook (TP_EXEC_INJECT_TIMEOUT)."""
+    GEMM's failure-path test hook (TP_EXEC_INJECT_TIMEOUT). static_weights:
+    the decode products may start reading their weights before the work
+    queued ahead of them on the stream finishes (TP_EXEC_STATIC_WEIGHTS)."""
     ex = tp_exec()
     ex.mode = mode
-    ex.flags = (_lib.EXEC_CHECKED if checked else 0) | (_lib.EXEC_INJECT_TIMEOUT if inject_timeout else 0)
+    ex.flags = ((_lib.EXEC_CHECKED if checked else 0) | (_lib.EXEC_INJECT_TIMEOUT if inject_timeout else 0) |
+                (_lib.EXEC_STATIC_WEIGHTS if static_weights else 0))
     ex.stream = _stream_handle(stream)
     ex.event = event.handle.value if event is not None else None
     ex.write_counts = write_counts.data_ptr() if write_counts is not None else None
@@ -421,7 +425,11 @@ class DecodeChain:
                   (("h", h), ("n", self.n), ("qkv", self.qkv), ("gu", self.gu), ("a", self.a), ("dd", self.dd))}
 
     def record_fused(self, ex: tp_exec | None = None) -> None:
-        """Two launches per layer: norm+QKV+gate/up+SiLU*mul, down+residual."""
+        """Two launches per layer (three with the down projection's K slices):
+        norm+QKV+gate/up+SiLU*mul, down+residual. The chain's weights stay
+        fixed while it runs, so the launches carry TP_EXEC_STATIC_WEIGHTS."""
+        ex = tp_exec.from_buffer_copy(ex) if ex is not None else make_exec()
+        ex.flags |= _lib.EXEC_STATIC_WEIGHTS
         for w_qkv, w_gu, w_down in self.layers:
             tp_decode_norm_qkv_gu(self.ctx, self.p["qkv"], self.p["a"], self.h, self.gamma, w_qkv, w_gu,
                                   self.eps, ex)

@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "TP_OK", 1: "TP_ERR_INVALID", 2: "TP_ERR_RANK", 3: "TP_ERR_AL
 # tp_exec.flags
 EXEC_CHECKED = 1
 EXEC_INJECT_TIMEOUT = 2
+EXEC_STATIC_WEIGHTS = 4
 # tp_dtype
 F32, BF16, F8E4M3, F64, I32, U32, U8 = range(7)
 # tp_map_kind

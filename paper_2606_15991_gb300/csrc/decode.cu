@@ -268,6 +268,7 @@ struct StreamArgs {
   int32_t slices;           // K slices (1, or > 1 with partial sums)
   int32_t xbufs;            // x slice buffers when slices > 1 (2..kSMaxXBufs)
   int32_t stages;           // ring stages (2..kSStages)
+  int32_t early_weights;    // weights may be copied before the dependency wait (TP_EXEC_STATIC_WEIGHTS)
   int64_t slice_cols;       // columns per slice, a multiple of kSCols, <= kSMaxXCols
   int64_t units0, units;    // units of problem 0, total units
   int64_t rows0, rows1;
@@ -329,11 +330,12 @@ __global__ void __launch_bounds__(kSThreads, 1)
     if (p.units > p.units0) tma_prefetch_desc(&map1);
   }
   __syncthreads();
-  // Programmatic dependent launch: the weights do not depend on the grids
-  // before this one, so the producer streams them at once, overlapping the
-  // previous kernel's tail; x (written by the previous kernels) is read only
-  // after the dependency wait (consumers; the producer before its first copy
-  // of an x slice).
+  // Programmatic dependent launch: when the caller vouches that the weights
+  // are not written by the grids before this one (early_weights), the
+  // producer streams them at once, overlapping the previous kernel's tail;
+  // otherwise it waits for those grids first. x (written by the previous
+  // kernels) is read only after the dependency wait (consumers; the
+  // producer before its first copy of an x slice).
   allow_dependents();
   // consumers only (warps 0-7): named barrier 1
   auto consumers_sync = [] { asm volatile("bar.sync 1, %0;" ::"n"(kSConsumers * 32) : "memory"); };
@@ -429,6 +431,7 @@ __global__ void __launch_bounds__(kSThreads, 1)
       int64_t t = 0;  // units taken by this CTA
       bool ok = true;
       const uint64_t pol = policy_evict_first();  // weights are read once
+      if (!p.early_weights) grid_dependency_wait();
       for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x, ++t) {
         bool second;
         int64_t rb;
@@ -453,7 +456,8 @@ __global__ void __launch_bounds__(kSThreads, 1)
           if (t == 0) {
             // consumers start on x only after this copy, so at most a ring's
             // worth of stages goes first
-            for (; st < stages_per_unit && st < nst && ok; ++st) ok = issue(st);
+            if (p.early_weights)
+              for (; st < stages_per_unit && st < nst && ok; ++st) ok = issue(st);
             if (!ok) break;
             grid_dependency_wait();  // x is the previous kernels' output
           }
@@ -875,6 +879,7 @@ tp_status tp_decode_norm_qkv_gu(tp_ctx* ctx, tp_partition* qkv, tp_partition* a_
   tp_status s = check_counts(ex);
   if (s != TP_OK) return s;
   Op o(__func__);
+  o.allow_static_weights = true;
   s = gamma ? o.begin(ctx, ex, {qkv, a_out}, {h, gamma, w_qkv, w_gu}) : o.begin(ctx, ex, {qkv, a_out}, {h, w_qkv, w_gu});
   if (s != TP_OK) return s;
   GemvArgs a{};
@@ -918,6 +923,7 @@ tp_status tp_decode_norm_qkv_gu(tp_ctx* ctx, tp_partition* qkv, tp_partition* a_
       sa.gamma = a.gamma;
       sa.counts = a.counts;
       sa.owner = a.owner;
+      sa.early_weights = (ex->flags & TP_EXEC_STATIC_WEIGHTS) ? 1 : 0;
       tp_status ls = launch_stream(ctx, sa, w_qkv, false, w_gu, true, o.stream);
       if (ls != TP_OK) {
         o.abort();
@@ -939,6 +945,7 @@ tp_status tp_decode_down_residual(tp_ctx* ctx, tp_partition* h, const tp_tensor*
   tp_status s = check_counts(ex);
   if (s != TP_OK) return s;
   Op o(__func__);
+  o.allow_static_weights = true;
   s = o.begin(ctx, ex, {h}, {w_down, a_in});
   if (s != TP_OK) return s;
   GemvArgs a{};
@@ -984,6 +991,7 @@ tp_status tp_decode_down_residual(tp_ctx* ctx, tp_partition* h, const tp_tensor*
     sa.y1 = a.y;
     sa.partial = ctx->d_partial;
     sa.x = a.x;
+    sa.early_weights = (ex->flags & TP_EXEC_STATIC_WEIGHTS) ? 1 : 0;
     sa.counts = sa.slices > 1 ? nullptr : a.counts;
     sa.owner = sa.slices > 1 ? nullptr : a.owner;
     tp_status ls = launch_stream(ctx, sa, w_down, false, w_down, false, o.stream);

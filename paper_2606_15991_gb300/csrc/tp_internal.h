@@ -158,6 +158,7 @@ struct Op {
   bool marked = false;
   bool allow_checked = false;  // the op implements TP_EXEC_CHECKED (set before begin)
   bool allow_inject = false;   // the op implements TP_EXEC_INJECT_TIMEOUT (set before begin)
+  bool allow_static_weights = false;  // the op implements TP_EXEC_STATIC_WEIGHTS (set before begin)
   DeviceGuard device;          // the context's device is current while the op launches
 
   tp_status begin(tp_ctx* c, const tp_exec* e, std::initializer_list<tp_partition*> outputs,

@@ -224,8 +224,10 @@ tp_status Op::begin_impl(tp_ctx* c, const tp_exec* e, const std::vector<tp_parti
   if (!ex) return fail(TP_ERR_INVALID, "null tp_exec");
   if (ex->mode < TP_SYNC || ex->mode > TP_CAPTURE)
     return fail(TP_ERR_INVALID, "tp_exec.mode must be TP_SYNC, TP_ASYNC or TP_CAPTURE");
-  if (ex->flags & ~(TP_EXEC_CHECKED | TP_EXEC_INJECT_TIMEOUT))
+  if (ex->flags & ~(TP_EXEC_CHECKED | TP_EXEC_INJECT_TIMEOUT | TP_EXEC_STATIC_WEIGHTS))
     return fail(TP_ERR_INVALID, "undefined tp_exec.flags bits");
+  if ((ex->flags & TP_EXEC_STATIC_WEIGHTS) && !allow_static_weights)
+    return fail(TP_ERR_UNSUPPORTED, "TP_EXEC_STATIC_WEIGHTS applies to the decode products only");
   if ((ex->flags & TP_EXEC_CHECKED) && !allow_checked)
     return fail(TP_ERR_UNSUPPORTED, "this operation has no device-checked launch (TP_EXEC_CHECKED)");
   if ((ex->flags & TP_EXEC_INJECT_TIMEOUT) && !allow_inject)

@@ -256,3 +256,61 @@ def test_streamed_layer_padded_weights(ctx, d, nq, ni, pad):
     assert ogemm.rel_frobenius(h.cpu(), href) <= 1e-5
     assert ogemm.rel_frobenius(ch.qkv.cpu(), qref) <= 1e-5
     ch.close()
+
+
+def test_weights_written_just_before_on_the_stream(ctx):
+    """A decode product whose weight matrix the previous launch on the same
+    stream writes (a tensor-core GEMM, whose kernels let the next one start
+    early): without TP_EXEC_STATIC_WEIGHTS the product reads the weights only
+    after that GEMM completes, so qkv and a match the FP64 oracle on the
+    weights the GEMM wrote. Queued with no host synchronisation between."""
+    d, nq, ni = 1024, 2048, 1536
+    g = torch.Generator(device="cuda")
+    g.manual_seed(21)
+    f = torch.randn(nq, 256, device="cuda", generator=g).to(torch.bfloat16) * 0.1
+    e = torch.randn(d, 256, device="cuda", generator=g).to(torch.bfloat16) * 0.1
+    w_qkv = torch.zeros(nq, d, device="cuda", dtype=torch.bfloat16)          # written by the GEMM below
+    w_gu = (torch.randn(2 * ni, d, device="cuda", generator=g) * 0.02).to(torch.bfloat16)
+    w_down = (torch.randn(d, ni, device="cuda", generator=g) * 0.02).to(torch.bfloat16)
+    h = _vec(d, 22)
+    h0 = h.clone()
+    ch = tp.DecodeChain(ctx, h, [(w_qkv, w_gu, w_down)])
+    s = torch.cuda.Stream()
+    ev = tp.tp_event_create(ctx)
+    torch.cuda.synchronize()
+    pw = tp.tp_partition_create(ctx, w_qkv, (256, 256))
+    tp.tp_partition_map(pw, tp.MAP_STRIDED, min(ctx.sm_count // 2, (nq // 256) * (d // 256)))
+    ex = tp.make_exec(tp.ASYNC, s, ev)
+    tp.tp_gemm(ctx, pw, f, e.t(), tp.gemm_config(bm=256, bn=256), ex)       # W_qkv = F E^T
+    tp.tp_decode_norm_qkv_gu(ctx, ch.p["qkv"], ch.p["a"], h, None, w_qkv, w_gu, 1e-6, ex)
+    tp.tp_event_wait(ev)
+    href, qref = odecode.chain(h0.cpu(), [(w_qkv.cpu(), w_gu.cpu(), torch.zeros(d, ni, dtype=torch.bfloat16))])
+    assert float(w_qkv.float().abs().max()) > 0
+    assert ogemm.rel_frobenius(ch.qkv.cpu(), qref) <= 1e-5
+    tp.tp_partition_destroy(pw)
+    tp.tp_event_destroy(ev)
+    ch.close()
+
+
+def test_static_weights_flag_is_for_the_decode_products(ctx):
+    """TP_EXEC_STATIC_WEIGHTS is accepted by the two decode products and
+    refused (TP_ERR_UNSUPPORTED) by other operations."""
+    x = _vec(4096, 3)
+    y = torch.empty_like(x)
+    p = tp.tp_partition_create(ctx, y, (4096,))
+    with pytest.raises(tp.TPError) as ei:
+        tp.tp_map_axpy(ctx, p, 1.0, x, x, tp.make_exec(static_weights=True))
+    assert ei.value.status == tp._lib.ERR_UNSUPPORTED
+    tp.tp_partition_destroy(p)
+    d, nq, ni = 264, 40, 40
+    layers = _layers(d, nq, ni, 1, seed=5)
+    h0 = _vec(d, 6)
+    h = h0.clone()
+    ch = tp.DecodeChain(ctx, h, layers)
+    w = layers[0]
+    flag = tp.make_exec(static_weights=True)
+    tp.tp_decode_norm_qkv_gu(ctx, ch.p["qkv"], ch.p["a"], h, None, w[0], w[1], 1e-6, flag)
+    tp.tp_decode_down_residual(ctx, ch.p["h"], w[2], ch.a, flag)
+    href, qref = odecode.chain(h0.cpu(), [(a.cpu(), b.cpu(), c.cpu()) for a, b, c in layers])
+    assert ogemm.rel_frobenius(h.cpu(), href) <= 1e-5
+    ch.close()
