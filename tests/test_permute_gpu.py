@@ -131,10 +131,13 @@ def test_rejections(ctx):
         tp.tp_permute_heads(ctx, p, s, 3, tp.make_exec(checked=True))
     assert e.value.status == tp._lib.ERR_UNSUPPORTED
     ex = tp.make_exec()
-    ex.flags = 4                                            # undefined bit
+    ex.flags = 8                                            # undefined bit
     with pytest.raises(tp.TPError) as e:
         tp.tp_permute_heads(ctx, p, s, 3, ex)
     assert e.value.status == tp._lib.ERR_INVALID
+    with pytest.raises(tp.TPError) as e:                    # a flag of the decode products only
+        tp.tp_permute_heads(ctx, p, s, 3, tp.make_exec(static_weights=True))
+    assert e.value.status == tp._lib.ERR_UNSUPPORTED
     tp.tp_partition_destroy(p)
 
 
