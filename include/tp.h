@@ -184,7 +184,16 @@ typedef struct tp_gemm_config {
   int32_t stages;      /* shared-memory ring depth                              */
   int32_t group_m;     /* raster band height in tiles (L2 reuse)                */
   int32_t num_programs;/* persistent programs; 0 = number of SMs (or pairs)     */
-  int32_t swap_ab;     /* grouped GEMM only: compute C^T = B^T A^T             */
+  int32_t swap_ab;     /* compute C^T = B^T A^T. Grouped GEMM: per plan. BF16
+                        * tensor-core tp_gemm: the partition's tiles are then
+                        * W x 128 (W = 32, 64 or 128 rows of C); a CTA pair
+                        * computes each as a 128 x W MMA tile whose rows are
+                        * C's columns (64 rows of B^T per CTA) and whose
+                        * columns are C's rows (W/2 rows of A per CTA), for
+                        * short M, where a normal tile would leave most of
+                        * the MMA's rows empty. No split_k, no narrow tiles
+                        * in the last round; other values than 0 and 1 are
+                        * reserved.                                           */
   int32_t split_k;     /* tensor-core GEMM, 128-row tiles: K slices per tile,
                         * 0 or 1 = none, 2, 4 or 8. A program is then a
                         * cluster of split_k CTAs; CTA s accumulates the K

@@ -53,7 +53,7 @@ constexpr uint32_t kStageC = 4u * 2u * 4096u;  // epilogue staging: 4 warps x 2 
 struct TcArgs {
   int64_t M, N, K;
   int32_t gm, gn;       // tile grid (gm * gn < 2^31)
-  int32_t rows;         // tile rows of one CTA: 64 or 128 (a CTA pair: 128 each, 256 per tile)
+  int32_t rows;         // MMA rows of one CTA: 64 or 128 (a CTA pair: 128 each, 256 per tile; swap: 64 each)
   int32_t bn;           // tile columns (32..256, multiple of 32)
   int32_t stages;
   int32_t kind;         // tp_map_kind (IDENTITY or STRIDED)
@@ -126,7 +126,9 @@ __device__ __forceinline__ void raster(uint32_t s, uint32_t gm, uint32_t gn, uin
   *tn = (int32_t)col;
 }
 
-template <bool kF8, bool kPair, bool kCount, bool kChecked>
+// kSwap (BF16 CTA pairs only): swap-AB tiles, the MMA computing C^T = B^T A^T
+// with its rows on C's columns.
+template <bool kF8, bool kPair, bool kCount, bool kChecked, bool kSwap = false>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b,
                    const __grid_constant__ CUtensorMap map_b_cut, const __grid_constant__ CUtensorMap map_c,
@@ -150,12 +152,12 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int32_t csize = kPair ? 2 : S;
   const int32_t prog = (int32_t)blockIdx.x / csize;
   const int32_t nprog = (int32_t)gridDim.x / csize;
-  const int tile_m = kPair ? 2 * BM : p.rows;
+  const int tile_m = kPair ? 2 * p.rows : p.rows;  // MMA rows of a tile
   const int b_rows = kPair ? p.bn / 2 : p.bn;
   // a stage holds kc K blocks of each operand, stacked: block j of A at
   // j * a_blk, of B at j * (its box rows * 128), each a 128-byte-swizzled
   // K-major tile
-  const uint32_t a_blk = (uint32_t)(kPair ? BM : p.rows) * 128;
+  const uint32_t a_blk = (uint32_t)p.rows * 128;
   const uint32_t a_stage = a_blk * (uint32_t)p.kc;
   const uint32_t b_stage = (uint32_t)b_rows * 128 * (uint32_t)p.kc;
   const uint32_t a0 = base;
@@ -242,8 +244,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ub_rows = kPair ? u.width / 2 : u.width;
         const CUtensorMap* mb = u.cut ? &map_b_cut : &map_b;
         const uint32_t utx = a_stage + (uint32_t)ub_rows * 128 * (uint32_t)p.kc;
-        const int32_t arow = tm * tile_m + (int32_t)rank * BM;
-        const int32_t brow = tn * p.bn + u.col + (int32_t)rank * ub_rows;
+        // swap-AB: the MMA's A operand is B^T (rows = C columns, tile column
+        // tn) and its B operand is A (rows = C rows, tile row tm)
+        const int32_t arow = (kSwap ? tn : tm) * tile_m + (int32_t)rank * p.rows;
+        const int32_t brow = (kSwap ? tm : tn) * p.bn + u.col + (int32_t)rank * ub_rows;
         for (int32_t kb = kb0; kb < kb1; kb += p.kc) {
           if (!mbar_wait(empty_bar(stage), phase ^ 1u, abort_flag, p.err, p.wait_ns)) { ok = false; break; }
           if (p.inject && s == prog && kb == kb0) {
@@ -343,9 +347,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   // ------------------------------------------------------------ epilogue
   // (warps 2..5 -> TMEM lane quadrants 2,3,0,1)
   const int quad = warp & 3;
-  // rows of this warp: 32 of a 128-row MMA, 16 (in lanes 0-15) of a 64-row one
-  const int wrows = (kPair || p.rows == BM) ? 32 : 16;
-  const int32_t warp_row0 = (int32_t)rank * BM + quad * wrows;  // first tile row of this warp
+  // rows of this warp: 32 of a 128-row MMA, 16 (in lanes 0-15) of a 64-row
+  // one
+  int wrows = p.rows == BM ? 32 : 16;
+  int32_t warp_row0 = (int32_t)rank * p.rows + quad * wrows;  // first tile row (MMA orientation) of this warp
+  int32_t swap_col = 0;  // swap-AB: first MMA column of this warp
+  if constexpr (kSwap) {
+    // an M = 128 MMA on a CTA pair leaves each CTA 64 D rows: columns
+    // [0, N/2) in TMEM lanes 0-63, columns [N/2, N) in lanes 64-127 (at TMEM
+    // columns 0..N/2-1), so each warp holds 32 rows x N/2 columns
+    wrows = 32;
+    warp_row0 = (int32_t)rank * p.rows + (quad & 1) * 32;
+    swap_col = (quad >> 1) * (p.bn / 2);
+  }
   const uint32_t tlane = (uint32_t)(quad * 32) << 16;         // TMEM lane offset of this warp
   // FP8 dequantisation factor 1 / (s_A * s_B), both steps in fp32
   const float scale = (p.scale_a && p.scale_b) ? 1.f / (*p.scale_a * *p.scale_b) : 1.f;
@@ -440,6 +454,24 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     ++nstaged;
   };
+  // swap-AB: lane i holds the MMA row n0 + i, i.e. column n0 + i of C, and
+  // r its FP32 values in C rows [m0, m0 + cols): 2-byte stores, consecutive
+  // lanes on consecutive columns
+  auto store_swap = [&](const uint32_t* r, int64_t n0, int64_t m0, int cols) {
+    const int64_t n = n0 + lane;
+    if (n >= p.N || m0 >= p.M) return;
+    const int lim = (int)min((int64_t)cols, p.M - m0);
+    __nv_bfloat16* dst = p.c + m0 * p.N + n;
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      if (i < lim) dst[(int64_t)i * p.N] = __float2bfloat16_rn(__uint_as_float(r[i]) * scale);
+    if constexpr (kCount) {
+      for (int i = 0; i < lim; ++i) {
+        atomicAdd(p.counts + (m0 + i) * p.N + n, 1u);
+        p.owner[(m0 + i) * p.N + n] = (int32_t)prog;
+      }
+    }
+  };
   bool counted = false;
   // Checked launch: each epilogue warp counts itself done right after its
   // last claim (still ahead of its last accumulator); the warp that counts
@@ -512,9 +544,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         sp_tn = tn;
         break;
       }
-      const int64_t row0 = (int64_t)tm * tile_m + warp_row0;
-      const int64_t col0 = (int64_t)tn * p.bn + u.col;
+      // first tile row and column of this warp in MMA orientation (swap-AB:
+      // rows are C columns, columns C rows)
+      const int64_t row0 = (int64_t)(kSwap ? tn : tm) * tile_m + warp_row0;
+      const int64_t col0 = (int64_t)(kSwap ? tm : tn) * p.bn + u.col;
       const uint32_t tacc = tmem_base + tlane + (uint32_t)(acc * p.bn);
+      if constexpr (kSwap) {
+        // this warp's N/2 MMA columns (C rows) in chunks of 32
+        const int half = p.bn / 2;
+#pragma unroll 1
+        for (int ch = 0; ch * 32 < half && store_ok; ++ch) {
+          uint32_t r[32];
+          tmem_ld32(tacc + (uint32_t)(ch * 32), r);
+          tmem_ld_wait();
+          store_swap(r, row0, col0 + swap_col + ch * 32, min(32, half - ch * 32));
+        }
+        release_acc(acc);
+        continue;
+      }
       const int nch = u.width / 32;
       int ch = 0;
       if (!kCount && p.stage_c) {
@@ -684,9 +731,9 @@ struct Maps {
   CUtensorMap a, b, b_cut, c, c64;
 };
 
-template <bool kF8, bool kPair, bool kCount, bool kChecked>
+template <bool kF8, bool kPair, bool kCount, bool kChecked, bool kSwap = false>
 cudaError_t launch_kernel(const Maps& m, const TcArgs& p, int grid, int csize, size_t smem, cudaStream_t st) {
-  auto k = gemm_tc_kernel<kF8, kPair, kCount, kChecked>;
+  auto k = gemm_tc_kernel<kF8, kPair, kCount, kChecked, kSwap>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 232448);
@@ -717,6 +764,15 @@ cudaError_t launch_inst(bool count, bool checked, const Maps& m, const TcArgs& p
                             : launch_kernel<kF8, kPair, false, true>(m, p, grid, csize, smem, st);
   return count ? launch_kernel<kF8, kPair, true, false>(m, p, grid, csize, smem, st)
                : launch_kernel<kF8, kPair, false, false>(m, p, grid, csize, smem, st);
+}
+
+// swap-AB tiles: BF16 on CTA pairs
+cudaError_t launch_swap(bool count, bool checked, const Maps& m, const TcArgs& p, int grid, size_t smem,
+                        cudaStream_t st) {
+  if (checked) return count ? launch_kernel<false, true, true, true, true>(m, p, grid, 2, smem, st)
+                            : launch_kernel<false, true, false, true, true>(m, p, grid, 2, smem, st);
+  return count ? launch_kernel<false, true, true, false, true>(m, p, grid, 2, smem, st)
+               : launch_kernel<false, true, false, false, true>(m, p, grid, 2, smem, st);
 }
 
 template <bool kF8>
@@ -823,15 +879,32 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   if ((ex->write_counts == nullptr) != (ex->write_owner == nullptr))
     return fail(TP_ERR_INVALID, "write_counts and write_owner must be given together");
   if (c->kind == TP_MAP_QUEUE) return fail(TP_ERR_UNSUPPORTED, "the tensor-core GEMM maps tiles by slot (identity/strided)");
-  const int bm = (int)c->tile[0], bn = (int)c->tile[1];
-  if (bm != BM / 2 && bm != BM && bm != 2 * BM)
-    return fail(TP_ERR_UNSUPPORTED, "tensor-core GEMM tiles have 64 or 128 rows (one CTA) or 256 rows (CTA pair)");
+  const int tile_r = (int)c->tile[0], tile_c = (int)c->tile[1];  // the partition's tile of C
+  if (cfg && cfg->bm && cfg->bm != tile_r) return fail(TP_ERR_SHAPE, "cfg.bm differs from the partition's tile");
+  if (cfg && cfg->bn && cfg->bn != tile_c) return fail(TP_ERR_SHAPE, "cfg.bn differs from the partition's tile");
+  // swap-AB (cfg.swap_ab): a C tile of W rows x 128 columns is computed as
+  // C^T = B^T A^T by a CTA pair, the MMA's 128 rows being C's columns (64
+  // per CTA) and its W columns C's rows (W/2 rows of A per CTA)
+  const bool swap = cfg && cfg->swap_ab != 0;
+  int bm, bn;  // MMA tile: rows (256 = CTA pair) and columns
+  if (swap) {
+    if (esize != 2) return fail(TP_ERR_UNSUPPORTED, "swap_ab applies to the BF16 GEMM");
+    if (tile_c != BM || (tile_r != 32 && tile_r != 64 && tile_r != 128))
+      return fail(TP_ERR_UNSUPPORTED, "swap_ab tiles have 32, 64 or 128 rows and 128 columns");
+    if (cfg->split_k > 1) return fail(TP_ERR_UNSUPPORTED, "swap_ab and split_k do not combine");
+    if (ex->flags & TP_EXEC_INJECT_TIMEOUT) return fail(TP_ERR_UNSUPPORTED, "TP_EXEC_INJECT_TIMEOUT applies to 128-row tiles");
+    bm = 2 * BM;  // a CTA pair
+    bn = tile_r;
+  } else {
+    bm = tile_r;
+    bn = tile_c;
+    if (bm != BM / 2 && bm != BM && bm != 2 * BM)
+      return fail(TP_ERR_UNSUPPORTED, "tensor-core GEMM tiles have 64 or 128 rows (one CTA) or 256 rows (CTA pair)");
+    if (bn < 32 || bn > 256 || bn % 32 || (bm == 2 * BM && bn % 64))
+      return fail(TP_ERR_UNSUPPORTED, "tile columns must be 32..256, a multiple of 32 (of 64 for 256-row tiles)");
+  }
   const bool pair = bm == 2 * BM;
-  const int rows = pair ? BM : bm;  // A rows per CTA and stage
-  if (bn < 32 || bn > 256 || bn % 32 || (pair && bn % 64))
-    return fail(TP_ERR_UNSUPPORTED, "tile columns must be 32..256, a multiple of 32 (of 64 for 256-row tiles)");
-  if (cfg && cfg->bm && cfg->bm != bm) return fail(TP_ERR_SHAPE, "cfg.bm differs from the partition's tile");
-  if (cfg && cfg->bn && cfg->bn != bn) return fail(TP_ERR_SHAPE, "cfg.bn differs from the partition's tile");
+  const int rows = swap ? BM / 2 : pair ? BM : bm;  // MMA rows per CTA and stage
   // K-major operands: A row-major (stride along K = 1), B stored N x K.
   if (a->strides[1] != 1 || b->strides[0] != 1)
     return fail(TP_ERR_UNSUPPORTED, "tensor-core GEMM needs K-major A (row-major M x K) and K-major B (stored N x K)");
@@ -899,16 +972,18 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   while (cols < 2 * bn) cols *= 2;
   p.tmem_cols = cols;
   SmemPlan plan;
-  s = plan_smem(pair, rows, bn, kc, split, cfg ? cfg->stages : 0, p.c_vec && !count, &plan);
+  // swap-AB tiles store C with plain stores: no staging area
+  s = plan_smem(pair, rows, bn, kc, split, cfg ? cfg->stages : 0, p.c_vec && !count && !swap, &plan);
   if (s != TP_OK) return s;
   kc = plan.kc;
   p.kc = kc;
   auto operand_map = [&](CUtensorMap* m, const void* ptr, int64_t rws, int64_t ld, int box_rows) {
     return kc > 1 ? make_map3(m, ptr, rws, K, ld, esize, box_rows, kc) : make_map(m, ptr, rws, K, ld, esize, box_rows);
   };
-  s = operand_map(&maps.a, a->ptr, M, lda, rows);
+  // the MMA's operands: A (rows of A) and B (rows of B^T), or swapped
+  s = swap ? operand_map(&maps.a, b->ptr, N, ldb, rows) : operand_map(&maps.a, a->ptr, M, lda, rows);
   if (s != TP_OK) return s;
-  s = operand_map(&maps.b, b->ptr, N, ldb, pair ? bn / 2 : bn);
+  s = swap ? operand_map(&maps.b, a->ptr, M, lda, bn / 2) : operand_map(&maps.b, b->ptr, N, ldb, pair ? bn / 2 : bn);
   if (s != TP_OK) return s;
   maps.b_cut = maps.b;
   p.stages = plan.stages;
@@ -933,7 +1008,7 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   p.total_slots = (int32_t)T;
   p.ncut = 1;
   p.bn_cut = bn;
-  if (c->kind == TP_MAP_STRIDED && split == 1) {
+  if (c->kind == TP_MAP_STRIDED && split == 1 && !swap) {
     const int64_t R = T % progs;
     const int unit = pair ? 64 : 32;  // narrow tiles keep whole 32-row B boxes per CTA
     int64_t S = 1;
@@ -959,8 +1034,9 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
     s = claims_for(ctx, p.claim_bits, &p.claims, &p.claim_done);
     if (s != TP_OK) return s;
   }
-  cudaError_t e = esize == 2 ? launch_any<false>(pair, count, checked, maps, p, (int)grid, csize, plan.smem, stream)
-                             : launch_any<true>(pair, count, checked, maps, p, (int)grid, csize, plan.smem, stream);
+  cudaError_t e = swap         ? launch_swap(count, checked, maps, p, (int)grid, plan.smem, stream)
+                 : esize == 2 ? launch_any<false>(pair, count, checked, maps, p, (int)grid, csize, plan.smem, stream)
+                              : launch_any<true>(pair, count, checked, maps, p, (int)grid, csize, plan.smem, stream);
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core GEMM launch");
   return TP_OK;
 }

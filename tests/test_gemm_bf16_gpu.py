@@ -462,3 +462,71 @@ def test_multi_block_stages_fallback_and_validation(ctx):
         with pytest.raises(tp.TPError) as e:
             _gemm(ctx, a, bt, bn=128, bm=128, P=3, bk=bad)
         assert e.value.status == tp._lib.ERR_INVALID
+
+
+def _swap_gemm(ctx, a, bt, w, P, bk=0, count=False, checked=False):
+    """C = A B on swap-AB tiles (cfg.swap_ab): the partition's tiles are W
+    rows x 128 columns of C, each computed as C^T = B^T A^T by a CTA pair."""
+    m, n = a.shape[0], bt.shape[0]
+    c = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
+    p = tp.tp_partition_create(ctx, c, (w, 128))
+    tp.tp_partition_map(p, tp.MAP_STRIDED, min(P, tp.tp_partition_query(p)["num_tiles"]))
+    counts = owner = None
+    if count:
+        counts = torch.zeros(m * n, dtype=torch.int32, device="cuda")
+        owner = torch.full((m * n,), -1, dtype=torch.int32, device="cuda")
+    tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=w, bn=128, bk=bk, swap_ab=1),
+               tp.make_exec(write_counts=counts, write_owner=owner, checked=checked))
+    info = tp.tp_partition_query(p)
+    tp.tp_partition_destroy(p)
+    return c, counts, owner, info
+
+
+@pytest.mark.parametrize("w", [32, 64, 128])
+@pytest.mark.parametrize("bk", [64, 256])
+@pytest.mark.parametrize("m,n,k", [(64, 1024, 1024), (37, 520, 2048), (128, 384, 1088), (1, 300, 192),
+                                   (100, 1160, 640)])
+def test_swap_ab_tiles(ctx, w, bk, m, n, k):
+    """Swap-AB tiles: the MMA's 128 rows are C columns (64 rows of B^T per
+    CTA of the pair) and its W columns are C rows (W/2 rows of A per CTA); the
+    epilogue writes each TMEM lane's values down a column of C. Integer inputs
+    give the exact product rounded once; random inputs are within the BF16
+    gate of the FP64 oracle and equal a normal tile's C; every element is
+    stored once, by the program the strided map gives its tile."""
+    a, bt = _operands(m, n, k, seed=w + k, kind="int")
+    c, counts, owner, info = _swap_gemm(ctx, a, bt, w, P=5, bk=bk, count=True)
+    assert np.array_equal(c.cpu().double().numpy(), lowp.round_bf16(ogemm.gemm(a.cpu(), bt.cpu().t())))
+    assert opart.check_counts(counts.cpu().numpy())["ok"]
+    assert np.array_equal(owner.cpu().numpy(),
+                          opart.gemm_owner_map_cut(m, n, w, 128, info["num_programs"], 1, limit=1))
+    a, bt = _operands(m, n, k, seed=w + k + 1)
+    c, _, _, _ = _swap_gemm(ctx, a, bt, w, P=7, bk=bk)
+    assert ogemm.rel_frobenius(c.cpu(), ogemm.gemm(a.cpu(), bt.cpu().t())) <= 5e-3
+    # each C element is accumulated over K in the same order as on a normal
+    # tile, so C is bit-identical to it (swap-AB is in the autotuner's
+    # single-pass class)
+    ref, _, _, _ = _gemm(ctx, a, bt, bn=64, bm=64, P=7)
+    assert torch.equal(c, ref)
+
+
+def test_swap_ab_checked_raw_and_validation(ctx):
+    """The checked launch claims swap-AB tiles like any other (same C); the
+    raw-pointer entry runs the same schedule; swap_ab with FP8, with tiles
+    other than W x 128, or with split_k is refused."""
+    m, n, k = 64, 1000, 512
+    a, bt = _operands(m, n, k, seed=41)
+    ref, _, _, _ = _swap_gemm(ctx, a, bt, 64, P=3, bk=128)
+    c, _, _, _ = _swap_gemm(ctx, a, bt, 64, P=3, bk=128, checked=True)
+    assert torch.equal(c, ref)
+    raw = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
+    tp.tp_gemm_unchecked(ctx, raw, a, bt.t(), tp.gemm_config(bm=64, bn=128, bk=128, swap_ab=1, num_programs=3))
+    torch.cuda.synchronize()
+    assert torch.equal(raw, ref)
+    for tile, kw in (((64, 64), {}), ((48, 128), {}), ((64, 128), {"split_k": 2})):
+        cc = torch.empty(m, n, device="cuda", dtype=torch.bfloat16)
+        p = tp.tp_partition_create(ctx, cc, tile)
+        tp.tp_partition_map(p, tp.MAP_STRIDED, 2)
+        with pytest.raises(tp.TPError) as e:
+            tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=tile[0], bn=tile[1], swap_ab=1, **kw))
+        assert e.value.status == tp._lib.ERR_UNSUPPORTED
+        tp.tp_partition_destroy(p)
