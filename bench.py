@@ -721,7 +721,7 @@ def small_gemm_row(tp, ctx, dev, stream):
             ms = _graph_time(tp, ctx, stream, lambda ex: tp.tp_gemm(ctx, p, a, bt.t(), cfg, ex), reps=reps)
             tp.tp_partition_destroy(p)
             row[name] = {"us": ms * 1e3, "tflops": fl / (ms * 1e-3) / 1e12,
-                         "config": {f: getattr(best, f) for f in ("bm", "bn", "bk", "group_m", "split_k")}}
+                         "config": {f: getattr(best, f) for f in ("bm", "bn", "bk", "group_m", "split_k", "swap_ab")}}
         if m <= 256:
             # the same product computed swap-AB (C^T = B^T A^T: 128 or 256 N rows
             # per MMA, N = M) by the grouped kernel as a one-problem group

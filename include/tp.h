@@ -507,14 +507,22 @@ tp_status tp_decode_down_residual(tp_ctx* ctx, tp_partition* h, const tp_tensor*
  * class unless the caller opts in to split-K with TP_TUNE_SPLIT_K, so a
  * tuned or proposed config never changes C unless asked to. */
 enum {
-  TP_TUNE_SPLIT_K = 1  /* also search the split-K configs (changes C's rounding) */
+  TP_TUNE_SPLIT_K = 1, /* also search the split-K configs (changes C's rounding) */
+  TP_TUNE_SWAP_AB = 2  /* also search the swap-AB configs (single-pass class;
+                        * tried on BF16 problems of at most W rows). Measured
+                        * on skinny shapes they ran within a few per cent of
+                        * 64-row tiles, and adding them to the proposer's
+                        * outputs raised its p90 regret, so the default
+                        * search and the proposer leave them out. */
 };
 /* The space (same order on every call; with flags = 0, index i is the MLP
  * proposer's output i): tile rows {64, 128 (one CTA), 256 (CTA pair)} x tile
  * columns {64, 128, 192, 256} x K per stage {1, 2, 4} K blocks (bk; the
  * deepest ring that fits) x raster bands {1, 8}, the 72 single-pass configs;
  * with TP_TUNE_SPLIT_K followed by the split-K programs of 128-row tiles:
- * (bn 128, split_k 2 / 4) and (bn 256, split_k 2 / 4 / 8), 77 configs. Writes up to `cap` configs to `out` (may be NULL) and the size
+ * (bn 128, split_k 2 / 4) and (bn 256, split_k 2 / 4 / 8). TP_TUNE_SWAP_AB
+ * inserts, after the 72, the swap-AB configs: W x 128 C tiles (bm = W = 32,
+ * 64, 128; bn 128; swap_ab 1) x K per stage {2, 4} K blocks. Writes up to `cap` configs to `out` (may be NULL) and the size
  * to *count. Errors: TP_ERR_INVALID (undefined flag bits), TP_ERR_UNSUPPORTED
  * (dtype). */
 tp_status tp_autotune_space(int32_t dtype, int32_t flags, tp_gemm_config* out, int32_t cap, int32_t* count);
@@ -542,9 +550,10 @@ tp_status tp_autotune_time(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t
  * and *out filled, else 0. */
 tp_status tp_autotune_lookup(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, int32_t flags,
                              tp_gemm_config* out, int32_t* found);
-/* Persist / restore the cache (text, "tp-autotune-cache v4": one line per
+/* Persist / restore the cache (text, "tp-autotune-cache v5": one line per
  * entry, M N K dtype flags bm bn bk stages group_m num_programs split_k
- * TFLOP/s). Load also reads v3 files (no bk column: bk 0) and v2 and v1
+ * swap_ab TFLOP/s). Load also reads v4 files (no swap_ab column: 0), v3
+ * files (no bk column: bk 0) and v2 and v1
  * files (no flags column; v1 lines also lack split_k), whose searches
  * covered the split-K configs: an entry is filed under TP_TUNE_SPLIT_K, and
  * a single-pass winner under flags 0 too. */

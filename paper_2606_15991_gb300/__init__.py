@@ -18,7 +18,7 @@ from ._lib import (ASYNC, CAPTURE, MAP_IDENTITY, MAP_QUEUE, MAP_STRIDED, SYNC, T
 
 __all__ = [
     "TPError", "SYNC", "ASYNC", "CAPTURE", "MAP_IDENTITY", "MAP_STRIDED", "MAP_QUEUE",
-    "tensor_desc", "make_exec", "gemm_config", "TUNE_SPLIT_K",
+    "tensor_desc", "make_exec", "gemm_config", "TUNE_SPLIT_K", "TUNE_SWAP_AB",
     "tp_version", "tp_ctx_create", "tp_ctx_destroy", "tp_ctx_info", "tp_tensor_init", "tp_tensor_view",
     "tp_partition_create", "tp_partition_map", "tp_partition_query", "tp_partition_destroy",
     "tp_event_create", "tp_event_query", "tp_event_wait", "tp_event_destroy",
@@ -458,12 +458,18 @@ def _cfg_dict(c: tp_gemm_config) -> dict:
 
 
 TUNE_SPLIT_K = 1
+TUNE_SWAP_AB = 2
 
 
-def tp_autotune_space(dtype: str = "bf16", split_k: bool = False) -> list:
+def _tune_flags(split_k: bool, swap_ab: bool) -> int:
+    return (TUNE_SPLIT_K if split_k else 0) | (TUNE_SWAP_AB if swap_ab else 0)
+
+
+def tp_autotune_space(dtype: str = "bf16", split_k: bool = False, swap_ab: bool = False) -> list:
     """The autotuner's config space: the single-pass configs (index i =
-    proposer output i), then, with split_k, the split-K configs."""
-    fl = TUNE_SPLIT_K if split_k else 0
+    proposer output i), then, with swap_ab, the swap-AB configs, then, with
+    split_k, the split-K configs."""
+    fl = _tune_flags(split_k, swap_ab)
     n = ctypes.c_int32()
     call("tp_autotune_space", _DT_CODE[dtype], fl, None, 0, ctypes.byref(n))
     arr = (tp_gemm_config * n.value)()
@@ -471,14 +477,15 @@ def tp_autotune_space(dtype: str = "bf16", split_k: bool = False) -> list:
     return [arr[i] for i in range(n.value)]
 
 
-def tp_autotune(ctx, M: int, N: int, K: int, dtype: str = "bf16", reps: int = 0, split_k: bool = False):
+def tp_autotune(ctx, M: int, N: int, K: int, dtype: str = "bf16", reps: int = 0, split_k: bool = False,
+                swap_ab: bool = False):
     """Exhaustive search: returns (best config, [TFLOP/s per config], best TFLOP/s)."""
-    cnt = len(tp_autotune_space(dtype, split_k))
+    cnt = len(tp_autotune_space(dtype, split_k, swap_ab))
     best = tp_gemm_config()
     table = (ctypes.c_float * cnt)()
     bt = ctypes.c_float()
     call("tp_autotune", ctx.handle, int(M), int(N), int(K), _DT_CODE[dtype], int(reps),
-         TUNE_SPLIT_K if split_k else 0, ctypes.byref(best), table, ctypes.byref(bt))
+         _tune_flags(split_k, swap_ab), ctypes.byref(best), table, ctypes.byref(bt))
     return best, list(table), bt.value
 
 
@@ -491,10 +498,11 @@ def tp_autotune_time(ctx, M: int, N: int, K: int, dtype: str, cfg: tp_gemm_confi
     return out.value
 
 
-def tp_autotune_lookup(ctx, M: int, N: int, K: int, dtype: str = "bf16", split_k: bool = False):
+def tp_autotune_lookup(ctx, M: int, N: int, K: int, dtype: str = "bf16", split_k: bool = False,
+                       swap_ab: bool = False):
     out = tp_gemm_config()
     found = ctypes.c_int32()
-    call("tp_autotune_lookup", ctx.handle, int(M), int(N), int(K), _DT_CODE[dtype], TUNE_SPLIT_K if split_k else 0,
+    call("tp_autotune_lookup", ctx.handle, int(M), int(N), int(K), _DT_CODE[dtype], _tune_flags(split_k, swap_ab),
          ctypes.byref(out), ctypes.byref(found))
     return out if found.value else None
 

@@ -44,6 +44,8 @@ struct TuneState {
   cudaStream_t stream = nullptr;
 };
 
+constexpr int32_t kTuneFlags = TP_TUNE_SPLIT_K | TP_TUNE_SWAP_AB;
+
 std::mutex g_states_mu;
 std::map<tp_ctx*, TuneState*> g_states;
 
@@ -54,9 +56,11 @@ TuneState* state(tp_ctx* ctx) {
   return s;
 }
 
-// The single-pass configs (one numerics class), then, with TP_TUNE_SPLIT_K,
-// the split-K configs. K per stage is 1, 2 or 4 K blocks of 128 bytes (64
-// bf16 / 128 fp8 elements), the deepest ring that fits.
+// The single-pass configs (one numerics class), then, with TP_TUNE_SWAP_AB,
+// swap-AB tiles of W x 128 on CTA pairs (the same class: every C element is
+// accumulated in the same K order), then, with TP_TUNE_SPLIT_K, the split-K
+// configs. K per stage is 1, 2 or 4 K blocks of 128 bytes (64 bf16 / 128 fp8
+// elements), the deepest ring that fits.
 std::vector<tp_gemm_config> space(int32_t dtype, int32_t flags) {
   std::vector<tp_gemm_config> v;
   const int kblk = dtype == TP_F8E4M3 ? 128 : 64;
@@ -71,6 +75,19 @@ std::vector<tp_gemm_config> space(int32_t dtype, int32_t flags) {
           c.group_m = gm;
           v.push_back(c);
         }
+  // swap-AB (BF16, short M): C tiles of W rows x 128 columns, stages of 2 or
+  // 4 K blocks (one block per stage streams B at two thirds of the rate)
+  if (flags & TP_TUNE_SWAP_AB)
+    for (int w : {32, 64, 128})
+      for (int kb : {2, 4}) {
+        tp_gemm_config c{};
+        c.bm = w;
+        c.bn = 128;
+        c.bk = kb * kblk;
+        c.group_m = 1;
+        c.swap_ab = 1;
+        v.push_back(c);
+      }
   if (!(flags & TP_TUNE_SPLIT_K)) return v;
   // split-K programs (128-row tiles; a cluster of split_k CTAs per tile) for
   // shapes with fewer tiles than SMs
@@ -87,16 +104,22 @@ std::vector<tp_gemm_config> space(int32_t dtype, int32_t flags) {
   return v;
 }
 
-// Whether config c of the space is tried on an M x N x K problem: a split
-// program holds one tile and needs at least split_k K blocks, and past two
-// waves of clusters it cannot win.
+}  // namespace
+
+// Whether config c of the space is tried on an M x N x K problem: swap-AB
+// tiles serve BF16 problems that one row of tiles covers (M <= W, so B is
+// read once); a split program holds one tile and needs at least split_k K
+// blocks, and past two waves of clusters it cannot win.
 bool autotune_config_runs(const tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype,
                           const tp_gemm_config& c) {
+  if (c.swap_ab) return dtype == TP_BF16 && M <= c.bm;
   if (c.split_k <= 1) return true;
   const int64_t tiles = ((M + c.bm - 1) / c.bm) * ((N + c.bn - 1) / c.bn);
   const int64_t kblk = dtype == TP_F8E4M3 ? 128 : 64;
   return (K + kblk - 1) / kblk >= c.split_k && tiles * c.split_k <= 2 * (int64_t)ctx->sm_count;
 }
+
+namespace {
 
 // Fills a workspace with finite values that exercise the tensor cores the
 // way real data does (a hash of the index, small magnitudes).
@@ -227,7 +250,7 @@ tp_status time_config(tp_ctx* ctx, TuneState* st, const TuneProblem& pb, const t
   part.grid[0] = (pb.M + c.bm - 1) / c.bm;
   part.grid[1] = (pb.N + c.bn - 1) / c.bn;
   part.num_tiles = part.grid[0] * part.grid[1];
-  const int64_t cap = c.bm == 256 ? ctx->sm_count / 2 : ctx->sm_count;  // CTA pairs, or CTAs
+  const int64_t cap = (c.bm == 256 || c.swap_ab) ? ctx->sm_count / 2 : ctx->sm_count;  // CTA pairs, or CTAs
   part.kind = TP_MAP_STRIDED;
   part.num_programs = std::min<int64_t>(part.num_tiles, cap);
   if (c.num_programs > 0) part.num_programs = std::min<int64_t>(part.num_tiles, c.num_programs);
@@ -250,7 +273,7 @@ tp_status time_config(tp_ctx* ctx, TuneState* st, const TuneProblem& pb, const t
 tp_status check_args(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, int32_t flags) {
   if (!ctx) return fail(TP_ERR_INVALID, "null context");
   if (dtype != TP_BF16 && dtype != TP_F8E4M3) return fail(TP_ERR_UNSUPPORTED, "dtype must be BF16 or F8E4M3");
-  if (flags & ~TP_TUNE_SPLIT_K) return fail(TP_ERR_INVALID, "undefined TP_TUNE_* flag bits");
+  if (flags & ~kTuneFlags) return fail(TP_ERR_INVALID, "undefined TP_TUNE_* flag bits");
   const int esize = dtype == TP_BF16 ? 2 : 1;
   if (M < 1 || N < 1 || K < 1 || (K * esize) % 16) return fail(TP_ERR_SHAPE, "need M, N, K >= 1 and K*esize % 16 == 0");
   std::lock_guard<std::mutex> lk(ctx->mu);
@@ -268,7 +291,7 @@ extern "C" {
 tp_status tp_autotune_space(int32_t dtype, int32_t flags, tp_gemm_config* out, int32_t cap, int32_t* count) {
   if (!count) return fail(TP_ERR_INVALID, "null count");
   if (dtype != TP_BF16 && dtype != TP_F8E4M3) return fail(TP_ERR_UNSUPPORTED, "dtype must be BF16 or F8E4M3");
-  if (flags & ~TP_TUNE_SPLIT_K) return fail(TP_ERR_INVALID, "undefined TP_TUNE_* flag bits");
+  if (flags & ~kTuneFlags) return fail(TP_ERR_INVALID, "undefined TP_TUNE_* flag bits");
   auto v = space(dtype, flags);
   *count = (int32_t)v.size();
   if (out)
@@ -324,7 +347,7 @@ tp_status tp_autotune_time(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t
                            int32_t reps, int32_t repeats, float* tflops_median) {
   if (!cfg || !tflops_median) return fail(TP_ERR_INVALID, "null argument");
   if (repeats < 1 || repeats > 64) return fail(TP_ERR_INVALID, "repeats must be 1..64");
-  tp_status s = check_args(ctx, M, N, K, dtype, cfg->split_k > 1 ? TP_TUNE_SPLIT_K : 0);
+  tp_status s = check_args(ctx, M, N, K, dtype, 0);
   if (s != TP_OK) return s;
   DeviceGuard guard(ctx);
   TuneState* st = state(ctx);
@@ -351,7 +374,7 @@ tp_status tp_autotune_time(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t
 tp_status tp_autotune_lookup(tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype, int32_t flags,
                              tp_gemm_config* out, int32_t* found) {
   if (!ctx || !found) return fail(TP_ERR_INVALID, "null argument");
-  if (flags & ~TP_TUNE_SPLIT_K) return fail(TP_ERR_INVALID, "undefined TP_TUNE_* flag bits");
+  if (flags & ~kTuneFlags) return fail(TP_ERR_INVALID, "undefined TP_TUNE_* flag bits");
   TuneState* st = state(ctx);
   std::lock_guard<std::mutex> lk(st->mu);
   auto it = st->cache.find(TuneKey{M, N, K, dtype, flags});
@@ -366,12 +389,12 @@ tp_status tp_autotune_save(tp_ctx* ctx, const char* path) {
   std::lock_guard<std::mutex> lk(st->mu);
   FILE* f = std::fopen(path, "w");
   if (!f) return fail(TP_ERR_INVALID, std::string("cannot write ") + path);
-  std::fprintf(f, "tp-autotune-cache v4\n");
+  std::fprintf(f, "tp-autotune-cache v5\n");
   for (auto& kv : st->cache) {
     const auto& c = kv.second.first;
-    std::fprintf(f, "%lld %lld %lld %d %d %d %d %d %d %d %d %d %.3f\n", (long long)kv.first.m, (long long)kv.first.n,
-                 (long long)kv.first.k, kv.first.dtype, kv.first.flags, c.bm, c.bn, c.bk, c.stages, c.group_m,
-                 c.num_programs, c.split_k, kv.second.second);
+    std::fprintf(f, "%lld %lld %lld %d %d %d %d %d %d %d %d %d %d %.3f\n", (long long)kv.first.m,
+                 (long long)kv.first.n, (long long)kv.first.k, kv.first.dtype, kv.first.flags, c.bm, c.bn, c.bk,
+                 c.stages, c.group_m, c.num_programs, c.split_k, c.swap_ab, kv.second.second);
   }
   std::fclose(f);
   return TP_OK;
@@ -381,29 +404,34 @@ tp_status tp_autotune_load(tp_ctx* ctx, const char* path) {
   if (!ctx || !path) return fail(TP_ERR_INVALID, "null argument");
   FILE* f = std::fopen(path, "r");
   if (!f) return fail(TP_ERR_INVALID, std::string("cannot read ") + path);
-  // v4 lines carry the search flags and bk; v3 lines lack bk; v2 and v1
-  // entries came from searches that included split-K (v1 lines also lack
-  // the split_k column)
+  // v5 lines carry swap_ab; v4 lines the search flags and bk; v3 lines lack
+  // bk; v2 and v1 entries came from searches that included split-K (v1 lines
+  // also lack the split_k column)
   char magic[64] = {};
   const bool ok = std::fgets(magic, sizeof magic, f) != nullptr;
   auto is = [&](const char* m) { return ok && std::string(magic).rfind(m, 0) == 0; };
-  const int ver = is("tp-autotune-cache v4")   ? 4
+  const int ver = is("tp-autotune-cache v5")   ? 5
+                  : is("tp-autotune-cache v4") ? 4
                   : is("tp-autotune-cache v3") ? 3
                   : is("tp-autotune-cache v2") ? 2
                   : is("tp-autotune-cache v1") ? 1
                                                : 0;
   if (!ver) {
     std::fclose(f);
-    return fail(TP_ERR_INVALID, "not an autotune cache (v1 to v4)");
+    return fail(TP_ERR_INVALID, "not an autotune cache (v1 to v5)");
   }
   TuneState* st = state(ctx);
   std::lock_guard<std::mutex> lk(st->mu);
   long long m, n, k;
-  int dt, fl = TP_TUNE_SPLIT_K, bm, bn, bk = 0, stages, gm, np, sk = 0;
+  int dt, fl = TP_TUNE_SPLIT_K, bm, bn, bk = 0, stages, gm, np, sk = 0, sw = 0;
   float tf;
   for (;;) {
     int got, want;
-    if (ver == 4) {
+    if (ver == 5) {
+      got = std::fscanf(f, "%lld %lld %lld %d %d %d %d %d %d %d %d %d %d %f", &m, &n, &k, &dt, &fl, &bm, &bn, &bk,
+                        &stages, &gm, &np, &sk, &sw, &tf);
+      want = 14;
+    } else if (ver == 4) {
       got = std::fscanf(f, "%lld %lld %lld %d %d %d %d %d %d %d %d %d %f", &m, &n, &k, &dt, &fl, &bm, &bn, &bk,
                         &stages, &gm, &np, &sk, &tf);
       want = 13;
@@ -420,7 +448,8 @@ tp_status tp_autotune_load(tp_ctx* ctx, const char* path) {
       want = 10;
     }
     if (got != want) break;
-    if ((fl & ~TP_TUNE_SPLIT_K) || (sk > 1 && !(fl & TP_TUNE_SPLIT_K))) continue;  // not a winner of such a search
+    if ((fl & ~kTuneFlags) || (sk > 1 && !(fl & TP_TUNE_SPLIT_K)) || (sw && !(fl & TP_TUNE_SWAP_AB)))
+      continue;  // not a winner of such a search
     tp_gemm_config c{};
     c.bm = bm;
     c.bn = bn;
@@ -429,6 +458,7 @@ tp_status tp_autotune_load(tp_ctx* ctx, const char* path) {
     c.group_m = gm;
     c.num_programs = np;
     c.split_k = sk;
+    c.swap_ab = sw;
     st->cache[TuneKey{m, n, k, dt, fl}] = {c, tf};
     // an older search over the whole space that picked a single-pass config
     // also holds the single-pass class's winner

@@ -404,10 +404,12 @@ tp_status tp_propose(tp_ctx* ctx, tp_mlp* n, int64_t M, int64_t N, int64_t K, in
   std::vector<float> y(count);
   e = cudaMemcpy(y.data(), n->y, count * sizeof(float), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "proposer scores");
-  // arg-max over the single-pass configs (ties keep the lower index)
-  int best = 0;
-  for (int i = 1; i < count; ++i)
-    if (y[i] > y[best]) best = i;
+  // arg-max over the single-pass configs the autotuner would try on this
+  // shape (ties keep the lower index)
+  int best = -1;
+  for (int i = 0; i < count; ++i)
+    if (autotune_config_runs(ctx, M, N, K, dtype, cfgs[i]) && (best < 0 || y[i] > y[best])) best = i;
+  if (best < 0) return fail(TP_ERR_UNSUPPORTED, "no config of the space runs on this shape");
   const bool in_range = M <= 16384 && N <= 16384 && K <= 16384;
   if (score) *score = y[best];
   if (y[best] >= min_score && in_range) {

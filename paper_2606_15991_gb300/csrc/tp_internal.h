@@ -204,6 +204,10 @@ tp_status launch_gemm_tc(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const
 // Programs of the tensor-core GEMM (CTA pairs for 256-row tiles, CTAs
 // otherwise) that can be resident at once for `cfg`.
 tp_status gemm_tc_resident(tp_ctx* ctx, const tp_gemm_config* cfg, int32_t* programs);
+// Whether the autotuner tries config c of its space on an M x N x K problem
+// of `dtype` (a config it does not try is never proposed for it either).
+bool autotune_config_runs(const tp_ctx* ctx, int64_t M, int64_t N, int64_t K, int32_t dtype,
+                          const tp_gemm_config& c);
 
 tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_tensor* b,
                               const tp_gemm_config* cfg, const tp_exec* ex, cudaStream_t stream, int esize,

@@ -189,15 +189,16 @@ def graph_time_ms(ctx, stream, record, reps: int, replays: int = 3) -> float:
 
 def tuned_config(ctx, best, tiles: int):
     """A launch config from an autotuned one: persistent programs (CTAs, CTA
-    pairs for 256-row tiles) up to the SM count, or one split program per
-    tile for a split-K config."""
+    pairs for 256-row and swap-AB tiles) up to the SM count, or one split
+    program per tile for a split-K config."""
     from . import gemm_config
     if best.split_k > 1:
         progs = tiles
     else:
-        progs = min(best.num_programs or (ctx.sm_count // (2 if best.bm == 256 else 1)), tiles)
+        pair = best.bm == 256 or best.swap_ab
+        progs = min(best.num_programs or (ctx.sm_count // (2 if pair else 1)), tiles)
     return gemm_config(bm=best.bm, bn=best.bn, bk=best.bk, stages=best.stages, group_m=best.group_m,
-                       num_programs=progs, split_k=best.split_k)
+                       num_programs=progs, swap_ab=best.swap_ab, split_k=best.split_k)
 
 
 class _Captured:

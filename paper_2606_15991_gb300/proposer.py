@@ -116,9 +116,9 @@ def scores(mlp, X) -> np.ndarray:
 def config_index(space, cfg) -> int:
     """Position of a proposed config in the autotuner's space (of its dtype:
     BF16 and FP8 configs differ in bk, K blocks of 64 or 128 elements)."""
-    key = (cfg.bm, cfg.bn, cfg.bk, cfg.stages, cfg.group_m, cfg.split_k)
+    key = (cfg.bm, cfg.bn, cfg.bk, cfg.stages, cfg.group_m, cfg.split_k, cfg.swap_ab)
     for i, c in enumerate(space):
-        if (c.bm, c.bn, c.bk, c.stages, c.group_m, c.split_k) == key:
+        if (c.bm, c.bn, c.bk, c.stages, c.group_m, c.split_k, c.swap_ab) == key:
             return i
     raise ValueError(f"config {key} is not in the space")
 

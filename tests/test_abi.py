@@ -144,26 +144,35 @@ def test_autotune_space_and_targets_on_the_host(built_lib):
     """The autotuner's space (host data): by default the 72 single-pass
     configs (rows 64, 128 or 256, columns 64..256, 1, 2 or 4 K blocks per
     stage, raster bands 1 or 8), which all compute C bit-identically; with
-    the split-K opt-in the same 72 followed by the split-K configs, each
-    with 128-row tiles and a column slice of at least 32 per K slice. BF16
-    and FP8 share the layout, with K blocks of 64 and 128 elements; undefined
-    flag bits are refused. Training targets train a config that did not run
-    towards 0."""
+    the swap-AB opt-in followed by 6 swap-AB configs (W x 128 C tiles, W =
+    32, 64 or 128, 2 or 4 K blocks per stage; the same class); with the
+    split-K opt-in followed by the split-K configs, each with 128-row tiles
+    and a column slice of at least 32 per K slice. BF16 and FP8 share the
+    layout, with K blocks of 64 and 128 elements; undefined flag bits are
+    refused. Training targets train a config that did not run towards 0."""
     whole = tp.tp_autotune_space("bf16")
     assert len(whole) == 72 and len(tp.tp_autotune_space("fp8")) == 72
     assert {(c.bm, c.bn, c.bk, c.group_m) for c in whole} == {
         (bm, bn, 64 * kb, g) for bm in (64, 128, 256) for bn in (64, 128, 192, 256) for kb in (1, 2, 4)
         for g in (1, 8)}
+    assert all(c.swap_ab == 0 for c in whole)
     assert [c.bk for c in tp.tp_autotune_space("fp8")] == [2 * c.bk for c in whole]
     assert all(c.split_k == 0 and c.stages == 0 for c in whole)
+    key = lambda c: (c.bm, c.bn, c.bk, c.stages, c.group_m, c.swap_ab)
+    sw = tp.tp_autotune_space("bf16", swap_ab=True)
+    assert [key(c) for c in sw[:72]] == [key(c) for c in whole]
+    assert [(c.bm, c.bn, c.bk, c.group_m, c.swap_ab, c.split_k) for c in sw[72:]] == [
+        (w, 128, 64 * kb, 1, 1, 0) for w in (32, 64, 128) for kb in (2, 4)]
+    both = tp.tp_autotune_space("bf16", split_k=True, swap_ab=True)
+    assert len(both) == 83 and [key(c) for c in both[:78]] == [key(c) for c in sw]
     full = tp.tp_autotune_space("bf16", split_k=True)
     assert len(full) == 77 and len(tp.tp_autotune_space("fp8", split_k=True)) == 77
-    key = lambda c: (c.bm, c.bn, c.bk, c.stages, c.group_m)
     assert [key(c) for c in full[:72]] == [key(c) for c in whole]
+    assert [key(c) for c in both[78:]] == [key(c) for c in full[72:]]
     split = full[72:]
     assert [(c.bn, c.split_k) for c in split] == [(128, 2), (128, 4), (256, 2), (256, 4), (256, 8)]
     assert all(c.bm == 128 and c.bn % (32 * c.split_k) == 0 for c in split)
     n = ctypes.c_int32()
-    assert _lib.lib().tp_autotune_space(_lib.BF16, 2, None, 0, ctypes.byref(n)) == _lib.ERR_INVALID
+    assert _lib.lib().tp_autotune_space(_lib.BF16, 4, None, 0, ctypes.byref(n)) == _lib.ERR_INVALID
     tg, mk = tp.tp_mlp_targets([3.0, 0.0, 1.5])
     assert tg == [1.0, 0.0, 0.5] and mk == [1.0, 1.0, 1.0]

@@ -104,7 +104,7 @@ def test_features_targets_and_save_load(ctx, tmp_path):
 @pytest.mark.parametrize("dtype", ["bf16", "fp8"])
 def test_autotune_table_cache_and_numerics(ctx, dtype, tmp_path):
     space = tp.tp_autotune_space(dtype)
-    assert len(space) == 72 and all(cfg.split_k <= 1 for cfg in space)
+    assert len(space) == 72 and all(cfg.split_k <= 1 and not cfg.swap_ab for cfg in space)
     M, N, K = 700, 900, 1024
     best, table, best_tf = tp.tp_autotune(ctx, M, N, K, dtype)
     assert len(table) == len(space) and all(t > 0 for t in table)
@@ -130,11 +130,12 @@ def test_autotune_table_cache_and_numerics(ctx, dtype, tmp_path):
         a = synth.to_bf16(synth.normal(M * K, 1)).reshape(M, K).cuda()
         bt = synth.to_bf16(synth.normal(N * K, 2)).reshape(N, K).cuda()
         ref = None
-        for cfg in tp.tp_autotune_space(dtype, split_k=True):
+        for cfg in tp.tp_autotune_space(dtype, split_k=True, swap_ab=True):
             c = torch.empty(M, N, dtype=torch.bfloat16, device="cuda")
             p = tp.tp_partition_create(ctx, c, (cfg.bm, cfg.bn))
             tiles = tp.tp_partition_query(p)["num_tiles"]
-            tp.tp_partition_map(p, tp.MAP_STRIDED, min(tiles, ctx.sm_count // (2 if cfg.bm == 256 else 1)))
+            pair = cfg.bm == 256 or cfg.swap_ab
+            tp.tp_partition_map(p, tp.MAP_STRIDED, min(tiles, ctx.sm_count // (2 if pair else 1)))
             tp.tp_gemm(ctx, p, a, bt.t(), cfg)
             tp.tp_partition_destroy(p)
             if cfg.split_k > 1:
@@ -211,7 +212,8 @@ def test_proposals_equal_exhaustive_pick_bit_for_bit(ctx, trained):
         prop, _, fb = tp.tp_propose(ctx, mlp, m, n, k, "bf16", min_score=-1e9)
         assert not fb and prop.split_k <= 1
         exh, _, _ = tp.tp_autotune(ctx, m, n, k, "bf16")
-        differ += (prop.bm, prop.bn, prop.bk, prop.group_m) != (exh.bm, exh.bn, exh.bk, exh.group_m)
+        differ += (prop.bm, prop.bn, prop.bk, prop.group_m, prop.swap_ab) != (exh.bm, exh.bn, exh.bk, exh.group_m,
+                                                                             exh.swap_ab)
         a = synth.to_bf16(synth.normal(m * k, 100 + i)).reshape(m, k).cuda()
         bt = synth.to_bf16(synth.normal(n * k, 200 + i)).reshape(n, k).cuda()
         outs = []
@@ -219,7 +221,8 @@ def test_proposals_equal_exhaustive_pick_bit_for_bit(ctx, trained):
             c = torch.full((m, n), float("nan"), dtype=torch.bfloat16, device="cuda")
             p = tp.tp_partition_create(ctx, c, (cfg.bm, cfg.bn))
             tiles = tp.tp_partition_query(p)["num_tiles"]
-            tp.tp_partition_map(p, tp.MAP_STRIDED, min(tiles, ctx.sm_count // (2 if cfg.bm == 256 else 1)))
+            pair = cfg.bm == 256 or cfg.swap_ab
+            tp.tp_partition_map(p, tp.MAP_STRIDED, min(tiles, ctx.sm_count // (2 if pair else 1)))
             tp.tp_gemm(ctx, p, a, bt.t(), cfg)
             tp.tp_partition_destroy(p)
             outs.append(c)
@@ -256,7 +259,7 @@ def test_autotune_cache_reads_older_files(ctx, tmp_path):
     """v1 and v2 cache lines (no flags column) came from searches that
     included split-K: a single-pass winner loads under both searches, a
     split winner only under the split-K search; v3 lines lack bk (0); v4
-    saves write the flags and bk."""
+    lines lack swap_ab (0); v5 saves write the flags, bk and swap_ab."""
     path = os.path.join(tmp_path, "v1.txt")
     with open(path, "w") as f:
         f.write("tp-autotune-cache v1\n")
@@ -282,7 +285,7 @@ def test_autotune_cache_reads_older_files(ctx, tmp_path):
     out = os.path.join(tmp_path, "v4.txt")
     tp.tp_autotune_save(ctx, out)
     lines = open(out).read().splitlines()
-    assert lines[0] == "tp-autotune-cache v4"
+    assert lines[0] == "tp-autotune-cache v5"
     assert any(line.split()[:12] == ["1111", "2222", "3344", "1", "0", "256", "128", "0", "3", "8", "76", "0"]
                for line in lines[1:])
     assert not any(line.split()[:5] == ["128", "256", "4096", "1", "0"] and line.split()[11] == "4"
@@ -291,3 +294,50 @@ def test_autotune_cache_reads_older_files(ctx, tmp_path):
                for line in lines[1:])
     tp.tp_autotune_load(ctx, out)
     assert tp.tp_autotune_lookup(ctx, 640, 384, 512, "bf16").bk == best.bk
+    path4 = os.path.join(tmp_path, "v4.txt")
+    with open(path4, "w") as f:
+        f.write("tp-autotune-cache v4\n")
+        f.write("64 8192 8192 1 0 64 64 256 0 1 0 0 290.0\n")
+    tp.tp_autotune_load(ctx, path4)
+    cfg = tp.tp_autotune_lookup(ctx, 64, 8192, 8192, "bf16")
+    assert (cfg.bm, cfg.bn, cfg.bk, cfg.swap_ab) == (64, 64, 256, 0)
+    swap = [c for c in tp.tp_autotune_space("bf16", swap_ab=True) if c.swap_ab][2]
+    path5 = os.path.join(tmp_path, "v5.txt")
+    with open(path5, "w") as f:
+        f.write("tp-autotune-cache v5\n")
+        f.write(f"32 4096 2048 1 2 {swap.bm} {swap.bn} {swap.bk} 0 1 0 0 1 150.0\n")
+        f.write(f"32 4096 4096 1 0 {swap.bm} {swap.bn} {swap.bk} 0 1 0 0 1 150.0\n")   # not from such a search
+    tp.tp_autotune_load(ctx, path5)
+    cfg = tp.tp_autotune_lookup(ctx, 32, 4096, 2048, "bf16", swap_ab=True)
+    assert (cfg.bm, cfg.bn, cfg.bk, cfg.swap_ab) == (swap.bm, swap.bn, swap.bk, 1)
+    assert tp.tp_autotune_lookup(ctx, 32, 4096, 4096, "bf16") is None
+
+
+def test_swap_ab_search_is_opt_in(ctx):
+    """TP_TUNE_SWAP_AB adds the swap-AB configs to the search: on a BF16
+    problem of 64 rows the W = 64 and W = 128 ones are timed (W = 32 tiles
+    would need two tile rows and are skipped), none on FP8; the winner is
+    cached under that flag, and it computes C bit for bit like the default
+    search's winner (both in the single-pass class)."""
+    M, N, K = 64, 2048, 1024
+    space = tp.tp_autotune_space("bf16", swap_ab=True)
+    best, table, _ = tp.tp_autotune(ctx, M, N, K, "bf16", swap_ab=True)
+    assert len(table) == len(space) == 78
+    assert all((t > 0) == (not c.swap_ab or c.bm >= M) for t, c in zip(table, space))
+    assert tp.tp_autotune_lookup(ctx, M, N, K, "bf16", swap_ab=True) is not None
+    _, t8, _ = tp.tp_autotune(ctx, M, N, K, "fp8", swap_ab=True)
+    assert all(t == 0 for t in t8[72:]) and all(t > 0 for t in t8[:72])
+    dflt, _, _ = tp.tp_autotune(ctx, M, N, K, "bf16")
+    a = synth.to_bf16(synth.normal(M * K, 11)).reshape(M, K).cuda()
+    bt = synth.to_bf16(synth.normal(N * K, 12)).reshape(N, K).cuda()
+    outs = []
+    for cfg in (best, dflt, space[74]):          # space[74]: W = 64, 2 K blocks per stage
+        c = torch.full((M, N), float("nan"), dtype=torch.bfloat16, device="cuda")
+        p = tp.tp_partition_create(ctx, c, (cfg.bm, cfg.bn))
+        tiles = tp.tp_partition_query(p)["num_tiles"]
+        pair = cfg.bm == 256 or cfg.swap_ab
+        tp.tp_partition_map(p, tp.MAP_STRIDED, min(tiles, ctx.sm_count // (2 if pair else 1)))
+        tp.tp_gemm(ctx, p, a, bt.t(), cfg)
+        tp.tp_partition_destroy(p)
+        outs.append(c)
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[1], outs[2])
