@@ -696,8 +696,9 @@ def _torch_graph_time(stream, fn, reps: int, replays: int = 3) -> float:
 
 def small_gemm_row(tp, ctx, dev, stream):
     """Small and skinny BF16 GEMMs on each shape's autotuned config (the
-    single-pass class, whose configs all compute C bit-identically) and on the
-    split-K opt-in's pick, against cuBLAS (torch.matmul) in the same run; for
+    single-pass class, whose configs all compute C bit-identically), on the
+    split-K opt-in's pick and, for M <= 128, on the swap-AB opt-in's pick
+    (same class), against cuBLAS (torch.matmul) in the same run; for
     M <= 256 also swap-AB through the grouped kernel (one-problem group)."""
     import torch
 
@@ -713,8 +714,11 @@ def small_gemm_row(tp, ctx, dev, stream):
         fl = 2.0 * m * n * k
         reps = 50
         row = {}
-        for name, split in (("single_pass", False), ("split_k_opt_in", True)):
-            best, _, _ = tp.tp_autotune(ctx, m, n, k, "bf16", split_k=split)
+        searches = [("single_pass", False, False), ("split_k_opt_in", True, False)]
+        if m <= 128:
+            searches.append(("swap_ab_opt_in", False, True))
+        for name, split, swap in searches:
+            best, _, _ = tp.tp_autotune(ctx, m, n, k, "bf16", split_k=split, swap_ab=swap)
             p = tp.tp_partition_create(ctx, c, (best.bm, best.bn))
             cfg = experiments.tuned_config(ctx, best, tp.tp_partition_query(p)["num_tiles"])
             tp.tp_partition_map(p, tp.MAP_STRIDED, cfg.num_programs)
@@ -733,7 +737,7 @@ def small_gemm_row(tp, ctx, dev, stream):
                                                                           "tflops": fl / (ms * 1e-3) / 1e12}
         ms_cb = _torch_graph_time(stream, lambda: torch.matmul(a, bt.t(), out=c), reps=reps)
         row["cublas_us"] = ms_cb * 1e3
-        for name in ("single_pass", "split_k_opt_in"):
+        for name, _, _ in searches:
             row[name]["vs_cublas"] = ms_cb / (row[name]["us"] * 1e-3)
         row["b_stream_gbs_single_pass"] = 2.0 * n * k / (row["single_pass"]["us"] * 1e-6) / 1e9
         out[f"{m}x{n}x{k}"] = row
