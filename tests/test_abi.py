@@ -176,3 +176,26 @@ def test_autotune_space_and_targets_on_the_host(built_lib):
     assert _lib.lib().tp_autotune_space(_lib.BF16, 4, None, 0, ctypes.byref(n)) == _lib.ERR_INVALID
     tg, mk = tp.tp_mlp_targets([3.0, 0.0, 1.5])
     assert tg == [1.0, 0.0, 0.5] and mk == [1.0, 1.0, 1.0]
+
+
+def test_binding_constants_match_the_header():
+    """Every enum constant the ctypes binding passes across the boundary
+    (status codes, dtypes, map kinds, launch modes, exec and tuning flags)
+    equals the value include/tp.h gives it."""
+    import re
+
+    header = open(_lib.HEADER).read()
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(TP_[A-Z0-9_]+)\s*=\s*(\d+)", header)}
+    status = {name: code for code, name in _lib.STATUS_NAMES.items()}
+    assert status == {k: v for k, v in consts.items() if k == "TP_OK" or k.startswith("TP_ERR_")}
+    expect = {
+        "TP_F32": _lib.F32, "TP_BF16": _lib.BF16, "TP_F8E4M3": _lib.F8E4M3, "TP_F64": _lib.F64,
+        "TP_I32": _lib.I32, "TP_U32": _lib.U32, "TP_U8": _lib.U8,
+        "TP_MAP_IDENTITY": _lib.MAP_IDENTITY, "TP_MAP_STRIDED": _lib.MAP_STRIDED, "TP_MAP_QUEUE": _lib.MAP_QUEUE,
+        "TP_SYNC": _lib.SYNC, "TP_ASYNC": _lib.ASYNC, "TP_CAPTURE": _lib.CAPTURE,
+        "TP_EXEC_CHECKED": _lib.EXEC_CHECKED, "TP_EXEC_INJECT_TIMEOUT": _lib.EXEC_INJECT_TIMEOUT,
+        "TP_EXEC_STATIC_WEIGHTS": _lib.EXEC_STATIC_WEIGHTS,
+        "TP_TUNE_SPLIT_K": tp.TUNE_SPLIT_K, "TP_TUNE_SWAP_AB": tp.TUNE_SWAP_AB,
+    }
+    for name, value in expect.items():
+        assert consts[name] == value, name
