@@ -389,13 +389,15 @@ tp_status tp_gemm(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, const tp_ten
  * defaults): CTA pairs for 256-row tiles, CTAs otherwise. A
  * persistent launch with more programs than this runs the extra ones after
  * others finish. With split_k > 1 the count is of split programs (clusters
- * of split_k CTAs). Errors: TP_ERR_INVALID, TP_ERR_UNSUPPORTED, TP_ERR_CUDA. */
+ * of split_k CTAs); with swap_ab of CTA pairs. Errors: TP_ERR_INVALID,
+ * TP_ERR_UNSUPPORTED, TP_ERR_CUDA. */
 tp_status tp_gemm_resident_programs(tp_ctx* ctx, const tp_gemm_config* cfg, int32_t* programs);
 
 /* The BF16 tensor-core GEMM against a raw output pointer: the unchecked
  * baseline of §5.1 (the same schedule with manual raw-pointer output access).
  * `c` is a contiguous BF16 M x N device buffer; A and B as for tp_gemm.
- * cfg->bm (64, 128 or 256) and cfg->bn give the tile; cfg->num_programs > 0
+ * cfg->bm (64, 128 or 256) and cfg->bn give the tile (with cfg->swap_ab: W =
+ * 32, 64 or 128 rows x 128 columns, on CTA pairs); cfg->num_programs > 0
  * maps tiles strided over that many programs (CTA pairs for bm = 256), 0
  * launches one program per tile; cfg->stages and cfg->group_m as for tp_gemm.
  * No partition is involved: nothing is checked against aliasing or work in

@@ -1042,6 +1042,23 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
 }
 
 tp_status gemm_tc_resident(tp_ctx* ctx, const tp_gemm_config* cfg, int32_t* programs) {
+  const int kc = cfg->bk >= 256 ? 4 : cfg->bk >= 128 ? 2 : 1;  // K blocks per stage (bf16 K blocks of 64)
+  (void)ctx;
+  if (cfg->swap_ab) {
+    // swap-AB tiles: CTA pairs, each CTA holding 64 rows of B^T and W/2 rows
+    // of A per K block, no staging area
+    const int w = cfg->bm ? cfg->bm : BM;
+    if ((w != 32 && w != 64 && w != 128) || (cfg->bn && cfg->bn != BM))
+      return fail(TP_ERR_UNSUPPORTED, "swap_ab tiles have 32, 64 or 128 rows and 128 columns");
+    if (cfg->split_k > 1) return fail(TP_ERR_UNSUPPORTED, "swap_ab and split_k do not combine");
+    SmemPlan plan;
+    tp_status s = plan_smem(true, BM / 2, w, kc, 1, cfg->stages, false, &plan);
+    if (s != TP_OK) return s;
+    const int pairs = max_active_clusters<true>(2, plan.smem);
+    if (pairs <= 0) return fail(TP_ERR_CUDA, "cudaOccupancyMaxActiveClusters failed");
+    *programs = pairs;
+    return TP_OK;
+  }
   const int bm = cfg->bm ? cfg->bm : BM, bn = cfg->bn ? cfg->bn : 256;
   if (bm != BM / 2 && bm != BM && bm != 2 * BM) return fail(TP_ERR_UNSUPPORTED, "tiles have 64, 128 or 256 rows");
   const bool pair = bm == 2 * BM;
@@ -1049,10 +1066,8 @@ tp_status gemm_tc_resident(tp_ctx* ctx, const tp_gemm_config* cfg, int32_t* prog
   if (split > 8 || (split & (split - 1))) return fail(TP_ERR_INVALID, "split_k must be 0, 1, 2, 4 or 8");
   if (split > 1 && bm != BM) return fail(TP_ERR_UNSUPPORTED, "split_k applies to 128-row tiles");
   SmemPlan plan;
-  const int kc = cfg->bk >= 256 ? 4 : cfg->bk >= 128 ? 2 : 1;  // K blocks per stage (bf16 K blocks of 64)
   tp_status s = plan_smem(pair, pair ? BM : bm, bn, kc, split, cfg->stages, true, &plan);
   if (s != TP_OK) return s;
-  (void)ctx;
   const int csize = pair ? 2 : split;
   const int clusters = pair ? max_active_clusters<true>(csize, plan.smem) : max_active_clusters<false>(csize, plan.smem);
   if (clusters <= 0) return fail(TP_ERR_CUDA, "cudaOccupancyMaxActiveClusters failed");

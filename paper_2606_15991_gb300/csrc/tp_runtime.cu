@@ -882,7 +882,9 @@ tp_status tp_gemm_unchecked(tp_ctx* ctx, void* c, const tp_tensor* a, const tp_t
   if (a->dtype != TP_BF16 || b->dtype != TP_BF16) return fail(TP_ERR_UNSUPPORTED, "BF16 operands only");
   const int64_t M = a->shape[0], K = a->shape[1], N = b->shape[1];
   if (b->shape[0] != K) return fail(TP_ERR_SHAPE, "need A: M x K, B: K x N");
-  if (cfg->bm != 64 && cfg->bm != 128 && cfg->bm != 256) return fail(TP_ERR_INVALID, "cfg.bm must be 64, 128 or 256");
+  if (cfg->swap_ab ? (cfg->bm != 32 && cfg->bm != 64 && cfg->bm != 128)
+                   : (cfg->bm != 64 && cfg->bm != 128 && cfg->bm != 256))
+    return fail(TP_ERR_INVALID, "cfg.bm must be 64, 128 or 256 (swap_ab: 32, 64 or 128)");
   if (cfg->bn <= 0) return fail(TP_ERR_INVALID, "cfg.bn must be given");
   // a stack descriptor of C's tiling; nothing is registered with the context
   tp_partition p;

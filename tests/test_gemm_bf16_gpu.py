@@ -387,6 +387,13 @@ def test_resident_programs(ctx):
     with pytest.raises(tp.TPError) as e:
         tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=96, bn=256))
     assert e.value.status == tp._lib.ERR_UNSUPPORTED
+    # swap-AB tiles run on CTA pairs
+    for w in (32, 64, 128):
+        sw = tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=w, bn=128, bk=256, swap_ab=1))
+        assert 0 < sw <= ctx.sm_count // 2, (w, sw)
+    with pytest.raises(tp.TPError) as e:
+        tp.tp_gemm_resident_programs(ctx, tp.gemm_config(bm=64, bn=64, swap_ab=1))
+    assert e.value.status == tp._lib.ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("bn", [96, 160, 224])
@@ -518,10 +525,11 @@ def test_swap_ab_checked_raw_and_validation(ctx):
     ref, _, _, _ = _swap_gemm(ctx, a, bt, 64, P=3, bk=128)
     c, _, _, _ = _swap_gemm(ctx, a, bt, 64, P=3, bk=128, checked=True)
     assert torch.equal(c, ref)
-    raw = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
-    tp.tp_gemm_unchecked(ctx, raw, a, bt.t(), tp.gemm_config(bm=64, bn=128, bk=128, swap_ab=1, num_programs=3))
-    torch.cuda.synchronize()
-    assert torch.equal(raw, ref)
+    for w in (64, 32):
+        raw = torch.full((m, n), float("nan"), device="cuda", dtype=torch.bfloat16)
+        tp.tp_gemm_unchecked(ctx, raw, a, bt.t(), tp.gemm_config(bm=w, bn=128, bk=128, swap_ab=1, num_programs=3))
+        torch.cuda.synchronize()
+        assert torch.equal(raw, ref), w
     for tile, kw in (((64, 64), {}), ((48, 128), {}), ((64, 128), {"split_k": 2})):
         cc = torch.empty(m, n, device="cuda", dtype=torch.bfloat16)
         p = tp.tp_partition_create(ctx, cc, tile)
