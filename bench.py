@@ -913,8 +913,8 @@ def proposer_row(tp, ctx, train_n: int, test_n: int, epochs: int, log=None) -> d
     """The learned-proposer experiment: exhaustive tables of `train_n` shapes
     (BF16 and FP8, x 72 single-pass configs: ~20k autotuner measurements at
     278 shapes) for training on the GPU, `test_n` held-out shapes tuned
-    exhaustively as the judge, proposals made by tp_propose. Regret is
-    reported twice: against the judge's one timing per config, and with the
+    exhaustively as the reference, proposals made by tp_propose. Regret is
+    reported twice: against the exhaustive search's one timing per config, and with the
     proposal, the exhaustive pick and the fixed default re-timed (median of 3
     independent timings each) so that the reference is not the maximum of
     noisy samples."""
@@ -949,7 +949,7 @@ def proposer_row(tp, ctx, train_n: int, test_n: int, epochs: int, log=None) -> d
     return {
         "space": "single-pass configs (bit-identical C; split-K excluded)", "configs": int(T.shape[1]),
         "train_shapes": len(train_shapes), "train_measurements": int(V.sum()), "test_shapes": len(test_shapes),
-        "judge_single_timing": r, "retimed_median_of_3": rt,
+        "exhaustive_single_timing": r, "retimed_median_of_3": rt,
         "default_config": {n: getattr(space[dflt], n) for n in ("bm", "bn", "bk", "stages", "group_m", "split_k")},
         "large_shapes": int(big.sum()),
         "large_mean_regret": float(reg[big].mean()) if big.any() else None,
