@@ -135,12 +135,22 @@ def evaluate(mlp, X, TF, default_index: int, min_score: float = 0.0, prop=None) 
     """Regret of the MLP's proposals (the given space indices, else the plain
     arg-max of its scores) and of the fixed default config."""
     S = scores(mlp, X)
-    best = TF.max(axis=1)
     if prop is None:
         prop = S.argmax(axis=1)
+    return regret_stats(TF, prop, default_index, S.max(axis=1), min_score)
+
+
+def regret_stats(TF, prop, default_index: int, top_score=None, min_score: float = 0.0) -> dict:
+    """Regret summary from exhaustive tables TF [shapes, configs] (TFLOP/s):
+    regret = 1 - TF[proposal] / max TF, for the proposals `prop` and for the
+    fixed config `default_index`; a shape whose top score is below
+    `min_score` goes to the exhaustive fallback, whose regret is 0."""
+    TF = np.asarray(TF, dtype=np.float64)
+    prop = np.asarray(prop)
+    best = TF.max(axis=1)
     reg = 1.0 - TF[np.arange(len(TF)), prop] / best
     reg_def = 1.0 - TF[:, default_index] / best
-    fallback = S.max(axis=1) < min_score
+    fallback = (np.zeros(len(TF), bool) if top_score is None else np.asarray(top_score) < min_score)
     reg_fb = np.where(fallback, 0.0, reg)   # the exhaustive fallback has zero regret by definition
     return {"median_regret": float(np.median(reg)), "p90_regret": float(np.percentile(reg, 90)),
             "mean_regret": float(reg.mean()),
