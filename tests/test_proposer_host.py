@@ -30,3 +30,25 @@ def test_default_config_is_best_on_average():
     T = np.array([[1.0, 0.9, 0.2], [0.5, 1.0, 1.0], [1.0, 0.8, 0.0]], np.float32)
     V = np.array([[1, 1, 1], [1, 1, 1], [1, 1, 0]], np.float32)
     assert proposer.default_config(T, V) == 1       # column sums 2.5, 2.7, 1.2
+
+
+def test_tuned_config_programs():
+    """A launch config from an autotuned one: persistent programs up to the
+    SM count in CTAs, or in CTA pairs for 256-row and swap-AB tiles, one
+    program per tile for split-K; swap_ab and the K per stage carry over."""
+    from types import SimpleNamespace
+
+    from paper_2606_15991_gb300 import experiments, gemm_config
+
+    ctx = SimpleNamespace(sm_count=152)
+    cases = [(gemm_config(bm=128, bn=256, bk=128), 1000, 152),
+             (gemm_config(bm=256, bn=256, group_m=8), 1000, 76),
+             (gemm_config(bm=64, bn=128, bk=256, swap_ab=1), 1000, 76),
+             (gemm_config(bm=64, bn=128, swap_ab=1), 40, 40),
+             (gemm_config(bm=128, bn=128, split_k=4), 24, 24),
+             (gemm_config(bm=128, bn=64, num_programs=7), 100, 7)]
+    for best, tiles, progs in cases:
+        cfg = experiments.tuned_config(ctx, best, tiles)
+        assert cfg.num_programs == progs, (best.bm, best.swap_ab, best.split_k)
+        assert (cfg.bm, cfg.bn, cfg.bk, cfg.swap_ab, cfg.split_k) == (best.bm, best.bn, best.bk, best.swap_ab,
+                                                                     best.split_k)
