@@ -808,6 +808,24 @@ def decode_row(tp, ctx, dev, stream, peaks):
                     "implementation streaming the weights once could reach against it"}
 
 
+def grouped_rooflines_ms(shapes, peaks) -> tuple:
+    """Roofline times (ms) of a group of BF16 GEMMs (M, N, K), each problem
+    2MNK flops and 2(MK + KN + MN) bytes. The grouped launch can overlap
+    HBM-bound and tensor-bound tiles, so its bound is max(total flops /
+    tensor peak, total bytes / HBM peak): at the burst bf16 peak, and at the
+    sustained one (the burst one when none is measured). The sum of the
+    problems' own bounds (no overlap) is returned third."""
+    flops = sum(2.0 * m * n * k for m, n, k in shapes)
+    bytes_ = sum(2.0 * (m * k + k * n + m * n) for m, n, k in shapes)
+    hbm = peaks["hbm_gbs"] * 1e9
+    t_overlap = max(flops / (peaks["bf16_tflops"] * 1e12), bytes_ / hbm) * 1e3
+    sust = peaks.get("bf16_tflops_sustained") or peaks["bf16_tflops"]
+    t_overlap_sust = max(flops / (sust * 1e12), bytes_ / hbm) * 1e3
+    t_sum = sum(max(2.0 * m * n * k / (peaks["bf16_tflops"] * 1e12), 2.0 * (m * k + k * n + m * n) / hbm)
+                for m, n, k in shapes) * 1e3
+    return t_overlap, t_overlap_sust, t_sum
+
+
 def grouped_row(tp, ctx, dev, stream, peaks):
     """64 BF16 GEMMs (M log-uniform on [1, 4096], four (K, N) pairs, seed 0):
     one persistent grouped launch against 64 plain per-call launches."""
@@ -881,14 +899,7 @@ def grouped_row(tp, ctx, dev, stream, peaks):
         tp.tp_partition_destroy(p)
     tp.tp_event_destroy(ev)
     tp.tp_grouped_plan_destroy(plan)
-    # overlap roofline: the launch can overlap HBM-bound and tensor-bound
-    # tiles, so its bound is max(total flops / tensor peak, total bytes / HBM
-    # peak); the sum of per-problem bounds (no overlap) is kept beside it
-    t_overlap = max(flops / (peaks["bf16_tflops"] * 1e12), bytes_ / (peaks["hbm_gbs"] * 1e9)) * 1e3
-    sust = peaks.get("bf16_tflops_sustained") or peaks["bf16_tflops"]
-    t_overlap_sust = max(flops / (sust * 1e12), bytes_ / (peaks["hbm_gbs"] * 1e9)) * 1e3
-    t_sum = sum(max(2.0 * m * n * k / (peaks["bf16_tflops"] * 1e12),
-                    2.0 * (m * k + k * n + m * n) / (peaks["hbm_gbs"] * 1e9)) for m, n, k in shapes) * 1e3
+    t_overlap, t_overlap_sust, t_sum = grouped_rooflines_ms(shapes, peaks)
     del probs
     torch.cuda.empty_cache()
     return {"ms_grouped": ms_grouped, "ms_plain_sync": res["plain_sync"], "ms_plain_chained": res["plain_chained"],
