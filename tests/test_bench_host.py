@@ -18,3 +18,26 @@ def test_grouped_rooflines_hand_worked():
     # without a sustained figure the burst peak stands in for it
     peaks.pop("bf16_tflops_sustained")
     assert bench.grouped_rooflines_ms(shapes, peaks)[1] == pytest.approx(2.002)
+
+
+def test_reference_arm_prints_its_line():
+    """`bench.py --impl reference` runs the oracle's maps step on the host
+    cores and prints one JSON line in the benchmark's form: impl, metric and
+    unit as the GPU line, a positive value, the cores it used, and an e2e
+    figure with no host-device copies."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "30", "--warmup", "0"],
+                         cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    import bench
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "TB/s"
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 30
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+    assert line["config"]["workload"] == bench.WORKLOAD
