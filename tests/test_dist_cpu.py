@@ -1,4 +1,4 @@
-"""The multi-process path of bench.py on CPU: two gloo ranks (one process
+"""The multi-process path of bench.py on CPU: two or four gloo ranks (one process
 per GPU on a GPU node) agree on the slowest rank's step time, read their
 rank from the launcher's environment, and the whole-job value is the
 world size times one rank's bytes over that time (weak scaling, no data
@@ -29,29 +29,31 @@ def _rank_main(rank, ws, port, q):
     ms = bench._barrier_max(10.0 + 5.0 * rank, ws, torch.device("cpu"))
     value = bench.weak_scaling_value(got_ws, 3.0e9, ms)
     all_ok = bench._all_ranks_ok(True, ws, torch.device("cpu"))
-    one_failed = bench._all_ranks_ok(rank == 0, ws, torch.device("cpu"))   # rank 1 reports a failure
+    one_failed = bench._all_ranks_ok(rank == 0, ws, torch.device("cpu"))   # ranks past 0 report a failure
     dist.barrier()
     dist.destroy_process_group()
     q.put((rank, got_ws, got_rank, got_local, ms, value, all_ok, one_failed))
 
 
-@pytest.mark.timeout(120)
-def test_two_gloo_ranks_take_the_max_step_time():
+@pytest.mark.timeout(150)
+@pytest.mark.parametrize("world", [2, 4])
+def test_gloo_ranks_take_the_max_step_time(world):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank_main, args=(r, world, port, q)) for r in range(world)]
     for p in procs:
         p.start()
-    out = sorted(q.get(timeout=90) for _ in procs)
+    out = sorted(q.get(timeout=120) for _ in procs)
     for p in procs:
         p.join(timeout=30)
         assert p.exitcode == 0
+    slowest = 10.0 + 5.0 * (world - 1)
     for rank, ws, r, local, ms, value, all_ok, one_failed in out:
         assert all_ok and not one_failed                   # every rank sees the same verdict
-        assert (ws, r, local) == (2, rank, rank)
-        assert ms == 15.0                                   # the slower rank's time, on every rank
-        assert value == pytest.approx(2 * 3.0e9 / 15e-3 / 1e12)
+        assert (ws, r, local) == (world, rank, rank)
+        assert ms == slowest                                # the slowest rank's time, on every rank
+        assert value == pytest.approx(world * 3.0e9 / (slowest * 1e-3) / 1e12)
 
 
 def test_single_process_defaults(monkeypatch):
