@@ -204,3 +204,45 @@ def test_grouped_queue_coverage():
         [i for i, t in enumerate(tc) for _ in range(t)]
     with pytest.raises(ValueError):
         grouped.queue_decode(total, tc)
+
+
+@pytest.mark.parametrize("T", [1, 5, 7, 33, 76, 100, 1024])
+@pytest.mark.parametrize("P", [1, 3, 4, 13, 76, 152])
+@pytest.mark.parametrize("bn,unit", [(64, 32), (128, 32), (256, 64), (192, 32)])
+def test_gemm_cut_schedule_properties(T, P, bn, unit):
+    """The cut schedule from its properties rather than its loop: whole tiles
+    first (one per program per round), then each of the R = T mod P tiles of
+    the partial round split into S narrow tiles with S a power of two, at
+    most the limit, no more narrow tiles than programs (R S <= P), each of a
+    whole number of units; and S is the largest such choice (doubling it
+    breaks one of these), S = 1 meaning nothing is cut."""
+    limit = 4
+    D, S = partition.gemm_cut_schedule(T, P, bn, unit, limit)
+    R = T % P
+    assert S >= 1 and S & (S - 1) == 0 and S <= limit
+    if S == 1:
+        assert D == T
+    else:
+        assert D == T - R and R * S <= P and (bn // S) % unit == 0 and bn % S == 0
+    feasible = lambda s: R > 0 and s <= limit and R * s <= P and bn % (s * unit) == 0
+    assert not feasible(2 * S)
+    # every slot of the schedule maps to a distinct (tile, column range) and
+    # the ranges of each tile cover its columns exactly once
+    cover = {}
+    slots = D + (T - D) * S
+    for s in range(slots):
+        if s < D:
+            cover.setdefault(s, []).append((0, bn))
+        else:
+            tile, j = D + (s - D) // S, (s - D) % S
+            cover.setdefault(tile, []).append((j * bn // S, (j + 1) * bn // S))
+    assert sorted(cover) == list(range(T))
+    for ranges in cover.values():
+        ranges.sort()
+        assert ranges[0][0] == 0 and ranges[-1][1] == bn
+        assert all(a[1] == b[0] for a, b in zip(ranges, ranges[1:]))
+    # the last round gives no program more than one narrow tile more than another
+    per_prog = np.zeros(P, dtype=np.int64)
+    for s in range(D, slots):
+        per_prog[s % P] += 1
+    assert per_prog.max() - per_prog.min() <= 1
