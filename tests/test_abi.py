@@ -199,3 +199,16 @@ def test_binding_constants_match_the_header():
     }
     for name, value in expect.items():
         assert consts[name] == value, name
+
+
+def test_mlp_features_on_the_host(built_lib):
+    """The proposer's input features (host code, no GPU): log2 M, log2 N,
+    log2 K and a one-hot dtype, equal to the oracle's within fp32 rounding;
+    a power of two gives its exponent exactly."""
+    from oracle import mlp as omlp
+
+    for (m, n, k), dt in (((1, 1, 16), "bf16"), ((1024, 3, 16384), "fp8"), ((777, 12345, 4100), "bf16")):
+        got = tp.tp_mlp_features(m, n, k, dt)
+        want = omlp.features(m, n, k, 0 if dt == "bf16" else 1)
+        assert np.allclose(got, want, rtol=1e-6, atol=1e-6), (m, n, k, dt)
+    assert tp.tp_mlp_features(4096, 8192, 16, "fp8") == [12.0, 13.0, 4.0, 0.0, 1.0]
