@@ -885,7 +885,8 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
   // swap-AB (cfg.swap_ab): a C tile of W rows x 128 columns is computed as
   // C^T = B^T A^T by a CTA pair, the MMA's 128 rows being C's columns (64
   // per CTA) and its W columns C's rows (W/2 rows of A per CTA)
-  const bool swap = cfg && cfg->swap_ab != 0;
+  if (cfg && (cfg->swap_ab < 0 || cfg->swap_ab > 1)) return fail(TP_ERR_INVALID, "swap_ab must be 0 or 1");
+  const bool swap = cfg && cfg->swap_ab == 1;
   int bm, bn;  // MMA tile: rows (256 = CTA pair) and columns
   if (swap) {
     if (esize != 2) return fail(TP_ERR_UNSUPPORTED, "swap_ab applies to the BF16 GEMM");
@@ -1044,6 +1045,7 @@ tp_status launch_gemm_tc_impl(tp_ctx* ctx, tp_partition* c, const tp_tensor* a, 
 tp_status gemm_tc_resident(tp_ctx* ctx, const tp_gemm_config* cfg, int32_t* programs) {
   const int kc = cfg->bk >= 256 ? 4 : cfg->bk >= 128 ? 2 : 1;  // K blocks per stage (bf16 K blocks of 64)
   (void)ctx;
+  if (cfg->swap_ab < 0 || cfg->swap_ab > 1) return fail(TP_ERR_INVALID, "swap_ab must be 0 or 1");
   if (cfg->swap_ab) {
     // swap-AB tiles: CTA pairs, each CTA holding 64 rows of B^T and W/2 rows
     // of A per K block, no staging area

@@ -538,3 +538,10 @@ def test_swap_ab_checked_raw_and_validation(ctx):
             tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=tile[0], bn=tile[1], swap_ab=1, **kw))
         assert e.value.status == tp._lib.ERR_UNSUPPORTED
         tp.tp_partition_destroy(p)
+    # swap_ab values other than 0 and 1 are reserved
+    cc = torch.empty(m, n, device="cuda", dtype=torch.bfloat16)
+    p = tp.tp_partition_create(ctx, cc, (64, 128))
+    with pytest.raises(tp.TPError) as e:
+        tp.tp_gemm(ctx, p, a, bt.t(), tp.gemm_config(bm=64, bn=128, swap_ab=2))
+    assert e.value.status == tp._lib.ERR_INVALID
+    tp.tp_partition_destroy(p)
